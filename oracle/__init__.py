@@ -1,0 +1,27 @@
+"""FP64 CPU oracle for nonnegative CP decomposition (NNCP) with HALS updates.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import or run
+anything in this package.  The GPU library never calls it, shares no code with
+it, and fails loudly instead of falling back to it.
+
+Every function here follows the paper "Parallel Nonnegative CP Decomposition
+of Dense Tensors" (Ballard, Hayashi, Kannan; arXiv:1806.07985) step by step in
+plain numpy float64: explicit matricizations, explicit Khatri-Rao products and
+library matmuls only, with no blocking, fusion or reordering beyond what the
+paper's definitions state.  Pins (tests that tie it to something other than
+itself) live in ``tests/test_oracle_pins.py``.
+
+Parity status per function (the pins are listed in each docstring):
+  * mttkrp_direct, mttkrp_dimtree, khatri_rao, matricize: pinned
+    (brute-force elementwise sums, rank-1 closed form, tree == direct).
+  * hals_sweep: pinned (R=1 closed form, convergence to the exact NNLS
+    solution from scipy.optimize.nnls, KKT conditions, monotone objective).
+  * normalize / fit_identity / explicit_residual / nncp_hals: pinned
+    (model invariance, identity == explicit residual, exact recovery of
+    noise-free low-rank tensors to < 1e-10, non-increasing objective).
+  * The final-fit value of a noisy solve has no external pin: it is the
+    oracle's own trajectory ("parity unpinned" for that number alone).
+"""
+
+from .nncp import *  # noqa: F401,F403

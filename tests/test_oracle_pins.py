@@ -1,0 +1,326 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test ties one oracle function to a brute-force definition, a closed form,
+a library routine on the equivalent problem, or an invariant the mathematics
+fixes, so that a dropped term, a wrong sign or index, or a transposed operand
+in the oracle fails here.  The last tests plant such mistakes in the oracle and
+check that a pin catches each one.
+"""
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_07985_gb300 import synth
+
+
+def _flat_pos(idx, dims):
+    # mode-1-fastest position, written out for the test (Sec. IV-C layout)
+    pos = 0
+    for k in reversed(range(len(dims))):
+        pos = pos * dims[k] + idx[k]
+    return pos
+
+
+def _brute_mttkrp(x, dims, H, n):
+    """M(n)(i, r) = sum over all other indices of X(i_1..i_N) prod_{k!=n} H_k(i_k, r)."""
+    R = H[0].shape[1]
+    M = np.zeros((dims[n], R))
+    for idx in itertools.product(*[range(d) for d in dims]):
+        v = x[_flat_pos(idx, dims)]
+        for r in range(R):
+            p = v
+            for k in range(len(dims)):
+                if k != n:
+                    p *= H[k][idx[k], r]
+            M[idx[n], r] += p
+    return M
+
+
+def _random_case(rng, N, R):
+    dims = tuple(int(d) for d in rng.integers(1, 6, size=N))
+    x = rng.standard_normal(int(np.prod(dims)))
+    H = [rng.standard_normal((d, R)) for d in dims]
+    return dims, x, H
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_mttkrp_direct_and_tree_match_brute_force(N):
+    rng = np.random.default_rng(100 + N)
+    for trial in range(4):
+        R = int(rng.integers(1, 5))
+        dims, x, H = _random_case(rng, N, R)
+        if trial == 0:
+            dims = tuple(range(2, 2 + N))  # all lengths distinct
+            x = rng.standard_normal(int(np.prod(dims)))
+            H = [rng.standard_normal((d, R)) for d in dims]
+        for n in range(N):
+            ref = _brute_mttkrp(x, dims, H, n)
+            scale = max(1.0, np.abs(ref).max())
+            got = oracle.mttkrp_direct(x, dims, H, n)
+            assert np.abs(got - ref).max() <= 1e-12 * scale
+            for s in range(1, N):
+                got_t = oracle.mttkrp_dimtree(x, dims, H, n, s)
+                assert np.abs(got_t - ref).max() <= 1e-12 * scale
+            got_rows = oracle.mttkrp_rows(x, dims, H, n, list(range(dims[n])))
+            assert np.abs(got_rows - ref).max() <= 1e-12 * scale
+
+
+def test_mttkrp_rank_one_closed_form():
+    # X = a_1 o ... o a_N  =>  M(n)(i, r) = a_n(i) * prod_{k!=n} <a_k, H_k(:, r)>
+    rng = np.random.default_rng(7)
+    dims = (7, 5, 6, 4)
+    a = [rng.random(d) for d in dims]
+    x = np.zeros(int(np.prod(dims)))
+    for idx in itertools.product(*[range(d) for d in dims]):
+        x[_flat_pos(idx, dims)] = np.prod([a[k][idx[k]] for k in range(4)])
+    R = 3
+    H = [rng.random((d, R)) for d in dims]
+    for n in range(4):
+        coef = np.ones(R)
+        for k in range(4):
+            if k != n:
+                coef *= a[k] @ H[k]
+        expect = np.outer(a[n], coef)
+        assert np.allclose(oracle.mttkrp_direct(x, dims, H, n), expect, rtol=1e-13, atol=0)
+        for s in (1, 2, 3):
+            assert np.allclose(oracle.mttkrp_dimtree(x, dims, H, n, s), expect,
+                               rtol=1e-13, atol=0)
+
+
+def test_partial_mttkrp_nodes_are_contractions_of_the_tensor():
+    # T_L(i_1..i_s, r) = sum_{i_{s+1}..i_N} X * prod_{k>s} H_k ; T_R likewise
+    rng = np.random.default_rng(11)
+    dims = (3, 4, 2, 5)
+    R = 2
+    x = rng.standard_normal(int(np.prod(dims)))
+    H = [rng.standard_normal((d, R)) for d in dims]
+    for s in (1, 2, 3):
+        IL = int(np.prod(dims[:s]))
+        TL = np.zeros((IL, R))
+        TR = np.zeros((x.size // IL, R))
+        for idx in itertools.product(*[range(d) for d in dims]):
+            v = x[_flat_pos(idx, dims)]
+            left = _flat_pos(idx[:s], dims[:s])
+            right = _flat_pos(idx[s:], dims[s:])
+            for r in range(R):
+                TL[left, r] += v * np.prod([H[k][idx[k], r] for k in range(s, 4)])
+                TR[right, r] += v * np.prod([H[k][idx[k], r] for k in range(s)])
+        assert np.allclose(oracle.partial_mttkrp_right(x, dims, H, s), TL, rtol=1e-12, atol=1e-12)
+        assert np.allclose(oracle.partial_mttkrp_left(x, dims, H, s), TR, rtol=1e-12, atol=1e-12)
+
+
+def test_default_root_split_balances_halves():
+    assert oracle.default_root_split((512, 512, 512)) == 1
+    assert oracle.default_root_split((512, 512, 32, 16)) == 1  # tie -> smaller s
+    assert oracle.default_root_split((100, 512, 32, 16)) == 2
+    assert oracle.default_root_split((64,) * 5) == 2
+    assert oracle.default_root_split((10, 20)) == 1
+
+
+def test_hals_rank_one_is_scalar_nnls():
+    # R = 1: one column step is the exact minimiser w = max(0, m / s)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        I = 9
+        M = rng.standard_normal((I, 1))
+        S = np.array([[rng.random() + 0.1]])
+        W = rng.random((I, 1)) * 5
+        oracle.hals_sweep(W, M, S)
+        assert np.allclose(W[:, 0], np.maximum(0.0, M[:, 0] / S[0, 0]), rtol=1e-14, atol=0)
+
+
+def _nnls_by_active_sets(S, m):
+    """Exact min_{w>=0} 1/2 w^T S w - m^T w by enumerating passive sets."""
+    R = len(m)
+    for k in range(R + 1):
+        for P in itertools.combinations(range(R), k):
+            w = np.zeros(R)
+            if P:
+                P = list(P)
+                w[P] = np.linalg.solve(S[np.ix_(P, P)], m[P])
+            if np.all(w >= -1e-12) and np.all(S @ w - m >= -1e-10):
+                return w
+    raise AssertionError("no KKT point")
+
+
+@pytest.mark.parametrize("R", [2, 3, 4, 5, 6])
+def test_hals_converges_to_exact_nnls(R):
+    scipy_optimize = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(20 + R)
+    A0 = rng.random((3 * R, R)) + 0.2 * np.eye(3 * R, R)
+    S = A0.T @ A0
+    I = 6
+    M = rng.standard_normal((I, R)) * 3
+    W = rng.random((I, R))
+    for _ in range(4000):
+        oracle.hals_sweep(W, M, S)
+    # equivalent least squares: A^T A = S, A^T b = m
+    A = np.linalg.cholesky(S).T
+    for i in range(I):
+        b = np.linalg.solve(A.T, M[i])
+        w_ref, _ = scipy_optimize.nnls(A, b)
+        assert np.allclose(W[i], w_ref, atol=1e-8)
+        if R <= 5:
+            assert np.allclose(W[i], _nnls_by_active_sets(S, M[i]), atol=1e-8)
+    # KKT: W >= 0, Q = W S - M >= 0, complementarity
+    Q = W @ S - M
+    assert W.min() >= 0
+    assert Q.min() >= -1e-9
+    assert np.abs(W * Q).max() <= 1e-9
+
+
+def test_hals_sweep_never_increases_objective():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        R = int(rng.integers(1, 8))
+        A0 = rng.random((2 * R + 1, R))
+        S = A0.T @ A0
+        M = rng.standard_normal((5, R))
+        W = rng.random((5, R))
+        before = oracle.hals_objective(W, M, S)
+        oracle.hals_sweep(W, M, S)
+        after = oracle.hals_objective(W, M, S)
+        assert after <= before + 1e-12 * max(1.0, abs(before))
+        assert W.min() >= 0
+
+
+def test_normalization_leaves_model_unchanged():
+    rng = np.random.default_rng(9)
+    dims = (4, 3, 5)
+    R = 3
+    W = [rng.random((d, R)) for d in dims]
+    x_before = oracle.reconstruct(np.ones(R), W, dims)
+    lam = np.ones(R)
+    H = []
+    for w in W:
+        h, c = oracle.normalize_columns(w)
+        H.append(h)
+        lam = lam * c
+    assert np.allclose(oracle.reconstruct(lam, H, dims), x_before, rtol=1e-13)
+    for h in H:
+        assert np.allclose(np.linalg.norm(h, axis=0), 1.0, rtol=1e-14)
+
+
+def test_reconstruct_matches_generator_layout():
+    # the generator's model tensor and the oracle's reconstruction agree entrywise
+    # with the written-out definition at a few positions
+    rng = np.random.default_rng(1)
+    dims = (3, 4, 2)
+    F = [rng.random((d, 2)) for d in dims]
+    x = synth.model_tensor(F, dims)
+    y = oracle.reconstruct(np.ones(2), F, dims)
+    for idx in itertools.product(*[range(d) for d in dims]):
+        v = sum(F[0][idx[0], r] * F[1][idx[1], r] * F[2][idx[2], r] for r in range(2))
+        assert abs(x[_flat_pos(idx, dims)] - v) < 1e-14
+        assert abs(y[_flat_pos(idx, dims)] - v) < 1e-14
+
+
+def _small_noisy(dims, R, seed=0):
+    x, _ = synth.lowrank_plus_noise(dims, R, seed, noise=0.05)
+    H0 = synth.init_factors(dims, R, seed + 1)
+    return x.astype(np.float64), H0
+
+
+def test_fit_identity_matches_explicit_residual():
+    dims, R = (6, 7, 5), 3
+    x, H0 = _small_noisy(dims, R)
+    for use_tree in (False, True):
+        res = oracle.nncp_hals(x, dims, H0, max_iters=15, use_dimtree=use_tree)
+        eps_exact = oracle.explicit_residual(x, dims, res["lam"], res["H"])
+        assert eps_exact > 1e-3
+        assert abs(res["eps"][-1] - eps_exact) < 1e-10
+
+
+def test_objective_nonincreasing_over_inner_iterations():
+    dims, R = (5, 6, 4, 3), 3
+    x, H0 = _small_noisy(dims, R, seed=4)
+    trace = []
+
+    def cb(event, H, lam, **_):
+        trace.append(np.sum((x - oracle.reconstruct(lam, H, dims)) ** 2))
+
+    oracle.nncp_hals(x, dims, H0, max_iters=10, use_dimtree=True, s=2, callback=cb)
+    assert len(trace) == 40
+    for a, b in zip(trace, trace[1:]):
+        assert b <= a * (1 + 1e-12)
+
+
+def test_tree_and_direct_solves_agree():
+    dims, R = (6, 5, 4, 3), 4
+    x, H0 = _small_noisy(dims, R, seed=2)
+    direct = oracle.nncp_hals(x, dims, H0, max_iters=12, use_dimtree=False)
+    for s in (1, 2, 3):
+        tree = oracle.nncp_hals(x, dims, H0, max_iters=12, use_dimtree=True, s=s)
+        assert np.allclose(tree["fits"], direct["fits"], rtol=0, atol=1e-12)
+        for a, b in zip(tree["H"], direct["H"]):
+            assert np.allclose(a, b, rtol=0, atol=1e-10)
+
+
+def _recovery_run(dims, R, seed, max_iters=5000):
+    rng = np.random.default_rng(seed)
+    F = [rng.random((d, R)) for d in dims]
+    x = synth.model_tensor(F, dims)  # exact, noise free, float64
+    H0 = [f + 1e-2 * rng.random(f.shape) for f in F]
+    res = oracle.nncp_hals(x, dims, H0, max_iters=max_iters, tol=0.0, use_dimtree=True)
+    return oracle.explicit_residual(x, dims, res["lam"], res["H"]), res
+
+
+@pytest.mark.parametrize("dims,R", [((8, 9, 10), 3), ((6, 7, 5, 4), 2)])
+def test_exact_low_rank_recovery(dims, R):
+    # noise-free nonnegative rank-R tensor, started from the truth perturbed by 1e-2
+    # (the paper only states that the residual goes to zero, Sec. V-A)
+    eps, res = _recovery_run(dims, R, seed=31)
+    assert eps < 1e-10, eps
+
+
+def test_exact_low_rank_recovery_random_start():
+    # a random start on an exact rank-2 model also drives the residual to zero
+    dims, R = (8, 9, 10), 2
+    rng = np.random.default_rng(17)
+    F = [rng.random((d, R)) for d in dims]
+    x = synth.model_tensor(F, dims)
+    H0 = synth.init_factors(dims, R, 18)
+    res = oracle.nncp_hals(x, dims, H0, max_iters=3000, tol=0.0)
+    assert oracle.explicit_residual(x, dims, res["lam"], res["H"]) < 1e-10
+
+
+# ---- the pins have teeth: plant a mistake in the oracle, a pin must fail ----
+
+def test_planted_krp_order_mistake_is_caught(monkeypatch):
+    def wrong_krp(A, B):
+        A = np.asarray(A, dtype=np.float64)
+        B = np.asarray(B, dtype=np.float64)
+        K = np.empty((A.shape[0] * B.shape[0], A.shape[1]))
+        for c in range(A.shape[1]):
+            K[:, c] = np.kron(B[:, c], A[:, c])  # operands swapped
+        return K
+
+    monkeypatch.setattr(oracle.nncp, "khatri_rao", wrong_krp)
+    with pytest.raises(AssertionError):
+        test_mttkrp_direct_and_tree_match_brute_force(3)
+
+
+def test_planted_hals_sign_mistake_is_caught(monkeypatch):
+    def wrong_sweep(W, M, S):
+        for r in range(W.shape[1]):
+            W[:, r] = np.maximum(0.0, W[:, r] + (M[:, r] + W @ S[:, r]) / S[r, r])
+        return W
+
+    monkeypatch.setattr(oracle, "hals_sweep", wrong_sweep)
+    with pytest.raises(AssertionError):
+        test_hals_rank_one_is_scalar_nnls()
+
+
+def test_planted_fit_mistake_is_caught(monkeypatch):
+    def wrong_fit(alpha, M_N, W_N, lam, S_N, G_N):
+        beta = float(np.sum(M_N * W_N))
+        gamma = float(lam @ (S_N * G_N) @ lam)
+        return math.sqrt(max(0.0, alpha - beta + gamma) / alpha), beta, gamma
+
+    monkeypatch.setattr(oracle.nncp, "fit_identity", wrong_fit)
+    with pytest.raises(AssertionError):
+        test_fit_identity_matches_explicit_residual()
