@@ -1,0 +1,375 @@
+"""Benchmark: dimension-tree MTTKRP inside NNCP-HALS on one GB300 per rank.
+
+A step is one outer BCD iteration of NNCP-HALS on the 512 x 512 x 512, R = 32
+synthetic workload (rank-32 U[0,1) factors + U[0,0.01) noise, init seed 1):
+both root partial MTTKRPs, the multi-TTVs, three HALS updates with Gram and
+normalisation, and the fit.  The metric is MTTKRP GB/s: tensor bytes the
+iteration's MTTKRPs must read (two passes over the float32 tensor, 2 x 512 MiB)
+divided by the step time.  The tensor (512 MiB) is larger than L2 (129 MB), so
+no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the method's single-tensor path has no exchange step on one GPU): value is
+the sum of all ranks' bytes over the slowest rank's time ("weak" scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DIMS = (512, 512, 512)
+RANK = 32
+ITERS_CONFIG = 50
+METRIC = "MTTKRP GB/s"
+UNIT = "GB/s"
+PRECISION_DTYPE = {"fp32_simt": "f32", "tf32": "tf32 (f32 accumulate)",
+                   "split_bf16x3": "bf16x3 (f32 accumulate)", "bf16_stored": "bf16 (f32 accumulate)"}
+
+
+def tensor_bytes_per_iter(dims):
+    n = 1
+    for d in dims:
+        n *= d
+    return 2 * 4 * n  # two float32 passes (root -> each half)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default=None,
+                   choices=["fp32_simt", "tf32", "split_bf16x3", "bf16_stored"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append({"sm": float(parts[2]), "max": float(parts[3]), "power": float(parts[4]),
+                             "hw": parts[6], "hwt": parts[7], "swt": parts[8], "pcap": parts[9]})
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        peak_power = max(r["power"] for r in rows)
+        loaded = [r for r in rows if r["power"] >= 0.5 * peak_power] or rows
+        reasons = set()
+        for r in loaded:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded),
+                "sm_max_mhz": max(r["max"] for r in loaded),
+                "reasons": sorted(reasons), "samples": len(loaded)}
+
+
+# ------------------------------------------------------------ roofline data --
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's source
+    is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    entry = json.load(open(path)).get(kernel_key)
+    if not entry:
+        return None
+    src = os.path.join(ROOT, entry["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if sha != entry.get("source_sha256"):
+        return None
+    return entry["bytes_per_launch"]
+
+
+# ----------------------------------------------------------------- our arm --
+
+def default_precision(nncp):
+    return "split_bf16x3" if "tcgen05" in nncp.nncp_version() else "fp32_simt"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1806_07985_gb300 import nncp, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    nncp.load()
+    prec_name = args.precision or default_precision(nncp)
+    prec = nncp.PRECISIONS[prec_name]
+
+    x, _ = synth.lowrank_plus_noise(DIMS, RANK, seed=0, noise=0.01)
+    H0 = synth.init_factors(DIMS, RANK, seed=1)
+    X = torch.from_numpy(x).cuda()
+    Xuse = X
+    if prec == nncp.NNCP_BF16_STORED:
+        Xuse = torch.empty(X.numel(), dtype=torch.bfloat16, device="cuda")
+        nncp.nncp_tensor_to_bf16(X, Xuse)
+    H = [torch.from_numpy(h.copy()).cuda() for h in H0]
+    ctx = nncp.Context(DIMS, RANK, precision=prec, root_split=1)
+    ctx.set_tensor(Xuse)
+    ctx.set_factors(H)
+    ctx.solve_begin()
+    bytes_step = tensor_bytes_per_iter(DIMS)
+
+    for _ in range(max(args.warmup, 3)):
+        ctx.iterate(1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.iterate(1)
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    kernels_per_iter = ctx.iteration_kernels()
+
+    # dominant kernel: the root partial MTTKRPs, timed with events on their stream
+    peak, peak_kind = measured_peaks()
+    pm = {}
+    reps = 20
+    for side in (0, 1):
+        rows = 512 if side == 0 else 512 * 512
+        out = torch.empty((rows, RANK), device="cuda")
+        for _ in range(3):
+            ctx.partial_mttkrp(side, out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            ctx.partial_mttkrp(side, out)
+        b.record()
+        torch.cuda.synchronize()
+        pm[side] = a.elapsed_time(b) / reps
+    x_bytes = Xuse.numel() * Xuse.element_size()
+    dom = max(pm, key=lambda s: pm[s])
+    achieved = x_bytes / (pm[dom] * 1e-3) / 1e9
+    kernel_key = f"pm_{'right' if dom == 0 else 'left'}_{prec_name}_512x512x512_R32"
+    traffic = recorded_traffic(kernel_key)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": kernel_key, "peak_kind": peak_kind,
+                "pm_ms": {"root_to_left": round(pm[0], 4), "root_to_right": round(pm[1], 4)},
+                "algorithmic_bytes_per_launch": x_bytes}
+
+    result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": PRECISION_DTYPE[prec_name], "data": "synthetic",
+              "config": {"workload": "nncp_hals_512x512x512_R32_dimtree_split1",
+                         "dims": list(DIMS), "rank": RANK, "precision": prec_name,
+                         "step": "one outer BCD iteration (2 root partial MTTKRPs, 2 multi-TTVs, "
+                                 "3 HALS updates, fit)",
+                         "bytes_per_step": bytes_step,
+                         "l2": "inputs larger than L2 (512 MiB tensor), no flush",
+                         "parallelism": f"replicas x{world}"},
+              "roofline": roofline, "clocks": clk,
+              "gpu_launches": kernels_per_iter * args.steps}
+
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(nncp, torch, x, H0, prec, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(x, H0)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(nncp, torch, x, H0, prec, world):
+    """One user call per step: nncp_solve_host on pinned host buffers, the
+    configuration's 50 iterations, host<->device copies inside the timed call."""
+    import numpy as np
+    Xh = torch.from_numpy(x).pin_memory()
+    Hh = [torch.from_numpy(h.copy()).pin_memory() for h in H0]
+    nncp.nncp_solve_host(DIMS, RANK, Xh, [h.clone().pin_memory() for h in Hh], prec, 1, 2, 0.0)
+    times = []
+    steps = 3
+    for _ in range(steps):
+        Hrun = [h.clone().pin_memory() for h in Hh]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nncp.nncp_solve_host(DIMS, RANK, Xh, Hrun, prec, 1, ITERS_CONFIG, 0.0)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    bytes_solve = ITERS_CONFIG * tensor_bytes_per_iter(DIMS)
+    h2d = x.nbytes + sum(h.nbytes for h in H0)
+    d2h = sum(h.nbytes for h in H0) + RANK * 8 + 8
+    return {"value": round(world * bytes_solve / t / 1e9, 1), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "step": f"nncp_solve_host: {ITERS_CONFIG} iterations from pinned host buffers",
+            "s_per_step": round(t, 4), "steps": steps}
+
+
+def cpu_baseline(x, H0):
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    xd = x.astype(np.float64)
+    oracle.nncp_hals(xd, DIMS, [h.astype(np.float64) for h in H0], max_iters=1, use_dimtree=True, s=1)
+    t = time.perf_counter() - t0
+    return {"value": round(tensor_bytes_per_iter(DIMS) / t / 1e9, 4), "unit": UNIT,
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one outer iteration (with initialisation) of the 512^3 R=32 solve, "
+                      "FP64 numpy oracle, dimension tree split 1",
+            "seconds": round(t, 2)}
+
+
+# ----------------------------------------------------------- reference arm --
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload and metric, on the host cores.
+    Each step is one outer iteration on a 512 x 512 x k slab of the tensor, k
+    chosen so the whole run stays within a few minutes."""
+    import numpy as np
+
+    import oracle
+    from paper_1806_07985_gb300 import synth
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    x, _ = synth.lowrank_plus_noise(DIMS, RANK, seed=0, noise=0.01)
+    H0 = synth.init_factors(DIMS, RANK, seed=1)
+    x3 = x.reshape(DIMS[2], DIMS[1], DIMS[0])
+
+    def step(k3):
+        dims = (DIMS[0], DIMS[1], k3)
+        xs = np.ascontiguousarray(x3[:k3]).reshape(-1).astype(np.float64)
+        H = [H0[0].astype(np.float64), H0[1].astype(np.float64), H0[2][:k3].astype(np.float64)]
+        t0 = time.perf_counter()
+        oracle.nncp_hals(xs, dims, H, max_iters=1, use_dimtree=True, s=1)
+        return time.perf_counter() - t0, tensor_bytes_per_iter(dims)
+
+    t_cal, _ = step(16)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    k3 = int(max(8, min(DIMS[2], 16 * budget / max(t_cal, 1e-3))) // 8 * 8)
+    for _ in range(args.warmup):
+        step(k3)
+    tot_t, tot_b = 0.0, 0
+    for _ in range(args.steps):
+        t, b = step(k3)
+        tot_t += t
+        tot_b += b
+    value = tot_b / tot_t / 1e9
+    sample = f"one outer iteration (with initialisation) on a 512x512x{k3} slab, FP64 numpy oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot_t / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "nncp_hals_512x512x512_R32_dimtree_split1", "dims": list(DIMS),
+                   "rank": RANK, "sample_dims": [DIMS[0], DIMS[1], k3]},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

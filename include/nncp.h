@@ -1,0 +1,166 @@
+/*
+ * nncp.h -- C ABI of the GB300 NNCP-HALS library (dimension-tree MTTKRP).
+ *
+ * Problem (Eq. 1 of "Parallel Nonnegative CP Decomposition of Dense Tensors",
+ * Ballard, Hayashi, Kannan, arXiv:1806.07985):
+ *     min_{H_n >= 0} || X - sum_r H_1(:,r) o ... o H_N(:,r) ||^2
+ * solved by block coordinate descent over whole factor matrices (Alg. 1, with
+ * the normalisation and error steps of Alg. 3), MTTKRPs through a dimension
+ * tree (Sec. IV-A), one HALS column sweep per block update (Sec. II-B), and the
+ * relative error from the identity of Sec. IV-B.
+ *
+ * Conventions shared by every call:
+ *   - Tensor X: dense, N-way, I_1 x ... x I_N, stored mode-1 fastest (the
+ *     layout of Sec. IV-C "Data Distribution": linear index
+ *     i_1 + I_1*(i_2 + I_2*(...)), 0-based).  float32, or bfloat16 in the
+ *     NNCP_BF16_STORED precision mode.  Device memory, 16-byte aligned.
+ *   - Factor H_n: I_n x R float32, ROW-major (the R entries of a row are
+ *     contiguous), device memory, 16-byte aligned.  (The paper's Armadillo
+ *     matrices are column-major; rows are what the HALS update and the
+ *     on-the-fly Khatri-Rao product read, so rows are contiguous here.)
+ *   - Modes are numbered 1..N at this boundary.
+ *   - Ownership: the caller owns X, the factors, outputs and the workspace;
+ *     the library never frees caller memory.  A context holds only pointers.
+ *   - Streams are passed as void* (a cudaStream_t); NULL is the legacy
+ *     default stream.
+ *   - Errors: every call returns an nncp_status; nothing aborts or throws
+ *     across the ABI.  On NNCP_ERR_INVALID_ARG the context is unchanged.
+ *     nncp_last_error() returns a message for the last failing call.
+ *   - Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef NNCP_H
+#define NNCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nncp_ctx nncp_ctx;
+
+typedef int nncp_status;
+#define NNCP_OK                 0
+#define NNCP_ERR_INVALID_ARG    1
+#define NNCP_ERR_OUT_OF_MEMORY  2
+#define NNCP_ERR_CUDA           3
+#define NNCP_ERR_NUMERIC        4   /* non-finite fit */
+#define NNCP_ERR_TIMEOUT        5
+#define NNCP_ERR_NOT_READY      6
+#define NNCP_ERR_UNSUPPORTED    7
+
+/* How the partial MTTKRPs (the two root branches of the dimension tree)
+ * contract the tensor.  All accumulate in float32. */
+typedef int nncp_precision;
+#define NNCP_FP32_SIMT     0   /* CUDA-core FFMA */
+#define NNCP_TF32          1   /* tcgen05 kind::tf32 on the float32 tensor */
+#define NNCP_SPLIT_BF16X3  2   /* tcgen05 kind::f16: x = hi + lo (bf16), hi*hi + hi*lo + lo*hi */
+#define NNCP_BF16_STORED   3   /* tensor stored as bf16; factors split hi + lo */
+
+/* Library version string and whether tcgen05 kernels were compiled in. */
+const char* nncp_version(void);
+
+/* Create a context for an N-way tensor with mode lengths dims[0..N-1] and
+ * rank R.  2 <= N <= 8, dims[n] >= 1, 1 <= R <= 128.  Defaults: precision
+ * NNCP_FP32_SIMT, root split chosen by nncp_default_split, stream NULL.
+ * The context owns no device memory until nncp_set_workspace. */
+nncp_status nncp_create(int N, const int64_t* dims, int R, nncp_ctx** out);
+
+/* Root split s of the dimension tree: modes 1..s versus s+1..N (Sec. IV-A,
+ * Fig. 1).  Returns the s in [1, N-1] that makes the products of the two
+ * halves' lengths closest (Sec. IV-C "Memory"), the smaller s on ties. */
+int nncp_default_split(int N, const int64_t* dims);
+
+/* precision: one of NNCP_*; root_split: 0 = default, else s in [1, N-1];
+ * stream: cudaStream_t the context launches on.  Invalidates captured graphs. */
+nncp_status nncp_set_options(nncp_ctx* ctx, nncp_precision precision, int root_split,
+                             void* stream);
+
+/* Bytes of device scratch the context needs for its current options
+ * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
+nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);
+
+/* Hand the context a caller-allocated device buffer of at least
+ * nncp_workspace_size bytes, 256-byte aligned.  The caller keeps it alive
+ * until nncp_destroy or the next nncp_set_workspace. */
+nncp_status nncp_set_workspace(nncp_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Point the context at the tensor (device, layout above).  The data must stay
+ * unchanged while the context uses it. */
+nncp_status nncp_set_tensor(nncp_ctx* ctx, const void* X_dev);
+
+/* Point the context at the N factor matrices (device, I_n x R row-major).
+ * nncp_solve reads the initial values there and leaves the result there. */
+nncp_status nncp_set_factors(nncp_ctx* ctx, float* const* H_dev);
+
+/* M_mode = X_(mode) (H_N (.) ... (.) H_{mode+1} (.) H_{mode-1} (.) ... (.) H_1)
+ * (Sec. II-A), for the current factors, into M_dev (I_mode x R row-major,
+ * device).  use_dimtree = 0: one direct pass over the tensor; 1: the root
+ * partial MTTKRP of the half holding `mode` followed by multi-TTVs down the
+ * tree (Sec. IV-A).  Asynchronous on the context's stream. */
+nncp_status nncp_mttkrp(nncp_ctx* ctx, int mode, int use_dimtree, float* M_dev);
+
+/* One root partial MTTKRP of the dimension tree (Sec. IV-A, Fig. 2a) for the
+ * current factors, in the context's precision mode:
+ *   side 0: T_L = X_(1:s) (H_N (.) ... (.) H_{s+1}),  (I_1...I_s) x R
+ *   side 1: T_R = X_(1:s)^T (H_s (.) ... (.) H_1),    (I_{s+1}...I_N) x R
+ * X_(1:s) is the column-major matricization with modes 1..s on the rows,
+ * which is the tensor's memory as it lies.  Rows of T run over the node's
+ * modes with the lowest fastest; T_dev is row-major (R contiguous), device.
+ * Asynchronous on the context's stream. */
+nncp_status nncp_partial_mttkrp(nncp_ctx* ctx, int side, float* T_dev);
+
+/* Full NNCP-HALS solve on the tensor and factors set above.
+ * Initialisation normalises the given factors (2-norm columns) and folds the
+ * norms into lambda; each outer iteration updates modes 1..N in order (BCD,
+ * Alg. 1) with MTTKRPs through the dimension tree and one HALS sweep, then
+ * computes fit = 1 - eps with eps from the Sec. IV-B identity.  Stops when
+ * |fit_k - fit_{k-1}| < tol (k >= 2) or k = max_iters.
+ * On return the factors hold H_1..H_N with unit-norm columns, lambda_out
+ * (host, R doubles, may be NULL) the weights, *iters_out the outer
+ * iterations run and *fit_out the last fit (either pointer may be NULL).
+ * Blocks until done.  NNCP_ERR_NUMERIC if the fit became non-finite. */
+nncp_status nncp_solve(nncp_ctx* ctx, int max_iters, double tol, double* lambda_out,
+                       int* iters_out, double* fit_out);
+
+/* Per-iteration fit history of the last nncp_solve (host array of at least
+ * max_iters doubles); *count receives the number of iterations. */
+nncp_status nncp_fit_history(const nncp_ctx* ctx, double* fits, int max_count, int* count);
+
+/* Fit of the current model [[lambda; H]].  exact = 0: the identity value from
+ * the last solve iteration; exact = 1: a full pass reconstructing every entry
+ * (float64 accumulation) to compute 1 - ||X - model|| / ||X||. */
+nncp_status nncp_fit(nncp_ctx* ctx, int exact, double* fit_out);
+
+/* Run exactly `iters` outer iterations on the device state left by a previous
+ * nncp_solve (or nncp_solve_begin), without host synchronisation: the unit
+ * that the benchmark times.  Uses a captured CUDA graph per iteration. */
+nncp_status nncp_solve_begin(nncp_ctx* ctx);
+nncp_status nncp_iterate(nncp_ctx* ctx, int iters);
+
+/* Number of kernels one captured outer iteration launches (*count). */
+nncp_status nncp_iteration_kernels(nncp_ctx* ctx, int* count);
+
+/* Convert a float32 tensor to the bfloat16 copy NNCP_BF16_STORED contracts
+ * (round to nearest even).  n elements, device pointers. */
+nncp_status nncp_tensor_to_bf16(const float* X_dev, uint16_t* Xb_dev, int64_t n, void* stream);
+
+/* One-call solve from HOST buffers: allocates device memory, copies the
+ * tensor and initial factors in, solves, copies factors, lambda and fit back.
+ * X_host: float32, mode-1 fastest; H_host[n]: I_n x R row-major (in: initial
+ * factors, out: normalised result). */
+nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_host,
+                            float* const* H_host, nncp_precision precision, int root_split,
+                            int max_iters, double tol, double* lambda_out, int* iters_out,
+                            double* fit_out);
+
+const char* nncp_last_error(const nncp_ctx* ctx);
+/* Message of the last failure of a call that had no context to record it in. */
+const char* nncp_global_error(void);
+void nncp_destroy(nncp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNCP_H */

@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of the NNCP library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nncp {
+
+constexpr int kMaxModes = 8;
+constexpr int kMaxRank = 128;
+constexpr int kFitCapacity = 1 << 16;  // fit history slots on the device
+
+// Khatri-Rao product of a list of factor matrices, formed on the fly.
+// Row k of the product over modes m_0 (fastest), m_1, ... is the Hadamard
+// product of rows k_0, k_1, ... of the factors, k = k_0 + dim_0*(k_1 + ...).
+// Factors are row-major dim x R.  nm = 0 means the all-ones row.
+struct KrpDesc {
+  int nm;
+  int64_t dim[kMaxModes];
+  const float* H[kMaxModes];
+};
+
+// Per-solve device state (lives in the caller's workspace).
+struct SolveState {
+  double* G;        // N x R x R, Gram of each normalised factor
+  double* S;        // R x R, Hadamard of Grams for the mode being updated
+  float* S32;       // R x R, S rounded to float32 (HALS arithmetic)
+  double* lam;      // R
+  double* gram_part;  // blocks x (R*R + 1): per-block W^T W and <M, W>
+  double* scalars;  // [0] alpha = ||X||^2, [1] beta, [2] gamma, [3] eps, [4] tol
+  double* fits;     // kFitCapacity
+  int* flags;       // [0] done, [1] status, [2] iteration count, [3] nonfinite
+};
+
+// ---- launchers (return cudaSuccess or the launch error) ----------------------
+
+// out(i, r) = sum_{l < L, q < Q} X[l + L*(i + I*q)] * KL(l, r) * KQ(q, r)
+// for i < I, r < R: the generic (direct or partial) MTTKRP on CUDA cores.
+// X is float32.  When the contraction is split across CTAs the per-chunk
+// results go to `partials` (capacity `part_cap` floats) and are summed in a
+// fixed order, so results are bitwise reproducible.
+cudaError_t launch_simt_mttkrp(const float* X, int64_t L, int64_t I, int64_t Q,
+                               const KrpDesc& KL, const KrpDesc& KQ, int R, float* out,
+                               float* partials, size_t part_cap, int num_sms,
+                               cudaStream_t st);
+size_t simt_mttkrp_partials(int64_t L, int64_t I, int64_t Q, int R, int num_sms);
+
+// Multi-TTV leaf: out(i, r) = sum_{k < K} T[((i + I*k) * R) + r] * KK(k, r).
+cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc& KK,
+                             int R, float* out, float* partials, size_t part_cap,
+                             int num_sms, cudaStream_t st);
+size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms);
+
+// Multi-TTV to the child node: out(j, r) = sum_{i < I} T[((i + I*j) * R) + r] * H(i, r).
+cudaError_t launch_mttv_first(const float* T, int64_t I, int64_t J, const float* H, int R,
+                              float* out, cudaStream_t st);
+
+// sum of squares of n float32 (or bf16) values into *out (float64), deterministic.
+cudaError_t launch_sumsq(const void* X, int bf16, int64_t n, double* partials, int nparts,
+                         double* out, const int* flags, cudaStream_t st);
+
+// float32 -> bf16 (round to nearest even).
+cudaError_t launch_to_bf16(const float* X, uint16_t* Y, int64_t n, cudaStream_t st);
+
+// ---- factor update kernels (update_kernels.cu) -----------------------------
+
+// Shared-memory opt-ins of every kernel that needs them; once per process and
+// device, before any launch or capture.
+cudaError_t kernel_attributes_init();
+cudaError_t tc_attributes_init();
+
+// HALS sweep on W = H diag(lam) for every row, in place in H, followed by the
+// per-block partials of W^T W and <M, W> into st.gram_part.
+cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveState st,
+                             cudaStream_t stream);
+int hals_gram_blocks(int64_t In);
+
+// Gram partials of H as given (initialisation: W = H).
+cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
+                             cudaStream_t stream);
+
+// Single-CTA finalise of a mode update:
+//   W^T W = sum of the partials; lam = sqrt(diag); G_n = D^-1 W^T W D^-1;
+//   H_n = W / lam (in place); if is_last: fit from the Sec. IV-B identity;
+//   S for mode next_mode.  init = 1: lam *= column norms instead of replacing.
+cudaError_t launch_finalize(float* H, int64_t In, int R, int N, int n, int next_mode,
+                            int nblocks, int is_last, int init, double tol, SolveState st,
+                            cudaStream_t stream);
+
+// lambda = 1, flags and fit counter cleared, tolerance stored (before initialisation).
+cudaError_t launch_solve_reset(SolveState st, int R, double tol, cudaStream_t stream);
+
+// S = Hadamard of every Gram but mode's (float64 and float32 copies).
+cudaError_t launch_compute_S(SolveState st, int N, int R, int mode, cudaStream_t stream);
+
+// Explicit residual ||X - [[lam; H]]||^2 accumulated in float64 into out[0];
+// out[1] = ||X||^2.
+cudaError_t launch_explicit_residual(const float* X, int N, const int64_t* dims, int R,
+                                     float* const* H, const double* lam, double* partials,
+                                     int nparts, double* out, cudaStream_t stream);
+
+}  // namespace nncp

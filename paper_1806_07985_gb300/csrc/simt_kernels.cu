@@ -1,0 +1,365 @@
+// CUDA-core kernels: generic MTTKRP over a (L, I, Q) view of the tensor,
+// multi-TTVs on dimension-tree nodes, sums of squares, bf16 conversion.
+//
+// The (L, I, Q) view: mode set split as [modes before] x [output modes] x
+// [modes after], so X[l + L*(i + I*q)] holds the entry with left index l,
+// output index i and right index q (mode-1-fastest layout, Sec. IV-C).
+//   * direct MTTKRP of mode n (Sec. II-A): L = I_1..I_{n-1}, I = I_n,
+//     Q = I_{n+1}..I_N;
+//   * partial MTTKRP root -> {1..s} (Sec. IV-A, Fig. 2a): L = 1,
+//     I = I_1..I_s, Q = I_{s+1}..I_N (contracts the slow modes);
+//   * partial MTTKRP root -> {s+1..N}: L = I_1..I_s, I = I_{s+1}..I_N, Q = 1
+//     (contracts the fast modes).
+// The Khatri-Rao rows are formed on the fly in shared memory from factor rows.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "nncp_internal.cuh"
+
+namespace nncp {
+
+namespace {
+
+constexpr int kBI = 128;  // output rows per CTA
+constexpr int kBK = 32;   // contraction tile
+constexpr int kRT = 32;   // rank columns per CTA
+constexpr int kThreads = 256;
+
+// Per-tile row offsets of the Khatri-Rao factors: for contraction index k,
+// off[m] = (row of mode m) * R, so KRP(k, r) = prod_m H_m[off[m] + r].
+struct TileRows {
+  int off[2 * kMaxModes];
+  long long xbase;  // X offset of (i = 0, k)
+  int valid;
+};
+
+__device__ __forceinline__ void decompose(const KrpDesc& d, long long k, int R, int* off) {
+  for (int m = 0; m < d.nm; ++m) {
+    long long dm = d.dim[m];
+    long long km = k % dm;
+    k /= dm;
+    off[m] = (int)(km * R);
+  }
+}
+
+__device__ __forceinline__ float krp_value(const KrpDesc& d, const int* off, int r) {
+  float v = 1.0f;
+  for (int m = 0; m < d.nm; ++m) v *= __ldg(d.H[m] + off[m] + r);
+  return v;
+}
+
+template <bool kSlow>
+__global__ void __launch_bounds__(kThreads)
+k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q, KrpDesc KL,
+              KrpDesc KQ, int R, long long kchunk, float* __restrict__ out,
+              long long out_chunk_stride) {
+  __shared__ __align__(16) float Xs[kBK][kBI + 4];
+  __shared__ __align__(16) float Ws[kBK][kRT];
+  __shared__ TileRows rows[kBK];
+
+  const long long Ktot = L * Q;
+  const long long i0 = (long long)blockIdx.x * kBI;
+  const int r0 = blockIdx.z * kRT;
+  const long long kbeg = (long long)blockIdx.y * kchunk;
+  const long long kend = min(Ktot, kbeg + kchunk);
+  const int tid = threadIdx.x;
+  const int tx = tid & 7;   // rank group: r0 + 4*tx .. +3
+  const int ty = tid >> 3;  // row group:  i0 + 4*ty .. +3
+
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+
+  for (long long k0 = kbeg; k0 < kend; k0 += kBK) {
+    if (tid < kBK) {
+      long long k = k0 + tid;
+      TileRows tr;
+      tr.valid = k < kend;
+      if (tr.valid) {
+        long long l = k % L, q = k / L;
+        decompose(KL, l, R, tr.off);
+        decompose(KQ, q, R, tr.off + kMaxModes);
+        tr.xbase = l + L * I * q;
+      } else {
+        tr.xbase = 0;
+      }
+      rows[tid] = tr;
+    }
+    __syncthreads();
+    for (int e = tid; e < kBK * kRT; e += kThreads) {
+      int kk = e / kRT, rr = e % kRT;
+      int r = r0 + rr;
+      float w = 0.0f;
+      if (rows[kk].valid && r < R)
+        w = krp_value(KL, rows[kk].off, r) * krp_value(KQ, rows[kk].off + kMaxModes, r);
+      Ws[kk][rr] = w;
+    }
+    // X tile: element (i, k) at xbase(k) + L*i; coalesce along whichever is contiguous
+    for (int e = tid; e < kBK * kBI; e += kThreads) {
+      int kk, ii;
+      if (kSlow) { kk = e / kBI; ii = e % kBI; }   // L == 1: rows contiguous in i
+      else       { kk = e % kBK; ii = e / kBK; }   // contiguous in k (l fastest)
+      long long i = i0 + ii;
+      float v = 0.0f;
+      if (rows[kk].valid && i < I) v = __ldg(X + rows[kk].xbase + L * i);
+      Xs[kk][ii] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kBK; ++kk) {
+      float4 xv = *reinterpret_cast<const float4*>(&Xs[kk][ty * 4]);
+      float4 wv = *reinterpret_cast<const float4*>(&Ws[kk][tx * 4]);
+      float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+      float wa[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], wa[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+
+  float* o = out + (long long)blockIdx.y * out_chunk_stride;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    long long i = i0 + ty * 4 + a;
+    if (i >= I) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int r = r0 + tx * 4 + b;
+      if (r < R) o[i * R + r] = acc[a][b];
+    }
+  }
+}
+
+// out[e] = sum_{c < C} part[c * E + e], in chunk order (deterministic).
+__global__ void k_reduce_chunks(const float* __restrict__ part, long long E, int C,
+                                float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E;
+       e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int c = 0; c < C; ++c) s += part[(long long)c * E + e];
+    out[e] = s;
+  }
+}
+
+// Multi-TTV leaf: out(i, r) = sum_k T[(i + I*k)*R + r] * KK(k, r).
+// Threads cover consecutive flattened (i, r) positions, so every k step reads
+// one contiguous run of the node temporary.
+__global__ void __launch_bounds__(kThreads)
+k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, int R,
+            long long kchunk, float* __restrict__ out, long long out_chunk_stride) {
+  extern __shared__ float smem[];
+  float* Ws = smem;  // kBK x R
+  __shared__ int offs[kBK][kMaxModes];
+  const long long E = I * R;
+  const long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const int r = (int)(e % R);
+  const long long kbeg = (long long)blockIdx.y * kchunk;
+  const long long kend = min(K, kbeg + kchunk);
+  float acc = 0.0f;
+  for (long long k0 = kbeg; k0 < kend; k0 += kBK) {
+    if (threadIdx.x < kBK) {
+      long long k = k0 + threadIdx.x;
+      if (k < kend) decompose(KK, k, R, offs[threadIdx.x]);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBK * R; t += kThreads) {
+      int kk = t / R, rr = t % R;
+      Ws[t] = (k0 + kk < kend) ? krp_value(KK, offs[kk], rr) : 0.0f;
+    }
+    __syncthreads();
+    if (e < E) {
+      int kn = (int)min((long long)kBK, kend - k0);
+      const float* Tp = T + (I * k0) * R + e;
+      for (int kk = 0; kk < kn; ++kk) acc = fmaf(__ldg(Tp + I * R * kk), Ws[kk * R + r], acc);
+    }
+    __syncthreads();
+  }
+  if (e < E) out[(long long)blockIdx.y * out_chunk_stride + e] = acc;
+}
+
+// Multi-TTV to the child node: out(j, r) = sum_i T[(i + I*j)*R + r] * H(i, r).
+// One CTA per j; thread (g, r) strides over i; a fixed-order reduction over g.
+__global__ void k_mttv_first(const float* __restrict__ T, long long I, const float* __restrict__ H,
+                             int R, int G, float* __restrict__ out) {
+  extern __shared__ float red[];  // G x R
+  const long long j = blockIdx.x;
+  const int r = threadIdx.x % R;
+  const int g = threadIdx.x / R;
+  float acc = 0.0f;
+  if (g < G) {
+    const float* Tj = T + I * j * R;
+    for (long long i = g; i < I; i += G) acc = fmaf(__ldg(Tj + i * R + r), __ldg(H + i * R + r), acc);
+    red[g * R + r] = acc;
+  }
+  __syncthreads();
+  if (g == 0) {
+    float s = 0.0f;
+    for (int gg = 0; gg < G; ++gg) s += red[gg * R + r];
+    out[j * R + r] = s;
+  }
+}
+
+__device__ __forceinline__ double block_sum_double(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  return t;  // valid in thread 0
+}
+
+__global__ void k_sumsq_partial(const void* __restrict__ Xv, int bf16, long long n,
+                                double* __restrict__ partials, const int* flags) {
+  if (flags && flags[0]) return;
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!bf16) {
+    const float* X = static_cast<const float*>(Xv);
+    const long long n4 = n / 4;
+    const float4* X4 = reinterpret_cast<const float4*>(X);
+    for (long long t = t0; t < n4; t += stride) {
+      float4 v = __ldg(X4 + t);
+      float s = v.x * v.x;
+      s = fmaf(v.y, v.y, s);
+      s = fmaf(v.z, v.z, s);
+      s = fmaf(v.w, v.w, s);
+      acc += (double)s;
+    }
+    for (long long t = n4 * 4 + t0; t < n; t += stride) acc += (double)X[t] * X[t];
+  } else {
+    const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(Xv);
+    for (long long t = t0; t < n; t += stride) {
+      float v = __bfloat162float(X[t]);
+      acc += (double)(v * v);
+    }
+  }
+  double tot = block_sum_double(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int n, double* out,
+                               const int* flags) {
+  if (flags && flags[0]) return;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partials[i];
+    out[0] = s;
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ X, __nv_bfloat16* __restrict__ Y, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    Y[t] = __float2bfloat16_rn(X[t]);
+}
+
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+// Split of the contraction across CTAs: enough CTAs for ~4 per SM, chunks of
+// whole tiles, at least 8 tiles per chunk.
+int choose_chunks(long long ctas_other, long long Ktot, int num_sms) {
+  long long target = 4LL * num_sms;
+  if (ctas_other >= target) return 1;
+  long long C = ceil_div(target, ctas_other);
+  long long max_c = max(1LL, ceil_div(Ktot, 8LL * kBK));
+  return (int)min(C, max_c);
+}
+
+}  // namespace
+
+size_t simt_mttkrp_partials(int64_t L, int64_t I, int64_t Q, int R, int num_sms) {
+  long long gx = ceil_div(I, kBI), gz = ceil_div(R, kRT);
+  int C = choose_chunks(gx * gz, (long long)L * Q, num_sms);
+  return C > 1 ? (size_t)C * I * R : 0;
+}
+
+cudaError_t launch_simt_mttkrp(const float* X, int64_t L, int64_t I, int64_t Q,
+                               const KrpDesc& KL, const KrpDesc& KQ, int R, float* out,
+                               float* partials, size_t part_cap, int num_sms,
+                               cudaStream_t st) {
+  long long Ktot = (long long)L * Q;
+  long long gx = ceil_div(I, kBI), gz = ceil_div(R, kRT);
+  int C = choose_chunks(gx * gz, Ktot, num_sms);
+  long long kchunk = ceil_div(ceil_div(Ktot, C), kBK) * kBK;
+  C = (int)ceil_div(Ktot, kchunk);
+  float* dst = out;
+  if (C > 1) {
+    if ((size_t)C * I * R > part_cap || partials == nullptr) return cudaErrorInvalidValue;
+    dst = partials;
+  }
+  dim3 grid((unsigned)gx, (unsigned)C, (unsigned)gz);
+  if (L == 1)
+    k_simt_mttkrp<true><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
+                                                   (long long)I * R);
+  else
+    k_simt_mttkrp<false><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
+                                                    (long long)I * R);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || C == 1) return e;
+  long long E = (long long)I * R;
+  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
+  k_reduce_chunks<<<blocks, 256, 0, st>>>(partials, E, C, out);
+  return cudaGetLastError();
+}
+
+size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
+  long long gx = ceil_div((long long)I * R, kThreads);
+  int C = choose_chunks(gx, K, num_sms);
+  return C > 1 ? (size_t)C * I * R : 0;
+}
+
+cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc& KK, int R,
+                             float* out, float* partials, size_t part_cap, int num_sms,
+                             cudaStream_t st) {
+  long long E = (long long)I * R;
+  long long gx = ceil_div(E, kThreads);
+  int C = choose_chunks(gx, K, num_sms);
+  long long kchunk = ceil_div(ceil_div(K, C), kBK) * kBK;
+  C = (int)ceil_div(K, kchunk);
+  float* dst = out;
+  if (C > 1) {
+    if ((size_t)C * E > part_cap || partials == nullptr) return cudaErrorInvalidValue;
+    dst = partials;
+  }
+  size_t smem = (size_t)kBK * R * sizeof(float);
+  k_mttv_leaf<<<dim3((unsigned)gx, (unsigned)C), kThreads, smem, st>>>(T, I, K, KK, R, kchunk,
+                                                                      dst, E);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || C == 1) return e;
+  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
+  k_reduce_chunks<<<blocks, 256, 0, st>>>(partials, E, C, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mttv_first(const float* T, int64_t I, int64_t J, const float* H, int R,
+                              float* out, cudaStream_t st) {
+  int G = max(1, 256 / R);
+  int threads = G * R;
+  size_t smem = (size_t)G * R * sizeof(float);
+  k_mttv_first<<<(unsigned)J, threads, smem, st>>>(T, I, H, R, G, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const void* X, int bf16, int64_t n, double* partials, int nparts,
+                         double* out, const int* flags, cudaStream_t st) {
+  k_sumsq_partial<<<nparts, 256, 0, st>>>(X, bf16, n, partials, flags);
+  k_sum_partials<<<1, 32, 0, st>>>(partials, nparts, out, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* X, uint16_t* Y, int64_t n, cudaStream_t st) {
+  int blocks = (int)min(ceil_div(n, 256), 152LL * 16);
+  if (blocks < 1) blocks = 1;
+  k_to_bf16<<<blocks, 256, 0, st>>>(X, reinterpret_cast<__nv_bfloat16*>(Y), n);
+  return cudaGetLastError();
+}
+
+}  // namespace nncp

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of the C ABI in ``include/nncp.h`` (argument marshalling only).
+
+Every compute step runs in the CUDA library ``_lib/libnncp.so``; this module
+only converts Python/torch arguments to pointers and sizes.  Loading fails
+loudly if the library has not been built: there is no fallback.
+
+Functions keep the C names (``nncp_create``, ``nncp_mttkrp`` ...).  ``Context``
+is a small convenience wrapper that allocates the workspace with torch.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libnncp.so")
+
+NNCP_OK = 0
+NNCP_ERR_INVALID_ARG = 1
+NNCP_ERR_OUT_OF_MEMORY = 2
+NNCP_ERR_CUDA = 3
+NNCP_ERR_NUMERIC = 4
+NNCP_ERR_TIMEOUT = 5
+NNCP_ERR_NOT_READY = 6
+NNCP_ERR_UNSUPPORTED = 7
+
+NNCP_FP32_SIMT = 0
+NNCP_TF32 = 1
+NNCP_SPLIT_BF16X3 = 2
+NNCP_BF16_STORED = 3
+
+PRECISIONS = {"fp32_simt": NNCP_FP32_SIMT, "tf32": NNCP_TF32,
+              "split_bf16x3": NNCP_SPLIT_BF16X3, "bf16_stored": NNCP_BF16_STORED}
+
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_dblp = ctypes.POINTER(ctypes.c_double)
+_c_intp = ctypes.POINTER(ctypes.c_int)
+_c_vpp = ctypes.POINTER(ctypes.c_void_p)
+
+# (name, restype, argtypes)
+_SIGNATURES = [
+    ("nncp_version", ctypes.c_char_p, []),
+    ("nncp_default_split", ctypes.c_int, [ctypes.c_int, _c_i64p]),
+    ("nncp_create", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("nncp_set_options", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("nncp_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("nncp_set_tensor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("nncp_set_factors", ctypes.c_int, [ctypes.c_void_p, _c_vpp]),
+    ("nncp_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_partial_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_iteration_kernels", ctypes.c_int, [ctypes.c_void_p, _c_intp]),
+    ("nncp_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_dblp, _c_intp, _c_dblp]),
+    ("nncp_fit_history", ctypes.c_int, [ctypes.c_void_p, _c_dblp, ctypes.c_int, _c_intp]),
+    ("nncp_fit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dblp]),
+    ("nncp_solve_begin", ctypes.c_int, [ctypes.c_void_p]),
+    ("nncp_iterate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("nncp_tensor_to_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("nncp_solve_host", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.c_void_p, _c_vpp,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       _c_dblp, _c_intp, _c_dblp]),
+    ("nncp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("nncp_global_error", ctypes.c_char_p, []),
+    ("nncp_destroy", None, [ctypes.c_void_p]),
+]
+
+_lib = None
+
+
+def exported_symbols():
+    return [name for name, _, _ in _SIGNATURES]
+
+
+def load(path=LIB_PATH):
+    """Load the library (once).  Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"NNCP CUDA library not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class NNCPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"nncp status {status}: {msg}")
+        self.status = status
+
+
+def _check(status, ctx=None):
+    if status != NNCP_OK:
+        lib = load()
+        msg = lib.nncp_last_error(ctx) if ctx else lib.nncp_global_error()
+        raise NNCPError(status, (msg or b"").decode())
+
+
+def _dims(dims):
+    return (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+# ---- functions with the C names ------------------------------------------------
+
+def nncp_version():
+    return load().nncp_version().decode()
+
+
+def nncp_default_split(dims):
+    return load().nncp_default_split(len(dims), _dims(dims))
+
+
+def nncp_create(dims, R):
+    ctx = ctypes.c_void_p()
+    _check(load().nncp_create(len(dims), _dims(dims), int(R), ctypes.byref(ctx)))
+    return ctx
+
+
+def nncp_set_options(ctx, precision=NNCP_FP32_SIMT, root_split=0, stream=None):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    _check(load().nncp_set_options(ctx, int(precision), int(root_split), _stream(stream)), ctx)
+
+
+def nncp_workspace_size(ctx):
+    n = ctypes.c_size_t()
+    _check(load().nncp_workspace_size(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def nncp_set_workspace(ctx, ws):
+    _check(load().nncp_set_workspace(ctx, _ptr(ws), ws.numel() * ws.element_size()), ctx)
+
+
+def nncp_set_tensor(ctx, X):
+    _check(load().nncp_set_tensor(ctx, _ptr(X)), ctx)
+
+
+def nncp_set_factors(ctx, H):
+    arr = (ctypes.c_void_p * len(H))(*[int(h.data_ptr()) for h in H])
+    _check(load().nncp_set_factors(ctx, arr), ctx)
+
+
+def nncp_mttkrp(ctx, mode, use_dimtree, M):
+    _check(load().nncp_mttkrp(ctx, int(mode), int(use_dimtree), _ptr(M)), ctx)
+
+
+def nncp_partial_mttkrp(ctx, side, T):
+    _check(load().nncp_partial_mttkrp(ctx, int(side), _ptr(T)), ctx)
+
+
+def nncp_iteration_kernels(ctx):
+    n = ctypes.c_int()
+    _check(load().nncp_iteration_kernels(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def nncp_solve(ctx, R, max_iters, tol):
+    lam = (ctypes.c_double * R)()
+    iters = ctypes.c_int()
+    fit = ctypes.c_double()
+    _check(load().nncp_solve(ctx, int(max_iters), float(tol), lam, ctypes.byref(iters),
+                             ctypes.byref(fit)), ctx)
+    return list(lam), iters.value, fit.value
+
+
+def nncp_fit_history(ctx, max_count):
+    buf = (ctypes.c_double * max_count)()
+    n = ctypes.c_int()
+    _check(load().nncp_fit_history(ctx, buf, int(max_count), ctypes.byref(n)), ctx)
+    return list(buf[: n.value])
+
+
+def nncp_fit(ctx, exact=False):
+    f = ctypes.c_double()
+    _check(load().nncp_fit(ctx, int(bool(exact)), ctypes.byref(f)), ctx)
+    return f.value
+
+
+def nncp_solve_begin(ctx):
+    _check(load().nncp_solve_begin(ctx), ctx)
+
+
+def nncp_iterate(ctx, iters):
+    _check(load().nncp_iterate(ctx, int(iters)), ctx)
+
+
+def nncp_tensor_to_bf16(X, Xb, stream=None):
+    _check(load().nncp_tensor_to_bf16(_ptr(X), _ptr(Xb), X.numel(), _stream(stream)))
+
+
+def nncp_solve_host(dims, R, X_host, H_host, precision=NNCP_FP32_SIMT, root_split=0,
+                    max_iters=50, tol=0.0):
+    """X_host: contiguous float32 numpy/torch CPU array; H_host: list of writable
+    contiguous float32 (I_n, R) arrays, overwritten with the result."""
+    def addr(a):
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return a.ctypes.data
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    arr = (ctypes.c_void_p * len(H_host))(*[addr(h) for h in H_host])
+    lam = (ctypes.c_double * R)()
+    iters = ctypes.c_int()
+    fit = ctypes.c_double()
+    _check(load().nncp_solve_host(len(dims), _dims(dims), int(R), ctypes.c_void_p(addr(X_host)),
+                                  arr, int(precision), int(root_split), int(max_iters),
+                                  float(tol), lam, ctypes.byref(iters), ctypes.byref(fit)))
+    return list(lam), iters.value, fit.value
+
+
+def nncp_last_error(ctx):
+    return load().nncp_last_error(ctx).decode()
+
+
+def nncp_destroy(ctx):
+    load().nncp_destroy(ctx)
+
+
+# ---- convenience wrapper ---------------------------------------------------------
+
+class Context:
+    """A context plus a torch-allocated workspace on the current CUDA device."""
+
+    def __init__(self, dims, R, precision=NNCP_FP32_SIMT, root_split=0, stream=None):
+        import torch
+        self.dims = tuple(int(d) for d in dims)
+        self.R = int(R)
+        self.ctx = nncp_create(self.dims, self.R)
+        self._keep = []
+        try:
+            nncp_set_options(self.ctx, precision, root_split, stream)
+            nbytes = nncp_workspace_size(self.ctx)
+            self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+            nncp_set_workspace(self.ctx, self.ws)
+        except Exception:
+            nncp_destroy(self.ctx)
+            raise
+
+    def set_tensor(self, X):
+        self._keep = [X] + self._keep[1:] if self._keep else [X]
+        nncp_set_tensor(self.ctx, X)
+
+    def set_factors(self, H):
+        self._factors = list(H)
+        nncp_set_factors(self.ctx, self._factors)
+
+    def mttkrp(self, mode, use_dimtree, out):
+        nncp_mttkrp(self.ctx, mode, use_dimtree, out)
+        return out
+
+    def partial_mttkrp(self, side, out):
+        nncp_partial_mttkrp(self.ctx, side, out)
+        return out
+
+    def iteration_kernels(self):
+        return nncp_iteration_kernels(self.ctx)
+
+    def solve(self, max_iters, tol=0.0):
+        return nncp_solve(self.ctx, self.R, max_iters, tol)
+
+    def fit_history(self, max_count=1 << 16):
+        return nncp_fit_history(self.ctx, max_count)
+
+    def fit(self, exact=False):
+        return nncp_fit(self.ctx, exact)
+
+    def solve_begin(self):
+        nncp_solve_begin(self.ctx)
+
+    def iterate(self, iters):
+        nncp_iterate(self.ctx, iters)
+
+    def close(self):
+        if self.ctx is not None:
+            nncp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
