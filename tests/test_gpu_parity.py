@@ -141,13 +141,16 @@ def test_solve_other_orders_and_splits(nn, dims, R, split):
 
 
 def test_convergence_stops_early_like_oracle(nn):
+    # the stopping test |fit_k - fit_(k-1)| < tol is a discrete decision: it is
+    # compared at a tol well above the float32 noise of the fit identity
+    # (eps^2 = (alpha - 2 beta + gamma) / alpha cancels, ~1e-6 at eps ~ 1e-2)
     dims, R = (20, 18, 16), 3
     x, _ = synth.lowrank_plus_noise(dims, R, seed=21, noise=0.01)
     H0 = synth.init_factors(dims, R, seed=22)
-    ref, (lam, k, fit, hist, exact, Hg) = _solve_both(nn, dims, R, 500, x, H0, tol=1e-6)
-    assert ref["iters"] < 500
-    assert abs(k - ref["iters"]) <= 2
-    assert abs(fit - ref["fits"][-1]) <= FIT_TOL
+    ref, (lam, k, fit, hist, exact, Hg) = _solve_both(nn, dims, R, 500, x, H0, tol=1e-4)
+    assert 2 <= ref["iters"] < 500
+    assert abs(k - ref["iters"]) <= 1
+    assert abs(fit - ref["fits"][k - 1]) <= FIT_TOL
 
 
 def test_solve_is_bitwise_reproducible(nn):
