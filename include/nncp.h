@@ -155,6 +155,38 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
                             int max_iters, double tol, double* lambda_out, int* iters_out,
                             double* fit_out);
 
+/* Direct MTTKRP of one mode that allocates nothing (the paper has no
+ * counterpart; this is a deployment convenience).
+ *
+ * For callers that must not allocate device memory: a host whose caching
+ * allocator has already reserved the free device memory (so a cudaMalloc would
+ * fail or fragment its pool), a plugin or UDF host that only hands in buffers
+ * it allocated itself, or a latency-critical serving loop in which cudaMalloc
+ * would synchronise the device and stall every other stream.
+ *
+ * Computes the same M_mode as nncp_mttkrp(ctx, mode, 0, M_dev) -- one direct
+ * float32 pass over X with the Khatri-Rao rows formed on the fly -- from the
+ * caller's X_dev (float32, mode-1 fastest), H_dev[0..N-1] (I_n x R row-major)
+ * and M_dev (I_mode x R row-major), all device pointers, 16-byte aligned.
+ * No context, no workspace: the split-K partial sums live in a file-scope
+ * __device__ array of NNCP_NOALLOC_SCRATCH_FLOATS floats (8 MiB) that every
+ * GPU which loads the library holds until the process exits.
+ *   - Sizes: I_mode * R must be at most NNCP_NOALLOC_SCRATCH_FLOATS / 2;
+ *     larger requests return NNCP_ERR_INVALID_ARG (nncp_global_error says
+ *     why) and launch nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call on a device shares the one array.  Each call overwrites the
+ *     partials it reads, so nothing needs clearing, but calls whose kernels
+ *     overlap on the GPU (different streams, or different host threads) race
+ *     on it: serialise them.
+ *   - Asynchronous on `stream` (cudaStream_t, NULL = legacy default). */
+#define NNCP_NOALLOC_SCRATCH_FLOATS (1 << 21)
+nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* X_dev,
+                                const float* const* H_dev, int mode, float* M_dev,
+                                void* stream);
+
 const char* nncp_last_error(const nncp_ctx* ctx);
 /* Message of the last failure of a call that had no context to record it in. */
 const char* nncp_global_error(void);

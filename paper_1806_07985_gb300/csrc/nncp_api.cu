@@ -347,6 +347,10 @@ nncp_status ensure_graph(nncp_ctx* c) {
 
 }  // namespace
 
+namespace nncp {
+void record_global_error(const char* msg) { g_error = msg; }
+}  // namespace nncp
+
 // =============================== C ABI ======================================
 
 extern "C" {

@@ -44,6 +44,13 @@ cudaError_t launch_simt_mttkrp(const float* X, int64_t L, int64_t I, int64_t Q,
                                float* partials, size_t part_cap, int num_sms,
                                cudaStream_t st);
 size_t simt_mttkrp_partials(int64_t L, int64_t I, int64_t Q, int R, int num_sms);
+cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int64_t Q,
+                                      const KrpDesc& KL, const KrpDesc& KQ, int R, float* out,
+                                      float* partials, size_t part_cap, int num_sms,
+                                      cudaStream_t st);
+
+// Records a message for nncp_global_error().
+void record_global_error(const char* msg);
 
 // Multi-TTV leaf: out(i, r) = sum_{k < K} T[((i + I*k) * R) + r] * KK(k, r).
 cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc& KK,

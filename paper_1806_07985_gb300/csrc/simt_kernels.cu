@@ -310,6 +310,38 @@ cudaError_t launch_simt_mttkrp(const float* X, int64_t L, int64_t I, int64_t Q,
   return cudaGetLastError();
 }
 
+// Same MTTKRP with the split-K chunk count capped so the partials fit in
+// `part_cap` floats (used by the entry point that allocates nothing).
+cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int64_t Q,
+                                      const KrpDesc& KL, const KrpDesc& KQ, int R, float* out,
+                                      float* partials, size_t part_cap, int num_sms,
+                                      cudaStream_t st) {
+  long long Ktot = (long long)L * Q;
+  long long gx = ceil_div(I, kBI), gz = ceil_div(R, kRT);
+  long long fit = (long long)(part_cap / ((size_t)I * R));
+  int C = (int)max(1LL, min((long long)choose_chunks(gx * gz, Ktot, num_sms), fit));
+  long long kchunk = ceil_div(ceil_div(Ktot, C), kBK) * kBK;
+  C = (int)ceil_div(Ktot, kchunk);
+  float* dst = out;
+  if (C > 1) {
+    if ((size_t)C * I * R > part_cap || partials == nullptr) return cudaErrorInvalidValue;
+    dst = partials;
+  }
+  dim3 grid((unsigned)gx, (unsigned)C, (unsigned)gz);
+  if (L == 1)
+    k_simt_mttkrp<true><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
+                                                   (long long)I * R);
+  else
+    k_simt_mttkrp<false><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
+                                                    (long long)I * R);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || C == 1) return e;
+  long long E = (long long)I * R;
+  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
+  k_reduce_chunks<<<blocks, 256, 0, st>>>(partials, E, C, out);
+  return cudaGetLastError();
+}
+
 size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
   long long gx = ceil_div((long long)I * R, kThreads);
   int C = choose_chunks(gx, K, num_sms);

@@ -60,6 +60,8 @@ _SIGNATURES = [
     ("nncp_solve_host", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.c_void_p, _c_vpp,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        _c_dblp, _c_intp, _c_dblp]),
+    ("nncp_mttkrp_noalloc", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.c_void_p,
+                                           _c_vpp, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("nncp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_global_error", ctypes.c_char_p, []),
     ("nncp_destroy", None, [ctypes.c_void_p]),
@@ -222,6 +224,14 @@ def nncp_solve_host(dims, R, X_host, H_host, precision=NNCP_FP32_SIMT, root_spli
                                   arr, int(precision), int(root_split), int(max_iters),
                                   float(tol), lam, ctypes.byref(iters), ctypes.byref(fit)))
     return list(lam), iters.value, fit.value
+
+
+def nncp_mttkrp_noalloc(dims, R, X, H, mode, M, stream=None):
+    """Direct MTTKRP of `mode` (1-based) that allocates nothing on the device;
+    X, H[n] and M are caller-owned CUDA tensors."""
+    arr = (ctypes.c_void_p * len(H))(*[int(h.data_ptr()) for h in H])
+    _check(load().nncp_mttkrp_noalloc(len(dims), _dims(dims), int(R), _ptr(X), arr, int(mode),
+                                      _ptr(M), _stream(stream)))
 
 
 def nncp_last_error(ctx):
