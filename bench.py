@@ -41,11 +41,11 @@ PRECISION_DTYPE = {"fp32_simt": "f32", "tf32": "tf32 (f32 accumulate)",
                    "split_bf16x3": "bf16x3 (f32 accumulate)", "bf16_stored": "bf16 (f32 accumulate)"}
 
 
-def tensor_bytes_per_iter(dims):
+def tensor_bytes_per_iter(dims, elem_bytes=4):
     n = 1
     for d in dims:
         n *= d
-    return 2 * 4 * n  # two float32 passes (root -> each half)
+    return 2 * elem_bytes * n  # two passes over the tensor (root -> each half)
 
 
 def parse():
@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None,
                    choices=["fp32_simt", "tf32", "split_bf16x3", "bf16_stored"])
+    p.add_argument("--mode", default="step", choices=["step", "pm"],
+                   help="pm: only the two root partial MTTKRPs, for kernel profiling")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -187,7 +189,19 @@ def run_ours(args):
     ctx.set_tensor(Xuse)
     ctx.set_factors(H)
     ctx.solve_begin()
-    bytes_step = tensor_bytes_per_iter(DIMS)
+    elem_bytes = Xuse.element_size()
+    bytes_step = tensor_bytes_per_iter(DIMS, elem_bytes)
+    if args.mode == "pm":
+        outs = [torch.empty((512, RANK), device="cuda"), torch.empty((512 * 512, RANK), device="cuda")]
+        for _ in range(args.warmup + args.steps):
+            ctx.partial_mttkrp(0, outs[0])
+            ctx.partial_mttkrp(1, outs[1])
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"mode": "pm", "precision": prec_name,
+                              "launches": 2 * (args.warmup + args.steps)}), flush=True)
+        ctx.close()
+        return
 
     for _ in range(max(args.warmup, 3)):
         ctx.iterate(1)
@@ -287,7 +301,7 @@ def run_e2e(nncp, torch, x, H0, prec, world):
         nncp.nncp_solve_host(DIMS, RANK, Xh, Hrun, prec, 1, ITERS_CONFIG, 0.0)
         times.append(time.perf_counter() - t0)
     t = float(np.median(times))
-    bytes_solve = ITERS_CONFIG * tensor_bytes_per_iter(DIMS)
+    bytes_solve = ITERS_CONFIG * tensor_bytes_per_iter(DIMS, 2 if prec == nncp.NNCP_BF16_STORED else 4)
     h2d = x.nbytes + sum(h.nbytes for h in H0)
     d2h = sum(h.nbytes for h in H0) + RANK * 8 + 8
     return {"value": round(world * bytes_solve / t / 1e9, 1), "unit": UNIT,

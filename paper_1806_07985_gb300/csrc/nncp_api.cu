@@ -457,6 +457,10 @@ nncp_status nncp_set_workspace(nncp_ctx* c, void* dev_ptr, size_t bytes) {
   c->ws_bytes = bytes;
   bind_workspace(c);
   drop_graph(c);
+  if (c->tc.bytes) {
+    CK(cudaMemsetAsync(c->tc.base, 0, 256, c->work));
+    CK(cudaStreamSynchronize(c->work));
+  }
   c->initialised = false;
   return NNCP_OK;
 }
@@ -589,6 +593,12 @@ nncp_status nncp_solve(nncp_ctx* c, int max_iters, double tol, double* lambda_ou
   if (iters_out) *iters_out = iters;
   if (fit_out) *fit_out = fit;
   if ((s = end_on_work(c)) != NNCP_OK) return s;
+  if (c->tc.bytes) {
+    int tc_err = 0;
+    CK(cudaMemcpy(&tc_err, tc_error_word(c->tc), sizeof(int), cudaMemcpyDeviceToHost));
+    if (tc_err)
+      return fail(c, NNCP_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (error word set)");
+  }
   if (c->host_flags[3]) return fail(c, NNCP_ERR_NUMERIC, "non-finite fit at iteration %d", iters);
   return NNCP_OK;
 }

@@ -52,6 +52,10 @@ cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int6
 // Records a message for nncp_global_error().
 void record_global_error(const char* msg);
 
+// out[e] = sum_{c < C} part[c * E + e] in chunk order (deterministic).
+cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out, int num_sms,
+                                 cudaStream_t st);
+
 // Multi-TTV leaf: out(i, r) = sum_{k < K} T[((i + I*k) * R) + r] * KK(k, r).
 cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc& KK,
                              int R, float* out, float* partials, size_t part_cap,

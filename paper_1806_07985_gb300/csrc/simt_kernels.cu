@@ -342,6 +342,14 @@ cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int6
   return cudaGetLastError();
 }
 
+cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out, int num_sms,
+                                 cudaStream_t st) {
+  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
+  if (blocks < 1) blocks = 1;
+  k_reduce_chunks<<<blocks, 256, 0, st>>>(part, E, C, out);
+  return cudaGetLastError();
+}
+
 size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
   long long gx = ceil_div((long long)I * R, kThreads);
   int C = choose_chunks(gx, K, num_sms);

@@ -1,20 +1,793 @@
+// Root partial MTTKRPs of the dimension tree (Sec. IV-A, Fig. 2a) on the
+// 5th-generation tensor cores of sm_103a: tcgen05.mma with TMEM accumulators,
+// tensor operands staged by TMA, Khatri-Rao rows formed on the fly in shared
+// memory (never written to HBM).
+//
+// The tensor is viewed as the column-major IL x IR matrix X_(1:s) that its
+// memory already is.  Two contractions:
+//   contract_fast: out(j, r) = sum_i X[i + IL*j] K(i, r)   (M = IR rows, K = IL)
+//   contract_slow: out(i, r) = sum_j X[i + IL*j] K(j, r)   (M = IL rows, K = IR)
+// A (128 output rows x 64 contraction elements per stage) is always handed to
+// the MMA K-major with the 128-byte swizzle.  contract_fast tiles arrive
+// K-major from TMA; contract_slow tiles arrive MN-major (no swizzle) and the
+// converter warps transpose them.  Precision modes:
+//   TF32         kind::tf32 on the float32 tensor (direct when K-major);
+//   SPLIT_BF16X3 x = hi + lo in bf16, K = Khi + Klo: D = hi*[Khi|Klo] + lo*Khi
+//                (three products, float32 accumulation in TMEM);
+//   BF16_STORED  the tensor is bf16 in HBM: D = X*[Khi|Klo].
+//
+// Warp roles (12 warps, one CTA per SM, persistent over work units):
+//   warp 0      TMA producer          warp 1      TMEM owner + MMA issuer
+//   warps 2-3   Khatri-Rao B builder  warps 4-7   converters (hi/lo split, transposes)
+//   warps 8-11  epilogue (tcgen05.ld TMEM -> registers -> global)
+// A work unit is one 128-row output tile over one contraction range; when the
+// output has fewer tiles than SMs the contraction is split and the per-range
+// partials are summed afterwards in a fixed order.
+//
+// Every mbarrier wait is bounded (about two seconds of clock64): on expiry
+// the kernel records an error word, stops issuing work, waits (bounded) for
+// its copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "../../include/nncp.h"
 #include "tc_kernels.cuh"
 
 namespace nncp {
 
-bool tc_available() { return false; }
+namespace {
 
-const char* tc_unsupported_reason(int, int, const int64_t*, int, int) {
-  return "tensor-core partial MTTKRP not built";
+constexpr int kKC = 64;  // contraction elements per stage
+constexpr int kSF = 3;   // raw (TMA) stages
+constexpr int kSC = 2;   // converted A stages
+constexpr int kSB = 3;   // B (Khatri-Rao) stages
+constexpr int kThreads = 384;
+constexpr int kWarpTMA = 0, kWarpMMA = 1, kWarpB = 2, kWarpConv = 4, kWarpEpi = 8;
+constexpr int kMaxRp = 64;
+constexpr long long kWaitCycles = 4000000000LL;
+
+constexpr int kRawBytes = 32768;
+constexpr int kConvBytes = 32768;
+constexpr int kBBytes = 2 * kMaxRp * 128;  // 16 KB
+constexpr int kOffRaw = 0;
+constexpr int kOffConv = kOffRaw + kSF * kRawBytes;
+constexpr int kOffB = kOffConv + kSC * kConvBytes;
+constexpr int kOffOffs = kOffB + kSB * kBBytes;                 // B builder row offsets
+constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;
+constexpr int kOffBar = kOffOffs + kOffsBytes;
+// barriers: raw full/empty, conv full/empty, B full/empty, acc full/empty x2, drain
+constexpr int kNumBars = 2 * kSF + 2 * kSC + 2 * kSB + 4 + 1;
+constexpr int kOffMisc = kOffBar + kNumBars * 8;
+constexpr int kSmemUse = kOffMisc + 64;
+constexpr int kSmemBytes = kSmemUse + 1024;  // + alignment slack
+
+struct TcParams {
+  int mode;
+  int contract_fast;
+  int direct;  // MMA reads the TMA stage (no converter)
+  int bf16x;   // tensor stored as bf16
+  long long M, K;
+  int R, Rp;
+  long long n_mt, nsplit, kper, n_units;
+  KrpDesc krp;
+  float* out;
+  int* err;
+};
+
+// ------------------------------------------------------------ PTX helpers --
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-size_t tc_scratch_bytes(int, const int64_t*, int, int, int, int) { return 0; }
-
-cudaError_t tc_partial_mttkrp(int, int, const void*, int64_t, int64_t, const KrpDesc&, int,
-                              float*, const TcScratch&, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-cudaError_t tc_attributes_init() { return cudaSuccess; }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and the abort flag set) when the wait expires or
+// another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_test(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+// OR of `pred` over the `nthreads` threads of named barrier `id` (also a barrier).
+__device__ __forceinline__ int bar_red_or(int id, int nthreads, int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return r;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO); LBO unused for this layout.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // LBO (16 B, ignored)
+  d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D float32, A/B type `ab` (1 = bf16 under kind::f16,
+// 2 = tf32 under kind::tf32), both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab, uint32_t n) {
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                       uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ float lds32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t lds16(uint32_t addr) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Byte address of 16-byte chunk `chunk` of row `row` in a K-major SW128 tile.
+__device__ __forceinline__ uint32_t sw128_chunk(uint32_t base, int row, int chunk) {
+  return base + row * 128 + (((chunk ^ row) & 7) << 4);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// hi = bf16(x), lo = bf16(x - hi) for 8 values, packed
+__device__ __forceinline__ void split8(const float* x, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]);
+    __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * i + 1]);
+    float r0 = x[2 * i] - __bfloat162float(h0);
+    float r1 = x[2 * i + 1] - __bfloat162float(h1);
+    __nv_bfloat162 hh;
+    hh.x = h0;
+    hh.y = h1;
+    hi[i] = *reinterpret_cast<uint32_t*>(&hh);
+    lo[i] = pack_bf16(r0, r1);
+  }
+}
+
+struct Unit {
+  long long mt, kbeg, kend;
+  int nk;
+};
+
+__device__ __forceinline__ Unit get_unit(const TcParams& p, long long u) {
+  Unit w;
+  w.mt = u % p.n_mt;
+  const long long kc = u / p.n_mt;
+  w.kbeg = kc * p.kper;
+  w.kend = min(p.K, w.kbeg + p.kper);
+  w.nk = (int)((w.kend - w.kbeg + kKC - 1) / kKC);
+  return w;
+}
+
+// ------------------------------------------------------------------ kernel --
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
+  extern __shared__ uint8_t smem_dyn[];
+  const uint32_t sbase_raw = smem_u32(smem_dyn);
+  const uint32_t sbase = (sbase_raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_dyn + (sbase - sbase_raw);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  const uint32_t raw0 = sbase + kOffRaw;
+  const uint32_t conv0 = sbase + kOffConv;
+  const uint32_t b0 = sbase + kOffB;
+  int* offs = reinterpret_cast<int*>(gbase + kOffOffs);  // [kSB][kKC][kMaxModes + 1]
+  const uint32_t bar0 = sbase + kOffBar;
+  auto raw_full = [&](int i) { return bar0 + 8u * i; };
+  auto raw_empty = [&](int i) { return bar0 + 8u * (kSF + i); };
+  auto conv_full = [&](int i) { return bar0 + 8u * (2 * kSF + i); };
+  auto conv_empty = [&](int i) { return bar0 + 8u * (2 * kSF + kSC + i); };
+  auto b_full = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + i); };
+  auto b_empty = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + kSB + i); };
+  auto acc_full = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + 2 * kSB + i); };
+  auto acc_empty = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + 2 * kSB + 2 + i); };
+  const uint32_t drain_bar = bar0 + 8u * (kNumBars - 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + kOffMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + kOffMisc + 8);
+
+  const int Rp = p.Rp;
+  const uint32_t acc_cols = 2u * Rp;  // per accumulator buffer
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < 2 * acc_cols) tmem_cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kSF; ++i) {
+      mbar_init(raw_full(i), 1);
+      mbar_init(raw_empty(i), p.direct ? 1 : 4);
+    }
+    for (int i = 0; i < kSC; ++i) {
+      mbar_init(conv_full(i), 4);
+      mbar_init(conv_empty(i), 1);
+    }
+    for (int i = 0; i < kSB; ++i) {
+      mbar_init(b_full(i), 2);
+      mbar_init(b_empty(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(acc_full(i), 1);
+      mbar_init(acc_empty(i), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kWarpMMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const long long n_units = p.n_units;
+  const int R = p.R;
+
+  if (warp == kWarpTMA) {
+    // ---------------------------------------------------------- producer --
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+      int sf = 0;
+      uint32_t ph = 0;
+      int issued[kSF] = {0, 0, 0};
+      const uint32_t tx = p.bf16x ? 16384u : 32768u;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const Unit w = get_unit(p, u);
+        for (int s = 0; s < w.nk; ++s) {
+          if (!mbar_wait(raw_empty(sf), ph ^ 1u, abort_flag, p.err)) { ok = false; break; }
+          mbar_arrive_tx(raw_full(sf), tx);
+          const int k0 = (int)(w.kbeg + (long long)s * kKC);
+          const int m0 = (int)(w.mt * 128);
+          const uint32_t dst = raw0 + sf * kRawBytes;
+          if (p.contract_fast) {
+            if (p.bf16x) {
+              tma_load_2d(dst, &tmap, k0, m0, raw_full(sf));
+            } else {
+              tma_load_2d(dst, &tmap, k0, m0, raw_full(sf));
+              tma_load_2d(dst + 16384, &tmap, k0 + 32, m0, raw_full(sf));
+            }
+          } else {
+            tma_load_2d(dst, &tmap, m0, k0, raw_full(sf));
+          }
+          ++issued[sf];
+          if (++sf == kSF) { sf = 0; ph ^= 1u; }
+        }
+      }
+      // wait for every copy this thread issued before the CTA can exit
+      for (int i = 0; i < kSF; ++i) {
+        if (issued[i] == 0) continue;
+        const uint32_t par = (uint32_t)((issued[i] - 1) & 1);
+        const long long t0 = clock64();
+        while (!mbar_test(raw_full(i), par) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == kWarpMMA) {
+    // --------------------------------------------------------- MMA issue --
+    if (lane == 0) {
+      int sa = 0, sb = 0;
+      uint32_t pha = 0, phb = 0;
+      const int nA = p.direct ? kSF : kSC;
+      bool ok = true;
+      long long li = 0;
+      const bool split = p.mode == NNCP_SPLIT_BF16X3;
+      const bool tf32 = p.mode == NNCP_TF32;
+      const uint32_t idesc_full = tf32 ? make_idesc(2, Rp) : make_idesc(1, 2 * Rp);
+      const uint32_t idesc_hi = make_idesc(1, Rp);
+      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
+        const Unit w = get_unit(p, u);
+        const int bsel = (int)(li & 1);
+        if (!mbar_wait(acc_empty(bsel), (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + bsel * acc_cols;
+        for (int s = 0; s < w.nk; ++s) {
+          const uint32_t afull = p.direct ? raw_full(sa) : conv_full(sa);
+          const uint32_t aempty = p.direct ? raw_empty(sa) : conv_empty(sa);
+          if (!mbar_wait(afull, pha, abort_flag, p.err) ||
+              !mbar_wait(b_full(sb), phb, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = p.direct ? raw0 + sa * kRawBytes : conv0 + sa * kConvBytes;
+          const uint32_t b = b0 + sb * kBBytes;
+          if (tf32) {
+            // two fp32 sub-tiles of 32 contraction elements, K = 8 per MMA
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint32_t t = kk >> 2, o = (kk & 3) * 32;
+              mma_tf32(d, sw128_desc(a + t * 16384 + o), sw128_desc(b + t * Rp * 128 + o),
+                       idesc_full, (s > 0 || kk > 0) ? 1u : 0u);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = kk * 32;
+              mma_f16(d, sw128_desc(a + o), sw128_desc(b + o), idesc_full,
+                      (s > 0 || kk > 0) ? 1u : 0u);
+              if (split) mma_f16(d, sw128_desc(a + 16384 + o), sw128_desc(b + o), idesc_hi, 1u);
+            }
+          }
+          mma_commit(aempty);
+          mma_commit(b_empty(sb));
+          if (++sa == nA) { sa = 0; pha ^= 1u; }
+          if (++sb == kSB) { sb = 0; phb ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(acc_full(bsel));
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(drain_bar);
+      const long long t0 = clock64();
+      while (!mbar_test(drain_bar, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else if (warp < kWarpConv) {
+    // ---------------------------------------------- Khatri-Rao B builder --
+    const int bt = threadIdx.x - kWarpB * 32;  // 0..63
+    const int bw = bt >> 5;                    // builder warp 0/1
+    const KrpDesc& kd = p.krp;
+    int sb = 0;
+    uint32_t ph = 0;
+    const bool tf32 = p.mode == NNCP_TF32;
+    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+      const Unit w = get_unit(p, u);
+      bool ok = true;
+      for (int s = 0; s < w.nk; ++s) {
+        if (!mbar_wait(b_empty(sb), ph ^ 1u, abort_flag, p.err)) { ok = false; }
+        // named barrier keeps the two builder warps in step even on abort
+        int* o = offs + (sb * kKC + bt) * (kMaxModes + 1);
+        if (ok) {
+          long long k = w.kbeg + (long long)s * kKC + bt;
+          o[kMaxModes] = k < w.kend;
+          long long rem = k;
+          for (int m = 0; m < kd.nm; ++m) {
+            const long long dm = kd.dim[m];
+            o[m] = (int)((rem % dm) * R);
+            rem /= dm;
+          }
+        }
+        ok = !bar_red_or(1, 64, !ok || *abort_flag);
+        if (!ok) break;
+        const uint32_t bt_base = b0 + sb * kBBytes;
+        // warp bw handles contraction elements [32 bw, 32 bw + 32) in groups of 8;
+        // lane handles rank rows lane and lane + 32
+        for (int g = 0; g < 4; ++g) {
+          const int kk0 = bw * 32 + g * 8;
+          for (int rr = lane; rr < Rp; rr += 32) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int* oe = offs + (sb * kKC + kk0 + e) * (kMaxModes + 1);
+              float x = 0.0f;
+              if (oe[kMaxModes] && rr < R) {
+                x = 1.0f;
+                for (int m = 0; m < kd.nm; ++m) x *= __ldg(kd.H[m] + oe[m] + rr);
+              }
+              v[e] = x;
+            }
+            if (tf32) {
+              // fp32 sub-tile kk0/32, 16-byte chunks (kk0%32)/4 and +1
+              const uint32_t sub = bt_base + (kk0 >> 5) * Rp * 128;
+              const int c0 = (kk0 & 31) >> 2;
+              sts128(sw128_chunk(sub, rr, c0), __float_as_uint(v[0]), __float_as_uint(v[1]),
+                     __float_as_uint(v[2]), __float_as_uint(v[3]));
+              sts128(sw128_chunk(sub, rr, c0 + 1), __float_as_uint(v[4]), __float_as_uint(v[5]),
+                     __float_as_uint(v[6]), __float_as_uint(v[7]));
+            } else {
+              uint32_t hi[4], lo[4];
+              split8(v, hi, lo);
+              const int c = kk0 >> 3;  // 16-byte chunk of 8 bf16
+              sts128(sw128_chunk(bt_base, rr, c), hi[0], hi[1], hi[2], hi[3]);
+              sts128(sw128_chunk(bt_base, Rp + rr, c), lo[0], lo[1], lo[2], lo[3]);
+            }
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(b_full(sb));
+        if (++sb == kSB) { sb = 0; ph ^= 1u; }
+      }
+      if (!ok) break;
+    }
+  } else if (warp < kWarpEpi) {
+    // ------------------------------------------------------- converters --
+    if (!p.direct) {
+      const int m = threadIdx.x - kWarpConv * 32;  // output row within the tile, 0..127
+      int sf = 0, sc = 0;
+      uint32_t phf = 0, phc = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const Unit w = get_unit(p, u);
+        for (int s = 0; s < w.nk; ++s) {
+          bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err) &&
+                     mbar_wait(conv_empty(sc), phc ^ 1u, abort_flag, p.err);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          const uint32_t src = raw0 + sf * kRawBytes;
+          const uint32_t dst = conv0 + sc * kConvBytes;
+          if (p.mode == NNCP_SPLIT_BF16X3) {
+#pragma unroll 2
+            for (int g = 0; g < 8; ++g) {  // 8 contraction elements per 16-byte bf16 chunk
+              float x[8];
+              if (p.contract_fast) {
+                // K-major fp32 source: sub-tile g/4, chunks 2g%8 and 2g%8+1
+                const uint32_t sub = src + (g >> 2) * 16384;
+                const float4 a = lds128(sw128_chunk(sub, m, (2 * g) & 7));
+                const float4 b = lds128(sw128_chunk(sub, m, ((2 * g) & 7) + 1));
+                x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+                x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+              } else {
+                // MN-major fp32 source: row j holds 128 consecutive i (512 B)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = lds32(src + (8 * g + e) * 512 + m * 4);
+              }
+              uint32_t hi[4], lo[4];
+              split8(x, hi, lo);
+              sts128(sw128_chunk(dst, m, g), hi[0], hi[1], hi[2], hi[3]);
+              sts128(sw128_chunk(dst + 16384, m, g), lo[0], lo[1], lo[2], lo[3]);
+            }
+          } else if (p.mode == NNCP_TF32) {
+            // MN-major fp32 -> K-major fp32 (two sub-tiles of 32)
+#pragma unroll 4
+            for (int c = 0; c < 16; ++c) {
+              const int k = 4 * c;
+              float x0 = lds32(src + (k + 0) * 512 + m * 4);
+              float x1 = lds32(src + (k + 1) * 512 + m * 4);
+              float x2 = lds32(src + (k + 2) * 512 + m * 4);
+              float x3 = lds32(src + (k + 3) * 512 + m * 4);
+              sts128(sw128_chunk(dst + (c >> 3) * 16384, m, c & 7), __float_as_uint(x0),
+                     __float_as_uint(x1), __float_as_uint(x2), __float_as_uint(x3));
+            }
+          } else {
+            // MN-major bf16 -> K-major bf16
+#pragma unroll 2
+            for (int g = 0; g < 8; ++g) {
+              uint32_t w4[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const uint32_t lo16 = lds16(src + (8 * g + 2 * e) * 256 + m * 2);
+                const uint32_t hi16 = lds16(src + (8 * g + 2 * e + 1) * 256 + m * 2);
+                w4[e] = lo16 | (hi16 << 16);
+              }
+              sts128(sw128_chunk(dst, m, g), w4[0], w4[1], w4[2], w4[3]);
+            }
+          }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(conv_full(sc));
+            mbar_arrive(raw_empty(sf));
+          }
+          if (++sf == kSF) { sf = 0; phf ^= 1u; }
+          if (++sc == kSC) { sc = 0; phc ^= 1u; }
+        }
+      }
+    }
+  } else {
+    // --------------------------------------------------------- epilogue --
+    const int q = warp & 3;  // TMEM lane quarter
+    const bool two = p.mode != NNCP_TF32;
+    long long li = 0;
+    for (long long u = blockIdx.x; u < n_units; u += gridDim.x, ++li) {
+      const Unit w = get_unit(p, u);
+      const int bsel = (int)(li & 1);
+      const bool got = mbar_wait(acc_full(bsel), (uint32_t)((li >> 1) & 1), abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      const long long row = w.mt * 128 + q * 32 + lane;
+      const long long kc = w.kbeg / p.kper;
+      float* dst = p.out + (p.nsplit > 1 ? kc * p.M * R : 0) + row * R;
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + bsel * acc_cols;
+      for (int c = 0; c < Rp; c += 16) {
+        float v[16], v2[16];
+        tmem_ld16(tbase + c, v);
+        if (two) tmem_ld16(tbase + Rp + c, v2);
+        tmem_ld_wait();
+        if (two) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += v2[i];
+        }
+        if (row < p.M) {
+          if ((R & 3) == 0 && c + 16 <= R) {
+            float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          } else {
+            for (int i = 0; i < 16; ++i)
+              if (c + i < R) dst[c + i] = v[i];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(bsel));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kWarpMMA) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------------------- host --
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool load_encode() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+struct Plan {
+  long long M, K, n_mt, nsplit, kper, n_units;
+  int Rp;
+};
+
+Plan plan_for(int contract_fast, int64_t IL, int64_t IR, int R, int num_sms) {
+  Plan pl;
+  pl.M = contract_fast ? IR : IL;
+  pl.K = contract_fast ? IL : IR;
+  pl.Rp = ((R + 15) / 16) * 16;
+  pl.n_mt = (pl.M + 127) / 128;
+  const long long kchunks = (pl.K + kKC - 1) / kKC;
+  long long ns = 1;
+  if (pl.n_mt < num_sms) ns = std::max(1LL, std::min(kchunks, (long long)num_sms / pl.n_mt));
+  pl.kper = ((kchunks + ns - 1) / ns) * kKC;
+  pl.nsplit = (pl.K + pl.kper - 1) / pl.kper;
+  pl.n_units = pl.n_mt * pl.nsplit;
+  return pl;
+}
+
+int64_t prod_range(const int64_t* d, int a, int b) {
+  int64_t p = 1;
+  for (int m = a; m <= b; ++m) p *= d[m];
+  return p;
+}
+
+}  // namespace
+
+bool tc_available() { return true; }
+
+const char* tc_unsupported_reason(int precision, int N, const int64_t* dims, int R, int split) {
+  if (precision != NNCP_TF32 && precision != NNCP_SPLIT_BF16X3 && precision != NNCP_BF16_STORED)
+    return "not a tensor-core precision";
+  if (R > kMaxRp) return "tensor-core partial MTTKRP supports R <= 64";
+  const int64_t IL = prod_range(dims, 0, split - 1);
+  const int64_t esz = precision == NNCP_BF16_STORED ? 2 : 4;
+  if ((IL * esz) % 16 != 0)
+    return "tensor-core partial MTTKRP needs I_1*...*I_s * element size to be a multiple of 16 bytes";
+  const int64_t IR = prod_range(dims, split, N - 1);
+  if (IL >= (1LL << 31) || IR >= (1LL << 31)) return "matricization too large for TMA coordinates";
+  return nullptr;
+}
+
+size_t tc_scratch_bytes(int N, const int64_t* dims, int R, int split, int precision, int num_sms) {
+  if (precision == NNCP_FP32_SIMT) return 0;
+  const int64_t IL = prod_range(dims, 0, split - 1), IR = prod_range(dims, split, N - 1);
+  size_t need = 0;
+  for (int cf = 0; cf < 2; ++cf) {
+    Plan pl = plan_for(cf, IL, IR, R, num_sms);
+    if (pl.nsplit > 1) need = std::max<size_t>(need, (size_t)pl.nsplit * pl.M * R * sizeof(float));
+  }
+  return 256 + need;
+}
+
+int* tc_error_word(const TcScratch& s) { return static_cast<int*>(s.base); }
+
+cudaError_t tc_attributes_init() {
+  return cudaFuncSetAttribute(k_tc_partial_mttkrp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSmemBytes);
+}
+
+cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, int64_t IL,
+                              int64_t IR, const KrpDesc& K, int R, float* out,
+                              const TcScratch& scratch, int num_sms, cudaStream_t st) {
+  if (!load_encode()) return cudaErrorNotSupported;
+  if (R > kMaxRp || !scratch.base) return cudaErrorInvalidValue;
+  const bool bf16x = precision == NNCP_BF16_STORED;
+  const int esz = bf16x ? 2 : 4;
+  if ((IL * esz) % 16 != 0) return cudaErrorInvalidValue;
+  Plan pl = plan_for(contract_fast, IL, IR, R, num_sms);
+
+  CUtensorMap map;
+  memset(&map, 0, sizeof map);
+  cuuint64_t gdim[2] = {(cuuint64_t)IL, (cuuint64_t)IR};
+  cuuint64_t gstride[1] = {(cuuint64_t)IL * esz};
+  cuuint32_t box[2];
+  CUtensorMapSwizzle swz;
+  if (contract_fast) {
+    box[0] = bf16x ? 64 : 32;  // 128 bytes of contraction elements
+    box[1] = 128;              // output rows
+    swz = CU_TENSOR_MAP_SWIZZLE_128B;
+  } else {
+    box[0] = 128;              // output rows (contiguous)
+    box[1] = kKC;              // contraction elements
+    swz = CU_TENSOR_MAP_SWIZZLE_NONE;
+  }
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = g_encode(&map, bf16x ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        2, const_cast<void*>(X), gdim, gstride, box, estride,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+  TcParams p;
+  memset(&p, 0, sizeof p);
+  p.mode = precision;
+  p.contract_fast = contract_fast;
+  p.bf16x = bf16x;
+  p.direct = contract_fast && precision != NNCP_SPLIT_BF16X3;
+  p.M = pl.M;
+  p.K = pl.K;
+  p.R = R;
+  p.Rp = pl.Rp;
+  p.n_mt = pl.n_mt;
+  p.nsplit = pl.nsplit;
+  p.kper = pl.kper;
+  p.n_units = pl.n_units;
+  p.krp = K;
+  p.err = tc_error_word(scratch);
+  float* partials = reinterpret_cast<float*>(static_cast<char*>(scratch.base) + 256);
+  p.out = pl.nsplit > 1 ? partials : out;
+  if (pl.nsplit > 1 && 256 + (size_t)pl.nsplit * pl.M * R * sizeof(float) > scratch.bytes)
+    return cudaErrorInvalidValue;
+
+  const int grid = (int)std::min<long long>(pl.n_units, num_sms);
+  k_tc_partial_mttkrp<<<grid, kThreads, kSmemBytes, st>>>(map, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || pl.nsplit == 1) return e;
+  return launch_reduce_chunks(partials, pl.M * R, (int)pl.nsplit, out, num_sms, st);
+}
 
 }  // namespace nncp

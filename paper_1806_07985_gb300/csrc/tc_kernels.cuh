@@ -22,6 +22,9 @@ bool tc_available();
 // tensor cores; otherwise a reason.
 const char* tc_unsupported_reason(int precision, int N, const int64_t* dims, int R, int split);
 
+// Device word the tensor-core kernels set to 1 when a bounded wait expired.
+int* tc_error_word(const TcScratch& s);
+
 size_t tc_scratch_bytes(int N, const int64_t* dims, int R, int split, int precision, int num_sms);
 
 // Root partial MTTKRP on tensor cores.  X viewed as the column-major
