@@ -51,6 +51,7 @@ struct nncp_ctx {
   // workspace views
   float* node[2][kMaxModes] = {};  // [half][depth] node temporaries (>= 2 modes)
   float* Mbuf = nullptr;
+  float* upd_part = nullptr;  // multi-CTA update partials
   float* partials = nullptr;
   size_t part_cap = 0;
   double* red_part = nullptr;
@@ -110,7 +111,7 @@ KrpDesc krp(const nncp_ctx* c, int first, int last) {
 struct Plan {
   size_t node_off[2][kMaxModes];
   size_t node_bytes[2][kMaxModes];
-  size_t M_off, part_off, part_cap, gram_off, G_off, S_off, S32_off, lam_off, scal_off,
+  size_t M_off, upd_off, part_off, part_cap, gram_off, G_off, S_off, S32_off, lam_off, scal_off,
       fits_off, flags_off, red_off;
   int red_nparts;
   size_t tc_off, tc_bytes;
@@ -140,6 +141,10 @@ Plan make_plan(const nncp_ctx* c) {
   int64_t maxIn = 0;
   for (int n = 0; n < N; ++n) maxIn = std::max(maxIn, c->dims[n]);
   p.M_off = take((size_t)maxIn * R * sizeof(float));
+  size_t upd = 4;
+  for (int n = 0; n < N; ++n)
+    if (multi_update_ok(c->dims[n], R)) upd = std::max(upd, multi_update_scratch(c->dims[n], R));
+  p.upd_off = take(upd * sizeof(float));
 
   // split-K partial capacity: max over every MTTKRP this context may launch
   size_t cap = 0;
@@ -188,6 +193,7 @@ void bind_workspace(nncp_ctx* c) {
     for (int d = 0; d < kMaxModes; ++d)
       c->node[h][d] = p.node_bytes[h][d] ? reinterpret_cast<float*>(w + p.node_off[h][d]) : nullptr;
   c->Mbuf = reinterpret_cast<float*>(w + p.M_off);
+  c->upd_part = reinterpret_cast<float*>(w + p.upd_off);
   c->partials = reinterpret_cast<float*>(w + p.part_off);
   c->part_cap = p.part_cap;
   c->st.gram_part = reinterpret_cast<double*>(w + p.gram_off);
@@ -238,6 +244,9 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st) {
 }
 
 cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
+  if (multi_update_ok(c->dims[n], c->R))
+    return launch_update_multi(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                               n == c->N - 1, c->st, c->upd_part, st);
   cudaError_t e = launch_hals_gram(c->H[n], c->Mbuf, c->dims[n], c->R, c->st, st);
   if (e != cudaSuccess) return e;
   return launch_finalize(c->H[n], c->dims[n], c->R, c->N, n, (n + 1) % c->N,

@@ -29,7 +29,7 @@ struct SolveState {
   double* gram_part;  // blocks x (R*R + 1): per-block W^T W and <M, W>
   double* scalars;  // [0] alpha = ||X||^2, [1] beta, [2] gamma, [3] eps, [4] tol
   double* fits;     // kFitCapacity
-  int* flags;       // [0] done, [1] status, [2] iteration count, [3] nonfinite
+  int* flags;       // [0] done, [1] status, [2] iteration count, [3] nonfinite, [8] CTA ticket
 };
 
 // ---- launchers (return cudaSuccess or the launch error) ----------------------
@@ -85,6 +85,15 @@ cudaError_t tc_attributes_init();
 cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveState st,
                              cudaStream_t stream);
 int hals_gram_blocks(int64_t In);
+
+// Whole mode update (HALS, Gram, normalisation, fit, next S) in one launch over
+// CTAs of 32 rows, used when multi_update_ok(In, R); `part` is device scratch of
+// multi_update_scratch(In, R) floats.
+bool multi_update_ok(int64_t In, int R);
+size_t multi_update_scratch(int64_t In, int R);
+cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
+                                int next_mode, int is_last, SolveState st, float* part,
+                                cudaStream_t stream);
 
 // Gram partials of H as given (initialisation: W = H).
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,

@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "nncp_internal.cuh"
 
 namespace nncp {
@@ -134,20 +136,30 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
   }
 }
 
-// out[e] = sum_{c < C} part[c * E + e], in chunk order (deterministic).
+// out[e] = sum_{c < C} part[c * E + e] (deterministic: four interleaved partial
+// sums over c = 0, 4, 8, ... / 1, 5, 9, ... combined in a fixed order).
 __global__ void k_reduce_chunks(const float* __restrict__ part, long long E, int C,
                                 float* __restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E;
        e += (long long)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int c = 0; c < C; ++c) s += part[(long long)c * E + e];
-    out[e] = s;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    int c = 0;
+    for (; c + 4 <= C; c += 4) {
+      s0 += __ldg(part + (long long)c * E + e);
+      s1 += __ldg(part + (long long)(c + 1) * E + e);
+      s2 += __ldg(part + (long long)(c + 2) * E + e);
+      s3 += __ldg(part + (long long)(c + 3) * E + e);
+    }
+    for (; c < C; ++c) s0 += __ldg(part + (long long)c * E + e);
+    out[e] = (s0 + s1) + (s2 + s3);
   }
 }
 
 // Multi-TTV leaf: out(i, r) = sum_k T[(i + I*k)*R + r] * KK(k, r).
-// Threads cover consecutive flattened (i, r) positions, so every k step reads
-// one contiguous run of the node temporary.
+// Threads cover consecutive flattened (i, r) positions (V per thread, V = 4
+// when R % 4 == 0), so every k step reads one contiguous run of the node
+// temporary; the k loop is unrolled to keep several loads in flight.
+template <int V>
 __global__ void __launch_bounds__(kThreads)
 k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, int R,
             long long kchunk, float* __restrict__ out, long long out_chunk_stride) {
@@ -155,11 +167,13 @@ k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, i
   float* Ws = smem;  // kBK x R
   __shared__ int offs[kBK][kMaxModes];
   const long long E = I * R;
-  const long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long e = ((long long)blockIdx.x * kThreads + threadIdx.x) * V;
   const int r = (int)(e % R);
   const long long kbeg = (long long)blockIdx.y * kchunk;
   const long long kend = min(K, kbeg + kchunk);
-  float acc = 0.0f;
+  float acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0.0f;
   for (long long k0 = kbeg; k0 < kend; k0 += kBK) {
     if (threadIdx.x < kBK) {
       long long k = k0 + threadIdx.x;
@@ -172,34 +186,71 @@ k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, i
     }
     __syncthreads();
     if (e < E) {
-      int kn = (int)min((long long)kBK, kend - k0);
+      const int kn = (int)min((long long)kBK, kend - k0);
       const float* Tp = T + (I * k0) * R + e;
-      for (int kk = 0; kk < kn; ++kk) acc = fmaf(__ldg(Tp + I * R * kk), Ws[kk * R + r], acc);
+      if (V == 4) {
+#pragma unroll 4
+        for (int kk = 0; kk < kn; ++kk) {
+          const float4 tv = __ldg(reinterpret_cast<const float4*>(Tp + I * R * kk));
+          const float4 wv = *reinterpret_cast<const float4*>(Ws + kk * R + r);
+          acc[0] = fmaf(tv.x, wv.x, acc[0]);
+          acc[V > 1 ? 1 : 0] = fmaf(tv.y, wv.y, acc[V > 1 ? 1 : 0]);
+          acc[V > 2 ? 2 : 0] = fmaf(tv.z, wv.z, acc[V > 2 ? 2 : 0]);
+          acc[V > 3 ? 3 : 0] = fmaf(tv.w, wv.w, acc[V > 3 ? 3 : 0]);
+        }
+      } else {
+#pragma unroll 4
+        for (int kk = 0; kk < kn; ++kk) acc[0] = fmaf(__ldg(Tp + I * R * kk), Ws[kk * R + r], acc[0]);
+      }
     }
     __syncthreads();
   }
-  if (e < E) out[(long long)blockIdx.y * out_chunk_stride + e] = acc;
+  if (e < E) {
+    float* o = out + (long long)blockIdx.y * out_chunk_stride + e;
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = acc[v];
+  }
 }
 
 // Multi-TTV to the child node: out(j, r) = sum_i T[(i + I*j)*R + r] * H(i, r).
-// One CTA per j; thread (g, r) strides over i; a fixed-order reduction over g.
+// One CTA per j; thread (g, r-group) strides over i (V = 4 consecutive ranks
+// per thread when R % 4 == 0); a fixed-order reduction over g.
+template <int V>
 __global__ void k_mttv_first(const float* __restrict__ T, long long I, const float* __restrict__ H,
                              int R, int G, float* __restrict__ out) {
   extern __shared__ float red[];  // G x R
   const long long j = blockIdx.x;
-  const int r = threadIdx.x % R;
-  const int g = threadIdx.x / R;
-  float acc = 0.0f;
+  const int RV = R / V;
+  const int rv = threadIdx.x % RV;
+  const int g = threadIdx.x / RV;
   if (g < G) {
     const float* Tj = T + I * j * R;
-    for (long long i = g; i < I; i += G) acc = fmaf(__ldg(Tj + i * R + r), __ldg(H + i * R + r), acc);
-    red[g * R + r] = acc;
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+    if (V == 4) {
+#pragma unroll 4
+      for (long long i = g; i < I; i += G) {
+        const float4 tv = __ldg(reinterpret_cast<const float4*>(Tj + i * R) + rv);
+        const float4 hv = __ldg(reinterpret_cast<const float4*>(H + i * R) + rv);
+        acc[0] = fmaf(tv.x, hv.x, acc[0]);
+        acc[V > 1 ? 1 : 0] = fmaf(tv.y, hv.y, acc[V > 1 ? 1 : 0]);
+        acc[V > 2 ? 2 : 0] = fmaf(tv.z, hv.z, acc[V > 2 ? 2 : 0]);
+        acc[V > 3 ? 3 : 0] = fmaf(tv.w, hv.w, acc[V > 3 ? 3 : 0]);
+      }
+    } else {
+#pragma unroll 4
+      for (long long i = g; i < I; i += G)
+        acc[0] = fmaf(__ldg(Tj + i * R + rv), __ldg(H + i * R + rv), acc[0]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) red[g * R + rv * V + v] = acc[v];
   }
   __syncthreads();
-  if (g == 0) {
-    float s = 0.0f;
-    for (int gg = 0; gg < G; ++gg) s += red[gg * R + r];
-    out[j * R + r] = s;
+  for (int t = threadIdx.x; t < R; t += blockDim.x) {
+    float sum = 0.0f;
+    for (int gg = 0; gg < G; ++gg) sum += red[gg * R + t];
+    out[j * R + t] = sum;
   }
 }
 
@@ -263,15 +314,19 @@ __global__ void k_to_bf16(const float* __restrict__ X, __nv_bfloat16* __restrict
 
 long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
-// Split of the contraction across CTAs: enough CTAs for ~4 per SM, chunks of
-// whole tiles, at least 8 tiles per chunk.
-int choose_chunks(long long ctas_other, long long Ktot, int num_sms) {
+// Split of the contraction across CTAs: enough CTAs for ~4 per SM, each
+// chunk at least `min_chunk` contraction elements.
+int choose_chunks(long long ctas_other, long long Ktot, int num_sms, long long min_chunk = 8LL * kBK) {
   long long target = 4LL * num_sms;
   if (ctas_other >= target) return 1;
   long long C = ceil_div(target, ctas_other);
-  long long max_c = max(1LL, ceil_div(Ktot, 8LL * kBK));
+  long long max_c = max(1LL, ceil_div(Ktot, min_chunk));
   return (int)min(C, max_c);
 }
+
+// Multi-TTV chunks: one contraction element is a whole I*R block of the node,
+// so chunks of 8 elements already stream enough bytes.
+constexpr long long kMttvMinChunk = 8;
 
 }  // namespace
 
@@ -351,18 +406,20 @@ cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out
 }
 
 size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
-  long long gx = ceil_div((long long)I * R, kThreads);
-  int C = choose_chunks(gx, K, num_sms);
+  const int V = (R % 4 == 0) ? 4 : 1;
+  long long gx = ceil_div(ceil_div((long long)I * R, V), kThreads);
+  int C = choose_chunks(gx, K, num_sms, kMttvMinChunk);
   return C > 1 ? (size_t)C * I * R : 0;
 }
 
 cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc& KK, int R,
                              float* out, float* partials, size_t part_cap, int num_sms,
                              cudaStream_t st) {
+  const int V = (R % 4 == 0) ? 4 : 1;
   long long E = (long long)I * R;
-  long long gx = ceil_div(E, kThreads);
-  int C = choose_chunks(gx, K, num_sms);
-  long long kchunk = ceil_div(ceil_div(K, C), kBK) * kBK;
+  long long gx = ceil_div(ceil_div(E, V), kThreads);
+  int C = choose_chunks(gx, K, num_sms, kMttvMinChunk);
+  long long kchunk = ceil_div(K, C);
   C = (int)ceil_div(K, kchunk);
   float* dst = out;
   if (C > 1) {
@@ -370,21 +427,29 @@ cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc
     dst = partials;
   }
   size_t smem = (size_t)kBK * R * sizeof(float);
-  k_mttv_leaf<<<dim3((unsigned)gx, (unsigned)C), kThreads, smem, st>>>(T, I, K, KK, R, kchunk,
-                                                                      dst, E);
+  if (V == 4)
+    k_mttv_leaf<4><<<dim3((unsigned)gx, (unsigned)C), kThreads, smem, st>>>(T, I, K, KK, R, kchunk,
+                                                                           dst, E);
+  else
+    k_mttv_leaf<1><<<dim3((unsigned)gx, (unsigned)C), kThreads, smem, st>>>(T, I, K, KK, R, kchunk,
+                                                                           dst, E);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || C == 1) return e;
-  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
-  k_reduce_chunks<<<blocks, 256, 0, st>>>(partials, E, C, out);
-  return cudaGetLastError();
+  return launch_reduce_chunks(partials, E, C, out, num_sms, st);
 }
 
 cudaError_t launch_mttv_first(const float* T, int64_t I, int64_t J, const float* H, int R,
                               float* out, cudaStream_t st) {
-  int G = max(1, 256 / R);
-  int threads = G * R;
+  const int V = (R % 4 == 0) ? 4 : 1;
+  const int RV = R / V;
+  int G = std::max(1, 256 / RV);
+  if (G > I) G = (int)I;
+  const int threads = G * RV;
   size_t smem = (size_t)G * R * sizeof(float);
-  k_mttv_first<<<(unsigned)J, threads, smem, st>>>(T, I, H, R, G, out);
+  if (V == 4)
+    k_mttv_first<4><<<(unsigned)J, threads, smem, st>>>(T, I, H, R, G, out);
+  else
+    k_mttv_first<1><<<(unsigned)J, threads, smem, st>>>(T, I, H, R, G, out);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,10 @@
 // A (128 output rows x 64 contraction elements per stage) is always handed to
 // the MMA K-major with the 128-byte swizzle.  contract_fast tiles arrive
 // K-major from TMA; contract_slow tiles arrive MN-major (no swizzle) and the
-// converter warps transpose them.  Precision modes:
+// converter warps transpose them.  Conversion is done in place: the converted
+// tile (bf16 hi + lo, or a transposed copy) has the size of its source, so each
+// converter thread reads its share into registers, a named barrier separates
+// the reads from the writes, and the result overwrites the TMA stage.  Precision modes:
 //   TF32         kind::tf32 on the float32 tensor (direct when K-major);
 //   SPLIT_BF16X3 x = hi + lo in bf16, K = Khi + Klo: D = hi*[Khi|Klo] + lo*Khi
 //                (three products, float32 accumulation in TMEM);
@@ -18,8 +21,12 @@
 //
 // Warp roles (12 warps, one CTA per SM, persistent over work units):
 //   warp 0      TMA producer          warp 1      TMEM owner + MMA issuer
-//   warps 2-3   Khatri-Rao B builder  warps 4-7   converters (hi/lo split, transposes)
-//   warps 8-11  epilogue (tcgen05.ld TMEM -> registers -> global)
+//   warps 2-7   Khatri-Rao B builders, two per B stage slot (each half of the
+//               stage's 64 contraction elements), so three stages are formed
+//               concurrently (their factor-row loads are L2 latency)
+//   warps 8-15  converters (hi/lo split, transposes); warps 8-11 also run the epilogue
+//               (tcgen05.ld TMEM -> registers -> global); a unit's epilogue runs
+//               after the next unit's conversions, TMEM being double-buffered.
 // A work unit is one 128-row output tile over one contraction range; when the
 // output has fewer tiles than SMs the contraction is split and the per-range
 // partials are summed afterwards in a fixed order.
@@ -44,28 +51,25 @@ namespace nncp {
 namespace {
 
 constexpr int kKC = 64;  // contraction elements per stage
-constexpr int kSF = 3;   // raw (TMA) stages
-constexpr int kSC = 2;   // converted A stages
-constexpr int kSB = 3;   // B (Khatri-Rao) stages
-constexpr int kThreads = 384;
-constexpr int kWarpTMA = 0, kWarpMMA = 1, kWarpB = 2, kWarpConv = 4, kWarpEpi = 8;
+constexpr int kMaxSF = 8;  // A (TMA) stages: sized at launch from the shared memory left
+constexpr int kSB = 3;     // B (Khatri-Rao) stages
+constexpr int kThreads = 512;
+constexpr int kWarpTMA = 0, kWarpMMA = 1, kWarpB = 2, kWarpConv = 8;
+constexpr int kConvThreads = 256;  // two converter threads per row (one per contraction half)
 constexpr int kMaxRp = 64;
 constexpr long long kWaitCycles = 4000000000LL;
 
-constexpr int kRawBytes = 32768;
-constexpr int kConvBytes = 32768;
-constexpr int kBBytes = 2 * kMaxRp * 128;  // 16 KB
-constexpr int kOffRaw = 0;
-constexpr int kOffConv = kOffRaw + kSF * kRawBytes;
-constexpr int kOffB = kOffConv + kSC * kConvBytes;
-constexpr int kOffOffs = kOffB + kSB * kBBytes;                 // B builder row offsets
-constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;
-constexpr int kOffBar = kOffOffs + kOffsBytes;
-// barriers: raw full/empty, conv full/empty, B full/empty, acc full/empty x2, drain
-constexpr int kNumBars = 2 * kSF + 2 * kSC + 2 * kSB + 4 + 1;
-constexpr int kOffMisc = kOffBar + kNumBars * 8;
-constexpr int kSmemUse = kOffMisc + 64;
-constexpr int kSmemBytes = kSmemUse + 1024;  // + alignment slack
+constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;  // B builder row offsets
+// barriers: raw full/empty/converted per A stage, B full/empty, acc full/empty x2, drain
+constexpr int kNumBars = 3 * kMaxSF + 2 * kSB + 4 + 1;
+constexpr int kMiscBytes = kNumBars * 8 + 256;
+constexpr int kSmemMax = 232448;  // 227 KB per CTA on sm_103a
+
+// Shared-memory carve-up, decided on the host per launch (all offsets 1024-aligned).
+struct SmemPlan {
+  int raw_bytes, nsf, b_bytes;
+  int off_raw, off_b, off_offs, off_bar, off_misc, total;
+};
 
 struct TcParams {
   int mode;
@@ -75,6 +79,7 @@ struct TcParams {
   long long M, K;
   int R, Rp;
   long long n_mt, nsplit, kper, n_units;
+  SmemPlan sm;
   KrpDesc krp;
   float* out;
   int* err;
@@ -257,19 +262,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// hi = bf16(x), lo = bf16(x - hi) for 8 values, packed
+// hi = bf16(x), lo = bf16(x - hi) for 8 values, packed in pairs (x - hi is
+// exact in float32, so hi + lo carries about 16 significant bits of x)
 __device__ __forceinline__ void split8(const float* x, uint32_t* hi, uint32_t* lo) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]);
-    __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * i + 1]);
-    float r0 = x[2 * i] - __bfloat162float(h0);
-    float r1 = x[2 * i + 1] - __bfloat162float(h1);
-    __nv_bfloat162 hh;
-    hh.x = h0;
-    hh.y = h1;
-    hi[i] = *reinterpret_cast<uint32_t*>(&hh);
-    lo[i] = pack_bf16(r0, r1);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+    hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+    lo[i] = *reinterpret_cast<const uint32_t*>(&l);
   }
 }
 
@@ -300,22 +302,27 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
-  const uint32_t raw0 = sbase + kOffRaw;
-  const uint32_t conv0 = sbase + kOffConv;
-  const uint32_t b0 = sbase + kOffB;
-  int* offs = reinterpret_cast<int*>(gbase + kOffOffs);  // [kSB][kKC][kMaxModes + 1]
-  const uint32_t bar0 = sbase + kOffBar;
+  const int kSF = p.sm.nsf;
+  const int kRawBytes = p.sm.raw_bytes;
+  const int kBBytes = p.sm.b_bytes;
+  const uint32_t raw0 = sbase + p.sm.off_raw;
+  const uint32_t b0 = sbase + p.sm.off_b;
+  int* offs = reinterpret_cast<int*>(gbase + p.sm.off_offs);  // [kSB][kKC][kMaxModes + 1]
+  const uint32_t bar0 = sbase + p.sm.off_bar;
   auto raw_full = [&](int i) { return bar0 + 8u * i; };
-  auto raw_empty = [&](int i) { return bar0 + 8u * (kSF + i); };
-  auto conv_full = [&](int i) { return bar0 + 8u * (2 * kSF + i); };
-  auto conv_empty = [&](int i) { return bar0 + 8u * (2 * kSF + kSC + i); };
-  auto b_full = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + i); };
-  auto b_empty = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + kSB + i); };
-  auto acc_full = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + 2 * kSB + i); };
-  auto acc_empty = [&](int i) { return bar0 + 8u * (2 * kSF + 2 * kSC + 2 * kSB + 2 + i); };
+  auto raw_empty = [&](int i) { return bar0 + 8u * (kMaxSF + i); };
+  auto conv_full = [&](int i) { return bar0 + 8u * (2 * kMaxSF + i); };
+  auto b_full = [&](int i) { return bar0 + 8u * (3 * kMaxSF + i); };
+  auto b_empty = [&](int i) { return bar0 + 8u * (3 * kMaxSF + kSB + i); };
+  auto acc_full = [&](int i) { return bar0 + 8u * (3 * kMaxSF + 2 * kSB + i); };
+  auto acc_empty = [&](int i) { return bar0 + 8u * (3 * kMaxSF + 2 * kSB + 2 + i); };
   const uint32_t drain_bar = bar0 + 8u * (kNumBars - 1);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + kOffMisc);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + kOffMisc + 8);
+  uint8_t* misc = gbase + p.sm.off_bar + kNumBars * 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 8);
+  // Khatri-Rao factor descriptors, copied to shared memory for the builders
+  const float** kH = reinterpret_cast<const float**>(misc + 64);   // [kMaxModes]
+  uint32_t* kdim = reinterpret_cast<uint32_t*>(misc + 128);        // [kMaxModes]
 
   const int Rp = p.Rp;
   const uint32_t acc_cols = 2u * Rp;  // per accumulator buffer
@@ -325,11 +332,8 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   if (threadIdx.x == 0) {
     for (int i = 0; i < kSF; ++i) {
       mbar_init(raw_full(i), 1);
-      mbar_init(raw_empty(i), p.direct ? 1 : 4);
-    }
-    for (int i = 0; i < kSC; ++i) {
-      mbar_init(conv_full(i), 4);
-      mbar_init(conv_empty(i), 1);
+      mbar_init(raw_empty(i), 1);
+      mbar_init(conv_full(i), kConvThreads / 32);
     }
     for (int i = 0; i < kSB; ++i) {
       mbar_init(b_full(i), 2);
@@ -341,6 +345,10 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
+    for (int m = 0; m < kMaxModes; ++m) {
+      kH[m] = m < p.krp.nm ? p.krp.H[m] : nullptr;
+      kdim[m] = m < p.krp.nm ? (uint32_t)p.krp.dim[m] : 1u;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kWarpMMA) {
@@ -364,7 +372,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
       int sf = 0;
       uint32_t ph = 0;
-      int issued[kSF] = {0, 0, 0};
+      int issued[kMaxSF] = {0, 0, 0, 0, 0, 0, 0, 0};
       const uint32_t tx = p.bf16x ? 16384u : 32768u;
       bool ok = true;
       for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
@@ -403,7 +411,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     if (lane == 0) {
       int sa = 0, sb = 0;
       uint32_t pha = 0, phb = 0;
-      const int nA = p.direct ? kSF : kSC;
+      const int nA = kSF;
       bool ok = true;
       long long li = 0;
       const bool split = p.mode == NNCP_SPLIT_BF16X3;
@@ -418,14 +426,14 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         const uint32_t d = tmem_base + bsel * acc_cols;
         for (int s = 0; s < w.nk; ++s) {
           const uint32_t afull = p.direct ? raw_full(sa) : conv_full(sa);
-          const uint32_t aempty = p.direct ? raw_empty(sa) : conv_empty(sa);
+          const uint32_t aempty = raw_empty(sa);
           if (!mbar_wait(afull, pha, abort_flag, p.err) ||
               !mbar_wait(b_full(sb), phb, abort_flag, p.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a = p.direct ? raw0 + sa * kRawBytes : conv0 + sa * kConvBytes;
+          const uint32_t a = raw0 + sa * kRawBytes;
           const uint32_t b = b0 + sb * kBBytes;
           if (tf32) {
             // two fp32 sub-tiles of 32 contraction elements, K = 8 per MMA
@@ -459,61 +467,76 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       }
     }
   } else if (warp < kWarpConv) {
-    // ---------------------------------------------- Khatri-Rao B builder --
-    const int bt = threadIdx.x - kWarpB * 32;  // 0..63
-    const int bw = bt >> 5;                    // builder warp 0/1
-    const KrpDesc& kd = p.krp;
-    int sb = 0;
-    uint32_t ph = 0;
+    // ---------------------------------------------- Khatri-Rao B builders --
+    // Builder warps 2w and 2w+1 form, for every stage t with t % kSB == w,
+    // contraction elements [32 h, 32 h + 32) of B slot w (h = warp parity).
+    const int bw = (warp - kWarpB) >> 1;
+    const int half = (warp - kWarpB) & 1;
+    const int nm = p.krp.nm;
     const bool tf32 = p.mode == NNCP_TF32;
-    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+    int* so = offs + bw * kKC * (kMaxModes + 1);  // this slot's offsets [kKC][kMaxModes + 1]
+    const uint32_t bt_base = b0 + bw * kBBytes;
+    long long t = 0;  // stage counter over this CTA's units
+    bool ok = true;
+    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const Unit w = get_unit(p, u);
-      bool ok = true;
-      for (int s = 0; s < w.nk; ++s) {
-        if (!mbar_wait(b_empty(sb), ph ^ 1u, abort_flag, p.err)) { ok = false; }
-        // named barrier keeps the two builder warps in step even on abort
-        int* o = offs + (sb * kKC + bt) * (kMaxModes + 1);
-        if (ok) {
-          long long k = w.kbeg + (long long)s * kKC + bt;
-          o[kMaxModes] = k < w.kend;
-          long long rem = k;
-          for (int m = 0; m < kd.nm; ++m) {
-            const long long dm = kd.dim[m];
-            o[m] = (int)((rem % dm) * R);
-            rem /= dm;
+      for (int s = 0; s < w.nk; ++s, ++t) {
+        if ((int)(t % kSB) != bw) continue;
+        const uint32_t use = (uint32_t)(t / kSB);
+        const bool got = mbar_wait(b_empty(bw), (use & 1u) ^ 1u, abort_flag, p.err);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        {
+          // row offsets of the contraction element this lane owns
+          const int kk = half * 32 + lane;
+          const long long k = w.kbeg + (long long)s * kKC + kk;
+          int* o = so + kk * (kMaxModes + 1);
+          const int valid = k < w.kend;
+          o[kMaxModes] = valid;
+          uint32_t rem = valid ? (uint32_t)k : 0u;
+#pragma unroll
+          for (int m = 0; m < kMaxModes; ++m) {
+            if (m < nm) {
+              const uint32_t dm = kdim[m];
+              o[m] = (int)((rem % dm) * (uint32_t)R);
+              rem /= dm;
+            }
           }
         }
-        ok = !bar_red_or(1, 64, !ok || *abort_flag);
-        if (!ok) break;
-        const uint32_t bt_base = b0 + sb * kBBytes;
-        // warp bw handles contraction elements [32 bw, 32 bw + 32) in groups of 8;
-        // lane handles rank rows lane and lane + 32
-        for (int g = 0; g < 4; ++g) {
-          const int kk0 = bw * 32 + g * 8;
-          for (int rr = lane; rr < Rp; rr += 32) {
-            float v[8];
+        __syncwarp();
+        // lane owns rank rows rr = lane (+32); all 32 factor loads of a row are
+        // issued before any is used
+        for (int rr = lane; rr < Rp; rr += 32) {
+          float v[32];
+          const int rs = rr < R ? rr : 0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int* oe = offs + (sb * kKC + kk0 + e) * (kMaxModes + 1);
-              float x = 0.0f;
-              if (oe[kMaxModes] && rr < R) {
-                x = 1.0f;
-                for (int m = 0; m < kd.nm; ++m) x *= __ldg(kd.H[m] + oe[m] + rr);
+          for (int m = 0; m < kMaxModes; ++m) {
+            if (m < nm) {
+              const float* hb = kH[m] + rs;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const float x = __ldg(hb + so[(half * 32 + e) * (kMaxModes + 1) + m]);
+                v[e] = m == 0 ? x : v[e] * x;
               }
-              v[e] = x;
             }
+          }
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (!(so[(half * 32 + e) * (kMaxModes + 1) + kMaxModes] && rr < R)) v[e] = 0.0f;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const float* x8 = v + 8 * g;
+            const int kk0 = half * 32 + 8 * g;
             if (tf32) {
-              // fp32 sub-tile kk0/32, 16-byte chunks (kk0%32)/4 and +1
               const uint32_t sub = bt_base + (kk0 >> 5) * Rp * 128;
               const int c0 = (kk0 & 31) >> 2;
-              sts128(sw128_chunk(sub, rr, c0), __float_as_uint(v[0]), __float_as_uint(v[1]),
-                     __float_as_uint(v[2]), __float_as_uint(v[3]));
-              sts128(sw128_chunk(sub, rr, c0 + 1), __float_as_uint(v[4]), __float_as_uint(v[5]),
-                     __float_as_uint(v[6]), __float_as_uint(v[7]));
+              sts128(sw128_chunk(sub, rr, c0), __float_as_uint(x8[0]), __float_as_uint(x8[1]),
+                     __float_as_uint(x8[2]), __float_as_uint(x8[3]));
+              sts128(sw128_chunk(sub, rr, c0 + 1), __float_as_uint(x8[4]), __float_as_uint(x8[5]),
+                     __float_as_uint(x8[6]), __float_as_uint(x8[7]));
             } else {
               uint32_t hi[4], lo[4];
-              split8(v, hi, lo);
-              const int c = kk0 >> 3;  // 16-byte chunk of 8 bf16
+              split8(x8, hi, lo);
+              const int c = kk0 >> 3;
               sts128(sw128_chunk(bt_base, rr, c), hi[0], hi[1], hi[2], hi[3]);
               sts128(sw128_chunk(bt_base, Rp + rr, c), lo[0], lo[1], lo[2], lo[3]);
             }
@@ -521,97 +544,27 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         }
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) mbar_arrive(b_full(sb));
-        if (++sb == kSB) { sb = 0; ph ^= 1u; }
-      }
-      if (!ok) break;
-    }
-  } else if (warp < kWarpEpi) {
-    // ------------------------------------------------------- converters --
-    if (!p.direct) {
-      const int m = threadIdx.x - kWarpConv * 32;  // output row within the tile, 0..127
-      int sf = 0, sc = 0;
-      uint32_t phf = 0, phc = 0;
-      bool ok = true;
-      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-        const Unit w = get_unit(p, u);
-        for (int s = 0; s < w.nk; ++s) {
-          bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err) &&
-                     mbar_wait(conv_empty(sc), phc ^ 1u, abort_flag, p.err);
-          if (!__all_sync(0xffffffffu, got)) {
-            ok = false;
-            break;
-          }
-          const uint32_t src = raw0 + sf * kRawBytes;
-          const uint32_t dst = conv0 + sc * kConvBytes;
-          if (p.mode == NNCP_SPLIT_BF16X3) {
-#pragma unroll 2
-            for (int g = 0; g < 8; ++g) {  // 8 contraction elements per 16-byte bf16 chunk
-              float x[8];
-              if (p.contract_fast) {
-                // K-major fp32 source: sub-tile g/4, chunks 2g%8 and 2g%8+1
-                const uint32_t sub = src + (g >> 2) * 16384;
-                const float4 a = lds128(sw128_chunk(sub, m, (2 * g) & 7));
-                const float4 b = lds128(sw128_chunk(sub, m, ((2 * g) & 7) + 1));
-                x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-                x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-              } else {
-                // MN-major fp32 source: row j holds 128 consecutive i (512 B)
-#pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = lds32(src + (8 * g + e) * 512 + m * 4);
-              }
-              uint32_t hi[4], lo[4];
-              split8(x, hi, lo);
-              sts128(sw128_chunk(dst, m, g), hi[0], hi[1], hi[2], hi[3]);
-              sts128(sw128_chunk(dst + 16384, m, g), lo[0], lo[1], lo[2], lo[3]);
-            }
-          } else if (p.mode == NNCP_TF32) {
-            // MN-major fp32 -> K-major fp32 (two sub-tiles of 32)
-#pragma unroll 4
-            for (int c = 0; c < 16; ++c) {
-              const int k = 4 * c;
-              float x0 = lds32(src + (k + 0) * 512 + m * 4);
-              float x1 = lds32(src + (k + 1) * 512 + m * 4);
-              float x2 = lds32(src + (k + 2) * 512 + m * 4);
-              float x3 = lds32(src + (k + 3) * 512 + m * 4);
-              sts128(sw128_chunk(dst + (c >> 3) * 16384, m, c & 7), __float_as_uint(x0),
-                     __float_as_uint(x1), __float_as_uint(x2), __float_as_uint(x3));
-            }
-          } else {
-            // MN-major bf16 -> K-major bf16
-#pragma unroll 2
-            for (int g = 0; g < 8; ++g) {
-              uint32_t w4[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const uint32_t lo16 = lds16(src + (8 * g + 2 * e) * 256 + m * 2);
-                const uint32_t hi16 = lds16(src + (8 * g + 2 * e + 1) * 256 + m * 2);
-                w4[e] = lo16 | (hi16 << 16);
-              }
-              sts128(sw128_chunk(dst, m, g), w4[0], w4[1], w4[2], w4[3]);
-            }
-          }
-          fence_proxy_async();
-          __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(conv_full(sc));
-            mbar_arrive(raw_empty(sf));
-          }
-          if (++sf == kSF) { sf = 0; phf ^= 1u; }
-          if (++sc == kSC) { sc = 0; phc ^= 1u; }
-        }
+        if (lane == 0) mbar_arrive(b_full(bw));
       }
     }
   } else {
-    // --------------------------------------------------------- epilogue --
-    const int q = warp & 3;  // TMEM lane quarter
+    // ---------------------------------------- converters + epilogue --
+    const int ct = threadIdx.x - kWarpConv * 32;  // 0..255
+    const int m = ct & 127;                       // converted row within the tile
+    const int kh = ct >> 7;                       // contraction half (elements 32 kh .. 32 kh + 31)
+    const bool epi_warp = kh == 0;                // warps 8-11 also run the epilogue
+    const int q = warp & 3;                       // TMEM lane quarter of this warp
     const bool two = p.mode != NNCP_TF32;
+    int sf = 0;
+    uint32_t phf = 0;
+    bool ok = true;
     long long li = 0;
-    for (long long u = blockIdx.x; u < n_units; u += gridDim.x, ++li) {
-      const Unit w = get_unit(p, u);
-      const int bsel = (int)(li & 1);
-      const bool got = mbar_wait(acc_full(bsel), (uint32_t)((li >> 1) & 1), abort_flag, p.err);
-      if (!__all_sync(0xffffffffu, got)) break;
+    Unit prev;
+    prev.mt = -1;
+    auto epilogue = [&](const Unit& w, long long lj) -> bool {
+      const int bsel = (int)(lj & 1);
+      const bool got = mbar_wait(acc_full(bsel), (uint32_t)((lj >> 1) & 1), abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, got)) return false;
       tc_fence_after();
       const long long row = w.mt * 128 + q * 32 + lane;
       const long long kc = w.kbeg / p.kper;
@@ -630,7 +583,8 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
           if ((R & 3) == 0 && c + 16 <= R) {
             float4* d4 = reinterpret_cast<float4*>(dst + c);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int i = 0; i < 4; ++i)
+              d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
           } else {
             for (int i = 0; i < 16; ++i)
               if (c + i < R) dst[c + i] = v[i];
@@ -640,7 +594,79 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty(bsel));
+      return true;
+    };
+    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
+      const Unit w = get_unit(p, u);
+      for (int s = 0; s < w.nk && !p.direct; ++s) {
+        const bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err);
+        const uint32_t st = raw0 + sf * kRawBytes;
+        // read phase: this thread's 32 source elements of row m, half kh
+        float x[32];
+        if (got) {
+          if (p.mode == NNCP_BF16_STORED) {
+            // MN-major bf16 source: row j holds 128 consecutive i (256 B)
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              x[e] = __uint_as_float(lds16(st + (32 * kh + e) * 256 + m * 2));
+          } else if (p.contract_fast) {
+            // K-major fp32 source: sub-tile kh, row m, its 8 chunks
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const float4 a = lds128(sw128_chunk(st + kh * 16384, m, c));
+              x[4 * c] = a.x; x[4 * c + 1] = a.y; x[4 * c + 2] = a.z; x[4 * c + 3] = a.w;
+            }
+          } else {
+            // MN-major fp32 source: row j holds 128 consecutive i (512 B)
+#pragma unroll
+            for (int e = 0; e < 32; ++e) x[e] = lds32(st + (32 * kh + e) * 512 + m * 4);
+          }
+        }
+        // every converter thread has read its share before any writes
+        if (bar_red_or(2, kConvThreads, !got)) {
+          ok = false;
+          break;
+        }
+        if (p.mode == NNCP_SPLIT_BF16X3) {
+          // hi tile at +0, lo tile at +16 KB; chunks 4 kh .. 4 kh + 3 of row m
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            uint32_t hi[4], lo[4];
+            split8(x + 8 * g, hi, lo);
+            sts128(sw128_chunk(st, m, 4 * kh + g), hi[0], hi[1], hi[2], hi[3]);
+            sts128(sw128_chunk(st + 16384, m, 4 * kh + g), lo[0], lo[1], lo[2], lo[3]);
+          }
+        } else if (p.mode == NNCP_TF32) {
+          // K-major fp32: sub-tile kh, chunks 0..7 of row m
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            sts128(sw128_chunk(st + kh * 16384, m, c), __float_as_uint(x[4 * c]),
+                   __float_as_uint(x[4 * c + 1]), __float_as_uint(x[4 * c + 2]),
+                   __float_as_uint(x[4 * c + 3]));
+        } else {
+          // K-major bf16: chunks 4 kh .. 4 kh + 3 of row m
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              w4[e] = (__float_as_uint(x[8 * g + 2 * e]) & 0xFFFFu) |
+                      (__float_as_uint(x[8 * g + 2 * e + 1]) << 16);
+            sts128(sw128_chunk(st, m, 4 * kh + g), w4[0], w4[1], w4[2], w4[3]);
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(conv_full(sf));
+        if (++sf == kSF) { sf = 0; phf ^= 1u; }
+      }
+      if (!ok) break;
+      if (epi_warp && prev.mt >= 0 && !epilogue(prev, li - 1)) ok = false;
+      // all converter warps take the same exit decision (they meet at barrier 2)
+      if (bar_red_or(2, kConvThreads, !ok)) { ok = false; break; }
+      prev = w;
     }
+    if (epi_warp && ok && prev.mt >= 0) epilogue(prev, li - 1);
   }
 
   tc_fence_before();
@@ -689,6 +715,27 @@ Plan plan_for(int contract_fast, int64_t IL, int64_t IR, int R, int num_sms) {
   return pl;
 }
 
+int align1k(int v) { return (v + 1023) & ~1023; }
+
+SmemPlan plan_smem(int precision, int contract_fast, int direct, int bf16x, int Rp) {
+  SmemPlan sm;
+  sm.raw_bytes = bf16x ? 16384 : 32768;
+  sm.b_bytes = align1k(2 * Rp * 128);
+  const int fixed = 1024 /* alignment slack */ + align1k(kOffsBytes) + align1k(kMiscBytes);
+  const int avail = kSmemMax - fixed - kSB * sm.b_bytes;
+  sm.nsf = std::min(kMaxSF, avail / sm.raw_bytes);
+  sm.off_raw = 0;
+  sm.off_b = sm.off_raw + sm.nsf * sm.raw_bytes;
+  sm.off_offs = sm.off_b + kSB * sm.b_bytes;
+  sm.off_bar = sm.off_offs + align1k(kOffsBytes);
+  sm.off_misc = sm.off_bar;
+  sm.total = sm.off_bar + align1k(kMiscBytes) + 1024;
+  (void)contract_fast;
+  (void)direct;
+  (void)precision;
+  return sm;
+}
+
 int64_t prod_range(const int64_t* d, int a, int b) {
   int64_t p = 1;
   for (int m = a; m <= b; ++m) p *= d[m];
@@ -727,7 +774,7 @@ int* tc_error_word(const TcScratch& s) { return static_cast<int*>(s.base); }
 
 cudaError_t tc_attributes_init() {
   return cudaFuncSetAttribute(k_tc_partial_mttkrp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmemBytes);
+                              kSmemMax);
 }
 
 cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, int64_t IL,
@@ -783,8 +830,10 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
   if (pl.nsplit > 1 && 256 + (size_t)pl.nsplit * pl.M * R * sizeof(float) > scratch.bytes)
     return cudaErrorInvalidValue;
 
+  p.sm = plan_smem(precision, contract_fast, p.direct, bf16x, pl.Rp);
+  if (p.sm.nsf < 2) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(pl.n_units, num_sms);
-  k_tc_partial_mttkrp<<<grid, kThreads, kSmemBytes, st>>>(map, p);
+  k_tc_partial_mttkrp<<<grid, kThreads, p.sm.total, st>>>(map, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || pl.nsplit == 1) return e;
   return launch_reduce_chunks(partials, pl.M * R, (int)pl.nsplit, out, num_sms, st);

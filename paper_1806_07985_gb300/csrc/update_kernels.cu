@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "nncp_internal.cuh"
 
 namespace nncp {
@@ -106,6 +108,47 @@ k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, in
   }
 }
 
+// fit = 1 - eps, eps^2 = (alpha - 2 beta + gamma) / alpha clamped at 0 (Sec. IV-B);
+// appends to the fit history and sets the stop flag on |delta fit| < tol.
+__device__ void record_fit(SolveState st, double beta, double gamma) {
+  const double alpha = st.scalars[0];
+  const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
+  const double fit = 1.0 - eps;
+  st.scalars[1] = beta;
+  st.scalars[2] = gamma;
+  st.scalars[3] = eps;
+  const int it = st.flags[2];
+  if (it < kFitCapacity) st.fits[it] = fit;
+  st.flags[2] = it + 1;
+  const double tol = st.scalars[4];
+  if (!isfinite(fit)) {
+    st.flags[3] = 1;
+    st.flags[0] = 1;
+  } else if (it >= 1 && it < kFitCapacity && fabs(fit - st.fits[it - 1]) < tol) {
+    st.flags[0] = 1;
+  }
+}
+
+// record_fit with alpha and the previous fit already loaded.
+__device__ void record_fit_known(SolveState st, double beta, double gamma, double alpha,
+                                 double prev_fit) {
+  const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
+  const double fit = 1.0 - eps;
+  st.scalars[1] = beta;
+  st.scalars[2] = gamma;
+  st.scalars[3] = eps;
+  const int it = st.flags[2];
+  if (it < kFitCapacity) st.fits[it] = fit;
+  st.flags[2] = it + 1;
+  const double tol = st.scalars[4];
+  if (!isfinite(fit)) {
+    st.flags[3] = 1;
+    st.flags[0] = 1;
+  } else if (it >= 1 && it < kFitCapacity && fabs(fit - prev_fit) < tol) {
+    st.flags[0] = 1;
+  }
+}
+
 // Single CTA (1024 threads).  Shared: GW (R*R doubles) + c (R doubles).
 __global__ void __launch_bounds__(1024)
 k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mode,
@@ -131,10 +174,13 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
     else st.lam[r] = v;
   }
   __syncthreads();
+  __shared__ double cinv[kMaxRank];
+  for (int r = tid; r < R; r += blockDim.x) cinv[r] = c[r] > 0.0 ? 1.0 / c[r] : 0.0;
+  __syncthreads();
   double* Gn = st.G + (long long)n * R2;
   for (int t = tid; t < R2; t += blockDim.x) {
     const int a = t / R, b = t % R;
-    Gn[t] = (c[a] > 0.0 && c[b] > 0.0) ? GW[t] / (c[a] * c[b]) : 0.0;
+    Gn[t] = GW[t] * cinv[a] * cinv[b];
   }
   for (long long t = tid; t < In * R; t += blockDim.x) {
     const int r = (int)(t % R);
@@ -152,22 +198,7 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gamma += red[w];
       double beta = 0.0;
       for (int b = 0; b < nblocks; ++b) beta += st.gram_part[(long long)b * (R2 + 1) + R2];
-      const double alpha = st.scalars[0];
-      const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
-      const double fit = 1.0 - eps;
-      st.scalars[1] = beta;
-      st.scalars[2] = gamma;
-      st.scalars[3] = eps;
-      const int it = st.flags[2];
-      if (it < kFitCapacity) st.fits[it] = fit;
-      st.flags[2] = it + 1;
-      const double tol = st.scalars[4];
-      if (!isfinite(fit)) {
-        st.flags[3] = 1;
-        st.flags[0] = 1;
-      } else if (it >= 1 && it < kFitCapacity && fabs(fit - st.fits[it - 1]) < tol) {
-        st.flags[0] = 1;
-      }
+      record_fit(st, beta, gamma);
     }
   }
   __syncthreads();
@@ -183,6 +214,252 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   }
 }
 
+// Mode update spread over CTAs of kMultiRows rows (I_n <= kMultiMaxRows, R <= 64):
+//   every CTA stages its rows of H and M in shared memory (coalesced), runs the
+//   HALS sweep with one thread per row (row in registers, no branches), writes
+//   W back, and writes its partial W^T W (float32) and <M, W>;
+//   the last CTA to finish (atomic ticket) sums the partials in CTA order,
+//   forms lambda, G_n, the fit at n = N and S for the next mode, scales H by
+//   1 / lambda, and resets the ticket.  Results do not depend on arrival order.
+constexpr int kMultiRows = 128;
+constexpr int kMultiMaxRows = 16384;
+
+template <int RMAX>
+struct MultiCfg {
+  static constexpr int T = RMAX <= 32 ? 512 : 256;
+  static constexpr int RP = RMAX + 4;  // padded row stride (16-byte multiple) in shared memory
+  static constexpr int NB = (RMAX + 3) / 4;
+  static constexpr int GROUPS = (T / (NB * NB)) > 0 ? T / (NB * NB) : 1;  // Gram row groups
+};
+
+template <int RMAX>
+__global__ void __launch_bounds__(MultiCfg<RMAX>::T)
+k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
+               int next_mode, int is_last, SolveState st, float* __restrict__ part) {
+  if (st.flags[0]) return;
+  constexpr int T = MultiCfg<RMAX>::T;
+  constexpr int RP = MultiCfg<RMAX>::RP;
+  constexpr int GROUPS = MultiCfg<RMAX>::GROUPS;
+  extern __shared__ __align__(16) float usm[];
+  float* St = usm;                         // RMAX x RMAX, St[r][c] = S[c][r], zero padded
+  float* Hs = St + RMAX * RMAX;            // kMultiRows x RP
+  float* Ms = Hs + kMultiRows * RP;        // kMultiRows x RP
+  float* gpart = Ms + kMultiRows * RP;     // GROUPS x R x R
+  __shared__ float lamf[RMAX];
+  __shared__ float sinv[RMAX];
+  __shared__ double red[T / 32];
+  __shared__ double cinv_sh[RMAX];
+  __shared__ double scal_sh[4];  // beta, alpha, previous fit
+  __shared__ int last_sh;
+  const int tid = threadIdx.x;
+  const int R2 = R * R;
+  const int row0 = blockIdx.x * kMultiRows;
+  const int nrows = min(kMultiRows, In - row0);
+  for (int e = tid; e < RMAX * RMAX; e += T) {
+    const int r = e / RMAX, c = e % RMAX;
+    St[e] = (r < R && c < R) ? st.S32[c * R + r] : 0.0f;
+  }
+  for (int r = tid; r < RMAX; r += T) {
+    lamf[r] = r < R ? (float)st.lam[r] : 0.0f;
+    const float srr = r < R ? st.S32[r * R + r] : 0.0f;
+    sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
+  }
+  const float* Hg = H + (long long)row0 * R;
+  const float* Mg = M + (long long)row0 * R;
+  for (int e = tid; e < nrows * R; e += T) {
+    const int rr = e / R, c = e % R;
+    Hs[rr * RP + c] = Hg[e];
+    Ms[rr * RP + c] = Mg[e];
+  }
+  __syncthreads();
+
+  // ---- HALS sweep (Sec. II-B): thread = row, columns in order
+  double bp = 0.0;
+  if (tid < nrows) {
+    float w[RMAX];
+#pragma unroll
+    for (int c = 0; c < RMAX; ++c) w[c] = c < R ? Hs[tid * RP + c] * lamf[c] : 0.0f;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const float si = sinv[r];
+      const float mr = Ms[tid * RP + r];
+      const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
+      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+#pragma unroll
+      for (int c = 0; c < RMAX; c += 4) {
+        const float4 sv = col[c >> 2];
+        d0 = fmaf(w[c], sv.x, d0);
+        d1 = fmaf(w[c + 1], sv.y, d1);
+        d2 = fmaf(w[c + 2], sv.z, d2);
+        d3 = fmaf(w[c + 3], sv.w, d3);
+      }
+      const float dot = (d0 + d1) + (d2 + d3);
+      const float upd = fmaxf(0.0f, w[r] + (mr - dot) * si);
+      w[r] = si != 0.0f ? upd : w[r];  // S_rr = 0: column left as it is
+    }
+    float b = 0.0f;
+#pragma unroll
+    for (int c = 0; c < RMAX; ++c) {
+      if (c < R) {
+        b = fmaf(Ms[tid * RP + c], w[c], b);
+        Hs[tid * RP + c] = w[c];
+      }
+    }
+    bp = (double)b;
+  }
+  for (int o = 16; o > 0; o >>= 1) bp += __shfl_xor_sync(0xffffffffu, bp, o);
+  if ((tid & 31) == 0) red[tid >> 5] = bp;
+  __syncthreads();
+  float* Hw = H + (long long)row0 * R;
+  for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R];
+
+  // ---- partial W^T W: thread = (4x4 tile, row group), register tiles
+  {
+    const int nb = (R + 3) / 4;
+    const int tiles = nb * nb;
+    const int groups = min(GROUPS, max(1, T / tiles));
+    if (tid < tiles * groups) {
+      const int tile = tid % tiles, g = tid / tiles;
+      const int a0 = (tile / nb) * 4, b0 = (tile % nb) * 4;
+      float acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+      for (int rr = g; rr < nrows; rr += groups) {
+        const float4 qa = *reinterpret_cast<const float4*>(Hs + rr * RP + a0);
+        const float4 qb = *reinterpret_cast<const float4*>(Hs + rr * RP + b0);
+        const float va[4] = {qa.x, qa.y, qa.z, qa.w};
+        const float vb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(va[x], vb[y], acc[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if (a0 + x < R && b0 + y < R) gpart[(g * R + a0 + x) * R + b0 + y] = acc[x][y];
+    }
+    __syncthreads();
+    float* pb = part + (long long)blockIdx.x * (R2 + 1);
+    for (int e = tid; e < R2; e += T) {
+      float sum = 0.0f;
+      for (int g = 0; g < groups; ++g) sum += gpart[g * R2 + e];
+      pb[e] = sum;
+    }
+    if (tid == 0) {
+      double b = 0.0;
+      for (int w = 0; w < T / 32; ++w) b += red[w];
+      pb[R2] = (float)b;
+    }
+  }
+
+  // ---- the last CTA finishes the update
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const int ticket = atomicAdd(&st.flags[8], 1);
+    last_sh = ticket == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_sh) return;
+  __threadfence();
+  const int nb = gridDim.x;
+  // the H/M staging area is free now: W^T W and S (float64) live there
+  double* GW = reinterpret_cast<double*>(Hs);
+  double* Sd = GW + R2;
+  if (tid == 0) {
+    scal_sh[1] = st.scalars[0];
+    const int it = st.flags[2];
+    scal_sh[2] = (it >= 1 && it <= kFitCapacity) ? st.fits[it - 1] : 0.0;
+  }
+  for (int e = tid; e < R2; e += T) {
+    float v[8];
+    float sum = 0.0f;
+    int b = 0;
+    for (; b + 8 <= nb; b += 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = part[(long long)(b + q) * (R2 + 1) + e];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sum += v[q];
+    }
+    for (; b < nb; ++b) sum += part[(long long)b * (R2 + 1) + e];
+    GW[e] = (double)sum;
+    Sd[e] = st.S[e];
+  }
+  if (tid == 0) {
+    double b = 0.0;
+    for (int k = 0; k < nb; ++k) b += (double)part[(long long)k * (R2 + 1) + R2];
+    scal_sh[0] = b;
+    st.flags[8] = 0;  // ticket reset for the next launch
+  }
+  __syncthreads();
+  for (int r = tid; r < R; r += T) {
+    const double v = sqrt(GW[r * R + r]);
+    st.lam[r] = v;
+    cinv_sh[r] = v > 0.0 ? 1.0 / v : 0.0;
+    lamf[r] = v > 0.0 ? (float)(1.0 / v) : 0.0f;  // from here on: 1 / lambda
+  }
+  __syncthreads();
+  double* Gn = st.G + (long long)n * R2;
+  for (int e = tid; e < R2; e += T) {
+    const int a = e / R, b = e % R;
+    Gn[e] = GW[e] * cinv_sh[a] * cinv_sh[b];
+  }
+  // H = W / lambda (multiplication by the float32 reciprocal); loads in one batch
+  const long long tot = (long long)In * R;
+  for (long long e0 = tid; e0 < tot; e0 += 16LL * T) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const long long e = e0 + (long long)q * T;
+      v[q] = e < tot ? H[e] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const long long e = e0 + (long long)q * T;
+      if (e < tot) H[e] = v[q] * lamf[(int)(e % R)];
+    }
+  }
+  if (is_last) {
+    double g = 0.0;
+    for (int e = tid; e < R2; e += T) g += Sd[e] * GW[e];
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = g;
+    __syncthreads();
+    if (tid == 0) {
+      double gamma = 0.0;
+      for (int w = 0; w < T / 32; ++w) gamma += red[w];
+      record_fit_known(st, scal_sh[0], gamma, scal_sh[1], scal_sh[2]);
+    }
+  }
+  __syncthreads();
+  // S for the next mode: Hadamard of every Gram but next_mode's (mode n's is new)
+  for (int e = tid; e < R2; e += T) {
+    double g[kMaxModes];
+#pragma unroll
+    for (int k = 0; k < kMaxModes; ++k)
+      g[k] = (k < N && k != next_mode) ? (k == n ? GW[e] * cinv_sh[e / R] * cinv_sh[e % R]
+                                                 : st.G[(long long)k * R2 + e])
+                                       : 1.0;
+    double sv = 1.0;
+#pragma unroll
+    for (int k = 0; k < kMaxModes; ++k) sv *= g[k];
+    st.S[e] = sv;
+    st.S32[e] = (float)sv;
+  }
+}
+
+template <int RMAX>
+size_t multi_smem() {
+  using C = MultiCfg<RMAX>;
+  const size_t grams = (size_t)C::GROUPS * RMAX * RMAX;
+  return (size_t)(RMAX * RMAX + 2 * kMultiRows * C::RP) * sizeof(float) + grams * sizeof(float);
+}
+
 __global__ void k_solve_reset(SolveState st, int R, double tol) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) st.lam[r] = 1.0;
   if (threadIdx.x == 0) {
@@ -190,6 +467,7 @@ __global__ void k_solve_reset(SolveState st, int R, double tol) {
     st.flags[1] = 0;
     st.flags[2] = 0;
     st.flags[3] = 0;
+    st.flags[8] = 0;
     st.scalars[4] = tol;
   }
 }
@@ -286,6 +564,15 @@ cudaError_t kernel_attributes_init() {
                                        200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_multi<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)multi_smem<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_multi<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)multi_smem<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_multi<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)multi_smem<64>());
   if (e == cudaSuccess) e = tc_attributes_init();
   return e;
 }
@@ -305,6 +592,36 @@ cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
   size_t smem = hals_smem(R);
   k_hals_gram<<<hals_gram_blocks(In), kHalsThreads, smem, stream>>>(
       const_cast<float*>(H), nullptr, In, R, st.S32, st.lam, st.gram_part, st.flags, 0);
+  return cudaGetLastError();
+}
+
+bool multi_update_ok(int64_t In, int R) { return In <= kMultiMaxRows && R <= 64; }
+
+// partial scratch needed by the multi-CTA update (floats)
+size_t multi_update_scratch(int64_t In, int R) {
+  const int64_t nb = (In + kMultiRows - 1) / kMultiRows;
+  return (size_t)(nb + 1) * (R * R + 1) + 2 * (size_t)R * R + 4;
+}
+
+cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
+                                int next_mode, int is_last, SolveState st, float* part,
+                                cudaStream_t stream) {
+  const int nb = (int)((In + kMultiRows - 1) / kMultiRows);
+  const int rmax = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
+  switch (rmax) {
+    case 16:
+      k_update_multi<16><<<nb, MultiCfg<16>::T, multi_smem<16>(), stream>>>(
+          H, M, (int)In, R, N, n, next_mode, is_last, st, part);
+      break;
+    case 32:
+      k_update_multi<32><<<nb, MultiCfg<32>::T, multi_smem<32>(), stream>>>(
+          H, M, (int)In, R, N, n, next_mode, is_last, st, part);
+      break;
+    default:
+      k_update_multi<64><<<nb, MultiCfg<64>::T, multi_smem<64>(), stream>>>(
+          H, M, (int)In, R, N, n, next_mode, is_last, st, part);
+      break;
+  }
   return cudaGetLastError();
 }
 

@@ -150,7 +150,8 @@ def test_convergence_stops_early_like_oracle(nn):
     ref, (lam, k, fit, hist, exact, Hg) = _solve_both(nn, dims, R, 500, x, H0, tol=1e-4)
     assert 2 <= ref["iters"] < 500
     assert abs(k - ref["iters"]) <= 1
-    assert abs(fit - ref["fits"][k - 1]) <= FIT_TOL
+    # the stop may land one iteration either side; compare at the common iteration
+    assert abs(fit - ref["fits"][min(k, ref["iters"]) - 1]) <= FIT_TOL
 
 
 def test_solve_is_bitwise_reproducible(nn):
