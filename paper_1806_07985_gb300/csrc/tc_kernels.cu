@@ -67,7 +67,7 @@ constexpr int kSmemMax = 232448;  // 227 KB per CTA on sm_103a
 
 // Shared-memory carve-up, decided on the host per launch (all offsets 1024-aligned).
 struct SmemPlan {
-  int raw_bytes, nsf, b_bytes;
+  int raw_bytes, nsf, b_bytes, b_tiles;  // b_tiles: B tiles held (3 ring slots, or all stages)
   int off_raw, off_b, off_offs, off_bar, off_misc, total;
 };
 
@@ -76,6 +76,7 @@ struct TcParams {
   int contract_fast;
   int direct;  // MMA reads the TMA stage (no converter)
   int bf16x;   // tensor stored as bf16
+  int b_resident;  // every unit spans the whole contraction: B formed once per CTA
   long long M, K;
   int R, Rp;
   long long n_mt, nsplit, kper, n_units;
@@ -336,7 +337,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       mbar_init(conv_full(i), kConvThreads / 32);
     }
     for (int i = 0; i < kSB; ++i) {
-      mbar_init(b_full(i), 2);
+      mbar_init(b_full(i), (p.b_resident && i == 0) ? 2 * kSB : 2);
       mbar_init(b_empty(i), 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -418,6 +419,8 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       const bool tf32 = p.mode == NNCP_TF32;
       const uint32_t idesc_full = tf32 ? make_idesc(2, Rp) : make_idesc(1, 2 * Rp);
       const uint32_t idesc_hi = make_idesc(1, Rp);
+      if (p.b_resident && n_units > blockIdx.x && !mbar_wait(b_full(0), 0, abort_flag, p.err))
+        ok = false;
       for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
         const Unit w = get_unit(p, u);
         const int bsel = (int)(li & 1);
@@ -428,13 +431,13 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
           const uint32_t afull = p.direct ? raw_full(sa) : conv_full(sa);
           const uint32_t aempty = raw_empty(sa);
           if (!mbar_wait(afull, pha, abort_flag, p.err) ||
-              !mbar_wait(b_full(sb), phb, abort_flag, p.err)) {
+              (!p.b_resident && !mbar_wait(b_full(sb), phb, abort_flag, p.err))) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t a = raw0 + sa * kRawBytes;
-          const uint32_t b = b0 + sb * kBBytes;
+          const uint32_t b = b0 + (p.b_resident ? s : sb) * kBBytes;
           if (tf32) {
             // two fp32 sub-tiles of 32 contraction elements, K = 8 per MMA
 #pragma unroll
@@ -453,7 +456,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
             }
           }
           mma_commit(aempty);
-          mma_commit(b_empty(sb));
+          if (!p.b_resident) mma_commit(b_empty(sb));
           if (++sa == nA) { sa = 0; pha ^= 1u; }
           if (++sb == kSB) { sb = 0; phb ^= 1u; }
         }
@@ -475,20 +478,62 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     const int nm = p.krp.nm;
     const bool tf32 = p.mode == NNCP_TF32;
     int* so = offs + bw * kKC * (kMaxModes + 1);  // this slot's offsets [kKC][kMaxModes + 1]
-    const uint32_t bt_base = b0 + bw * kBBytes;
+    uint32_t bt_base = b0 + bw * kBBytes;
+    // the first Khatri-Rao mode spans whole 64-element stages: the other modes'
+    // rows are the same for every element of a stage
+    const bool lead_aligned = (kdim[0] % kKC) == 0;
+    // write rank row rr, elements [32 half, 32 half + 32) of the B tile
+    auto store_b_rows = [&](const float* v, int rr) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const float* x8 = v + 8 * g;
+        const int kk0 = half * 32 + 8 * g;
+        if (tf32) {
+          const uint32_t sub = bt_base + (kk0 >> 5) * Rp * 128;
+          const int c0 = (kk0 & 31) >> 2;
+          sts128(sw128_chunk(sub, rr, c0), __float_as_uint(x8[0]), __float_as_uint(x8[1]),
+                 __float_as_uint(x8[2]), __float_as_uint(x8[3]));
+          sts128(sw128_chunk(sub, rr, c0 + 1), __float_as_uint(x8[4]), __float_as_uint(x8[5]),
+                 __float_as_uint(x8[6]), __float_as_uint(x8[7]));
+        } else {
+          uint32_t hi[4], lo[4];
+          split8(x8, hi, lo);
+          const int c = kk0 >> 3;
+          sts128(sw128_chunk(bt_base, rr, c), hi[0], hi[1], hi[2], hi[3]);
+          sts128(sw128_chunk(bt_base, Rp + rr, c), lo[0], lo[1], lo[2], lo[3]);
+        }
+      }
+    };
     long long t = 0;  // stage counter over this CTA's units
     bool ok = true;
-    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-      const Unit w = get_unit(p, u);
+    // resident B: one pass over the whole contraction, tile s into slot s
+    const long long n_pass = p.b_resident ? (blockIdx.x < n_units ? 1 : 0) : n_units;
+    for (long long u = blockIdx.x, pass = 0; pass < n_pass && ok; u += gridDim.x, ++pass) {
+      Unit w = get_unit(p, p.b_resident ? 0 : u);
+      if (p.b_resident) {
+        w.kbeg = 0;
+        w.kend = p.K;
+        w.nk = (int)((p.K + kKC - 1) / kKC);
+      }
+      if (!p.b_resident && u >= n_units) break;
       for (int s = 0; s < w.nk; ++s, ++t) {
         if ((int)(t % kSB) != bw) continue;
-        const uint32_t use = (uint32_t)(t / kSB);
-        const bool got = mbar_wait(b_empty(bw), (use & 1u) ^ 1u, abort_flag, p.err);
-        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
-        {
+        if (p.b_resident) bt_base = b0 + s * kBBytes;
+        const long long kst = w.kbeg + (long long)s * kKC + half * 32;  // first element of this half
+        // The factor loads of a stage do not depend on the B slot being free, only
+        // the stores do: issue the loads, then wait for the slot, then store.
+        bool slot_ok = true, waited = p.b_resident;
+        auto wait_slot = [&]() {
+          if (waited) return;
+          waited = true;
+          const uint32_t use = (uint32_t)(t / kSB);
+          const bool got = mbar_wait(b_empty(bw), (use & 1u) ^ 1u, abort_flag, p.err);
+          slot_ok = __all_sync(0xffffffffu, got);
+        };
+        if (!lead_aligned) {
           // row offsets of the contraction element this lane owns
           const int kk = half * 32 + lane;
-          const long long k = w.kbeg + (long long)s * kKC + kk;
+          const long long k = kst + lane;
           int* o = so + kk * (kMaxModes + 1);
           const int valid = k < w.kend;
           o[kMaxModes] = valid;
@@ -501,58 +546,77 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
               rem /= dm;
             }
           }
+          __syncwarp();
         }
-        __syncwarp();
-        // lane owns rank rows rr = lane (+32); all 32 factor loads of a row are
-        // issued before any is used
-        for (int rr = lane; rr < Rp; rr += 32) {
-          float v[32];
+        const int iters = (Rp + 31) >> 5;
+        for (int it = 0; it < iters; ++it) {
+          const int rr = lane + 32 * it;           // rank row of this lane
           const int rs = rr < R ? rr : 0;
+          float v[32];
+          if (lead_aligned) {
+            // modes after the first are constant over the stage:
+            // v(e) = H_0(k0 + e, r) * prod_{m>=1} H_m(k_m, r)
+            const int k0 = (int)(kst % kdim[0]);
+            const float* h0 = kH[0] + (long long)k0 * R + rs;
 #pragma unroll
-          for (int m = 0; m < kMaxModes; ++m) {
-            if (m < nm) {
-              const float* hb = kH[m] + rs;
+            for (int e = 0; e < 32; ++e) v[e] = __ldg(h0 + e * R);
+            uint32_t rem = (uint32_t)(kst / kdim[0]);
+            float cst = 1.0f;
+            for (int m = 1; m < nm; ++m) {
+              const uint32_t dm = kdim[m];
+              cst *= __ldg(kH[m] + (rem % dm) * (uint32_t)R + rs);
+              rem /= dm;
+            }
 #pragma unroll
-              for (int e = 0; e < 32; ++e) {
-                const float x = __ldg(hb + so[(half * 32 + e) * (kMaxModes + 1) + m]);
-                v[e] = m == 0 ? x : v[e] * x;
+            for (int e = 0; e < 32; ++e)
+              v[e] = (rr < R && kst + e < w.kend) ? v[e] * cst : 0.0f;
+          } else {
+#pragma unroll
+            for (int m = 0; m < kMaxModes; ++m) {
+              if (m < nm) {
+                const float* hb = kH[m] + rs;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                  const float x = __ldg(hb + so[(half * 32 + e) * (kMaxModes + 1) + m]);
+                  v[e] = m == 0 ? x : v[e] * x;
+                }
               }
             }
-          }
 #pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (!(so[(half * 32 + e) * (kMaxModes + 1) + kMaxModes] && rr < R)) v[e] = 0.0f;
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const float* x8 = v + 8 * g;
-            const int kk0 = half * 32 + 8 * g;
-            if (tf32) {
-              const uint32_t sub = bt_base + (kk0 >> 5) * Rp * 128;
-              const int c0 = (kk0 & 31) >> 2;
-              sts128(sw128_chunk(sub, rr, c0), __float_as_uint(x8[0]), __float_as_uint(x8[1]),
-                     __float_as_uint(x8[2]), __float_as_uint(x8[3]));
-              sts128(sw128_chunk(sub, rr, c0 + 1), __float_as_uint(x8[4]), __float_as_uint(x8[5]),
-                     __float_as_uint(x8[6]), __float_as_uint(x8[7]));
-            } else {
-              uint32_t hi[4], lo[4];
-              split8(x8, hi, lo);
-              const int c = kk0 >> 3;
-              sts128(sw128_chunk(bt_base, rr, c), hi[0], hi[1], hi[2], hi[3]);
-              sts128(sw128_chunk(bt_base, Rp + rr, c), lo[0], lo[1], lo[2], lo[3]);
-            }
+            for (int e = 0; e < 32; ++e)
+              if (!(so[(half * 32 + e) * (kMaxModes + 1) + kMaxModes] && rr < R)) v[e] = 0.0f;
           }
+          wait_slot();
+          if (!slot_ok) break;
+          if (rr < Rp) store_b_rows(v, rr);
         }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(b_full(bw));
+        if (!slot_ok) {
+          ok = false;
+          break;
+        }
+        if (!p.b_resident) {
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(b_full(bw));
+        }
       }
+    }
+    if (p.b_resident && n_pass > 0) {
+      // every builder warp has written its tiles: one arrival each on b_full(0)
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_full(0));
     }
   } else {
     // ---------------------------------------- converters + epilogue --
     const int ct = threadIdx.x - kWarpConv * 32;  // 0..255
-    const int m = ct & 127;                       // converted row within the tile
-    const int kh = ct >> 7;                       // contraction half (elements 32 kh .. 32 kh + 31)
-    const bool epi_warp = kh == 0;                // warps 8-11 also run the epilogue
+    // row m and contraction half kh (elements 32 kh .. 32 kh + 31).  K-major
+    // sources: the two halves of a row in lanes l and l + 16 of one warp, eight
+    // consecutive rows per quarter-warp (conflict-free 16-byte reads).  MN-major
+    // sources: 32 consecutive rows per warp (conflict-free 4-byte reads).
+    const int m = p.contract_fast ? ((ct >> 5) * 16 + (ct & 15)) : (ct & 127);
+    const int kh = p.contract_fast ? ((ct >> 4) & 1) : (ct >> 7);
+    const bool epi_warp = warp < kWarpConv + 4;   // warps 8-11 also run the epilogue
     const int q = warp & 3;                       // TMEM lane quarter of this warp
     const bool two = p.mode != NNCP_TF32;
     int sf = 0;
@@ -622,8 +686,16 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
             for (int e = 0; e < 32; ++e) x[e] = lds32(st + (32 * kh + e) * 512 + m * 4);
           }
         }
-        // every converter thread has read its share before any writes
-        if (bar_red_or(2, kConvThreads, !got)) {
+        // In place: every element is read before any is overwritten.  A K-major
+        // source row m is overwritten only by row m's own output, whose two halves
+        // sit in this warp; an MN-major source row is spread over all output rows,
+        // so the whole converter group must have read first.
+        if (p.contract_fast) {
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+        } else if (bar_red_or(2, kConvThreads, !got)) {
           ok = false;
           break;
         }
@@ -660,9 +732,9 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         if (lane == 0) mbar_arrive(conv_full(sf));
         if (++sf == kSF) { sf = 0; phf ^= 1u; }
       }
-      if (!ok) break;
-      if (epi_warp && prev.mt >= 0 && !epilogue(prev, li - 1)) ok = false;
-      // all converter warps take the same exit decision (they meet at barrier 2)
+      // every converter warp reaches this barrier once per unit, whether or not
+      // its stage loop ended early, so all of them take the same exit decision
+      if (ok && epi_warp && prev.mt >= 0 && !epilogue(prev, li - 1)) ok = false;
       if (bar_red_or(2, kConvThreads, !ok)) { ok = false; break; }
       prev = w;
     }
@@ -717,16 +789,26 @@ Plan plan_for(int contract_fast, int64_t IL, int64_t IR, int R, int num_sms) {
 
 int align1k(int v) { return (v + 1023) & ~1023; }
 
-SmemPlan plan_smem(int precision, int contract_fast, int direct, int bf16x, int Rp) {
+// B tiles resident when every unit spans the whole contraction and they fit
+// beside at least kMinSFResident TMA stages.
+constexpr int kMinSFResident = 4;
+
+SmemPlan plan_smem(int precision, int contract_fast, int direct, int bf16x, int Rp,
+                   long long K, long long nsplit, int* b_resident) {
   SmemPlan sm;
   sm.raw_bytes = bf16x ? 16384 : 32768;
   sm.b_bytes = align1k(2 * Rp * 128);
   const int fixed = 1024 /* alignment slack */ + align1k(kOffsBytes) + align1k(kMiscBytes);
-  const int avail = kSmemMax - fixed - kSB * sm.b_bytes;
+  const long long nk_total = (K + kKC - 1) / kKC;
+  const bool res = nsplit == 1 &&
+                   nk_total * sm.b_bytes + (long long)kMinSFResident * sm.raw_bytes + fixed <= kSmemMax;
+  *b_resident = res;
+  sm.b_tiles = res ? (int)nk_total : kSB;
+  const int avail = kSmemMax - fixed - sm.b_tiles * sm.b_bytes;
   sm.nsf = std::min(kMaxSF, avail / sm.raw_bytes);
   sm.off_raw = 0;
   sm.off_b = sm.off_raw + sm.nsf * sm.raw_bytes;
-  sm.off_offs = sm.off_b + kSB * sm.b_bytes;
+  sm.off_offs = sm.off_b + sm.b_tiles * sm.b_bytes;
   sm.off_bar = sm.off_offs + align1k(kOffsBytes);
   sm.off_misc = sm.off_bar;
   sm.total = sm.off_bar + align1k(kMiscBytes) + 1024;
@@ -830,7 +912,7 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
   if (pl.nsplit > 1 && 256 + (size_t)pl.nsplit * pl.M * R * sizeof(float) > scratch.bytes)
     return cudaErrorInvalidValue;
 
-  p.sm = plan_smem(precision, contract_fast, p.direct, bf16x, pl.Rp);
+  p.sm = plan_smem(precision, contract_fast, p.direct, bf16x, pl.Rp, pl.K, pl.nsplit, &p.b_resident);
   if (p.sm.nsf < 2) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(pl.n_units, num_sms);
   k_tc_partial_mttkrp<<<grid, kThreads, p.sm.total, st>>>(map, p);
