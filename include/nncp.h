@@ -155,6 +155,33 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
                             int max_iters, double tol, double* lambda_out, int* iters_out,
                             double* fit_out);
 
+/* ---- Batched solver: many independent problems of one order N ----------
+ * `count` tensors, tensor t with mode lengths dims[t*N .. t*N+N-1] (each in
+ * [1, 256]) and rank R[t] (in [1, 64]), all solved by the NNCP-HALS iteration
+ * of nncp_solve (Alg. 1 with the normalisation and error steps of Alg. 3,
+ * Sec. II-B HALS, Sec. IV-B fit) with root split 1 for every tensor, so one
+ * outer iteration is the same sequence of launches for the whole batch
+ * (captured once as a CUDA graph).  Each tensor stops on its own
+ * |fit_k - fit_{k-1}| < tol or at max_iters; a tensor's results are the same
+ * bits whatever else is in the batch.  Same layouts as above: X_t float32
+ * mode-1 fastest, H_t,n I_n x R_t row-major, device memory, caller-owned.
+ * max_iters at create sizes the per-tensor fit history. */
+typedef struct nncp_batch nncp_batch;
+nncp_status nncp_batch_create(int count, int N, const int64_t* dims, const int* R, int max_iters,
+                              nncp_batch** out);
+nncp_status nncp_batch_workspace_size(const nncp_batch* b, size_t* bytes);
+/* Caller-allocated device buffer (256-byte aligned) of nncp_batch_workspace_size bytes. */
+nncp_status nncp_batch_set_workspace(nncp_batch* b, void* dev_ptr, size_t bytes);
+/* X_dev[t] for t < count; H_dev[t*N + n] for factor n of tensor t. */
+nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float* const* H_dev);
+/* Solve all tensors; factors are overwritten with the normalised results.
+ * iters_out[t], fits_out[t] (host, count entries) and lambda_out (host, sum of
+ * R_t doubles, tensor after tensor) may each be NULL.  Blocks until done. */
+nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iters_out,
+                             double* fits_out, double* lambda_out, void* stream);
+const char* nncp_batch_last_error(const nncp_batch* b);
+void nncp_batch_destroy(nncp_batch* b);
+
 /* Direct MTTKRP of one mode that allocates nothing (the paper has no
  * counterpart; this is a deployment convenience).
  *

@@ -1,0 +1,373 @@
+// C ABI of the batched solver: many independent NNCP-HALS problems of one
+// order N advanced together, one graph-captured outer iteration at a time.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/nncp.h"
+#include "batch_kernels.cuh"
+
+using namespace nncp;
+
+struct nncp_batch {
+  int count = 0, N = 0, rmax = 16, fit_cap = 0;
+  std::vector<int64_t> dims;  // count x N
+  std::vector<int> R;
+  std::vector<BTensor> ts;    // host copy of the descriptors
+  std::vector<int2> pmr_items, pml_items, alpha_items;
+  std::vector<int> alpha_first, lam_off;
+  // workspace layout (byte offsets)
+  size_t off_ts = 0, off_pmr = 0, off_pml = 0, off_alpha_items = 0, off_alpha_first = 0,
+         off_alpha_part = 0, off_done = 0, off_out_iters = 0, off_out_fits = 0, off_out_lam = 0,
+         off_lam_off = 0, off_nonfinite = 0, off_tensors = 0, total = 0;
+  std::vector<size_t> t_off;  // per-tensor slice offsets
+  char* ws = nullptr;
+  cudaStream_t work = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int* host_done = nullptr;
+  bool have_data = false;
+  std::string err;
+};
+
+namespace {
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+nncp_status bfail(nncp_batch* b, nncp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  record_global_error(buf);
+  return s;
+}
+
+#define BCK(call)                                                                 \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) return bfail(b, NNCP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// per-tensor workspace slice: node buffers, M, partials, state
+size_t tensor_slice(const nncp_batch* b, int t, BTensor* d, char* base) {
+  const int N = b->N, R = b->R[t];
+  const int64_t* dm = &b->dims[(size_t)t * N];
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = al(off + bytes);
+    return base ? base + o : nullptr;
+  };
+  int64_t maxI = 0, I = 1;
+  for (int n = 0; n < N; ++n) {
+    maxI = std::max(maxI, dm[n]);
+    I *= dm[n];
+  }
+  // partial chunks of the root -> {1} MTTKRP: about 32K tensor elements each
+  const int64_t J = I / dm[0];
+  int64_t jchunk = std::max<int64_t>(32, (32768 / dm[0] + 31) / 32 * 32);
+  jchunk = std::min(jchunk, J);
+  const int nchunk = (int)((J + jchunk - 1) / jchunk);
+  if (d) {
+    memset(d, 0, sizeof *d);
+    d->N = N;
+    d->R = R;
+    for (int n = 0; n < N; ++n) d->dims[n] = dm[n];
+    d->I = I;
+    d->jchunk = jchunk;
+    d->nchunk = nchunk;
+    d->fit_cap = b->fit_cap;
+  }
+  for (int a = 1; a + 1 < N; ++a) {
+    int64_t sz = 1;
+    for (int m = a; m < N; ++m) sz *= dm[m];
+    char* p = take((size_t)sz * R * sizeof(float));
+    if (d) d->node[a] = reinterpret_cast<float*>(p);
+  }
+  char* pM = take((size_t)maxI * R * sizeof(float));
+  char* pP = take((size_t)nchunk * dm[0] * R * sizeof(float));
+  char* pG = take((size_t)N * R * R * sizeof(double));
+  char* pS = take((size_t)R * R * sizeof(double));
+  char* pS32 = take((size_t)R * R * sizeof(float));
+  char* pL = take((size_t)R * sizeof(double));
+  char* pF = take((size_t)b->fit_cap * sizeof(double));
+  char* pSc = take(4 * sizeof(double));
+  char* pFl = take(4 * sizeof(int));
+  if (d) {
+    d->M = reinterpret_cast<float*>(pM);
+    if (N == 2) d->node[1] = d->M;
+    d->part = reinterpret_cast<float*>(pP);
+    d->G = reinterpret_cast<double*>(pG);
+    d->S = reinterpret_cast<double*>(pS);
+    d->S32 = reinterpret_cast<float*>(pS32);
+    d->lam = reinterpret_cast<double*>(pL);
+    d->fits = reinterpret_cast<double*>(pF);
+    d->scal = reinterpret_cast<double*>(pSc);
+    d->flags = reinterpret_cast<int*>(pFl);
+  }
+  return off;
+}
+
+void plan(nncp_batch* b) {
+  const int C = b->count;
+  b->pmr_items.clear();
+  b->pml_items.clear();
+  b->alpha_items.clear();
+  b->alpha_first.assign(C + 1, 0);
+  b->lam_off.assign(C, 0);
+  b->ts.assign(C, BTensor());
+  b->t_off.assign(C, 0);
+  size_t tot_lam = 0;
+  for (int t = 0; t < C; ++t) {
+    tensor_slice(b, t, &b->ts[t], nullptr);
+    const BTensor& d = b->ts[t];
+    for (int c = 0; c < d.nchunk; ++c) b->pmr_items.push_back(make_int2(t, c));
+    const int64_t J = d.I / d.dims[0];
+    for (int64_t jb = 0; jb * 128 < J; ++jb) b->pml_items.push_back(make_int2(t, (int)jb));
+    b->alpha_first[t] = (int)b->alpha_items.size();
+    for (int64_t c = 0; c * kAlphaChunk < d.I; ++c) b->alpha_items.push_back(make_int2(t, (int)c));
+    b->lam_off[t] = (int)tot_lam;
+    tot_lam += d.R;
+  }
+  b->alpha_first[C] = (int)b->alpha_items.size();
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = al(off + bytes);
+    return o;
+  };
+  b->off_ts = take(C * sizeof(BTensor));
+  b->off_pmr = take(std::max<size_t>(1, b->pmr_items.size()) * sizeof(int2));
+  b->off_pml = take(std::max<size_t>(1, b->pml_items.size()) * sizeof(int2));
+  b->off_alpha_items = take(std::max<size_t>(1, b->alpha_items.size()) * sizeof(int2));
+  b->off_alpha_first = take((C + 1) * sizeof(int));
+  b->off_alpha_part = take(std::max<size_t>(1, b->alpha_items.size()) * sizeof(double));
+  b->off_done = take(sizeof(int) * 4);
+  b->off_out_iters = take(C * sizeof(int));
+  b->off_out_fits = take(C * sizeof(double));
+  b->off_out_lam = take(std::max<size_t>(1, tot_lam) * sizeof(double));
+  b->off_lam_off = take(C * sizeof(int));
+  b->off_nonfinite = take(C * sizeof(int));
+  b->off_tensors = off;
+  for (int t = 0; t < C; ++t) {
+    b->t_off[t] = off;
+    off += al(tensor_slice(b, t, nullptr, nullptr));
+  }
+  b->total = off;
+}
+
+template <typename T>
+T* at(nncp_batch* b, size_t off) {
+  return reinterpret_cast<T*>(b->ws + off);
+}
+
+cudaError_t run_iteration(nncp_batch* b, cudaStream_t st) {
+  BTensor* ts = at<BTensor>(b, b->off_ts);
+  int* done = at<int>(b, b->off_done);
+  const int C = b->count, N = b->N;
+  cudaError_t e = launch_b_pm_right(b->rmax, ts, at<int2>(b, b->off_pmr), (int)b->pmr_items.size(), C, st);
+  if (e == cudaSuccess) e = launch_b_update(b->rmax, ts, C, 0, done, st);
+  if (e == cudaSuccess) e = launch_b_pm_left(b->rmax, ts, at<int2>(b, b->off_pml), (int)b->pml_items.size(), st);
+  // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
+  for (int a = 1; a < N && e == cudaSuccess; ++a) {
+    if (a == N - 1) {
+      e = launch_b_update(b->rmax, ts, C, a, done, st);
+      break;
+    }
+    e = launch_b_mttv_leaf(ts, C, a, st);
+    if (e == cudaSuccess) e = launch_b_update(b->rmax, ts, C, a, done, st);
+    if (e == cudaSuccess) e = launch_b_mttv_first(ts, C, a, st);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+nncp_status nncp_batch_create(int count, int N, const int64_t* dims, const int* R, int max_iters,
+                              nncp_batch** out) {
+  if (!out) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !dims || !R) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "empty batch");
+  if (N < 2 || N > kMaxModes) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "N=%d not in [2,8]", N);
+  if (max_iters < 1 || max_iters > 65536)
+    return bfail(nullptr, NNCP_ERR_INVALID_ARG, "max_iters %d not in [1, 65536]", max_iters);
+  int rmax = 1;
+  for (int t = 0; t < count; ++t) {
+    if (R[t] < 1 || R[t] > kBatchMaxRank)
+      return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: R=%d not in [1,%d]", t, R[t], kBatchMaxRank);
+    rmax = std::max(rmax, R[t]);
+    for (int n = 0; n < N; ++n) {
+      const int64_t d = dims[(size_t)t * N + n];
+      if (d < 1 || d > kBatchMaxI)
+        return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: dims[%d]=%lld not in [1,%d]", t, n,
+                     (long long)d, kBatchMaxI);
+    }
+  }
+  nncp_batch* b = new (std::nothrow) nncp_batch();
+  if (!b) return bfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "host allocation failed");
+  b->count = count;
+  b->N = N;
+  b->rmax = rmax <= 16 ? 16 : (rmax <= 32 ? 32 : 64);
+  b->fit_cap = max_iters;
+  b->dims.assign(dims, dims + (size_t)count * N);
+  b->R.assign(R, R + count);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->host_done, 4 * sizeof(int));
+  if (e == cudaSuccess) e = batch_attributes_init();
+  if (e != cudaSuccess) {
+    nncp_status s = bfail(nullptr, NNCP_ERR_CUDA, "nncp_batch_create: %s", cudaGetErrorString(e));
+    nncp_batch_destroy(b);
+    return s;
+  }
+  plan(b);
+  *out = b;
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_workspace_size(const nncp_batch* b, size_t* bytes) {
+  if (!b || !bytes) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null argument");
+  *bytes = b->total;
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_set_workspace(nncp_batch* b, void* dev_ptr, size_t bytes) {
+  if (!b) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null batch");
+  if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255))
+    return bfail(b, NNCP_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+  if (bytes < b->total) return bfail(b, NNCP_ERR_INVALID_ARG, "workspace %zu < %zu bytes", bytes, b->total);
+  b->ws = static_cast<char*>(dev_ptr);
+  for (int t = 0; t < b->count; ++t) {
+    const float* X = b->ts[t].X;
+    float* H[kMaxModes];
+    for (int n = 0; n < kMaxModes; ++n) H[n] = b->ts[t].H[n];
+    tensor_slice(b, t, &b->ts[t], b->ws + b->t_off[t]);
+    b->ts[t].X = X;
+    for (int n = 0; n < kMaxModes; ++n) b->ts[t].H[n] = H[n];
+  }
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  BCK(cudaMemcpyAsync(b->ws + b->off_pmr, b->pmr_items.data(), b->pmr_items.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice, b->work));
+  BCK(cudaMemcpyAsync(b->ws + b->off_pml, b->pml_items.data(), b->pml_items.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice, b->work));
+  BCK(cudaMemcpyAsync(b->ws + b->off_alpha_items, b->alpha_items.data(),
+                      b->alpha_items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->work));
+  BCK(cudaMemcpyAsync(b->ws + b->off_alpha_first, b->alpha_first.data(),
+                      b->alpha_first.size() * sizeof(int), cudaMemcpyHostToDevice, b->work));
+  BCK(cudaMemcpyAsync(b->ws + b->off_lam_off, b->lam_off.data(), b->lam_off.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, b->work));
+  BCK(cudaStreamSynchronize(b->work));
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float* const* H_dev) {
+  if (!b || !X_dev || !H_dev) return bfail(b, NNCP_ERR_INVALID_ARG, "null argument");
+  if (!b->ws) return bfail(b, NNCP_ERR_INVALID_ARG, "workspace not set");
+  for (int t = 0; t < b->count; ++t) {
+    if (!X_dev[t]) return bfail(b, NNCP_ERR_INVALID_ARG, "tensor %d is NULL", t);
+    b->ts[t].X = X_dev[t];
+    for (int n = 0; n < b->N; ++n) {
+      float* h = H_dev[(size_t)t * b->N + n];
+      if (!h) return bfail(b, NNCP_ERR_INVALID_ARG, "factor %d of tensor %d is NULL", n + 1, t);
+      b->ts[t].H[n] = h;
+    }
+  }
+  BCK(cudaMemcpyAsync(b->ws + b->off_ts, b->ts.data(), b->ts.size() * sizeof(BTensor),
+                      cudaMemcpyHostToDevice, b->work));
+  BCK(cudaStreamSynchronize(b->work));
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->have_data = true;
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iters_out,
+                             double* fits_out, double* lambda_out, void* stream) {
+  if (!b) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null batch");
+  if (!b->have_data) return bfail(b, NNCP_ERR_INVALID_ARG, "data not set");
+  if (max_iters < 1 || max_iters > b->fit_cap)
+    return bfail(b, NNCP_ERR_INVALID_ARG, "max_iters %d not in [1, %d]", max_iters, b->fit_cap);
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev;
+  BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  BCK(cudaEventRecord(ev, user));
+  BCK(cudaStreamWaitEvent(b->work, ev, 0));
+  int* done = at<int>(b, b->off_done);
+  BCK(cudaMemsetAsync(done, 0, sizeof(int), b->work));
+  BCK(launch_b_init(at<BTensor>(b, b->off_ts), b->count, at<int2>(b, b->off_alpha_items),
+                    (int)b->alpha_items.size(), at<double>(b, b->off_alpha_part),
+                    at<int>(b, b->off_alpha_first), tol, max_iters, b->work));
+  if (!b->graph) {
+    cudaGraph_t g;
+    BCK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = run_iteration(b, b->work);
+    cudaError_t e2 = cudaStreamEndCapture(b->work, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (e2 == cudaSuccess) cudaGraphDestroy(g);
+      return bfail(b, NNCP_ERR_CUDA, "capturing the batched iteration: %s",
+                   cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return bfail(b, NNCP_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  int launched = 0, every = 4;
+  while (launched < max_iters) {
+    const int n = std::min(every, max_iters - launched);
+    for (int k = 0; k < n; ++k) BCK(cudaGraphLaunch(b->graph, b->work));
+    launched += n;
+    BCK(cudaMemcpyAsync(b->host_done, done, sizeof(int), cudaMemcpyDeviceToHost, b->work));
+    BCK(cudaStreamSynchronize(b->work));
+    if (b->host_done[0] >= b->count) break;
+    every = std::min(every * 2, 16);
+  }
+  int* d_iters = at<int>(b, b->off_out_iters);
+  double* d_fits = at<double>(b, b->off_out_fits);
+  double* d_lam = at<double>(b, b->off_out_lam);
+  int* d_nf = at<int>(b, b->off_nonfinite);
+  BCK(launch_b_gather(at<BTensor>(b, b->off_ts), b->count, d_iters, d_fits,
+                      lambda_out ? d_lam : nullptr, at<int>(b, b->off_lam_off), d_nf, b->work));
+  std::vector<int> nf(b->count);
+  if (iters_out)
+    BCK(cudaMemcpyAsync(iters_out, d_iters, b->count * sizeof(int), cudaMemcpyDeviceToHost, b->work));
+  if (fits_out)
+    BCK(cudaMemcpyAsync(fits_out, d_fits, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->work));
+  if (lambda_out) {
+    size_t tot = 0;
+    for (int t = 0; t < b->count; ++t) tot += b->R[t];
+    BCK(cudaMemcpyAsync(lambda_out, d_lam, tot * sizeof(double), cudaMemcpyDeviceToHost, b->work));
+  }
+  BCK(cudaMemcpyAsync(nf.data(), d_nf, b->count * sizeof(int), cudaMemcpyDeviceToHost, b->work));
+  BCK(cudaStreamSynchronize(b->work));
+  BCK(cudaEventRecord(ev, b->work));
+  BCK(cudaStreamWaitEvent(user, ev, 0));
+  cudaEventDestroy(ev);
+  for (int t = 0; t < b->count; ++t)
+    if (nf[t]) return bfail(b, NNCP_ERR_NUMERIC, "tensor %d: non-finite fit", t);
+  return NNCP_OK;
+}
+
+const char* nncp_batch_last_error(const nncp_batch* b) { return b ? b->err.c_str() : nncp_global_error(); }
+
+void nncp_batch_destroy(nncp_batch* b) {
+  if (!b) return;
+  if (b->work) cudaStreamSynchronize(b->work);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->work) cudaStreamDestroy(b->work);
+  if (b->host_done) cudaFreeHost(b->host_done);
+  delete b;
+}
+
+}  // extern "C"

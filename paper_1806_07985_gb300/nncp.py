@@ -62,6 +62,15 @@ _SIGNATURES = [
                                        _c_dblp, _c_intp, _c_dblp]),
     ("nncp_mttkrp_noalloc", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.c_void_p,
                                            _c_vpp, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("nncp_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _c_i64p, _c_intp, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("nncp_batch_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("nncp_batch_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("nncp_batch_set_data", ctypes.c_int, [ctypes.c_void_p, _c_vpp, _c_vpp]),
+    ("nncp_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_intp, _c_dblp,
+                                        _c_dblp, ctypes.c_void_p]),
+    ("nncp_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("nncp_batch_destroy", None, [ctypes.c_void_p]),
     ("nncp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_global_error", ctypes.c_char_p, []),
     ("nncp_destroy", None, [ctypes.c_void_p]),
@@ -232,6 +241,66 @@ def nncp_mttkrp_noalloc(dims, R, X, H, mode, M, stream=None):
     arr = (ctypes.c_void_p * len(H))(*[int(h.data_ptr()) for h in H])
     _check(load().nncp_mttkrp_noalloc(len(dims), _dims(dims), int(R), _ptr(X), arr, int(mode),
                                       _ptr(M), _stream(stream)))
+
+
+def _bcheck(status, b):
+    if status != NNCP_OK:
+        lib = load()
+        msg = lib.nncp_batch_last_error(b) if b else lib.nncp_global_error()
+        raise NNCPError(status, (msg or b"").decode())
+
+
+class Batch:
+    """Batched solver over torch CUDA tensors (argument marshalling only).
+
+    shapes: list of per-tensor mode-length tuples (all of one order N);
+    ranks: list of per-tensor ranks.  The workspace is allocated with torch."""
+
+    def __init__(self, shapes, ranks, max_iters):
+        import torch
+        self.N = len(shapes[0])
+        self.count = len(shapes)
+        self.ranks = [int(r) for r in ranks]
+        flat = [int(d) for sh in shapes for d in sh]
+        dims = (ctypes.c_int64 * len(flat))(*flat)
+        R = (ctypes.c_int * self.count)(*self.ranks)
+        self.b = ctypes.c_void_p()
+        _bcheck(load().nncp_batch_create(self.count, self.N, dims, R, int(max_iters),
+                                         ctypes.byref(self.b)), None)
+        n = ctypes.c_size_t()
+        _bcheck(load().nncp_batch_workspace_size(self.b, ctypes.byref(n)), self.b)
+        self.ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device="cuda")
+        _bcheck(load().nncp_batch_set_workspace(self.b, _ptr(self.ws), n.value), self.b)
+
+    def set_data(self, X, H):
+        """X: list of count tensors; H: list of count lists of N factor tensors."""
+        self._keep = (list(X), [list(h) for h in H])
+        xs = (ctypes.c_void_p * self.count)(*[int(x.data_ptr()) for x in X])
+        hs = (ctypes.c_void_p * (self.count * self.N))(*[int(f.data_ptr()) for h in H for f in h])
+        _bcheck(load().nncp_batch_set_data(self.b, xs, hs), self.b)
+
+    def solve(self, max_iters, tol, stream=None):
+        iters = (ctypes.c_int * self.count)()
+        fits = (ctypes.c_double * self.count)()
+        lam = (ctypes.c_double * max(1, sum(self.ranks)))()
+        _bcheck(load().nncp_batch_solve(self.b, int(max_iters), float(tol), iters, fits, lam,
+                                        _stream(stream)), self.b)
+        lams, o = [], 0
+        for r in self.ranks:
+            lams.append(list(lam[o:o + r]))
+            o += r
+        return list(iters), list(fits), lams
+
+    def close(self):
+        if self.b:
+            load().nncp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def nncp_last_error(ctx):

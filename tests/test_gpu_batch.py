@@ -1,0 +1,90 @@
+"""GPU parity of the batched solver (many independent NNCP-HALS problems).
+
+Each tensor of a batch is checked against the FP64 oracle run on that tensor
+alone with the same root split (1) and stopping rule; a tensor's result must
+be bitwise identical whether it is solved alone or inside a larger batch.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_07985_gb300 import synth
+from tests._util import ensure_built, rel_fro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nn():
+    ensure_built()
+    from paper_1806_07985_gb300 import nncp
+    return nncp
+
+
+def _problems(count, seed0=0, N=3, lo=8, hi=40, ranks=(2, 3, 4, 8)):
+    rng = np.random.default_rng(seed0)
+    probs = []
+    for t in range(count):
+        dims = tuple(int(d) for d in rng.integers(lo, hi + 1, size=N))
+        R = int(ranks[int(rng.integers(len(ranks)))])
+        x, _ = synth.lowrank_plus_noise(dims, R, seed=1000 + seed0 * 97 + t, noise=0.01)
+        H0 = synth.init_factors(dims, R, seed=5000 + seed0 * 97 + t)
+        probs.append((dims, R, x, H0))
+    return probs
+
+
+def _run_batch(nn, probs, iters, tol=0.0):
+    b = nn.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=max(iters, 1))
+    try:
+        X = [torch.from_numpy(p[2]).cuda() for p in probs]
+        H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
+        b.set_data(X, H)
+        k, fits, lams = b.solve(iters, tol)
+        return k, fits, lams, [[h.cpu().numpy() for h in hs] for hs in H]
+    finally:
+        b.close()
+
+
+@pytest.mark.parametrize("N", [3, 4, 2])
+def test_batch_matches_oracle(nn, N):
+    probs = _problems(12 if N == 3 else 6, seed0=N, N=N, hi=40 if N < 4 else 14)
+    iters = 10
+    k, fits, lams, Hs = _run_batch(nn, probs, iters)
+    for t, (dims, R, x, H0) in enumerate(probs):
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=iters, use_dimtree=True, s=1)
+        assert k[t] == iters
+        assert abs(fits[t] - ref["fits"][-1]) <= 1e-4, (t, dims, R, fits[t], ref["fits"][-1])
+        for n in range(N):
+            assert rel_fro(Hs[t][n], ref["H"][n]) <= 1e-3, (t, n)
+        assert rel_fro(np.array(lams[t]), ref["lam"]) <= 1e-3
+
+
+def test_batch_results_do_not_depend_on_the_batch(nn):
+    probs = _problems(9, seed0=11)
+    k_all, f_all, l_all, H_all = _run_batch(nn, probs, 6)
+    for t in (0, 4, 8):
+        k1, f1, l1, H1 = _run_batch(nn, [probs[t]], 6)
+        assert k1[0] == k_all[t] and f1[0] == f_all[t] and l1[0] == l_all[t]
+        for a, b in zip(H1[0], H_all[t]):
+            assert np.array_equal(a, b)
+
+
+def test_batch_stops_each_tensor_on_its_own(nn):
+    probs = _problems(8, seed0=21)
+    k, fits, lams, Hs = _run_batch(nn, probs, 300, tol=1e-4)
+    for t, (dims, R, x, H0) in enumerate(probs):
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=300, tol=1e-4, use_dimtree=True, s=1)
+        assert k[t] < 300
+        assert abs(k[t] - ref["iters"]) <= 1, (t, k[t], ref["iters"])
+        assert abs(fits[t] - ref["fits"][min(k[t], ref["iters"]) - 1]) <= 1e-4
+
+
+def test_batch_rejects_out_of_range_shapes(nn):
+    with pytest.raises(nn.NNCPError):
+        nn.Batch([(300, 4, 4)], [4], max_iters=4)   # mode longer than 256
+    with pytest.raises(nn.NNCPError):
+        nn.Batch([(10, 4, 4)], [65], max_iters=4)   # rank above 64
