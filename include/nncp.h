@@ -157,7 +157,8 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
 
 /* ---- Batched solver: many independent problems of one order N ----------
  * `count` tensors, tensor t with mode lengths dims[t*N .. t*N+N-1] (each in
- * [1, 256]) and rank R[t] (in [1, 64]), all solved by the NNCP-HALS iteration
+ * [1, 256], at most 2^31 - 1 elements) and rank R[t] (in [1, 64]), all solved
+ * by the NNCP-HALS iteration
  * of nncp_solve (Alg. 1 with the normalisation and error steps of Alg. 3,
  * Sec. II-B HALS, Sec. IV-B fit) with root split 1 for every tensor, so one
  * outer iteration is the same sequence of launches for the whole batch
@@ -172,7 +173,8 @@ nncp_status nncp_batch_create(int count, int N, const int64_t* dims, const int* 
 nncp_status nncp_batch_workspace_size(const nncp_batch* b, size_t* bytes);
 /* Caller-allocated device buffer (256-byte aligned) of nncp_batch_workspace_size bytes. */
 nncp_status nncp_batch_set_workspace(nncp_batch* b, void* dev_ptr, size_t bytes);
-/* X_dev[t] for t < count; H_dev[t*N + n] for factor n of tensor t. */
+/* X_dev[t] for t < count; H_dev[t*N + n] for factor n of tensor t; every
+ * pointer 16-byte aligned (NNCP_ERR_INVALID_ARG otherwise). */
 nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float* const* H_dev);
 /* Solve all tensors; factors are overwritten with the normalised results.
  * iters_out[t], fits_out[t] (host, count entries) and lambda_out (host, sum of

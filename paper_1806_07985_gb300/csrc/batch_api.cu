@@ -16,6 +16,7 @@ using namespace nncp;
 
 struct nncp_batch {
   int count = 0, N = 0, rmax = 16, fit_cap = 0;
+  int hs_floats = 0;          // H_1 in shared memory: max I_1 x padded R
   std::vector<int64_t> dims;  // count x N
   std::vector<int> R;
   std::vector<BTensor> ts;    // host copy of the descriptors
@@ -70,10 +71,12 @@ size_t tensor_slice(const nncp_batch* b, int t, BTensor* d, char* base) {
     maxI = std::max(maxI, dm[n]);
     I *= dm[n];
   }
-  // partial chunks of the root -> {1} MTTKRP: about 32K tensor elements each
+  // partial chunks of the root -> {1} MTTKRP: whole tiles, about
+  // kRightTileTarget tensor elements each
   const int64_t J = I / dm[0];
-  int64_t jchunk = std::max<int64_t>(32, (32768 / dm[0] + 31) / 32 * 32);
-  jchunk = std::min(jchunk, J);
+  const int rows_r = b_rows_right((int)dm[0], R);
+  const int64_t tiles = std::max<int64_t>(1, kRightTileTarget / ((int64_t)rows_r * dm[0]));
+  const int64_t jchunk = tiles * rows_r;
   const int nchunk = (int)((J + jchunk - 1) / jchunk);
   if (d) {
     memset(d, 0, sizeof *d);
@@ -83,6 +86,8 @@ size_t tensor_slice(const nncp_batch* b, int t, BTensor* d, char* base) {
     d->I = I;
     d->jchunk = jchunk;
     d->nchunk = nchunk;
+    d->rows_r = rows_r;
+    d->rows_l = b_rows_left((int)dm[0]);
     d->fit_cap = b->fit_cap;
   }
   for (int a = 1; a + 1 < N; ++a) {
@@ -121,6 +126,7 @@ void plan(nncp_batch* b) {
   b->pml_items.clear();
   b->alpha_items.clear();
   b->alpha_first.assign(C + 1, 0);
+  b->hs_floats = 0;
   b->lam_off.assign(C, 0);
   b->ts.assign(C, BTensor());
   b->t_off.assign(C, 0);
@@ -130,7 +136,9 @@ void plan(nncp_batch* b) {
     const BTensor& d = b->ts[t];
     for (int c = 0; c < d.nchunk; ++c) b->pmr_items.push_back(make_int2(t, c));
     const int64_t J = d.I / d.dims[0];
-    for (int64_t jb = 0; jb * 128 < J; ++jb) b->pml_items.push_back(make_int2(t, (int)jb));
+    const int64_t left_rows = (int64_t)d.rows_l * kLeftItemTiles;
+    for (int64_t jb = 0; jb * left_rows < J; ++jb) b->pml_items.push_back(make_int2(t, (int)jb));
+    b->hs_floats = std::max(b->hs_floats, (int)d.dims[0] * b_rank_pad(d.R));
     b->alpha_first[t] = (int)b->alpha_items.size();
     for (int64_t c = 0; c * kAlphaChunk < d.I; ++c) b->alpha_items.push_back(make_int2(t, (int)c));
     b->lam_off[t] = (int)tot_lam;
@@ -174,7 +182,8 @@ cudaError_t run_iteration(nncp_batch* b, cudaStream_t st) {
   const int C = b->count, N = b->N;
   cudaError_t e = launch_b_pm_right(b->rmax, ts, at<int2>(b, b->off_pmr), (int)b->pmr_items.size(), C, st);
   if (e == cudaSuccess) e = launch_b_update(b->rmax, ts, C, 0, done, st);
-  if (e == cudaSuccess) e = launch_b_pm_left(b->rmax, ts, at<int2>(b, b->off_pml), (int)b->pml_items.size(), st);
+  if (e == cudaSuccess) e = launch_b_pm_left(b->rmax, ts, at<int2>(b, b->off_pml), (int)b->pml_items.size(),
+                                              b->hs_floats, st);
   // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
   for (int a = 1; a < N && e == cudaSuccess; ++a) {
     if (a == N - 1) {
@@ -205,11 +214,16 @@ nncp_status nncp_batch_create(int count, int N, const int64_t* dims, const int* 
     if (R[t] < 1 || R[t] > kBatchMaxRank)
       return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: R=%d not in [1,%d]", t, R[t], kBatchMaxRank);
     rmax = std::max(rmax, R[t]);
+    int64_t I = 1;
     for (int n = 0; n < N; ++n) {
       const int64_t d = dims[(size_t)t * N + n];
       if (d < 1 || d > kBatchMaxI)
         return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: dims[%d]=%lld not in [1,%d]", t, n,
                      (long long)d, kBatchMaxI);
+      I *= d;
+      if (I > kBatchMaxElems)
+        return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: more than %lld elements", t,
+                     (long long)kBatchMaxElems);
     }
   }
   nncp_batch* b = new (std::nothrow) nncp_batch();
@@ -273,11 +287,14 @@ nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float*
   if (!b || !X_dev || !H_dev) return bfail(b, NNCP_ERR_INVALID_ARG, "null argument");
   if (!b->ws) return bfail(b, NNCP_ERR_INVALID_ARG, "workspace not set");
   for (int t = 0; t < b->count; ++t) {
-    if (!X_dev[t]) return bfail(b, NNCP_ERR_INVALID_ARG, "tensor %d is NULL", t);
+    if (!X_dev[t] || (reinterpret_cast<uintptr_t>(X_dev[t]) & 15))
+      return bfail(b, NNCP_ERR_INVALID_ARG, "tensor %d is NULL or not 16-byte aligned", t);
     b->ts[t].X = X_dev[t];
     for (int n = 0; n < b->N; ++n) {
       float* h = H_dev[(size_t)t * b->N + n];
-      if (!h) return bfail(b, NNCP_ERR_INVALID_ARG, "factor %d of tensor %d is NULL", n + 1, t);
+      if (!h || (reinterpret_cast<uintptr_t>(h) & 15))
+        return bfail(b, NNCP_ERR_INVALID_ARG, "factor %d of tensor %d is NULL or not 16-byte aligned",
+                     n + 1, t);
       b->ts[t].H[n] = h;
     }
   }

@@ -108,64 +108,227 @@ __global__ void k_b_init(BTensor* __restrict__ ts, const double* __restrict__ al
 }
 
 // ------------------------------------------------ partial MTTKRPs (root) --
+//
+// Both root contractions stream X_(1)^T (rows j of I_1 contiguous floats) in
+// tiles of whole rows.  A tile is fetched into registers (eight float4 per
+// thread, every load issued before any is used) one tile ahead of the
+// compute, then stored to shared memory; the thread mapping is sized from
+// the tensor's own rank, and when one tile holds too few (row, rank-group)
+// pairs for 256 threads the contraction range is split over thread groups
+// whose partial sums are added in group order.
 
-// root -> node {1}: part[c](i, r) = sum_{j in chunk c} X[i + I1 j] K(j, r),
-// K = H_N (.) ... (.) H_2.  Item (tensor, chunk); thread = row i (I1 <= 256).
-template <int RMAX>
-__global__ void __launch_bounds__(256)
-k_b_pm_right(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
-  const int2 it = items[blockIdx.x];
-  const BTensor& t = ts[it.x];
-  if (tensor_done(t)) return;
-  const int R = t.R, N = t.N;
-  const int I1 = (int)t.dims[0];
-  const long long J = t.I / I1;
-  const long long j0 = (long long)it.y * t.jchunk;
-  const long long j1 = min(J, j0 + t.jchunk);
-  __shared__ float Xs[kTileJ][kBatchMaxI + 1];
-  __shared__ __align__(16) float Ws[kTileJ][RMAX];
-  __shared__ int offs[kTileJ][kMaxModes];
-  const int tid = threadIdx.x;
-  float acc[RMAX];
+constexpr int kThreads = 256;
+// Split groups are sized for kGroupThreads whatever the block size, so the
+// summation order of an output depends only on its tensor's shape.
+constexpr int kGroupThreads = 256;
+
+// floats [0, L) of src (16-byte aligned), streamed (X is read once per pass)
+template <int NT, int V4>
+__device__ __forceinline__ void tile_fetch(const float* __restrict__ src, int L, float4 (&r)[V4]) {
 #pragma unroll
-  for (int r = 0; r < RMAX; ++r) acc[r] = 0.0f;
-  for (long long jt = j0; jt < j1; jt += kTileJ) {
-    const int nj = (int)min((long long)kTileJ, j1 - jt);
-    if (tid < kTileJ && tid < nj) krp_offsets(t, 1, N, jt + tid, offs[tid]);
-    // the tile's columns are contiguous: nj * I1 floats
-    const float* xb = t.X + jt * I1;
-    for (int e = tid; e < nj * I1; e += blockDim.x) Xs[e / I1][e % I1] = xb[e];
-    __syncthreads();
-    for (int e = tid; e < kTileJ * RMAX; e += blockDim.x) {
-      const int jj = e / RMAX, r = e % RMAX;
-      float w = 0.0f;
-      if (jj < nj && r < R) {
-        w = 1.0f;
-        for (int m = 1; m < N; ++m) w *= t.H[m][offs[jj][m - 1] + r];
-      }
-      Ws[jj][r] = w;
+  for (int k = 0; k < V4; ++k) {
+    const int e = 4 * ((int)threadIdx.x + NT * k);
+    if (e + 3 < L) {
+      r[k] = __ldcs(reinterpret_cast<const float4*>(src + e));
+    } else {
+      r[k].x = e < L ? __ldcs(src + e) : 0.0f;
+      r[k].y = e + 1 < L ? __ldcs(src + e + 1) : 0.0f;
+      r[k].z = e + 2 < L ? __ldcs(src + e + 2) : 0.0f;
+      r[k].w = 0.0f;
     }
-    __syncthreads();
-    if (tid < I1) {
-      for (int jj = 0; jj < nj; ++jj) {
-        const float x = Xs[jj][tid];
+  }
+}
+
+// the tile as fetched: Xs[e] = src[e]
+template <int NT, int V4>
+__device__ __forceinline__ void tile_store_dense(float* Xs, int L, const float4 (&r)[V4]) {
 #pragma unroll
-        for (int r = 0; r < RMAX; r += 4) {
-          const float4 w = *reinterpret_cast<const float4*>(&Ws[jj][r]);
-          acc[r] = fmaf(x, w.x, acc[r]);
-          acc[r + 1] = fmaf(x, w.y, acc[r + 1]);
-          acc[r + 2] = fmaf(x, w.z, acc[r + 2]);
-          acc[r + 3] = fmaf(x, w.w, acc[r + 3]);
+  for (int k = 0; k < V4; ++k) {
+    const int e = 4 * ((int)threadIdx.x + NT * k);
+    if (e + 3 < L) {
+      *reinterpret_cast<float4*>(Xs + e) = r[k];
+    } else {
+      if (e < L) Xs[e] = r[k].x;
+      if (e + 1 < L) Xs[e + 1] = r[k].y;
+      if (e + 2 < L) Xs[e + 2] = r[k].z;
+    }
+  }
+}
+
+// rows of I1 floats at an odd stride S (so threads reading one column of
+// consecutive rows hit distinct banks): Xs[row * S + col] = src[row * I1 + col]
+template <int NT, int V4>
+__device__ __forceinline__ void tile_store_rows(float* Xs, int L, int I1, int S,
+                                                const float4 (&r)[V4]) {
+  if (S == I1) {
+    tile_store_dense<NT, V4>(Xs, L, r);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < V4; ++k) {
+    const int e = 4 * ((int)threadIdx.x + NT * k);
+    if (e < L) {
+      int row = e / I1, col = e - row * I1;
+      const float v[4] = {r[k].x, r[k].y, r[k].z, r[k].w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (e + b < L) Xs[row * S + col] = v[b];
+        if (++col == I1) {
+          col = 0;
+          ++row;
         }
       }
     }
-    __syncthreads();
   }
-  if (tid < I1) {
-    float* out = t.part + ((long long)it.y * I1 + tid) * R;
+}
+
+// ranks r0 .. r0 + 3 of a factor row (zero beyond R); vector load when R % 4 == 0
+__device__ __forceinline__ float4 ld_rank4(const float* __restrict__ row, int r0, int R) {
+  if ((R & 3) == 0) {
+    if (r0 >= R) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    return __ldg(reinterpret_cast<const float4*>(row + r0));
+  }
+  float4 h;
+  h.x = r0 < R ? __ldg(row + r0) : 0.0f;
+  h.y = r0 + 1 < R ? __ldg(row + r0 + 1) : 0.0f;
+  h.z = r0 + 2 < R ? __ldg(row + r0 + 2) : 0.0f;
+  h.w = r0 + 3 < R ? __ldg(row + r0 + 3) : 0.0f;
+  return h;
+}
+
+__device__ __forceinline__ void fma4(float (&a)[4], float x, const float4& w) {
+  a[0] = fmaf(x, w.x, a[0]);
+  a[1] = fmaf(x, w.y, a[1]);
+  a[2] = fmaf(x, w.z, a[2]);
+  a[3] = fmaf(x, w.w, a[3]);
+}
+
+// root -> node {1}: part[c](i, r) = sum_{j in chunk c} X[i + I1 j] K(j, r),
+// K = H_N (.) ... (.) H_2 (rows formed per tile, never stored whole).
+// Item (tensor, chunk).  Thread = row i with all RQB = b_rq(R) rank groups;
+// 256 / I1 column groups split each tile's rows (j = g, g + G, ...) and are
+// added in group order at the end of the chunk.
+template <int RQB, bool PF>
+__device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float* Xs, float* Ws) {
+  constexpr int V4 = kTileFloats / 4 / kThreads;
+  constexpr int WU = kWsFloats / 4 / kThreads;
+  const int tid = threadIdx.x;
+  const int R = t.R, N = t.N;
+  const int I1 = (int)t.dims[0];
+  const int nj = t.rows_r;
+  const int J = (int)(t.I / I1);
+  const int j0 = chunk * (int)t.jchunk;
+  const int j1 = min(J, j0 + (int)t.jchunk);
+  const int G = kGroupThreads / I1;
+  const int g = tid / I1, i = tid - g * I1;
+  const bool act = g < G;
+  float acc[RQB][4];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r)
-      if (r < R) out[r] = acc[r];
+  for (int u = 0; u < RQB; ++u)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[u][b] = 0.0f;
+  const int ntile = (j1 - j0 + nj - 1) / nj;
+  float4 xr[V4];
+  if (PF) tile_fetch<kThreads, V4>(t.X + (long long)j0 * I1, min(nj, j1 - j0) * I1, xr);
+  const float4* W4 = reinterpret_cast<const float4*>(Ws);
+  for (int k = 0; k < ntile; ++k) {
+    const int jt = j0 + k * nj, njk = min(nj, j1 - jt);
+    __syncthreads();
+    if (!PF) tile_fetch<kThreads, V4>(t.X + (long long)jt * I1, njk * I1, xr);
+    tile_store_dense<kThreads, V4>(Xs, njk * I1, xr);
+    if (PF && k + 1 < ntile) {
+      const int jn = jt + nj;
+      tile_fetch<kThreads, V4>(t.X + (long long)jn * I1, min(nj, j1 - jn) * I1, xr);
+    }
+    // Khatri-Rao rows of the tile: float4 entries (row, rank group), nj * RQB <= 1024
+    {
+      float4 w[WU];
+      int rem[WU];
+#pragma unroll
+      for (int u = 0; u < WU; ++u) {
+        rem[u] = jt + (tid + kThreads * u) / RQB;
+        w[u] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+      }
+      for (int m = 1; m < N; ++m) {
+        const int dm = (int)t.dims[m];
+        const float* Hm = t.H[m];
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+          const int e = tid + kThreads * u;
+          if (e / RQB < njk) {
+            const int jm = rem[u] % dm;
+            rem[u] /= dm;
+            const float4 h = ld_rank4(Hm + jm * R, 4 * (e % RQB), R);
+            w[u].x *= h.x;
+            w[u].y *= h.y;
+            w[u].z *= h.z;
+            w[u].w *= h.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < WU; ++u) {
+        const int e = tid + kThreads * u;
+        if (e / RQB < njk) reinterpret_cast<float4*>(Ws)[e] = w[u];
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const float* xp = Xs + i;
+#pragma unroll 2
+      for (int jj = g; jj < njk; jj += G) {
+        const float x = xp[jj * I1];
+#pragma unroll
+        for (int u = 0; u < RQB; ++u) fma4(acc[u], x, W4[jj * RQB + u]);
+      }
+    }
+  }
+  float* out = t.part + (long long)chunk * I1 * R;
+  if (G > 1) {
+    float4* red = reinterpret_cast<float4*>(Xs);  // G * I1 <= 256 float4
+#pragma unroll
+    for (int u = 0; u < RQB; ++u) {
+      __syncthreads();
+      if (act) red[tid] = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+      __syncthreads();
+      if (tid < I1) {
+        float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int gg = 0; gg < G; ++gg) {
+          const float4 v = red[gg * I1 + tid];
+          s4[0] += v.x;
+          s4[1] += v.y;
+          s4[2] += v.z;
+          s4[3] += v.w;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (4 * u + b < R) out[tid * R + 4 * u + b] = s4[b];
+      }
+    }
+  } else if (act) {
+#pragma unroll
+    for (int u = 0; u < RQB; ++u)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * u + b < R) out[i * R + 4 * u + b] = acc[u][b];
+  }
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(kThreads, 2)
+k_b_pm_right(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
+  extern __shared__ __align__(16) float smem[];
+  const int2 it = items[blockIdx.x];
+  const BTensor& t = ts[it.x];
+  if (tensor_done(t)) return;
+  float* Xs = smem;                // kTileFloats
+  float* Ws = smem + kTileFloats;  // kWsFloats: rows x padded rank
+  switch (b_rq(t.R)) {
+    case 1: pm_right_item<1, true>(t, it.y, Xs, Ws); break;
+    case 2: pm_right_item<2, true>(t, it.y, Xs, Ws); break;
+    case 4: pm_right_item<4, true>(t, it.y, Xs, Ws); break;
+    case 8: if constexpr (RMAX >= 32) pm_right_item<8, true>(t, it.y, Xs, Ws); break;
+    default: if constexpr (RMAX >= 64) pm_right_item<16, false>(t, it.y, Xs, Ws); break;
   }
 }
 
@@ -181,55 +344,141 @@ __global__ void k_b_reduce_m(const BTensor* __restrict__ ts) {
   }
 }
 
+constexpr int kLeftRedFloats = 4 * kThreads;
+constexpr int kLeftV4 = kTileFloats / 4 / kThreads;
+
+__host__ __device__ constexpr int left_fixed_floats() {
+  return kTileFloats + kLeftMaxRows + kLeftRedFloats;
+}
+
 // root -> node {2..N}: T(j, r) = sum_i X[i + I1 j] H_1(i, r).  Item (tensor,
-// block of 128 rows j); thread = row j; contraction in tiles of 32 i.
+// kLeftItemTiles tiles of rows j); H_1 (rank padded to b_rank_pad(R) with
+// zeros) sits in shared memory.  Thread = (row j, block of RQB rank groups);
+// when a tile has fewer than 256 such pairs (then RQB = 1) the i range is
+// split over groups added in group order.
+template <int RQB, bool PF>
+__device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* Xs, float* red,
+                                             float* Hs) {
+  const int tid = threadIdx.x;
+  const int R = t.R, Rq = b_rq(R), Rp = 4 * Rq;
+  const int I1 = (int)t.dims[0], S = I1 | 1;
+  const int nj = t.rows_l;
+  const int J = (int)(t.I / I1);
+  const int jb0 = item * nj * kLeftItemTiles;
+  const int jb1 = min(J, jb0 + nj * kLeftItemTiles);
+  const int NB = Rq / RQB;  // rank blocks per row
+  const int P = nj * NB;
+  const int G = P >= kGroupThreads ? 1 : kGroupThreads / P;
+  const int npass = (P + kThreads - 1) / kThreads;
+  const int g = G > 1 ? tid / P : 0;
+  const int ia = g * I1 / G, ib = (g + 1) * I1 / G;
+  float4 xr[kLeftV4];
+  if (PF) tile_fetch<kThreads, kLeftV4>(t.X + (long long)jb0 * I1, min(nj, jb1 - jb0) * I1, xr);
+  {
+    const float* H1 = t.H[0];
+    if (R == Rp) {
+      const int n4 = I1 * Rq;
+      for (int v0 = tid; v0 < n4; v0 += 4 * kThreads) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * kThreads;
+          if (v < n4) h[u] = __ldg(reinterpret_cast<const float4*>(H1) + v);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * kThreads;
+          if (v < n4) reinterpret_cast<float4*>(Hs)[v] = h[u];
+        }
+      }
+    } else {
+      for (int e = tid; e < I1 * Rp; e += kThreads) {
+        const int i = e / Rp, r = e - i * Rp;
+        Hs[e] = r < R ? __ldg(H1 + i * R + r) : 0.0f;
+      }
+    }
+  }
+  const float4* H4 = reinterpret_cast<const float4*>(Hs);
+  float* T = t.node[1];
+  const int ntile = (jb1 - jb0 + nj - 1) / nj;
+  for (int k = 0; k < ntile; ++k) {
+    const int jt = jb0 + k * nj, njk = min(nj, jb1 - jt);
+    __syncthreads();
+    if (!PF) tile_fetch<kThreads, kLeftV4>(t.X + (long long)jt * I1, njk * I1, xr);
+    tile_store_rows<kThreads, kLeftV4>(Xs, njk * I1, I1, S, xr);
+    if (PF && k + 1 < ntile) {
+      const int jn = jt + nj;
+      tile_fetch<kThreads, kLeftV4>(t.X + (long long)jn * I1, min(nj, jb1 - jn) * I1, xr);
+    }
+    __syncthreads();
+    for (int p = 0; p < npass; ++p) {
+      const int pair = G > 1 ? tid - g * P : tid + kThreads * p;
+      const int jl = pair / NB, qb = pair - jl * NB;
+      const bool v = g < G && pair < P && jl < njk;
+      float a[RQB][4];
+#pragma unroll
+      for (int u = 0; u < RQB; ++u)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) a[u][b] = 0.0f;
+      if (v) {
+        const float* xp = Xs + jl * S;
+        const float4* hp = H4 + qb * RQB;
+#pragma unroll 4
+        for (int i = ia; i < ib; ++i) {
+          const float x = xp[i];
+#pragma unroll
+          for (int u = 0; u < RQB; ++u) fma4(a[u], x, hp[i * Rq + u]);
+        }
+      }
+      if (G > 1) {  // RQB == 1 here
+        if (g < G) reinterpret_cast<float4*>(red)[tid] = make_float4(a[0][0], a[0][1], a[0][2], a[0][3]);
+        __syncthreads();
+        if (tid < P) {
+          const int jl0 = tid / NB, q0 = tid - jl0 * NB;
+          if (jl0 < njk) {
+            float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int gg = 0; gg < G; ++gg) {
+              const float4 w = reinterpret_cast<const float4*>(red)[gg * P + tid];
+              s4[0] += w.x;
+              s4[1] += w.y;
+              s4[2] += w.z;
+              s4[3] += w.w;
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (4 * q0 + b < R) T[(long long)(jt + jl0) * R + 4 * q0 + b] = s4[b];
+          }
+        }
+        __syncthreads();
+      } else if (v) {
+#pragma unroll
+        for (int u = 0; u < RQB; ++u)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = 4 * (qb * RQB + u) + b;
+            if (r < R) T[(long long)(jt + jl) * R + r] = a[u][b];
+          }
+      }
+    }
+  }
+}
+
 template <int RMAX>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kThreads, 2)
 k_b_pm_left(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
+  extern __shared__ __align__(16) float smem[];
   const int2 it = items[blockIdx.x];
   const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
-  const int R = t.R;
-  const int I1 = (int)t.dims[0];
-  const long long J = t.I / I1;
-  const long long jb = (long long)it.y * 128;
-  const int nj = (int)min(128LL, J - jb);
-  __shared__ float Xs[128][33];
-  __shared__ __align__(16) float Hs[32][RMAX];
-  const int tid = threadIdx.x;
-  float acc[RMAX];
-#pragma unroll
-  for (int r = 0; r < RMAX; ++r) acc[r] = 0.0f;
-  const float* H1 = t.H[0];
-  for (int i0 = 0; i0 < I1; i0 += 32) {
-    const int ni = min(32, I1 - i0);
-    for (int e = tid; e < 128 * 32; e += 128) {
-      const int jj = e >> 5, ii = e & 31;
-      Xs[jj][ii] = (jj < nj && ii < ni) ? t.X[(jb + jj) * I1 + i0 + ii] : 0.0f;
-    }
-    for (int e = tid; e < 32 * RMAX; e += 128) {
-      const int ii = e / RMAX, r = e % RMAX;
-      Hs[ii][r] = (ii < ni && r < R) ? H1[(i0 + ii) * R + r] : 0.0f;
-    }
-    __syncthreads();
-    for (int ii = 0; ii < ni; ++ii) {
-      const float x = Xs[tid][ii];
-#pragma unroll
-      for (int r = 0; r < RMAX; r += 4) {
-        const float4 h = *reinterpret_cast<const float4*>(&Hs[ii][r]);
-        acc[r] = fmaf(x, h.x, acc[r]);
-        acc[r + 1] = fmaf(x, h.y, acc[r + 1]);
-        acc[r + 2] = fmaf(x, h.z, acc[r + 2]);
-        acc[r + 3] = fmaf(x, h.w, acc[r + 3]);
-      }
-    }
-    __syncthreads();
-  }
-  if (tid < nj) {
-    float* out = t.node[1] + (jb + tid) * R;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r)
-      if (r < R) out[r] = acc[r];
+  float* Xs = smem;                                // rows at odd stride
+  float* red = smem + kTileFloats + kLeftMaxRows;  // kLeftRedFloats
+  float* Hs = red + kLeftRedFloats;                // I1 x padded rank
+  switch (b_rqb_left((int)t.dims[0], t.R)) {
+    case 1: pm_left_item<1, true>(t, it.y, Xs, red, Hs); break;
+    case 2: pm_left_item<2, true>(t, it.y, Xs, red, Hs); break;
+    case 4: pm_left_item<4, true>(t, it.y, Xs, red, Hs); break;
+    case 8: if constexpr (RMAX >= 32) pm_left_item<8, true>(t, it.y, Xs, red, Hs); break;
+    default: if constexpr (RMAX >= 64) pm_left_item<16, false>(t, it.y, Xs, red, Hs); break;
   }
 }
 
@@ -461,6 +710,14 @@ cudaError_t batch_attributes_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_b_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)update_smem<64>());
+  const int right = (kTileFloats + kWsFloats) * (int)sizeof(float);
+  const int left = (left_fixed_floats() + kBatchMaxI * kBatchMaxRank) * (int)sizeof(float);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
   return e;
 }
 
@@ -474,21 +731,23 @@ cudaError_t launch_b_init(BTensor* ts, int count, const int2* alpha_items, int n
 
 cudaError_t launch_b_pm_right(int rmax, const BTensor* ts, const int2* items, int n_items,
                               int count, cudaStream_t st) {
+  const size_t sm = (size_t)(kTileFloats + kWsFloats) * sizeof(float);
   if (n_items > 0) {
-    if (rmax <= 16) k_b_pm_right<16><<<n_items, 256, 0, st>>>(ts, items);
-    else if (rmax <= 32) k_b_pm_right<32><<<n_items, 256, 0, st>>>(ts, items);
-    else k_b_pm_right<64><<<n_items, 256, 0, st>>>(ts, items);
+    if (rmax <= 16) k_b_pm_right<16><<<n_items, kThreads, sm, st>>>(ts, items);
+    else if (rmax <= 32) k_b_pm_right<32><<<n_items, kThreads, sm, st>>>(ts, items);
+    else k_b_pm_right<64><<<n_items, kThreads, sm, st>>>(ts, items);
   }
   k_b_reduce_m<<<count, 256, 0, st>>>(ts);
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_pm_left(int rmax, const BTensor* ts, const int2* items, int n_items,
-                             cudaStream_t st) {
+                             int hs_floats, cudaStream_t st) {
   if (n_items == 0) return cudaSuccess;
-  if (rmax <= 16) k_b_pm_left<16><<<n_items, 128, 0, st>>>(ts, items);
-  else if (rmax <= 32) k_b_pm_left<32><<<n_items, 128, 0, st>>>(ts, items);
-  else k_b_pm_left<64><<<n_items, 128, 0, st>>>(ts, items);
+  const size_t sm = (size_t)(left_fixed_floats() + hs_floats) * sizeof(float);
+  if (rmax <= 16) k_b_pm_left<16><<<n_items, kThreads, sm, st>>>(ts, items);
+  else if (rmax <= 32) k_b_pm_left<32><<<n_items, kThreads, sm, st>>>(ts, items);
+  else k_b_pm_left<64><<<n_items, kThreads, sm, st>>>(ts, items);
   return cudaGetLastError();
 }
 
