@@ -1,5 +1,7 @@
 // C ABI of the batched solver: many independent NNCP-HALS problems of one
 // order N advanced together, one graph-captured outer iteration at a time.
+// Also the host side shared with the server: per-tensor layout and the work
+// lists of a batch composition.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -12,20 +14,176 @@
 #include "../../include/nncp.h"
 #include "batch_kernels.cuh"
 
+namespace nncp {
+
+namespace {
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+}  // namespace
+
+size_t b_tensor_layout(int N, const int64_t* dm, int R, int fit_cap, BTensor* d, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = al(off + bytes);
+    return base ? base + o : nullptr;
+  };
+  int64_t maxI = 0, I = 1;
+  for (int n = 0; n < N; ++n) {
+    maxI = std::max(maxI, dm[n]);
+    I *= dm[n];
+  }
+  // root -> {1}: chunks of whole tiles, about kRightTileTarget elements, at most kMaxChunks
+  const int64_t J = I / dm[0];
+  const int rows_r = b_rows_right((int)dm[0], R);
+  int64_t tiles = std::max<int64_t>(1, kRightTileTarget / ((int64_t)rows_r * dm[0]));
+  tiles = std::max<int64_t>(tiles, cdiv(J, (int64_t)kMaxChunks * rows_r));
+  const int64_t jchunk = tiles * rows_r;
+  const int nchunk = (int)cdiv(J, jchunk);
+  // node {a..N} phases: leaf chunks (at most kMaxChunks) and child row blocks
+  int leaf_kc[kMaxModes] = {0}, leaf_nkc[kMaxModes] = {0}, first_jb[kMaxModes] = {0};
+  int64_t lpart_floats = 1;
+  for (int a = 1; a + 1 < N; ++a) {
+    int64_t K = 1;
+    for (int m = a + 1; m < N; ++m) K *= dm[m];
+    const int64_t E = dm[a] * R;
+    int64_t kc = std::max<int64_t>(1, kItemElems / std::min<int64_t>(E, kLeafBlock));
+    kc = std::max<int64_t>(kc, cdiv(K, kMaxChunks));
+    leaf_kc[a] = (int)kc;
+    leaf_nkc[a] = (int)cdiv(K, kc);
+    lpart_floats = std::max<int64_t>(lpart_floats, leaf_nkc[a] * E);
+    first_jb[a] = (int)std::max<int64_t>(1, kItemElems / E);
+  }
+  if (d) {
+    memset(d, 0, sizeof *d);
+    d->N = N;
+    d->R = R;
+    for (int n = 0; n < N; ++n) d->dims[n] = dm[n];
+    d->I = I;
+    d->jchunk = jchunk;
+    d->nchunk = nchunk;
+    d->rows_r = rows_r;
+    d->rows_l = b_rows_left((int)dm[0]);
+    for (int a = 0; a < kMaxModes; ++a) {
+      d->leaf_kc[a] = leaf_kc[a];
+      d->leaf_nkc[a] = leaf_nkc[a];
+      d->first_jb[a] = first_jb[a];
+    }
+    d->fit_cap = fit_cap;
+    d->max_iters = fit_cap;
+  }
+  for (int a = 1; a + 1 < N; ++a) {
+    int64_t sz = 1;
+    for (int m = a; m < N; ++m) sz *= dm[m];
+    char* p = take((size_t)sz * R * sizeof(float));
+    if (d) d->node[a] = reinterpret_cast<float*>(p);
+  }
+  char* pM = take((size_t)maxI * R * sizeof(float));
+  char* pP = take((size_t)nchunk * dm[0] * R * sizeof(float));
+  char* pLP = take((size_t)lpart_floats * sizeof(float));
+  char* pG = take((size_t)N * R * R * sizeof(double));
+  char* pS = take((size_t)R * R * sizeof(double));
+  char* pS32 = take((size_t)R * R * sizeof(float));
+  char* pL = take((size_t)R * sizeof(double));
+  char* pF = take((size_t)fit_cap * sizeof(double));
+  char* pSc = take(4 * sizeof(double));
+  char* pFl = take(4 * sizeof(int));
+  if (d) {
+    d->M = reinterpret_cast<float*>(pM);
+    if (N == 2) d->node[1] = d->M;
+    d->part = reinterpret_cast<float*>(pP);
+    d->lpart = reinterpret_cast<float*>(pLP);
+    d->G = reinterpret_cast<double*>(pG);
+    d->S = reinterpret_cast<double*>(pS);
+    d->S32 = reinterpret_cast<float*>(pS32);
+    d->lam = reinterpret_cast<double*>(pL);
+    d->fits = reinterpret_cast<double*>(pF);
+    d->scal = reinterpret_cast<double*>(pSc);
+    d->flags = reinterpret_cast<int*>(pFl);
+  }
+  return off;
+}
+
+void b_build_plan(const BTensor* ts, int C, int N, BPlan* p) {
+  p->count = C;
+  p->N = N;
+  p->items.clear();
+  p->alpha_first.assign(C + 1, 0);
+  p->lam_off.assign(C, 0);
+  p->lam_total = 0;
+  int rmax = 1;
+  p->hs_floats = 0;
+  for (int t = 0; t < C; ++t) {
+    rmax = std::max(rmax, ts[t].R);
+    p->hs_floats = std::max(p->hs_floats, (int)ts[t].dims[0] * b_rank_pad(ts[t].R));
+    p->lam_off[t] = (int)p->lam_total;
+    p->lam_total += ts[t].R;
+  }
+  p->rmax = rmax <= 16 ? 16 : (rmax <= 32 ? 32 : 64);
+  auto begin = [&](BPhase& ph) { ph.off = (int)p->items.size(); };
+  auto end = [&](BPhase& ph) { ph.count = (int)p->items.size() - ph.off; };
+  auto push = [&](int t, int64_t y, int64_t z) {
+    p->items.push_back(make_int4(t, (int)y, (int)z, 0));
+  };
+  begin(p->alpha);
+  for (int t = 0; t < C; ++t) {
+    p->alpha_first[t] = (int)p->items.size() - p->alpha.off;
+    for (int64_t c = 0; c * kAlphaChunk < ts[t].I; ++c) push(t, c, 0);
+  }
+  end(p->alpha);
+  p->alpha_first[C] = p->alpha.count;
+  begin(p->pmr);
+  for (int t = 0; t < C; ++t)
+    for (int c = 0; c < ts[t].nchunk; ++c) push(t, c, 0);
+  end(p->pmr);
+  begin(p->pmr_red);
+  for (int t = 0; t < C; ++t)
+    for (int64_t b = 0; b < cdiv(ts[t].dims[0] * ts[t].R, kReduceBlock); ++b) push(t, b, 0);
+  end(p->pmr_red);
+  begin(p->pml);
+  for (int t = 0; t < C; ++t) {
+    const int64_t J = ts[t].I / ts[t].dims[0];
+    const int64_t rows = (int64_t)ts[t].rows_l * kLeftItemTiles;
+    for (int64_t b = 0; b < cdiv(J, rows); ++b) push(t, b, 0);
+  }
+  end(p->pml);
+  for (int a = 0; a < kMaxModes; ++a) p->leaf[a] = p->leaf_red[a] = p->first[a] = BPhase();
+  for (int a = 1; a + 1 < N; ++a) {
+    begin(p->leaf[a]);
+    for (int t = 0; t < C; ++t) {
+      const int64_t E = ts[t].dims[a] * ts[t].R;
+      for (int c = 0; c < ts[t].leaf_nkc[a]; ++c)
+        for (int64_t b = 0; b < cdiv(E, kLeafBlock); ++b) push(t, c, b);
+    }
+    end(p->leaf[a]);
+    begin(p->leaf_red[a]);
+    for (int t = 0; t < C; ++t)
+      for (int64_t b = 0; b < cdiv(ts[t].dims[a] * ts[t].R, kReduceBlock); ++b) push(t, b, a);
+    end(p->leaf_red[a]);
+    begin(p->first[a]);
+    for (int t = 0; t < C; ++t) {
+      int64_t K = 1;
+      for (int m = a + 1; m < N; ++m) K *= ts[t].dims[m];
+      for (int64_t b = 0; b < cdiv(K, ts[t].first_jb[a]); ++b) push(t, b, 0);
+    }
+    end(p->first[a]);
+  }
+}
+
+}  // namespace nncp
+
 using namespace nncp;
 
 struct nncp_batch {
-  int count = 0, N = 0, rmax = 16, fit_cap = 0;
-  int hs_floats = 0;          // H_1 in shared memory: max I_1 x padded R
+  int count = 0, N = 0, fit_cap = 0;
   std::vector<int64_t> dims;  // count x N
   std::vector<int> R;
   std::vector<BTensor> ts;    // host copy of the descriptors
-  std::vector<int2> pmr_items, pml_items, alpha_items;
-  std::vector<int> alpha_first, lam_off;
+  BPlan plan;
   // workspace layout (byte offsets)
-  size_t off_ts = 0, off_pmr = 0, off_pml = 0, off_alpha_items = 0, off_alpha_first = 0,
-         off_alpha_part = 0, off_done = 0, off_out_iters = 0, off_out_fits = 0, off_out_lam = 0,
-         off_lam_off = 0, off_nonfinite = 0, off_tensors = 0, total = 0;
+  size_t off_ts = 0, off_items = 0, off_alpha_first = 0, off_alpha_part = 0, off_done = 0,
+         off_out_iters = 0, off_out_fits = 0, off_out_lam = 0, off_lam_off = 0, off_nonfinite = 0,
+         off_tensors = 0, total = 0;
   std::vector<size_t> t_off;  // per-tensor slice offsets
   char* ws = nullptr;
   cudaStream_t work = nullptr;
@@ -36,8 +194,6 @@ struct nncp_batch {
 };
 
 namespace {
-
-size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 nncp_status bfail(nncp_batch* b, nncp_status s, const char* fmt, ...) {
   char buf[512];
@@ -56,95 +212,13 @@ nncp_status bfail(nncp_batch* b, nncp_status s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return bfail(b, NNCP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-// per-tensor workspace slice: node buffers, M, partials, state
-size_t tensor_slice(const nncp_batch* b, int t, BTensor* d, char* base) {
-  const int N = b->N, R = b->R[t];
-  const int64_t* dm = &b->dims[(size_t)t * N];
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    size_t o = off;
-    off = al(off + bytes);
-    return base ? base + o : nullptr;
-  };
-  int64_t maxI = 0, I = 1;
-  for (int n = 0; n < N; ++n) {
-    maxI = std::max(maxI, dm[n]);
-    I *= dm[n];
-  }
-  // partial chunks of the root -> {1} MTTKRP: whole tiles, about
-  // kRightTileTarget tensor elements each
-  const int64_t J = I / dm[0];
-  const int rows_r = b_rows_right((int)dm[0], R);
-  const int64_t tiles = std::max<int64_t>(1, kRightTileTarget / ((int64_t)rows_r * dm[0]));
-  const int64_t jchunk = tiles * rows_r;
-  const int nchunk = (int)((J + jchunk - 1) / jchunk);
-  if (d) {
-    memset(d, 0, sizeof *d);
-    d->N = N;
-    d->R = R;
-    for (int n = 0; n < N; ++n) d->dims[n] = dm[n];
-    d->I = I;
-    d->jchunk = jchunk;
-    d->nchunk = nchunk;
-    d->rows_r = rows_r;
-    d->rows_l = b_rows_left((int)dm[0]);
-    d->fit_cap = b->fit_cap;
-  }
-  for (int a = 1; a + 1 < N; ++a) {
-    int64_t sz = 1;
-    for (int m = a; m < N; ++m) sz *= dm[m];
-    char* p = take((size_t)sz * R * sizeof(float));
-    if (d) d->node[a] = reinterpret_cast<float*>(p);
-  }
-  char* pM = take((size_t)maxI * R * sizeof(float));
-  char* pP = take((size_t)nchunk * dm[0] * R * sizeof(float));
-  char* pG = take((size_t)N * R * R * sizeof(double));
-  char* pS = take((size_t)R * R * sizeof(double));
-  char* pS32 = take((size_t)R * R * sizeof(float));
-  char* pL = take((size_t)R * sizeof(double));
-  char* pF = take((size_t)b->fit_cap * sizeof(double));
-  char* pSc = take(4 * sizeof(double));
-  char* pFl = take(4 * sizeof(int));
-  if (d) {
-    d->M = reinterpret_cast<float*>(pM);
-    if (N == 2) d->node[1] = d->M;
-    d->part = reinterpret_cast<float*>(pP);
-    d->G = reinterpret_cast<double*>(pG);
-    d->S = reinterpret_cast<double*>(pS);
-    d->S32 = reinterpret_cast<float*>(pS32);
-    d->lam = reinterpret_cast<double*>(pL);
-    d->fits = reinterpret_cast<double*>(pF);
-    d->scal = reinterpret_cast<double*>(pSc);
-    d->flags = reinterpret_cast<int*>(pFl);
-  }
-  return off;
-}
-
 void plan(nncp_batch* b) {
   const int C = b->count;
-  b->pmr_items.clear();
-  b->pml_items.clear();
-  b->alpha_items.clear();
-  b->alpha_first.assign(C + 1, 0);
-  b->hs_floats = 0;
-  b->lam_off.assign(C, 0);
   b->ts.assign(C, BTensor());
   b->t_off.assign(C, 0);
-  size_t tot_lam = 0;
-  for (int t = 0; t < C; ++t) {
-    tensor_slice(b, t, &b->ts[t], nullptr);
-    const BTensor& d = b->ts[t];
-    for (int c = 0; c < d.nchunk; ++c) b->pmr_items.push_back(make_int2(t, c));
-    const int64_t J = d.I / d.dims[0];
-    const int64_t left_rows = (int64_t)d.rows_l * kLeftItemTiles;
-    for (int64_t jb = 0; jb * left_rows < J; ++jb) b->pml_items.push_back(make_int2(t, (int)jb));
-    b->hs_floats = std::max(b->hs_floats, (int)d.dims[0] * b_rank_pad(d.R));
-    b->alpha_first[t] = (int)b->alpha_items.size();
-    for (int64_t c = 0; c * kAlphaChunk < d.I; ++c) b->alpha_items.push_back(make_int2(t, (int)c));
-    b->lam_off[t] = (int)tot_lam;
-    tot_lam += d.R;
-  }
-  b->alpha_first[C] = (int)b->alpha_items.size();
+  for (int t = 0; t < C; ++t)
+    b_tensor_layout(b->N, &b->dims[(size_t)t * b->N], b->R[t], b->fit_cap, &b->ts[t], nullptr);
+  b_build_plan(b->ts.data(), C, b->N, &b->plan);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -152,21 +226,19 @@ void plan(nncp_batch* b) {
     return o;
   };
   b->off_ts = take(C * sizeof(BTensor));
-  b->off_pmr = take(std::max<size_t>(1, b->pmr_items.size()) * sizeof(int2));
-  b->off_pml = take(std::max<size_t>(1, b->pml_items.size()) * sizeof(int2));
-  b->off_alpha_items = take(std::max<size_t>(1, b->alpha_items.size()) * sizeof(int2));
+  b->off_items = take(std::max<size_t>(1, b->plan.items.size()) * sizeof(int4));
   b->off_alpha_first = take((C + 1) * sizeof(int));
-  b->off_alpha_part = take(std::max<size_t>(1, b->alpha_items.size()) * sizeof(double));
+  b->off_alpha_part = take(std::max(1, b->plan.alpha.count) * sizeof(double));
   b->off_done = take(sizeof(int) * 4);
   b->off_out_iters = take(C * sizeof(int));
   b->off_out_fits = take(C * sizeof(double));
-  b->off_out_lam = take(std::max<size_t>(1, tot_lam) * sizeof(double));
+  b->off_out_lam = take(std::max<size_t>(1, b->plan.lam_total) * sizeof(double));
   b->off_lam_off = take(C * sizeof(int));
   b->off_nonfinite = take(C * sizeof(int));
   b->off_tensors = off;
   for (int t = 0; t < C; ++t) {
     b->t_off[t] = off;
-    off += al(tensor_slice(b, t, nullptr, nullptr));
+    off += al(b_tensor_layout(b->N, &b->dims[(size_t)t * b->N], b->R[t], b->fit_cap, nullptr, nullptr));
   }
   b->total = off;
 }
@@ -174,27 +246,6 @@ void plan(nncp_batch* b) {
 template <typename T>
 T* at(nncp_batch* b, size_t off) {
   return reinterpret_cast<T*>(b->ws + off);
-}
-
-cudaError_t run_iteration(nncp_batch* b, cudaStream_t st) {
-  BTensor* ts = at<BTensor>(b, b->off_ts);
-  int* done = at<int>(b, b->off_done);
-  const int C = b->count, N = b->N;
-  cudaError_t e = launch_b_pm_right(b->rmax, ts, at<int2>(b, b->off_pmr), (int)b->pmr_items.size(), C, st);
-  if (e == cudaSuccess) e = launch_b_update(b->rmax, ts, C, 0, done, st);
-  if (e == cudaSuccess) e = launch_b_pm_left(b->rmax, ts, at<int2>(b, b->off_pml), (int)b->pml_items.size(),
-                                              b->hs_floats, st);
-  // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
-  for (int a = 1; a < N && e == cudaSuccess; ++a) {
-    if (a == N - 1) {
-      e = launch_b_update(b->rmax, ts, C, a, done, st);
-      break;
-    }
-    e = launch_b_mttv_leaf(ts, C, a, st);
-    if (e == cudaSuccess) e = launch_b_update(b->rmax, ts, C, a, done, st);
-    if (e == cudaSuccess) e = launch_b_mttv_first(ts, C, a, st);
-  }
-  return e;
 }
 
 }  // namespace
@@ -209,11 +260,9 @@ nncp_status nncp_batch_create(int count, int N, const int64_t* dims, const int* 
   if (N < 2 || N > kMaxModes) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "N=%d not in [2,8]", N);
   if (max_iters < 1 || max_iters > 65536)
     return bfail(nullptr, NNCP_ERR_INVALID_ARG, "max_iters %d not in [1, 65536]", max_iters);
-  int rmax = 1;
   for (int t = 0; t < count; ++t) {
     if (R[t] < 1 || R[t] > kBatchMaxRank)
       return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: R=%d not in [1,%d]", t, R[t], kBatchMaxRank);
-    rmax = std::max(rmax, R[t]);
     int64_t I = 1;
     for (int n = 0; n < N; ++n) {
       const int64_t d = dims[(size_t)t * N + n];
@@ -230,7 +279,6 @@ nncp_status nncp_batch_create(int count, int N, const int64_t* dims, const int* 
   if (!b) return bfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "host allocation failed");
   b->count = count;
   b->N = N;
-  b->rmax = rmax <= 16 ? 16 : (rmax <= 32 ? 32 : 64);
   b->fit_cap = max_iters;
   b->dims.assign(dims, dims + (size_t)count * N);
   b->R.assign(R, R + count);
@@ -263,21 +311,19 @@ nncp_status nncp_batch_set_workspace(nncp_batch* b, void* dev_ptr, size_t bytes)
     const float* X = b->ts[t].X;
     float* H[kMaxModes];
     for (int n = 0; n < kMaxModes; ++n) H[n] = b->ts[t].H[n];
-    tensor_slice(b, t, &b->ts[t], b->ws + b->t_off[t]);
+    b_tensor_layout(b->N, &b->dims[(size_t)t * b->N], b->R[t], b->fit_cap, &b->ts[t],
+                    b->ws + b->t_off[t]);
     b->ts[t].X = X;
     for (int n = 0; n < kMaxModes; ++n) b->ts[t].H[n] = H[n];
   }
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
-  BCK(cudaMemcpyAsync(b->ws + b->off_pmr, b->pmr_items.data(), b->pmr_items.size() * sizeof(int2),
+  const BPlan& p = b->plan;
+  BCK(cudaMemcpyAsync(b->ws + b->off_items, p.items.data(), p.items.size() * sizeof(int4),
                       cudaMemcpyHostToDevice, b->work));
-  BCK(cudaMemcpyAsync(b->ws + b->off_pml, b->pml_items.data(), b->pml_items.size() * sizeof(int2),
-                      cudaMemcpyHostToDevice, b->work));
-  BCK(cudaMemcpyAsync(b->ws + b->off_alpha_items, b->alpha_items.data(),
-                      b->alpha_items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->work));
-  BCK(cudaMemcpyAsync(b->ws + b->off_alpha_first, b->alpha_first.data(),
-                      b->alpha_first.size() * sizeof(int), cudaMemcpyHostToDevice, b->work));
-  BCK(cudaMemcpyAsync(b->ws + b->off_lam_off, b->lam_off.data(), b->lam_off.size() * sizeof(int),
+  BCK(cudaMemcpyAsync(b->ws + b->off_alpha_first, p.alpha_first.data(),
+                      p.alpha_first.size() * sizeof(int), cudaMemcpyHostToDevice, b->work));
+  BCK(cudaMemcpyAsync(b->ws + b->off_lam_off, p.lam_off.data(), p.lam_off.size() * sizeof(int),
                       cudaMemcpyHostToDevice, b->work));
   BCK(cudaStreamSynchronize(b->work));
   return NNCP_OK;
@@ -289,20 +335,17 @@ nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float*
   for (int t = 0; t < b->count; ++t) {
     if (!X_dev[t] || (reinterpret_cast<uintptr_t>(X_dev[t]) & 15))
       return bfail(b, NNCP_ERR_INVALID_ARG, "tensor %d is NULL or not 16-byte aligned", t);
-    b->ts[t].X = X_dev[t];
     for (int n = 0; n < b->N; ++n) {
       float* h = H_dev[(size_t)t * b->N + n];
       if (!h || (reinterpret_cast<uintptr_t>(h) & 15))
         return bfail(b, NNCP_ERR_INVALID_ARG, "factor %d of tensor %d is NULL or not 16-byte aligned",
                      n + 1, t);
-      b->ts[t].H[n] = h;
     }
   }
-  BCK(cudaMemcpyAsync(b->ws + b->off_ts, b->ts.data(), b->ts.size() * sizeof(BTensor),
-                      cudaMemcpyHostToDevice, b->work));
-  BCK(cudaStreamSynchronize(b->work));
-  if (b->graph) cudaGraphExecDestroy(b->graph);
-  b->graph = nullptr;
+  for (int t = 0; t < b->count; ++t) {
+    b->ts[t].X = X_dev[t];
+    for (int n = 0; n < b->N; ++n) b->ts[t].H[n] = H_dev[(size_t)t * b->N + n];
+  }
   b->have_data = true;
   return NNCP_OK;
 }
@@ -314,19 +357,26 @@ nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iter
   if (max_iters < 1 || max_iters > b->fit_cap)
     return bfail(b, NNCP_ERR_INVALID_ARG, "max_iters %d not in [1, %d]", max_iters, b->fit_cap);
   cudaStream_t user = static_cast<cudaStream_t>(stream);
+  for (int t = 0; t < b->count; ++t) {
+    b->ts[t].max_iters = max_iters;
+    b->ts[t].tol = tol;
+  }
+  BTensor* d_ts = at<BTensor>(b, b->off_ts);
+  const int4* d_items = at<int4>(b, b->off_items);
   cudaEvent_t ev;
   BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   BCK(cudaEventRecord(ev, user));
   BCK(cudaStreamWaitEvent(b->work, ev, 0));
+  BCK(cudaMemcpyAsync(d_ts, b->ts.data(), b->ts.size() * sizeof(BTensor), cudaMemcpyHostToDevice,
+                      b->work));
   int* done = at<int>(b, b->off_done);
   BCK(cudaMemsetAsync(done, 0, sizeof(int), b->work));
-  BCK(launch_b_init(at<BTensor>(b, b->off_ts), b->count, at<int2>(b, b->off_alpha_items),
-                    (int)b->alpha_items.size(), at<double>(b, b->off_alpha_part),
-                    at<int>(b, b->off_alpha_first), tol, max_iters, b->work));
+  BCK(b_launch_init(b->plan, d_ts, d_items, at<double>(b, b->off_alpha_part),
+                    at<int>(b, b->off_alpha_first), b->work));
   if (!b->graph) {
     cudaGraph_t g;
     BCK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = run_iteration(b, b->work);
+    cudaError_t e = b_launch_iteration(b->plan, d_ts, d_items, done, b->work);
     cudaError_t e2 = cudaStreamEndCapture(b->work, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (e2 == cudaSuccess) cudaGraphDestroy(g);
@@ -354,18 +404,16 @@ nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iter
   double* d_fits = at<double>(b, b->off_out_fits);
   double* d_lam = at<double>(b, b->off_out_lam);
   int* d_nf = at<int>(b, b->off_nonfinite);
-  BCK(launch_b_gather(at<BTensor>(b, b->off_ts), b->count, d_iters, d_fits,
-                      lambda_out ? d_lam : nullptr, at<int>(b, b->off_lam_off), d_nf, b->work));
+  BCK(launch_b_gather(d_ts, b->count, d_iters, d_fits, lambda_out ? d_lam : nullptr,
+                      at<int>(b, b->off_lam_off), d_nf, b->work));
   std::vector<int> nf(b->count);
   if (iters_out)
     BCK(cudaMemcpyAsync(iters_out, d_iters, b->count * sizeof(int), cudaMemcpyDeviceToHost, b->work));
   if (fits_out)
     BCK(cudaMemcpyAsync(fits_out, d_fits, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->work));
-  if (lambda_out) {
-    size_t tot = 0;
-    for (int t = 0; t < b->count; ++t) tot += b->R[t];
-    BCK(cudaMemcpyAsync(lambda_out, d_lam, tot * sizeof(double), cudaMemcpyDeviceToHost, b->work));
-  }
+  if (lambda_out)
+    BCK(cudaMemcpyAsync(lambda_out, d_lam, b->plan.lam_total * sizeof(double),
+                        cudaMemcpyDeviceToHost, b->work));
   BCK(cudaMemcpyAsync(nf.data(), d_nf, b->count * sizeof(int), cudaMemcpyDeviceToHost, b->work));
   BCK(cudaStreamSynchronize(b->work));
   BCK(cudaEventRecord(ev, b->work));

@@ -15,31 +15,29 @@ namespace nncp {
 
 namespace {
 
-constexpr int kTileJ = 32;  // contraction tile of the batched partial MTTKRPs
-
 __device__ __forceinline__ bool tensor_done(const BTensor& t) { return t.flags[0] != 0; }
-
-// KRP row offsets of element k over modes [m0, m1) of tensor t: off[m - m0] = k_m * R
-__device__ __forceinline__ void krp_offsets(const BTensor& t, int m0, int m1, long long k, int* off) {
-  for (int m = m0; m < m1; ++m) {
-    const long long dm = t.dims[m];
-    off[m - m0] = (int)((k % dm) * t.R);
-    k /= dm;
-  }
-}
 
 // ---------------------------------------------------------------- init --
 
-// alpha partials: item (tensor, chunk of kAlphaChunk elements) -> alpha_part[item]
-__global__ void k_b_sumsq(const BTensor* __restrict__ ts, const int2* __restrict__ items,
-                          double* __restrict__ alpha_part) {
-  const int2 it = items[blockIdx.x];
+// alpha partials: item (tensor, chunk of kAlphaChunk elements) -> alpha_part[item];
+// squares summed four at a time in FP32, the rest in FP64 (fixed order)
+__global__ void __launch_bounds__(256) k_b_sumsq(const BTensor* __restrict__ ts,
+                                                 const int4* __restrict__ items,
+                                                 double* __restrict__ alpha_part) {
+  const int4 it = items[blockIdx.x];
   const BTensor& t = ts[it.x];
   const long long e0 = (long long)it.y * kAlphaChunk;
-  const long long e1 = min((long long)t.I, e0 + kAlphaChunk);
+  const int n = (int)min(kAlphaChunk, t.I - e0);
+  const float* x = t.X + e0;
+  const int n4 = n >> 2;
   double acc = 0.0;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const float v = t.X[e];
+#pragma unroll 4
+  for (int v = threadIdx.x; v < n4; v += blockDim.x) {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(x) + v);
+    acc += (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+  }
+  if ((int)threadIdx.x < n - 4 * n4) {
+    const float v = x[4 * n4 + threadIdx.x];
     acc += (double)(v * v);
   }
   __shared__ double red[32];
@@ -57,7 +55,7 @@ __global__ void k_b_sumsq(const BTensor* __restrict__ ts, const int2* __restrict
 // (lambda = product of the column norms), G_n = H_n^T H_n, S for mode 1,
 // flags and fit history cleared (Alg. 3 initialisation).
 __global__ void k_b_init(BTensor* __restrict__ ts, const double* __restrict__ alpha_part,
-                         const int* __restrict__ alpha_first, double tol, int max_iters) {
+                         const int* __restrict__ alpha_first) {
   BTensor& t = ts[blockIdx.x];
   const int R = t.R, N = t.N, R2 = R * R;
   __shared__ double lam[kBatchMaxRank];
@@ -66,8 +64,7 @@ __global__ void k_b_init(BTensor* __restrict__ ts, const double* __restrict__ al
     double a = 0.0;
     for (int c = alpha_first[blockIdx.x]; c < alpha_first[blockIdx.x + 1]; ++c) a += alpha_part[c];
     t.scal[0] = a;
-    t.scal[1] = tol;
-    t.max_iters = max_iters;
+    t.scal[1] = t.tol;
     t.flags[0] = 0;
     t.flags[1] = 0;
     t.flags[2] = 0;
@@ -316,9 +313,9 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
 
 template <int RMAX>
 __global__ void __launch_bounds__(kThreads, 2)
-k_b_pm_right(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
+k_b_pm_right(const BTensor* __restrict__ ts, const int4* __restrict__ items) {
   extern __shared__ __align__(16) float smem[];
-  const int2 it = items[blockIdx.x];
+  const int4 it = items[blockIdx.x];
   const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
   float* Xs = smem;                // kTileFloats
@@ -332,14 +329,23 @@ k_b_pm_right(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
   }
 }
 
-// M(1) = sum of the chunks' partials in chunk order; CTA per tensor
-__global__ void k_b_reduce_m(const BTensor* __restrict__ ts) {
-  const BTensor& t = ts[blockIdx.x];
+// M = sum of a phase's partial chunks in chunk order.  Item (tensor, block of
+// kReduceBlock outputs, a): a = 0 sums the root -> {1} partials (M(1)),
+// a >= 1 the leaf partials of node {a..N} (M(a)).
+__global__ void __launch_bounds__(kReduceBlock) k_b_reduce(const BTensor* __restrict__ ts,
+                                                           const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
-  const int E = (int)t.dims[0] * t.R;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+  const int a = it.z;
+  const int E = (int)t.dims[a] * t.R;
+  const int nparts = a == 0 ? t.nchunk : t.leaf_nkc[a];
+  const float* src = a == 0 ? t.part : t.lpart;
+  const int e = it.y * kReduceBlock + threadIdx.x;
+  if (e < E) {
     float s = 0.0f;
-    for (int c = 0; c < t.nchunk; ++c) s += t.part[(long long)c * E + e];
+#pragma unroll 4
+    for (int c = 0; c < nparts; ++c) s += src[(long long)c * E + e];
     t.M[e] = s;
   }
 }
@@ -465,9 +471,9 @@ __device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* 
 
 template <int RMAX>
 __global__ void __launch_bounds__(kThreads, 2)
-k_b_pm_left(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
+k_b_pm_left(const BTensor* __restrict__ ts, const int4* __restrict__ items) {
   extern __shared__ __align__(16) float smem[];
-  const int2 it = items[blockIdx.x];
+  const int4 it = items[blockIdx.x];
   const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
   float* Xs = smem;                                // rows at odd stride
@@ -484,76 +490,116 @@ k_b_pm_left(const BTensor* __restrict__ ts, const int2* __restrict__ items) {
 
 // ---------------------------------------------------------- multi-TTVs --
 
-// leaf M(a) from node {a..N}: M(i, r) = sum_k T[(i + I_a k) R + r] KK(k, r),
-// KK = H_N (.) ... (.) H_{a+1}; CTA per tensor, threads over (i, r).
-__global__ void k_b_mttv_leaf(const BTensor* __restrict__ ts, int a) {
-  const BTensor& t = ts[blockIdx.x];
+// leaf M(a) from node {a..N} (Fig. 1): M(i, r) = sum_k T[(i + I_a k) R + r] KK(k, r),
+// KK = H_N (.) ... (.) H_{a+1}.  Item (tensor, chunk c of leaf_kc[a] rows k,
+// block of kLeafBlock outputs).  For each k the node slice of all (i, r) is
+// contiguous, so thread = output e = i R + r reads it coalesced; KK rows are
+// formed per tile of kLeafTileK rows in shared memory.  Writes lpart[c].
+__global__ void __launch_bounds__(256) k_b_mttv_leaf(const BTensor* __restrict__ ts,
+                                                     const int4* __restrict__ items, int a) {
+  const int4 it = items[blockIdx.x];
+  const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
+  __shared__ float KKs[kLeafTileK * kBatchMaxRank];
+  const int tid = threadIdx.x;
   const int R = t.R, N = t.N;
-  const int Ia = (int)t.dims[a];
-  long long K = 1;
-  for (int m = a + 1; m < N; ++m) K *= t.dims[m];
+  const int E = (int)t.dims[a] * R;
+  int K = 1;
+  for (int m = a + 1; m < N; ++m) K *= (int)t.dims[m];
+  const int kc = t.leaf_kc[a];
+  const int k0 = it.y * kc, k1 = min(K, k0 + kc);
+  int ep[4], rp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ep[q] = it.z * kLeafBlock + tid + 256 * q;
+    rp[q] = ep[q] % R;
+  }
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   const float* T = t.node[a];
-  __shared__ int offs[kTileJ][kMaxModes];
-  __shared__ float Ws[kTileJ][kBatchMaxRank];
-  const int E = Ia * R;
-  for (int eb = 0; eb < E; eb += 4 * (int)blockDim.x) {
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // outputs eb + threadIdx.x + q * blockDim
-    for (long long k0 = 0; k0 < K; k0 += kTileJ) {
-      const int nk = (int)min((long long)kTileJ, K - k0);
-      if (threadIdx.x < nk) krp_offsets(t, a + 1, N, k0 + threadIdx.x, offs[threadIdx.x]);
-      __syncthreads();
-      for (int e = threadIdx.x; e < kTileJ * R; e += blockDim.x) {
-        const int kk = e / R, r = e % R;
-        float w = 0.0f;
-        if (kk < nk) {
-          w = 1.0f;
-          for (int m = a + 1; m < N; ++m) w *= t.H[m][offs[kk][m - a - 1] + r];
-        }
-        Ws[kk][r] = w;
-      }
-      __syncthreads();
+  for (int kt = k0; kt < k1; kt += kLeafTileK) {
+    const int nk = min(kLeafTileK, k1 - kt);
+    __syncthreads();
+    // KK rows of the tile: entries x = kk R + r < nk R <= 4096, four per thread at a time
+    for (int x0 = tid; x0 < nk * R; x0 += 4 * 256) {
+      float w[4];
+      int rem[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = eb + threadIdx.x + q * blockDim.x;
-        if (e < E) {
-          const int r = e % R;
-          const float* tp = T + k0 * (long long)E + e;
-          float s = acc[q];
-          for (int kk = 0; kk < nk; ++kk) s = fmaf(tp[(long long)kk * E], Ws[kk][r], s);
-          acc[q] = s;
+      for (int u = 0; u < 4; ++u) {
+        rem[u] = kt + (x0 + 256 * u) / R;
+        w[u] = 1.0f;
+      }
+      for (int m = a + 1; m < N; ++m) {
+        const int dm = (int)t.dims[m];
+        const float* Hm = t.H[m];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int x = x0 + 256 * u;
+          if (x < nk * R) {
+            const int jm = rem[u] % dm;
+            rem[u] /= dm;
+            w[u] *= __ldg(Hm + jm * R + x % R);
+          }
         }
       }
-      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int x = x0 + 256 * u;
+        if (x < nk * R) KKs[x] = w[u];
+      }
     }
+    __syncthreads();
+    const float* Tb = T + (long long)kt * E;
+#pragma unroll 4
+    for (int kk = 0; kk < nk; ++kk) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = eb + threadIdx.x + q * blockDim.x;
-      if (e < E) t.M[e] = acc[q];
+      for (int q = 0; q < 4; ++q)
+        if (ep[q] < E) acc[q] = fmaf(Tb[(long long)kk * E + ep[q]], KKs[kk * R + rp[q]], acc[q]);
     }
   }
+  float* out = t.lpart + (long long)it.y * E;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (ep[q] < E) out[ep[q]] = acc[q];
 }
 
 // child node {a+1..N} from node {a..N}: out(j, r) = sum_i T[(i + I_a j) R + r] H_a(i, r)
-// (the updated H_a); output is M when the child is a leaf.  CTA per tensor.
-__global__ void k_b_mttv_first(const BTensor* __restrict__ ts, int a) {
-  const BTensor& t = ts[blockIdx.x];
+// with the updated H_a; the output is M when the child is a leaf.  Item
+// (tensor, block of first_jb[a] rows j); warp per row j: lanes = (i phase,
+// rank) read the row's I_a x R block coalesced, then add their i phases in
+// a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_b_mttv_first(const BTensor* __restrict__ ts,
+                                                      const int4* __restrict__ items, int a) {
+  const int4 it = items[blockIdx.x];
+  const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
   const int R = t.R, N = t.N;
   const int Ia = (int)t.dims[a];
-  long long Jn = 1;
-  for (int m = a + 1; m < N; ++m) Jn *= t.dims[m];
+  const int E = Ia * R;
+  int K = 1;
+  for (int m = a + 1; m < N; ++m) K *= (int)t.dims[m];
+  const int jb = t.first_jb[a];
+  const int j0 = it.y * jb, j1 = min(K, j0 + jb);
   const float* T = t.node[a];
   float* out = (a + 1 == N - 1) ? t.M : t.node[a + 1];
   const float* Ha = t.H[a];
-  const long long E = Jn * R;
-  for (long long e = threadIdx.x; e < E; e += blockDim.x) {
-    const long long j = e / R;
-    const int r = (int)(e % R);
-    const float* tp = T + (j * Ia) * R + r;
-    float s = 0.0f;
-    for (int i = 0; i < Ia; ++i) s = fmaf(tp[(long long)i * R], Ha[i * R + r], s);
-    out[e] = s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int rb = 0; rb < R; rb += 32) {
+    const int Rb = min(32, R - rb), S = 32 / Rb;
+    const int sub = lane / Rb, r = rb + lane - sub * Rb;
+    const bool act = sub < S;
+    for (int j = j0 + warp; j < j1; j += nwarp) {
+      const float* Tj = T + (long long)j * E;
+      float acc = 0.0f;
+      if (act) {
+#pragma unroll 4
+        for (int i = sub; i < Ia; i += S) acc = fmaf(Tj[i * R + r], __ldg(Ha + i * R + r), acc);
+      }
+      for (int o = 1; o < S; o <<= 1) {
+        const float v = __shfl_down_sync(0xffffffffu, acc, o * Rb);
+        if (act && (sub & (2 * o - 1)) == 0 && sub + o < S) acc += v;
+      }
+      if (act && sub == 0) out[(long long)j * R + r] = acc;
+    }
   }
 }
 
@@ -721,57 +767,81 @@ cudaError_t batch_attributes_init() {
   return e;
 }
 
-cudaError_t launch_b_init(BTensor* ts, int count, const int2* alpha_items, int n_alpha_items,
-                          double* alpha_part, const int* alpha_first, double tol, int max_iters,
-                          cudaStream_t st) {
-  if (n_alpha_items > 0) k_b_sumsq<<<n_alpha_items, 256, 0, st>>>(ts, alpha_items, alpha_part);
-  k_b_init<<<count, 256, 0, st>>>(ts, alpha_part, alpha_first, tol, max_iters);
-  return cudaGetLastError();
-}
+namespace {
 
-cudaError_t launch_b_pm_right(int rmax, const BTensor* ts, const int2* items, int n_items,
-                              int count, cudaStream_t st) {
+cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, cudaStream_t st) {
   const size_t sm = (size_t)(kTileFloats + kWsFloats) * sizeof(float);
-  if (n_items > 0) {
-    if (rmax <= 16) k_b_pm_right<16><<<n_items, kThreads, sm, st>>>(ts, items);
-    else if (rmax <= 32) k_b_pm_right<32><<<n_items, kThreads, sm, st>>>(ts, items);
-    else k_b_pm_right<64><<<n_items, kThreads, sm, st>>>(ts, items);
+  const int n = p.pmr.count;
+  const int4* it = items + p.pmr.off;
+  if (n > 0) {
+    if (p.rmax <= 16) k_b_pm_right<16><<<n, kThreads, sm, st>>>(ts, it);
+    else if (p.rmax <= 32) k_b_pm_right<32><<<n, kThreads, sm, st>>>(ts, it);
+    else k_b_pm_right<64><<<n, kThreads, sm, st>>>(ts, it);
   }
-  k_b_reduce_m<<<count, 256, 0, st>>>(ts);
+  if (p.pmr_red.count > 0)
+    k_b_reduce<<<p.pmr_red.count, kReduceBlock, 0, st>>>(ts, items + p.pmr_red.off);
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_pm_left(int rmax, const BTensor* ts, const int2* items, int n_items,
-                             int hs_floats, cudaStream_t st) {
-  if (n_items == 0) return cudaSuccess;
-  const size_t sm = (size_t)(left_fixed_floats() + hs_floats) * sizeof(float);
-  if (rmax <= 16) k_b_pm_left<16><<<n_items, kThreads, sm, st>>>(ts, items);
-  else if (rmax <= 32) k_b_pm_left<32><<<n_items, kThreads, sm, st>>>(ts, items);
-  else k_b_pm_left<64><<<n_items, kThreads, sm, st>>>(ts, items);
+cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, cudaStream_t st) {
+  const int n = p.pml.count;
+  if (n == 0) return cudaSuccess;
+  const int4* it = items + p.pml.off;
+  const size_t sm = (size_t)(left_fixed_floats() + p.hs_floats) * sizeof(float);
+  if (p.rmax <= 16) k_b_pm_left<16><<<n, kThreads, sm, st>>>(ts, it);
+  else if (p.rmax <= 32) k_b_pm_left<32><<<n, kThreads, sm, st>>>(ts, it);
+  else k_b_pm_left<64><<<n, kThreads, sm, st>>>(ts, it);
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_mttv_leaf(const BTensor* ts, int count, int a, cudaStream_t st) {
-  k_b_mttv_leaf<<<count, 256, 0, st>>>(ts, a);
+cudaError_t launch_update(const BPlan& p, BTensor* ts, int n, int* done_count, cudaStream_t st) {
+  if (p.rmax <= 16) k_b_update<16><<<p.count, 256, update_smem<16>(), st>>>(ts, n, done_count);
+  else if (p.rmax <= 32) k_b_update<32><<<p.count, 256, update_smem<32>(), st>>>(ts, n, done_count);
+  else k_b_update<64><<<p.count, 256, update_smem<64>(), st>>>(ts, n, done_count);
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_mttv_first(const BTensor* ts, int count, int a, cudaStream_t st) {
-  k_b_mttv_first<<<count, 256, 0, st>>>(ts, a);
+}  // namespace
+
+cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double* alpha_part,
+                          const int* alpha_first, cudaStream_t st) {
+  if (p.count == 0) return cudaSuccess;
+  if (p.alpha.count > 0)
+    k_b_sumsq<<<p.alpha.count, 256, 0, st>>>(ts, items + p.alpha.off, alpha_part);
+  k_b_init<<<p.count, 256, 0, st>>>(ts, alpha_part, alpha_first);
   return cudaGetLastError();
+}
+
+cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, int* done_count,
+                               cudaStream_t st) {
+  if (p.count == 0) return cudaSuccess;
+  const int N = p.N;
+  cudaError_t e = launch_pm_right(p, ts, items, st);
+  if (e == cudaSuccess) e = launch_update(p, ts, 0, done_count, st);
+  if (e == cudaSuccess) e = launch_pm_left(p, ts, items, st);
+  // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
+  for (int a = 1; a < N && e == cudaSuccess; ++a) {
+    if (a == N - 1) {
+      e = launch_update(p, ts, a, done_count, st);
+      break;
+    }
+    if (p.leaf[a].count > 0)
+      k_b_mttv_leaf<<<p.leaf[a].count, 256, 0, st>>>(ts, items + p.leaf[a].off, a);
+    if (p.leaf_red[a].count > 0)
+      k_b_reduce<<<p.leaf_red[a].count, kReduceBlock, 0, st>>>(ts, items + p.leaf_red[a].off);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_update(p, ts, a, done_count, st);
+    if (e == cudaSuccess && p.first[a].count > 0) {
+      k_b_mttv_first<<<p.first[a].count, 256, 0, st>>>(ts, items + p.first[a].off, a);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
 }
 
 cudaError_t launch_b_gather(const BTensor* ts, int count, int* iters, double* fits,
                             double* lam, const int* lam_off, int* nonfinite, cudaStream_t st) {
   k_b_gather<<<(count + 255) / 256, 256, 0, st>>>(ts, count, iters, fits, lam, lam_off, nonfinite);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_b_update(int rmax, BTensor* ts, int count, int n, int* done_count,
-                            cudaStream_t st) {
-  if (rmax <= 16) k_b_update<16><<<count, 256, update_smem<16>(), st>>>(ts, n, done_count);
-  else if (rmax <= 32) k_b_update<32><<<count, 256, update_smem<32>(), st>>>(ts, n, done_count);
-  else k_b_update<64><<<count, 256, update_smem<64>(), st>>>(ts, n, done_count);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nncp_internal.cuh"
 
 namespace nncp {
@@ -46,7 +48,15 @@ __host__ __device__ inline int b_rqb_left(int I1, int R) {
   return q;
 }
 
+// Other phases: elements of a tensor (or of a dimension-tree node) per work item.
+constexpr int kItemElems = 65536;
+constexpr int kMaxChunks = 256;       // partial-sum chunks per tensor and phase
+constexpr int kLeafTileK = 64;        // rows k per Khatri-Rao tile of a leaf multi-TTV
+constexpr int kLeafBlock = 1024;      // outputs (i, r) per leaf item
+constexpr int kReduceBlock = 256;     // outputs per reduction item
+
 // One tensor of a batch: shapes, caller buffers, and its slice of the workspace.
+// Everything below `X` is laid out by b_tensor_layout from the shape alone.
 struct BTensor {
   int N, R;
   int64_t dims[kMaxModes];
@@ -56,11 +66,16 @@ struct BTensor {
   float* node[kMaxModes];  // node {d..N} (0-based d = 1..N-2); node[1] = M when N = 2
   float* M;             // max_n I_n x R
   float* part;          // root -> {1} partials: nchunk x I_1 x R
+  float* lpart;         // leaf partials: leaf_nkc[a] x I_a x R
   long long jchunk;     // columns of X_(1) per partial chunk (multiple of rows_r)
   int nchunk;
   int rows_r, rows_l;   // tile rows of the root -> {1} / root -> {2..N} kernels
+  int leaf_kc[kMaxModes];   // rows k per leaf chunk of node {a..N}
+  int leaf_nkc[kMaxModes];  // leaf chunks of node {a..N}
+  int first_jb[kMaxModes];  // rows j per item of node {a..N} -> node {a+1..N}
   int fit_cap;          // fit history slots
-  int max_iters;
+  int max_iters;        // stopping rule (set by the host before init)
+  double tol;
   double* G;            // N x R x R
   double* S;            // R x R
   float* S32;           // R x R
@@ -70,18 +85,33 @@ struct BTensor {
   int* flags;           // [0] done, [1] iterations, [2] non-finite fit
 };
 
+// Work lists of one batch composition: every phase of the iteration is one
+// launch over a contiguous range of (tensor, y, z, 0) items.
+struct BPhase {
+  int off = 0, count = 0;
+};
+struct BPlan {
+  int count = 0, N = 0, rmax = 16, hs_floats = 0;
+  std::vector<int4> items;
+  BPhase alpha, pmr, pmr_red, pml;
+  BPhase leaf[kMaxModes], leaf_red[kMaxModes], first[kMaxModes];
+  std::vector<int> alpha_first;  // per tensor, into the alpha phase (count + 1 entries)
+  std::vector<int> lam_off;      // per tensor, into a packed lambda array
+  size_t lam_total = 0;
+};
+
+// Lays out one tensor's slice (node buffers, M, partials, state) at `base`
+// (sizes only when base is NULL) and fills the shape-derived fields of *d.
+size_t b_tensor_layout(int N, const int64_t* dims, int R, int fit_cap, BTensor* d, char* base);
+void b_build_plan(const BTensor* ts, int count, int N, BPlan* p);
+
 cudaError_t batch_attributes_init();
-cudaError_t launch_b_init(BTensor* ts, int count, const int2* alpha_items, int n_alpha_items,
-                          double* alpha_part, const int* alpha_first, double tol, int max_iters,
-                          cudaStream_t st);
-cudaError_t launch_b_pm_right(int rmax, const BTensor* ts, const int2* items, int n_items,
-                              int count, cudaStream_t st);
-cudaError_t launch_b_pm_left(int rmax, const BTensor* ts, const int2* items, int n_items,
-                             int hs_floats, cudaStream_t st);
-cudaError_t launch_b_mttv_leaf(const BTensor* ts, int count, int a, cudaStream_t st);
-cudaError_t launch_b_mttv_first(const BTensor* ts, int count, int a, cudaStream_t st);
-cudaError_t launch_b_update(int rmax, BTensor* ts, int count, int n, int* done_count,
-                            cudaStream_t st);
+// alpha, normalisation, Grams and S of every tensor of the plan
+cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double* alpha_part,
+                          const int* alpha_first, cudaStream_t st);
+// one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1)
+cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, int* done_count,
+                               cudaStream_t st);
 // per tensor: iterations, last fit, lambda into contiguous arrays
 cudaError_t launch_b_gather(const BTensor* ts, int count, int* iters, double* fits,
                             double* lam, const int* lam_off, int* nonfinite, cudaStream_t st);

@@ -88,3 +88,48 @@ def test_batch_rejects_out_of_range_shapes(nn):
         nn.Batch([(300, 4, 4)], [4], max_iters=4)   # mode longer than 256
     with pytest.raises(nn.NNCPError):
         nn.Batch([(10, 4, 4)], [65], max_iters=4)   # rank above 64
+
+
+def test_batch_wide_ranks_and_long_modes(nn):
+    # ranks up to 64 (the widest kernel instances), a 256-long first mode and
+    # ragged shapes; checked against the oracle after a few iterations
+    rng = np.random.default_rng(77)
+    probs = []
+    for t, (dims, R) in enumerate([((256, 9, 7), 5), ((33, 40, 17), 64), ((70, 3, 130), 33),
+                                   ((1, 50, 60), 12), ((129, 64, 5), 20)]):
+        x, _ = synth.lowrank_plus_noise(dims, R, seed=3000 + t, noise=0.01)
+        probs.append((dims, R, x, synth.init_factors(dims, R, seed=4000 + t)))
+    iters = 5
+    k, fits, lams, Hs = _run_batch(nn, probs, iters)
+    for t, (dims, R, x, H0) in enumerate(probs):
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=iters, use_dimtree=True, s=1)
+        assert abs(fits[t] - ref["fits"][-1]) <= 1e-4, (t, dims, R)
+        for n in range(3):
+            assert rel_fro(Hs[t][n], ref["H"][n]) <= 1e-3, (t, n)
+
+
+@pytest.mark.parametrize("N,lo,hi", [(4, 6, 30), (5, 3, 12)])
+def test_batch_higher_orders_larger_nodes(nn, N, lo, hi):
+    probs = _problems(5, seed0=40 + N, N=N, lo=lo, hi=hi, ranks=(3, 16, 40))
+    iters = 4
+    k, fits, lams, Hs = _run_batch(nn, probs, iters)
+    for t, (dims, R, x, H0) in enumerate(probs):
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=iters, use_dimtree=True, s=1)
+        assert abs(fits[t] - ref["fits"][-1]) <= 1e-4, (t, dims, R)
+        for n in range(N):
+            assert rel_fro(Hs[t][n], ref["H"][n]) <= 1e-3, (t, n)
+
+
+def test_batch_bits_do_not_depend_on_the_widest_rank(nn):
+    # the same small-rank tensor alone (16-wide kernels) and beside an R=64
+    # tensor (64-wide kernels) gives the same bits
+    small = _problems(2, seed0=91, ranks=(4,))
+    wide = _problems(1, seed0=92, ranks=(64,))
+    k1, f1, l1, H1 = _run_batch(nn, small, 6)
+    k2, f2, l2, H2 = _run_batch(nn, small + wide, 6)
+    for t in range(2):
+        assert k1[t] == k2[t] and f1[t] == f2[t] and l1[t] == l2[t]
+        for a, b in zip(H1[t], H2[t]):
+            assert np.array_equal(a, b)
