@@ -216,6 +216,67 @@ nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* 
                                 const float* const* H_dev, int mode, float* M_dev,
                                 void* stream);
 
+/* ---- Server: continuous batching of independent solve requests ----------
+ * The serving form of the batched solver (same iteration, same limits:
+ * order 2..8, modes of 1..256, rank 1..64, at most 2^31 - 1 elements; the
+ * paper has no counterpart -- each request is one NNCP-HALS problem of
+ * Alg. 1 / Alg. 3 with root split 1).  A worker thread owns one device pool
+ * of hbm_budget_bytes, taken with cudaMalloc at create on the device current
+ * then.  Requests wait in submission order; the one at the head is admitted
+ * when its footprint (tensor, factors, dimension-tree nodes, partial sums and
+ * solver state: nncp_server_footprint) fits in the pool and fewer than
+ * max_slots requests are active; admission copies its tensor and initial
+ * factors to the device.  Between two sweeps the active set may change; one
+ * sweep advances every active request by one outer iteration; a request
+ * leaves when its own stopping rule holds (|fit_k - fit_{k-1}| < tol, or
+ * max_iters), its factors and lambda are copied back and its pool space is
+ * freed.  A request's results are the same bits whatever else is active.
+ * No call blocks without a bound: submit copies and returns, wait gives up
+ * after timeout_ms. */
+typedef struct nncp_server nncp_server;
+typedef struct {
+  int N;                            /* order */
+  const int64_t* dims;              /* N mode lengths */
+  int R;                            /* rank */
+  const float* X_host;              /* I_1...I_N floats, mode-1 fastest; copied by submit */
+  const float* const* H_init_host;  /* N pointers, I_n x R row-major; copied by submit */
+  int max_iters;                    /* 1..65536 */
+  double tol;                       /* stop when |fit_k - fit_{k-1}| < tol */
+} nncp_request;
+typedef struct {
+  nncp_status status;       /* NNCP_OK, NNCP_ERR_NUMERIC (non-finite fit) or NNCP_ERR_CUDA */
+  int iters;                /* outer iterations run */
+  double fit;               /* 1 - eps of the last iteration (Sec. IV-B identity) */
+  const double* lambda;     /* R weights, server-owned until nncp_server_release */
+  const float* const* H;    /* N column-normalised factors, I_n x R row-major, server-owned */
+  double t_submit, t_admit, t_done;  /* seconds on the server clock */
+} nncp_result;
+typedef struct {
+  uint64_t submitted, completed, sweeps;
+  int active, queued, peak_active;
+  size_t budget, bytes_in_use, peak_bytes_in_use;
+} nncp_server_stats;
+/* max_slots >= 1: most requests active at once. */
+nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_server** out);
+/* Device bytes a request takes from the pool (NNCP_ERR_INVALID_ARG if its
+ * shape is outside the limits). */
+nncp_status nncp_server_footprint(int N, const int64_t* dims, int R, int max_iters, size_t* bytes);
+/* Copies the request; *ticket identifies it.  NNCP_ERR_INVALID_ARG if the
+ * shape is outside the limits or the footprint exceeds the budget. */
+nncp_status nncp_server_submit(nncp_server* s, const nncp_request* req, uint64_t* ticket);
+/* NNCP_ERR_NOT_READY until the request is done; then fills *res. */
+nncp_status nncp_server_poll(nncp_server* s, uint64_t ticket, nncp_result* res);
+/* Waits at most timeout_ms (>= 0): NNCP_ERR_TIMEOUT if still not done. */
+nncp_status nncp_server_wait(nncp_server* s, uint64_t ticket, int timeout_ms, nncp_result* res);
+/* Frees a done request's results (its pointers in nncp_result die). */
+nncp_status nncp_server_release(nncp_server* s, uint64_t ticket);
+nncp_status nncp_server_get_stats(nncp_server* s, nncp_server_stats* st);
+/* Seconds since create on the clock of the t_* fields. */
+double nncp_server_clock(const nncp_server* s);
+const char* nncp_server_last_error(const nncp_server* s);
+/* Stops the worker after its current sweep; pending requests are dropped. */
+void nncp_server_destroy(nncp_server* s);
+
 const char* nncp_last_error(const nncp_ctx* ctx);
 /* Message of the last failure of a call that had no context to record it in. */
 const char* nncp_global_error(void);

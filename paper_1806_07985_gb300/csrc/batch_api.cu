@@ -420,7 +420,7 @@ nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iter
   BCK(cudaStreamWaitEvent(user, ev, 0));
   cudaEventDestroy(ev);
   for (int t = 0; t < b->count; ++t)
-    if (nf[t]) return bfail(b, NNCP_ERR_NUMERIC, "tensor %d: non-finite fit", t);
+    if (nf[t] & 1) return bfail(b, NNCP_ERR_NUMERIC, "tensor %d: non-finite fit", t);
   return NNCP_OK;
 }
 

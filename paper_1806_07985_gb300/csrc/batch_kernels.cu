@@ -734,7 +734,7 @@ __global__ void k_b_gather(const BTensor* __restrict__ ts, int count, int* iters
     const int k = t.flags[1];
     iters[b] = k;
     fits[b] = (k >= 1 && k <= t.fit_cap) ? t.fits[k - 1] : 0.0;
-    nonfinite[b] = t.flags[2];
+    nonfinite[b] = (t.flags[2] ? 1 : 0) | (t.flags[0] ? 2 : 0);  // bit 0 non-finite, bit 1 done
     if (lam)
       for (int r = 0; r < t.R; ++r) lam[lam_off[b] + r] = t.lam[r];
   }

@@ -112,7 +112,8 @@ cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double
 // one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1)
 cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, int* done_count,
                                cudaStream_t st);
-// per tensor: iterations, last fit, lambda into contiguous arrays
+// per tensor: iterations, last fit, lambda into contiguous arrays, and a state
+// word (bit 0: non-finite fit, bit 1: stopped)
 cudaError_t launch_b_gather(const BTensor* ts, int count, int* iters, double* fits,
                             double* lam, const int* lam_off, int* nonfinite, cudaStream_t st);
 

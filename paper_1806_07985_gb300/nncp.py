@@ -71,6 +71,17 @@ _SIGNATURES = [
                                         _c_dblp, ctypes.c_void_p]),
     ("nncp_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_batch_destroy", None, [ctypes.c_void_p]),
+    ("nncp_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("nncp_server_footprint", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    ("nncp_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    ("nncp_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    ("nncp_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_server_release", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("nncp_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("nncp_server_clock", ctypes.c_double, [ctypes.c_void_p]),
+    ("nncp_server_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("nncp_server_destroy", None, [ctypes.c_void_p]),
     ("nncp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_global_error", ctypes.c_char_p, []),
     ("nncp_destroy", None, [ctypes.c_void_p]),
@@ -301,6 +312,115 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("dims", _c_i64p), ("R", ctypes.c_int),
+                ("X_host", ctypes.c_void_p), ("H_init_host", _c_vpp),
+                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("fit", ctypes.c_double),
+                ("lam", _c_dblp), ("H", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("sweeps", ctypes.c_uint64), ("active", ctypes.c_int), ("queued", ctypes.c_int),
+                ("peak_active", ctypes.c_int), ("budget", ctypes.c_size_t),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes_in_use", ctypes.c_size_t)]
+
+
+def nncp_server_footprint(dims, R, max_iters):
+    n = ctypes.c_size_t()
+    _check(load().nncp_server_footprint(len(dims), _dims(dims), int(R), int(max_iters),
+                                        ctypes.byref(n)))
+    return n.value
+
+
+class Server:
+    """Serving loop over host numpy arrays (argument marshalling only).
+
+    submit() copies the request into the library and returns a ticket;
+    poll()/wait() return None / raise TimeoutError until the request is done,
+    then a dict with the status, iterations, fit, lambda, factors (numpy
+    copies) and the submit/admit/done times on the server clock."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        self.s = ctypes.c_void_p()
+        _scheck(load().nncp_server_create(int(hbm_budget_bytes), int(max_slots),
+                                          ctypes.byref(self.s)), None)
+        self._shapes = {}
+
+    def submit(self, dims, R, X, H, max_iters, tol):
+        import numpy as np
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1)
+        H = [np.ascontiguousarray(h, dtype=np.float32) for h in H]
+        d = _dims(dims)
+        hp = (ctypes.c_void_p * len(H))(*[h.ctypes.data for h in H])
+        req = _Request(len(dims), ctypes.cast(d, _c_i64p), int(R), X.ctypes.data,
+                       ctypes.cast(hp, _c_vpp), int(max_iters), float(tol))
+        t = ctypes.c_uint64()
+        _scheck(load().nncp_server_submit(self.s, ctypes.byref(req), ctypes.byref(t)), self.s)
+        self._shapes[t.value] = (tuple(int(x) for x in dims), int(R))
+        return t.value
+
+    def _result(self, ticket, res):
+        import numpy as np
+        dims, R = self._shapes[ticket]
+        H = [np.ctypeslib.as_array(res.H[n], shape=(dims[n], R)).copy() for n in range(len(dims))]
+        lam = np.ctypeslib.as_array(res.lam, shape=(R,)).copy() if res.lam else None
+        return {"status": res.status, "iters": res.iters, "fit": res.fit, "lambda": lam, "H": H,
+                "t_submit": res.t_submit, "t_admit": res.t_admit, "t_done": res.t_done}
+
+    def poll(self, ticket):
+        res = _Result()
+        st = load().nncp_server_poll(self.s, ticket, ctypes.byref(res))
+        if st == NNCP_ERR_NOT_READY:
+            return None
+        _scheck(st, self.s)
+        return self._result(ticket, res)
+
+    def wait(self, ticket, timeout_ms):
+        res = _Result()
+        st = load().nncp_server_wait(self.s, ticket, int(timeout_ms), ctypes.byref(res))
+        if st == NNCP_ERR_TIMEOUT:
+            raise TimeoutError(f"request {ticket} not done after {timeout_ms} ms")
+        _scheck(st, self.s)
+        return self._result(ticket, res)
+
+    def release(self, ticket):
+        _scheck(load().nncp_server_release(self.s, ticket), self.s)
+        self._shapes.pop(ticket, None)
+
+    def stats(self):
+        st = _Stats()
+        _scheck(load().nncp_server_get_stats(self.s, ctypes.byref(st)), self.s)
+        return {k: getattr(st, k) for k, _ in _Stats._fields_}
+
+    def clock(self):
+        return load().nncp_server_clock(self.s)
+
+    def close(self):
+        if self.s:
+            load().nncp_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scheck(status, s):
+    if status != NNCP_OK:
+        lib = load()
+        msg = lib.nncp_server_last_error(s) if s else lib.nncp_global_error()
+        raise NNCPError(status, (msg or b"").decode())
 
 
 def nncp_last_error(ctx):
