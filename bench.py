@@ -60,6 +60,12 @@ def parse():
                    help="pm: only the two root partial MTTKRPs, for kernel profiling")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the 4096-tensor batched solve (context line 'batched')")
+    p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--no-serving", action="store_true",
+                   help="skip the serving-loop sample (context line 'serving')")
+    p.add_argument("--serve-requests", type=int, default=32)
     return p.parse_args()
 
 
@@ -278,6 +284,10 @@ def run_ours(args):
         result["e2e"] = run_e2e(nncp, torch, x, H0, prec, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(x, H0)
+    if rank == 0 and world == 1 and not args.no_batched:
+        result["batched"] = run_batched(nncp, torch, args.batch_count)
+    if rank == 0 and world == 1 and not args.no_serving:
+        result["serving"] = run_serving(nncp, torch, args.serve_requests)
     if rank == 0:
         print(json.dumps(result), flush=True)
     ctx.close()
@@ -323,6 +333,168 @@ def cpu_baseline(x, H0):
             "sample": "one outer iteration (with initialisation) of the 512^3 R=32 solve, "
                       "FP64 numpy oracle, dimension tree split 1",
             "seconds": round(t, 2)}
+
+
+# ------------------------------------------------- batched and serving lines --
+
+BATCH_ITERS, BATCH_TOL = 200, 1e-5      # stopping rule of the 4096-tensor workload
+SERVE_ITERS, SERVE_TOL = 150, 1e-4      # stopping rule of the serving workload
+
+
+def run_batched(nncp, torch, count):
+    """4096 uneven 3-way tensors (I_n log-uniform in [16, 128], R in {4, 8, 16})
+    solved together to |dfit| < 1e-5 or 200 iterations, against the plain
+    one-problem-at-a-time solver on an evenly spaced sample of 32 of them."""
+    import numpy as np
+
+    from paper_1806_07985_gb300 import synth
+    probs = [synth.batch_problem(t) for t in range(count)]
+    X = [torch.from_numpy(p[2]).cuda() for p in probs]
+    H0 = [[torch.from_numpy(h).cuda() for h in p[3]] for p in probs]
+    H = [[h.clone() for h in hs] for hs in H0]
+    b = nncp.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=BATCH_ITERS)
+    b.set_data(X, H)
+    b.solve(3, 0.0)                      # graph capture and warm-up
+    for hs, h0 in zip(H, H0):
+        for a, c in zip(hs, h0):
+            a.copy_(c)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    iters, fits, _ = b.solve(BATCH_ITERS, BATCH_TOL)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    b.close()
+    elems = [int(np.prod(p[0])) for p in probs]
+    tensor_bytes = sum(2 * 4 * e * k for e, k in zip(elems, iters))
+    sample = list(range(0, count, max(1, count // 32)))[:32]
+    ctxs = []
+    for q in sample:
+        c = nncp.Context(probs[q][0], probs[q][1], precision=nncp.NNCP_FP32_SIMT, root_split=1)
+        c.set_tensor(X[q])
+        ctxs.append(c)
+    Hp = [[h.clone() for h in H0[q]] for q in sample]
+    ctxs[0].set_factors(Hp[0])
+    ctxs[0].solve(3, 0.0)
+    for hs, q in zip(Hp, sample):
+        for a, c in zip(hs, H0[q]):
+            a.copy_(c)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for c, hs in zip(ctxs, Hp):
+        c.set_factors(hs)
+        plain.append(c.solve(BATCH_ITERS, BATCH_TOL))
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    dfit = max(abs(plain[i][2] - fits[q]) for i, q in enumerate(sample))
+    return {"workload": f"{count} 3-way tensors, I_n log-uniform [16,128], R in {{4,8,16}}, "
+                        f"|dfit|<{BATCH_TOL:g} or {BATCH_ITERS} iters, FP32",
+            "solves_per_s": round(count / t, 1), "seconds": round(t, 4),
+            "iters_mean": round(float(np.mean(iters)), 1), "iters_max": int(max(iters)),
+            "tensor_GBps": round(tensor_bytes / t / 1e9, 1),
+            "plain_solves_per_s": round(len(sample) / tp, 2),
+            "plain_sample": len(sample), "speedup": round(count / t / (len(sample) / tp), 1),
+            "max_abs_fit_diff_vs_plain": float(f"{dfit:.3g}")}
+
+
+def _percentiles(v):
+    import numpy as np
+    return {"p50_ms": round(1e3 * float(np.percentile(v, 50)), 2),
+            "p99_ms": round(1e3 * float(np.percentile(v, 99)), 2)}
+
+
+def run_serving(nncp, torch, count):
+    """Sample of the serving workload: requests 0..count-1 (order 3-5, I_n
+    log-uniform [16, 256], at most 64 Mi elements, R in {8, 16, 32, 64},
+    |dfit| < 1e-4 or 150 iterations) through the server: (i) saturation, all
+    submitted at once; (ii) Poisson arrivals at 0.5x and 0.8x of (i)'s rate;
+    latency = result - submit, host copies included.  The plain path runs the
+    same requests one at a time (nncp_solve_host, host copies inside); its
+    latency under the same arrivals is that of a FIFO single server with the
+    measured service times."""
+    import numpy as np
+
+    from paper_1806_07985_gb300 import synth
+    reqs = [synth.serving_request(q) for q in range(count)]
+    elems = [int(np.prod(r[0])) for r in reqs]
+    free = torch.cuda.mem_get_info()[0]
+    budget = int(min(96 << 30, 0.6 * free))
+    slots = count
+
+    def submit_all(srv, arrivals=None):
+        tickets = []
+        t_start = srv.clock()
+        for q, (dims, R, x, H0) in enumerate(reqs):
+            if arrivals is not None:
+                delay = t_start + arrivals[q] - srv.clock()
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(srv.submit(dims, R, x, H0, SERVE_ITERS, SERVE_TOL, precision=prec))
+        out = [srv.wait(t, 600000) for t in tickets]
+        for t in tickets:
+            srv.release(t)
+        return out
+
+    prec = default_precision(nncp)
+    warm = nncp.Server(budget, slots)
+    w = [warm.submit(d, R, x, H0, 3, 0.0, precision=prec) for d, R, x, H0 in reqs[:3]]
+    for t in w:
+        warm.wait(t, 600000)
+    warm.close()
+    srv = nncp.Server(budget, slots)
+    sat = submit_all(srv)
+    span = max(r["t_done"] for r in sat) - min(r["t_submit"] for r in sat)
+    cap = count / span
+    stats = srv.stats()
+    loads = {}
+    for rho in (0.5, 0.8):
+        arr = synth.poisson_arrivals(count, rho * cap, seed=5)
+        arr = arr - arr[0]
+        out = submit_all(srv, arr)
+        loads[rho] = (arr, [r["t_done"] - r["t_submit"] for r in out])
+    srv.close()
+    # the plain path: one request at a time, its best precision per request
+    service, plain_fit, plain_prec = [], [], {}
+    for dims, R, x, H0 in reqs:
+        Xh = torch.from_numpy(x).pin_memory()
+        Hh = [torch.from_numpy(h.copy()).pin_memory() for h in H0]
+        t0 = time.perf_counter()
+        try:
+            name = default_precision(nncp)
+            _, k, f = nncp.nncp_solve_host(dims, R, Xh, Hh, name, 0, SERVE_ITERS, SERVE_TOL)
+        except nncp.NNCPError as e:
+            if e.status != nncp.NNCP_ERR_UNSUPPORTED:
+                raise
+            Hh = [torch.from_numpy(h.copy()).pin_memory() for h in H0]
+            t0 = time.perf_counter()
+            name = "fp32_simt"
+            _, k, f = nncp.nncp_solve_host(dims, R, Xh, Hh, name, 0, SERVE_ITERS, SERVE_TOL)
+        service.append(time.perf_counter() - t0)
+        plain_fit.append(f)
+        plain_prec[name] = plain_prec.get(name, 0) + 1
+    out = {"workload": f"serving requests 0..{count - 1}: order 3-5, I_n log-uniform [16,256], "
+                       f"<= 64Mi elements, R in {{8,16,32,64}}, |dfit|<{SERVE_TOL:g} or "
+                       f"{SERVE_ITERS} iters, FP32",
+           "requests": count, "elements_total": int(sum(elems)),
+           "hbm_budget_bytes": budget, "peak_bytes_in_use": stats["peak_bytes_in_use"],
+           "saturation_solves_per_s": round(cap, 2),
+           "plain_solves_per_s": round(count / sum(service), 2),
+           "plain_precisions": plain_prec,
+           "max_abs_fit_diff_vs_plain": float(f"{max(abs(a['fit'] - b) for a, b in zip(sat, plain_fit)):.3g}")}
+    for rho, (arr, lat) in loads.items():
+        # plain path as a FIFO single server under the same arrivals
+        wait_q, plain_lat = 0.0, []
+        for q in range(count):
+            if q:
+                wait_q = max(0.0, wait_q + service[q - 1] - (arr[q] - arr[q - 1]))
+            plain_lat.append(wait_q + service[q])
+        out[f"load_{rho}"] = {"rate_per_s": round(rho * cap, 2), "server": _percentiles(lat),
+                              "plain_fifo": _percentiles(plain_lat)}
+    return out
 
 
 # ----------------------------------------------------------- reference arm --

@@ -149,7 +149,13 @@ nncp_status nncp_tensor_to_bf16(const float* X_dev, uint16_t* Xb_dev, int64_t n,
 /* One-call solve from HOST buffers: allocates device memory, copies the
  * tensor and initial factors in, solves, copies factors, lambda and fit back.
  * X_host: float32, mode-1 fastest; H_host[n]: I_n x R row-major (in: initial
- * factors, out: normalised result). */
+ * factors, out: normalised result).  A tensor-core precision on a shape it
+ * cannot tile (I_1...I_s times the element size not a multiple of 16 bytes)
+ * runs with mode 1 stored padded by zero slices to a multiple of 4 (8 for
+ * NNCP_BF16_STORED) and H_1 given matching zero rows: a HALS row update with
+ * m = 0 and w = 0 yields 0, so those rows stay zero, add nothing to the Grams,
+ * lambda or the fit, and the iteration is that of the unpadded problem up to
+ * rounding (Sec. II-B update rule).  Only the first I_1 rows are returned. */
 nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_host,
                             float* const* H_host, nncp_precision precision, int root_split,
                             int max_iters, double tol, double* lambda_out, int* iters_out,
@@ -217,22 +223,33 @@ nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* 
                                 void* stream);
 
 /* ---- Server: continuous batching of independent solve requests ----------
- * The serving form of the batched solver (same iteration, same limits:
- * order 2..8, modes of 1..256, rank 1..64, at most 2^31 - 1 elements; the
- * paper has no counterpart -- each request is one NNCP-HALS problem of
- * Alg. 1 / Alg. 3 with root split 1).  A worker thread owns one device pool
- * of hbm_budget_bytes, taken with cudaMalloc at create on the device current
- * then.  Requests wait in submission order; the one at the head is admitted
- * when its footprint (tensor, factors, dimension-tree nodes, partial sums and
- * solver state: nncp_server_footprint) fits in the pool and fewer than
- * max_slots requests are active; admission copies its tensor and initial
- * factors to the device.  Between two sweeps the active set may change; one
- * sweep advances every active request by one outer iteration; a request
- * leaves when its own stopping rule holds (|fit_k - fit_{k-1}| < tol, or
- * max_iters), its factors and lambda are copied back and its pool space is
- * freed.  A request's results are the same bits whatever else is active.
+ * Each request is one NNCP-HALS problem (Alg. 1 with the normalisation and
+ * error steps of Alg. 3, Sec. II-B HALS, Sec. IV-B fit; the paper has no
+ * serving counterpart) within the batched limits: order 2..8, modes of
+ * 1..256, rank 1..64, at most 2^31 - 1 elements.  A worker thread owns one
+ * device pool of hbm_budget_bytes, taken with cudaMalloc at create on the
+ * device current then.  Requests wait in submission order; the one at the
+ * head is admitted when its footprint (nncp_server_footprint: tensor,
+ * factors, dimension-tree nodes, partial sums, solver state) fits in the
+ * pool and fewer than max_slots requests are active; admission copies its
+ * tensor and initial factors to the device.  Between two sweeps the active
+ * set may change; one sweep advances every active request by one outer
+ * iteration; a request leaves when its own stopping rule holds
+ * (|fit_k - fit_{k-1}| < tol, or max_iters), its factors and lambda are
+ * copied back and its pool space is freed.  A request's results are the same
+ * bits whatever else is active.
+ * Two lanes: requests of fewer than NNCP_SERVER_SOLO_ELEMS elements (or the
+ * threshold given to nncp_server_create_ex) share
+ * the batched FP32 iteration of their order (root split 1, the same bits as
+ * nncp_batch_solve); larger ones, which fill the GPU alone, each run the
+ * single-problem solver of nncp_solve on their own stream -- root split by
+ * nncp_default_split, the request's precision (mode 1 padded as in
+ * nncp_solve_host where that lets the tensor-core path tile the shape, FP32
+ * SIMT where nothing does), the same bits as nncp_solve_host with that
+ * precision and root_split 0.
  * No call blocks without a bound: submit copies and returns, wait gives up
  * after timeout_ms. */
+#define NNCP_SERVER_SOLO_ELEMS (1LL << 22)
 typedef struct nncp_server nncp_server;
 typedef struct {
   int N;                            /* order */
@@ -242,6 +259,7 @@ typedef struct {
   const float* const* H_init_host;  /* N pointers, I_n x R row-major; copied by submit */
   int max_iters;                    /* 1..65536 */
   double tol;                       /* stop when |fit_k - fit_{k-1}| < tol */
+  nncp_precision precision;         /* solo lane: NNCP_FP32_SIMT, NNCP_TF32 or NNCP_SPLIT_BF16X3 */
 } nncp_request;
 typedef struct {
   nncp_status status;       /* NNCP_OK, NNCP_ERR_NUMERIC (non-finite fit) or NNCP_ERR_CUDA */
@@ -258,9 +276,14 @@ typedef struct {
 } nncp_server_stats;
 /* max_slots >= 1: most requests active at once. */
 nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_server** out);
+/* As nncp_server_create, with the lane threshold: requests of at least
+ * solo_elems elements (>= 1) take the solo lane. */
+nncp_status nncp_server_create_ex(size_t hbm_budget_bytes, int max_slots, int64_t solo_elems,
+                                  nncp_server** out);
 /* Device bytes a request takes from the pool (NNCP_ERR_INVALID_ARG if its
  * shape is outside the limits). */
-nncp_status nncp_server_footprint(int N, const int64_t* dims, int R, int max_iters, size_t* bytes);
+nncp_status nncp_server_footprint(const nncp_server* s, int N, const int64_t* dims, int R,
+                                  int max_iters, nncp_precision precision, size_t* bytes);
 /* Copies the request; *ticket identifies it.  NNCP_ERR_INVALID_ARG if the
  * shape is outside the limits or the footprint exceeds the budget. */
 nncp_status nncp_server_submit(nncp_server* s, const nncp_request* req, uint64_t* ticket);

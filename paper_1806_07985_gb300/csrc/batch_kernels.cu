@@ -621,11 +621,14 @@ k_b_update(BTensor* __restrict__ ts, int n, int* __restrict__ done_count) {
   extern __shared__ __align__(16) float bsm[];
   float* St = bsm;                 // RMAX x RMAX, St[r][c] = S[c][r], zero padded
   float* Ws = St + RMAX * RMAX;    // kBatchMaxI x RP (W, then H)
+  float* Ms = Ws + kBatchMaxI * RP;  // kBatchMaxI x RP (M)
   __shared__ float lamf[RMAX], sinv[RMAX];
   __shared__ double GW[kBatchMaxRank * kBatchMaxRank];
   __shared__ double cinv[kBatchMaxRank];
   __shared__ double red[8];
   float* Hn = t.H[n];
+  // staging with the global loads of a loop issued in batches
+#pragma unroll 4
   for (int e = tid; e < RMAX * RMAX; e += blockDim.x) {
     const int r = e / RMAX, c = e % RMAX;
     St[e] = (r < R && c < R) ? t.S32[c * R + r] : 0.0f;
@@ -636,30 +639,38 @@ k_b_update(BTensor* __restrict__ ts, int n, int* __restrict__ done_count) {
     sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
   }
   __syncthreads();
+#pragma unroll 4
+  for (int e = tid; e < In * R; e += blockDim.x) {
+    const int i = e / R, c = e - i * R;
+    Ws[i * RP + c] = Hn[e] * lamf[c];
+    Ms[i * RP + c] = t.M[e];
+  }
+  for (int i = tid; i < In; i += blockDim.x)
+    for (int c = R; c < RMAX; ++c) Ws[i * RP + c] = 0.0f;
+  __syncthreads();
   double bp = 0.0;
   for (int i = tid; i < In; i += blockDim.x) {
-    float w[RMAX];
-#pragma unroll
-    for (int c = 0; c < RMAX; ++c) w[c] = c < R ? Hn[i * R + c] * lamf[c] : 0.0f;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
+    // row W(i, :) updated in place in shared memory (odd stride: one bank per
+    // thread); rolled column loop, unrolled dot product (see the HALS sweep
+    // of the single-problem update)
+    float* wrow = Ws + i * RP;
+    const float* mrow = Ms + i * RP;
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
       const float si = sinv[r];
-      const float mr = r < R ? t.M[i * R + r] : 0.0f;
+      const float mr = mrow[r];
       float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
       for (int c = 0; c < RMAX; c += 2) {
-        d0 = fmaf(w[c], St[r * RMAX + c], d0);
-        d1 = fmaf(w[c + 1], St[r * RMAX + c + 1], d1);
+        d0 = fmaf(wrow[c], St[r * RMAX + c], d0);
+        d1 = fmaf(wrow[c + 1], St[r * RMAX + c + 1], d1);
       }
-      const float upd = fmaxf(0.0f, w[r] + (mr - (d0 + d1)) * si);
-      w[r] = si != 0.0f ? upd : w[r];
+      const float wr = wrow[r];
+      const float upd = fmaxf(0.0f, wr + (mr - (d0 + d1)) * si);
+      wrow[r] = si != 0.0f ? upd : wr;
     }
     float b = 0.0f;
-#pragma unroll
-    for (int c = 0; c < RMAX; ++c) {
-      if (c < R) b = fmaf(t.M[i * R + c], w[c], b);
-      Ws[i * RP + c] = w[c];
-    }
+    for (int c = 0; c < R; ++c) b = fmaf(mrow[c], wrow[c], b);
     bp += (double)b;
   }
   for (int o = 16; o > 0; o >>= 1) bp += __shfl_xor_sync(0xffffffffu, bp, o);
@@ -742,7 +753,7 @@ __global__ void k_b_gather(const BTensor* __restrict__ ts, int count, int* iters
 
 template <int RMAX>
 size_t update_smem() {
-  return (size_t)(RMAX * RMAX + kBatchMaxI * (RMAX + 1)) * sizeof(float);
+  return (size_t)(RMAX * RMAX + 2 * kBatchMaxI * (RMAX + 1)) * sizeof(float);
 }
 
 }  // namespace

@@ -362,6 +362,41 @@ void record_global_error(const char* msg) { g_error = msg; }
 
 // =============================== C ABI ======================================
 
+namespace nncp {
+
+int ctx_solve_begin_tol(nncp_ctx* c, double tol) {
+  nncp_status s = check_ready(c);
+  if (s != NNCP_OK) return s;
+  if ((s = begin_on_work(c)) != NNCP_OK) return s;
+  if ((s = solve_init(c, tol)) != NNCP_OK) return s;
+  if ((s = ensure_graph(c)) != NNCP_OK) return s;
+  return end_on_work(c);
+}
+
+int64_t tc_padded_mode1(int precision, int N, const int64_t* dims, int R, int root_split) {
+  if (precision != NNCP_TF32 && precision != NNCP_SPLIT_BF16X3 && precision != NNCP_BF16_STORED)
+    return dims[0];
+  if (N < 2 || N > kMaxModes) return dims[0];
+  const int s0 = root_split ? root_split : nncp_default_split(N, dims);
+  if (!tc_unsupported_reason(precision, N, dims, R, s0)) return dims[0];
+  const int64_t q = precision == NNCP_BF16_STORED ? 8 : 4;
+  int64_t pd[kMaxModes];
+  for (int n = 0; n < N; ++n) pd[n] = dims[n];
+  pd[0] = (dims[0] + q - 1) / q * q;
+  const int s1 = root_split ? root_split : nncp_default_split(N, pd);
+  return tc_unsupported_reason(precision, N, pd, R, s1) ? dims[0] : pd[0];
+}
+
+void ctx_device_state(const nncp_ctx* c, const int** flags, const double** lam,
+                      const double** fits, const int** tc_error) {
+  *flags = c->st.flags;
+  *lam = c->st.lam;
+  *fits = c->st.fits;
+  *tc_error = c->tc.bytes ? tc_error_word(c->tc) : nullptr;
+}
+
+}  // namespace nncp
+
 extern "C" {
 
 const char* nncp_version(void) {
@@ -668,8 +703,15 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
                             int max_iters, double tol, double* lambda_out, int* iters_out,
                             double* fit_out) {
   if (!X_host || !H_host) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null host buffer");
+  if (N < 2 || N > kMaxModes || !dims) return fail(nullptr, NNCP_ERR_INVALID_ARG, "N=%d not in [2,8]", N);
+  // a tensor-core precision on a shape it cannot tile: store mode 1 padded
+  // with zero slices (H_1 with zero rows, which HALS keeps zero)
+  int64_t pd[kMaxModes];
+  for (int n = 0; n < N; ++n) pd[n] = dims[n];
+  if (dims[0] >= 1 && R >= 1) pd[0] = tc_padded_mode1(precision, N, dims, R, root_split);
+  const bool padded = pd[0] != dims[0];
   nncp_ctx* c = nullptr;
-  nncp_status s = nncp_create(N, dims, R, &c);
+  nncp_status s = nncp_create(N, pd, R, &c);
   if (s != NNCP_OK) return s;
   void* dX = nullptr;
   void* dXb = nullptr;
@@ -701,7 +743,14 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
     return s;
   }
   CKH(cudaMalloc(&dX, (size_t)c->I * sizeof(float)));
-  CKH(cudaMemcpyAsync(dX, X_host, (size_t)c->I * sizeof(float), cudaMemcpyHostToDevice, st));
+  if (padded) {
+    const size_t rows = (size_t)(c->I / pd[0]);
+    CKH(cudaMemsetAsync(dX, 0, (size_t)c->I * sizeof(float), st));
+    CKH(cudaMemcpy2DAsync(dX, (size_t)pd[0] * sizeof(float), X_host, (size_t)dims[0] * sizeof(float),
+                          (size_t)dims[0] * sizeof(float), rows, cudaMemcpyHostToDevice, st));
+  } else {
+    CKH(cudaMemcpyAsync(dX, X_host, (size_t)c->I * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
   const void* Xuse = dX;
   if (precision == NNCP_BF16_STORED) {
     CKH(cudaMalloc(&dXb, (size_t)c->I * 2));
@@ -709,7 +758,8 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
     Xuse = dXb;
   }
   for (int n = 0; n < N; ++n) {
-    CKH(cudaMalloc(&dH[n], (size_t)dims[n] * R * sizeof(float)));
+    CKH(cudaMalloc(&dH[n], (size_t)pd[n] * R * sizeof(float)));
+    if (pd[n] != dims[n]) CKH(cudaMemsetAsync(dH[n], 0, (size_t)pd[n] * R * sizeof(float), st));
     CKH(cudaMemcpyAsync(dH[n], H_host[n], (size_t)dims[n] * R * sizeof(float),
                         cudaMemcpyHostToDevice, st));
   }

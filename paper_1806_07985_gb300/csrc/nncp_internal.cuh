@@ -52,6 +52,27 @@ cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int6
 // Records a message for nncp_global_error().
 void record_global_error(const char* msg);
 
+}  // namespace nncp
+
+struct nncp_ctx;
+
+namespace nncp {
+
+// Serving hooks on a plain context: initialise a solve with stopping
+// tolerance tol (as nncp_solve does) without running it, and the device
+// addresses of its state: flags[4] = {done, -, iterations, non-finite},
+// lambda (R), the fit history, and the tensor-core error word (NULL when the
+// context has no tensor-core scratch).
+int ctx_solve_begin_tol(nncp_ctx* c, double tol);
+// Mode-1 length to store a host tensor with so that a tensor-core precision
+// can run it: when I_1...I_s times the element size is not a multiple of 16
+// bytes for the split in use, I_1 rounded up to a multiple of 16 bytes' worth
+// of elements (zero slices, with zero rows in H_1).  dims[0] otherwise, or
+// when padding does not make the shape supported.
+int64_t tc_padded_mode1(int precision, int N, const int64_t* dims, int R, int root_split);
+void ctx_device_state(const nncp_ctx* c, const int** flags, const double** lam,
+                      const double** fits, const int** tc_error);
+
 // out[e] = sum_{c < C} part[c * E + e] in chunk order (deterministic).
 cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out, int num_sms,
                                  cudaStream_t st);

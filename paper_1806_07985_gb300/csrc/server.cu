@@ -86,7 +86,11 @@ struct Request {
   std::vector<const float*> Hp;
   std::vector<double> lam;
   size_t bytes = 0, off = 0;          // pool block
-  BTensor desc;
+  BTensor desc;                       // batched lane
+  nncp_ctx* ctx = nullptr;            // solo lane: a single-problem context
+  size_t ws_bytes = 0;
+  int64_t I1p = 0;                    // solo lane: stored mode-1 length (padded)
+  int* h_flags = nullptr;             // solo lane: pinned copy of the context's flags
   bool done = false;
   nncp_status status = NNCP_OK;
   int iters = 0;
@@ -110,6 +114,10 @@ struct Group {
   std::vector<double> h_fits;
 };
 
+bool valid_precision(int p) {
+  return p == NNCP_FP32_SIMT || p == NNCP_TF32 || p == NNCP_SPLIT_BF16X3;
+}
+
 bool valid_shape(int N, const int64_t* dims, int R, int max_iters) {
   if (N < 2 || N > kMaxModes || !dims || R < 1 || R > kBatchMaxRank) return false;
   if (max_iters < 1 || max_iters > 65536) return false;
@@ -122,26 +130,66 @@ bool valid_shape(int N, const int64_t* dims, int R, int max_iters) {
   return true;
 }
 
-size_t footprint(int N, const int64_t* dims, int R, int max_iters) {
+int64_t elems(int N, const int64_t* dims) {
   int64_t I = 1;
-  size_t b = 0;
-  for (int n = 0; n < N; ++n) {
-    I *= dims[n];
-    b += al((size_t)dims[n] * R * sizeof(float));
+  for (int n = 0; n < N; ++n) I *= dims[n];
+  return I;
+}
+
+bool solo_lane(int N, const int64_t* dims, int64_t solo_elems) { return elems(N, dims) >= solo_elems; }
+
+// tensor and factors, then the lane's workspace (ws_bytes for the solo lane)
+size_t footprint(int N, const int64_t* dims, int R, int max_iters, bool solo, size_t ws_bytes,
+                 int64_t I1p) {
+  const int64_t I1 = solo ? I1p : dims[0];
+  size_t b = al((size_t)(elems(N, dims) / dims[0] * I1) * sizeof(float));
+  b += al((size_t)I1 * R * sizeof(float));
+  for (int n = 1; n < N; ++n) b += al((size_t)dims[n] * R * sizeof(float));
+  if (solo) return b + al(ws_bytes);
+  return b + al(b_tensor_layout(N, dims, R, max_iters, nullptr, nullptr));
+}
+
+// Solo lane: a context with the requested precision and the automatic root
+// split, on mode 1 padded as nncp_solve_host pads it (*I1p), or FP32 SIMT on
+// the unpadded shape where the tensor-core path refuses it anyway.
+nncp_status make_solo_ctx(int N, const int64_t* dims, int R, int precision, cudaStream_t st,
+                          nncp_ctx** out, size_t* ws, int64_t* I1p) {
+  int64_t pd[kMaxModes];
+  for (int n = 0; n < N; ++n) pd[n] = dims[n];
+  pd[0] = tc_padded_mode1(precision, N, dims, R, 0);
+  nncp_ctx* c = nullptr;
+  nncp_status e = nncp_create(N, pd, R, &c);
+  if (e != NNCP_OK) return e;
+  e = nncp_set_options(c, precision, 0, st);
+  if (e == NNCP_ERR_UNSUPPORTED && precision != NNCP_FP32_SIMT) {
+    nncp_destroy(c);
+    c = nullptr;
+    pd[0] = dims[0];
+    e = nncp_create(N, pd, R, &c);
+    if (e != NNCP_OK) return e;
+    e = nncp_set_options(c, NNCP_FP32_SIMT, 0, st);
   }
-  b += al((size_t)I * sizeof(float));
-  b += al(b_tensor_layout(N, dims, R, max_iters, nullptr, nullptr));
-  return b;
+  if (e == NNCP_OK) e = nncp_workspace_size(c, ws);
+  if (e != NNCP_OK) {
+    nncp_destroy(c);
+    return e;
+  }
+  *out = c;
+  *I1p = pd[0];
+  return NNCP_OK;
 }
 
 }  // namespace
 
 struct nncp_server {
   size_t budget = 0;
+  int64_t solo_elems = NNCP_SERVER_SOLO_ELEMS;
   int max_slots = 1, device = 0;
   char* pool_base = nullptr;
   Pool pool;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;   // batched lane
+  cudaStream_t st2 = nullptr;  // solo lane (each context also has its own work stream)
+  std::vector<Request*> solo;  // active solo-lane requests
   // scratch for admissions (init) and the done counter the update kernel bumps
   BTensor* d_init_ts = nullptr;
   int4* d_init_items = nullptr;
@@ -205,9 +253,34 @@ cudaError_t admit_one(nncp_server* s, Request* r) {
     o += al(bytes);
     return p;
   };
-  float* X = reinterpret_cast<float*>(take((size_t)r->I * sizeof(float)));
+  const int64_t I1 = r->ctx ? r->I1p : r->dims[0];
+  const int64_t rows = r->I / r->dims[0];
+  float* X = reinterpret_cast<float*>(take((size_t)(rows * I1) * sizeof(float)));
   float* H[kMaxModes];
-  for (int n = 0; n < r->N; ++n) H[n] = reinterpret_cast<float*>(take((size_t)r->dims[n] * r->R * sizeof(float)));
+  H[0] = reinterpret_cast<float*>(take((size_t)I1 * r->R * sizeof(float)));
+  for (int n = 1; n < r->N; ++n) H[n] = reinterpret_cast<float*>(take((size_t)r->dims[n] * r->R * sizeof(float)));
+  if (r->ctx) {
+    char* ws = take(0);
+    cudaError_t e = cudaSuccess;
+    if (I1 != r->dims[0]) {  // zero slices of mode 1 and zero rows of H_1
+      e = cudaMemsetAsync(X, 0, (size_t)(rows * I1) * sizeof(float), s->st2);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(X, (size_t)I1 * sizeof(float), r->X.data(), (size_t)r->dims[0] * sizeof(float),
+                              (size_t)r->dims[0] * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice, s->st2);
+      if (e == cudaSuccess) e = cudaMemsetAsync(H[0], 0, (size_t)I1 * r->R * sizeof(float), s->st2);
+    } else {
+      e = cudaMemcpyAsync(X, r->X.data(), r->X.size() * sizeof(float), cudaMemcpyHostToDevice, s->st2);
+    }
+    for (int n = 0; n < r->N && e == cudaSuccess; ++n)
+      e = cudaMemcpyAsync(H[n], r->H[n].data(), r->H[n].size() * sizeof(float), cudaMemcpyHostToDevice, s->st2);
+    if (e == cudaSuccess) e = cudaMallocHost(&r->h_flags, 4 * sizeof(int));
+    if (e != cudaSuccess) return e;
+    for (int n = 0; n < r->N; ++n) r->desc.H[n] = H[n];
+    if (nncp_set_workspace(r->ctx, ws, r->ws_bytes) != NNCP_OK || nncp_set_tensor(r->ctx, X) != NNCP_OK ||
+        nncp_set_factors(r->ctx, H) != NNCP_OK || ctx_solve_begin_tol(r->ctx, r->tol) != NNCP_OK)
+      return cudaErrorUnknown;
+    return cudaSuccess;
+  }
   b_tensor_layout(r->N, r->dims, r->R, r->max_iters, &r->desc, take(0));
   r->desc.X = X;
   for (int n = 0; n < r->N; ++n) r->desc.H[n] = H[n];
@@ -289,6 +362,36 @@ cudaError_t retire(nncp_server* s, Request* r, int iters, double fit, int state)
   return e;
 }
 
+// Solo lane: flags {done, -, iterations, non-finite} were read after the sweep.
+cudaError_t retire_solo(nncp_server* s, Request* r) {
+  const int* dflags;
+  const double *dlam, *dfits;
+  const int* dtc;
+  ctx_device_state(r->ctx, &dflags, &dlam, &dfits, &dtc);
+  const int iters = r->h_flags[2];
+  cudaError_t e = cudaSuccess;
+  for (int n = 0; n < r->N && e == cudaSuccess; ++n)
+    e = cudaMemcpyAsync(r->H[n].data(), r->desc.H[n], r->H[n].size() * sizeof(float),
+                        cudaMemcpyDeviceToHost, s->st2);
+  r->lam.resize(r->R);
+  double fit = 0.0;
+  int tc_err = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r->lam.data(), dlam, r->R * sizeof(double), cudaMemcpyDeviceToHost, s->st2);
+  if (e == cudaSuccess && iters > 0)
+    e = cudaMemcpyAsync(&fit, dfits + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost, s->st2);
+  if (e == cudaSuccess && dtc) e = cudaMemcpyAsync(&tc_err, dtc, sizeof(int), cudaMemcpyDeviceToHost, s->st2);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st2);
+  r->iters = iters;
+  r->fit = fit;
+  r->status = tc_err ? NNCP_ERR_TIMEOUT : (r->h_flags[3] ? NNCP_ERR_NUMERIC : NNCP_OK);
+  nncp_destroy(r->ctx);
+  r->ctx = nullptr;
+  cudaFreeHost(r->h_flags);
+  r->h_flags = nullptr;
+  return e;
+}
+
 void fail_all(nncp_server* s, const char* what, cudaError_t e) {
   std::lock_guard<std::mutex> g(s->mu);
   char buf[512];
@@ -307,6 +410,7 @@ void fail_all(nncp_server* s, const char* what, cudaError_t e) {
   }
   s->queue.clear();
   for (auto& grp : s->groups) grp.members.clear();
+  s->solo.clear();
   s->active = 0;
   s->cv_done.notify_all();
 }
@@ -338,9 +442,12 @@ void worker_main(nncp_server* s) {
       }
     }
     cudaError_t e = cudaSuccess;
-    for (Request* r : fresh)
+    std::vector<Request*> fresh_batched;
+    for (Request* r : fresh) {
       if (e == cudaSuccess) e = admit_one(s, r);
-    if (e == cudaSuccess) e = init_new(s, fresh);
+      if (!r->ctx) fresh_batched.push_back(r);
+    }
+    if (e == cudaSuccess) e = init_new(s, fresh_batched);
     if (e != cudaSuccess) {
       fail_all(s, "admission", e);
       return;
@@ -350,8 +457,12 @@ void worker_main(nncp_server* s) {
       for (Request* r : fresh) {
         r->X.clear();
         r->X.shrink_to_fit();
-        s->groups[r->N].members.push_back(r);
-        s->groups[r->N].dirty = true;
+        if (r->ctx) {
+          s->solo.push_back(r);
+        } else {
+          s->groups[r->N].members.push_back(r);
+          s->groups[r->N].dirty = true;
+        }
       }
       s->active += (int)fresh.size();
       s->stats.active = s->active;
@@ -372,7 +483,20 @@ void worker_main(nncp_server* s) {
       if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_fits.data(), g.d_fits, C * sizeof(double), cudaMemcpyDeviceToHost, s->st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_state.data(), g.d_state, C * sizeof(int), cudaMemcpyDeviceToHost, s->st);
     }
+    for (Request* r : s->solo) {
+      if (e != cudaSuccess) break;
+      const int* dflags;
+      const double *dlam, *dfits;
+      const int* dtc;
+      ctx_device_state(r->ctx, &dflags, &dlam, &dfits, &dtc);
+      if (nncp_iterate(r->ctx, 1) != NNCP_OK) {
+        e = cudaErrorUnknown;
+        break;
+      }
+      e = cudaMemcpyAsync(r->h_flags, dflags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s->st2);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st2);
     if (e != cudaSuccess) {
       fail_all(s, "sweep", e);
       return;
@@ -397,6 +521,18 @@ void worker_main(nncp_server* s) {
         g.members.swap(keep);
         g.dirty = true;
       }
+    }
+    if (e == cudaSuccess) {
+      std::vector<Request*> keep;
+      for (Request* r : s->solo) {
+        if (e == cudaSuccess && (r->h_flags[0] || r->h_flags[3] || r->h_flags[2] >= r->max_iters)) {
+          e = retire_solo(s, r);
+          finished.push_back(r);
+        } else {
+          keep.push_back(r);
+        }
+      }
+      s->solo.swap(keep);
     }
     if (e != cudaSuccess) {
       fail_all(s, "retire", e);
@@ -437,26 +573,43 @@ void fill_result(Request* r, nncp_result* res) {
 
 extern "C" {
 
-nncp_status nncp_server_footprint(int N, const int64_t* dims, int R, int max_iters, size_t* bytes) {
-  if (!bytes || !valid_shape(N, dims, R, max_iters))
-    return sfail(nullptr, NNCP_ERR_INVALID_ARG, "request shape outside the server's limits");
-  *bytes = footprint(N, dims, R, max_iters);
+nncp_status nncp_server_footprint(const nncp_server* s, int N, const int64_t* dims, int R,
+                                  int max_iters, nncp_precision precision, size_t* bytes) {
+  if (!s || !bytes || !valid_shape(N, dims, R, max_iters) || !valid_precision(precision))
+    return sfail(nullptr, NNCP_ERR_INVALID_ARG, "request outside the server's limits");
+  size_t ws = 0;
+  int64_t I1p = dims[0];
+  const bool solo = solo_lane(N, dims, s->solo_elems);
+  if (solo) {
+    nncp_ctx* c = nullptr;
+    nncp_status e = make_solo_ctx(N, dims, R, precision, nullptr, &c, &ws, &I1p);
+    if (e != NNCP_OK) return e;
+    nncp_destroy(c);
+  }
+  *bytes = footprint(N, dims, R, max_iters, solo, ws, I1p);
   return NNCP_OK;
 }
 
 nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_server** out) {
+  return nncp_server_create_ex(hbm_budget_bytes, max_slots, NNCP_SERVER_SOLO_ELEMS, out);
+}
+
+nncp_status nncp_server_create_ex(size_t hbm_budget_bytes, int max_slots, int64_t solo_elems,
+                                  nncp_server** out) {
   if (!out) return sfail(nullptr, NNCP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (hbm_budget_bytes < 4096 || max_slots < 1)
-    return sfail(nullptr, NNCP_ERR_INVALID_ARG, "budget below 4 KiB or max_slots < 1");
+  if (hbm_budget_bytes < 4096 || max_slots < 1 || solo_elems < 1)
+    return sfail(nullptr, NNCP_ERR_INVALID_ARG, "budget below 4 KiB, max_slots < 1 or solo_elems < 1");
   std::unique_ptr<nncp_server> s(new (std::nothrow) nncp_server());
   if (!s) return sfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "host allocation failed");
+  s->solo_elems = solo_elems;
   s->budget = al(hbm_budget_bytes - 255);
   s->max_slots = max_slots;
   s->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = batch_attributes_init();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_done, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s->d_done, 0, sizeof(int));
   if (e == cudaSuccess) {
@@ -465,6 +618,7 @@ nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_serv
       s->pool_base = nullptr;
       cudaGetLastError();
       if (s->st) cudaStreamDestroy(s->st);
+      if (s->st2) cudaStreamDestroy(s->st2);
       if (s->d_done) cudaFree(s->d_done);
       return sfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "pool of %zu bytes: %s", s->budget,
                    cudaGetErrorString(e));
@@ -472,6 +626,7 @@ nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_serv
   }
   if (e != cudaSuccess) {
     if (s->st) cudaStreamDestroy(s->st);
+    if (s->st2) cudaStreamDestroy(s->st2);
     if (s->d_done) cudaFree(s->d_done);
     return sfail(nullptr, NNCP_ERR_CUDA, "nncp_server_create: %s", cudaGetErrorString(e));
   }
@@ -485,16 +640,25 @@ nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_serv
 
 nncp_status nncp_server_submit(nncp_server* s, const nncp_request* q, uint64_t* ticket) {
   if (!s || !q || !ticket) return sfail(s, NNCP_ERR_INVALID_ARG, "null argument");
-  if (!valid_shape(q->N, q->dims, q->R, q->max_iters))
-    return sfail(s, NNCP_ERR_INVALID_ARG, "request shape outside the server's limits");
+  if (!valid_shape(q->N, q->dims, q->R, q->max_iters) || !valid_precision(q->precision))
+    return sfail(s, NNCP_ERR_INVALID_ARG, "request outside the server's limits");
   if (!q->X_host || !q->H_init_host) return sfail(s, NNCP_ERR_INVALID_ARG, "null tensor or factors");
   for (int n = 0; n < q->N; ++n)
     if (!q->H_init_host[n]) return sfail(s, NNCP_ERR_INVALID_ARG, "factor %d is NULL", n + 1);
-  const size_t bytes = footprint(q->N, q->dims, q->R, q->max_iters);
-  if (bytes > s->budget)
-    return sfail(s, NNCP_ERR_INVALID_ARG, "request needs %zu bytes, budget is %zu", bytes, s->budget);
+  const double t_submit = s->now();
   std::unique_ptr<Request> r(new (std::nothrow) Request());
   if (!r) return sfail(s, NNCP_ERR_OUT_OF_MEMORY, "host allocation failed");
+  const bool solo = solo_lane(q->N, q->dims, s->solo_elems);
+  if (solo) {
+    nncp_status e = make_solo_ctx(q->N, q->dims, q->R, q->precision, s->st2, &r->ctx, &r->ws_bytes,
+                                  &r->I1p);
+    if (e != NNCP_OK) return sfail(s, e, "solo-lane context: %s", nncp_global_error());
+  }
+  const size_t bytes = footprint(q->N, q->dims, q->R, q->max_iters, solo, r->ws_bytes, r->I1p);
+  if (bytes > s->budget) {
+    if (r->ctx) nncp_destroy(r->ctx);
+    return sfail(s, NNCP_ERR_INVALID_ARG, "request needs %zu bytes, budget is %zu", bytes, s->budget);
+  }
   r->N = q->N;
   r->R = q->R;
   r->max_iters = q->max_iters;
@@ -511,13 +675,17 @@ nncp_status nncp_server_submit(nncp_server* s, const nncp_request* q, uint64_t* 
     for (int n = 0; n < q->N; ++n)
       r->H[n].assign(q->H_init_host[n], q->H_init_host[n] + r->dims[n] * r->R);
   } catch (...) {
+    if (r->ctx) nncp_destroy(r->ctx);
     return sfail(s, NNCP_ERR_OUT_OF_MEMORY, "host copy of the request failed");
   }
   {
     std::lock_guard<std::mutex> g(s->mu);
-    if (s->broken) return NNCP_ERR_CUDA;
+    if (s->broken) {
+      if (r->ctx) nncp_destroy(r->ctx);
+      return NNCP_ERR_CUDA;
+    }
     r->ticket = s->next_ticket++;
-    r->t_submit = s->now();
+    r->t_submit = t_submit;
     *ticket = r->ticket;
     s->queue.push_back(r.get());
     s->reqs.emplace(r->ticket, std::move(r));
@@ -581,6 +749,12 @@ void nncp_server_destroy(nncp_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   if (s->st) cudaStreamSynchronize(s->st);
+  if (s->st2) cudaStreamSynchronize(s->st2);
+  for (auto& kv : s->reqs) {
+    Request* r = kv.second.get();
+    if (r->ctx) nncp_destroy(r->ctx);
+    if (r->h_flags) cudaFreeHost(r->h_flags);
+  }
   for (auto& g : s->groups) {
     if (g.d_ts) cudaFree(g.d_ts);
     if (g.d_items) cudaFree(g.d_items);
@@ -595,6 +769,7 @@ void nncp_server_destroy(nncp_server* s) {
   if (s->d_done) cudaFree(s->d_done);
   if (s->pool_base) cudaFree(s->pool_base);
   if (s->st) cudaStreamDestroy(s->st);
+  if (s->st2) cudaStreamDestroy(s->st2);
   delete s;
 }
 

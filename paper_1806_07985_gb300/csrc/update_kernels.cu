@@ -214,37 +214,43 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   }
 }
 
-// Mode update spread over CTAs of kMultiRows rows (I_n <= kMultiMaxRows, R <= 64):
+// Mode update spread over CTAs of MultiCfg<RMAX>::ROWS rows (I_n <= kMultiMaxRows, R <= 64):
 //   every CTA stages its rows of H and M in shared memory (coalesced), runs the
-//   HALS sweep with one thread per row (row in registers, no branches), writes
-//   W back, and writes its partial W^T W (float32) and <M, W>;
-//   the last CTA to finish (atomic ticket) sums the partials in CTA order,
-//   forms lambda, G_n, the fit at n = N and S for the next mode, scales H by
-//   1 / lambda, and resets the ticket.  Results do not depend on arrival order.
-constexpr int kMultiRows = 128;
+//   HALS sweep (Sec. II-B) with one thread per row, and forms its partial W^T W
+//   (float32) and <M, W>.  A single CTA finishes on its own from shared
+//   memory; otherwise every CTA writes W and its partials and the last CTA to
+//   finish (atomic ticket) sums the partials in CTA order and scales H by
+//   1 / lambda.  The finishing CTA forms lambda, G_n, the fit at n = N and S
+//   for the next mode.  Results do not depend on arrival order.
+constexpr int kMultiThreads = 512;
 constexpr int kMultiMaxRows = 16384;
 
 template <int RMAX>
 struct MultiCfg {
-  static constexpr int T = RMAX <= 32 ? 512 : 256;
-  static constexpr int RP = RMAX + 4;  // padded row stride (16-byte multiple) in shared memory
-  static constexpr int NB = (RMAX + 3) / 4;
-  static constexpr int GROUPS = (T / (NB * NB)) > 0 ? T / (NB * NB) : 1;  // Gram row groups
+  static constexpr int T = kMultiThreads;
+  // rows per CTA, one HALS thread each (a mode of up to ROWS rows is updated
+  // by one CTA without a global round trip)
+  static constexpr int ROWS = 128;
+  static constexpr int RP = RMAX + 4;        // padded row stride (16-byte multiple) in shared memory
+  static constexpr int NB = RMAX / 4;
+  static constexpr int GROUPS = T / (NB * NB);  // Gram row groups (>= 2)
 };
 
+int multi_rows(int R) { return R <= 32 ? MultiCfg<32>::ROWS : MultiCfg<64>::ROWS; }  // all 128
+
 template <int RMAX>
-__global__ void __launch_bounds__(MultiCfg<RMAX>::T)
+__global__ void __launch_bounds__(kMultiThreads, 1)
 k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
                int next_mode, int is_last, SolveState st, float* __restrict__ part) {
   if (st.flags[0]) return;
-  constexpr int T = MultiCfg<RMAX>::T;
-  constexpr int RP = MultiCfg<RMAX>::RP;
-  constexpr int GROUPS = MultiCfg<RMAX>::GROUPS;
+  using C = MultiCfg<RMAX>;
+  constexpr int T = C::T, ROWS = C::ROWS, RP = C::RP, GROUPS = C::GROUPS;
+  static_assert(GROUPS >= 2, "W^T W in float64 reuses the Gram partial area");
   extern __shared__ __align__(16) float usm[];
-  float* St = usm;                         // RMAX x RMAX, St[r][c] = S[c][r], zero padded
-  float* Hs = St + RMAX * RMAX;            // kMultiRows x RP
-  float* Ms = Hs + kMultiRows * RP;        // kMultiRows x RP
-  float* gpart = Ms + kMultiRows * RP;     // GROUPS x R x R
+  float* St = usm;                      // RMAX x RMAX, St[r][c] = S[c][r], zero padded
+  float* Hs = St + RMAX * RMAX;         // ROWS x RP: H, then W
+  float* Ms = Hs + ROWS * RP;           // ROWS x RP
+  float* gpart = Ms + ROWS * RP;        // GROUPS x R x R, then W^T W in float64
   __shared__ float lamf[RMAX];
   __shared__ float sinv[RMAX];
   __shared__ double red[T / 32];
@@ -253,8 +259,11 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   __shared__ int last_sh;
   const int tid = threadIdx.x;
   const int R2 = R * R;
-  const int row0 = blockIdx.x * kMultiRows;
-  const int nrows = min(kMultiRows, In - row0);
+  const int row0 = blockIdx.x * ROWS;
+  const int nrows = min(ROWS, In - row0);
+  const bool single = gridDim.x == 1;
+  // staging: every loop issues its global loads in batches
+#pragma unroll
   for (int e = tid; e < RMAX * RMAX; e += T) {
     const int r = e / RMAX, c = e % RMAX;
     St[e] = (r < R && c < R) ? st.S32[c * R + r] : 0.0f;
@@ -266,6 +275,7 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   }
   const float* Hg = H + (long long)row0 * R;
   const float* Mg = M + (long long)row0 * R;
+#pragma unroll 4
   for (int e = tid; e < nrows * R; e += T) {
     const int rr = e / R, c = e % R;
     Hs[rr * RP + c] = Hg[e];
@@ -273,127 +283,180 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   }
   __syncthreads();
 
-  // ---- HALS sweep (Sec. II-B): thread = row, columns in order
+  // ---- HALS sweep (Sec. II-B): thread = row, columns in order.  Up to 32
+  // columns the row lives in registers (fully unrolled sweep); at 64 that
+  // straight-line code is too long to fetch once per warp, so the row is
+  // updated in place in its shared-memory row by a rolled column loop.  Both
+  // form each dot product in the same order, so they give the same bits.
   double bp = 0.0;
   if (tid < nrows) {
-    float w[RMAX];
-#pragma unroll
-    for (int c = 0; c < RMAX; ++c) w[c] = c < R ? Hs[tid * RP + c] * lamf[c] : 0.0f;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      const float si = sinv[r];
-      const float mr = Ms[tid * RP + r];
-      const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
-      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
-#pragma unroll
-      for (int c = 0; c < RMAX; c += 4) {
-        const float4 sv = col[c >> 2];
-        d0 = fmaf(w[c], sv.x, d0);
-        d1 = fmaf(w[c + 1], sv.y, d1);
-        d2 = fmaf(w[c + 2], sv.z, d2);
-        d3 = fmaf(w[c + 3], sv.w, d3);
-      }
-      const float dot = (d0 + d1) + (d2 + d3);
-      const float upd = fmaxf(0.0f, w[r] + (mr - dot) * si);
-      w[r] = si != 0.0f ? upd : w[r];  // S_rr = 0: column left as it is
-    }
     float b = 0.0f;
+    if constexpr (RMAX <= 32) {
+      float w[RMAX];
 #pragma unroll
-    for (int c = 0; c < RMAX; ++c) {
-      if (c < R) {
-        b = fmaf(Ms[tid * RP + c], w[c], b);
-        Hs[tid * RP + c] = w[c];
+      for (int c = 0; c < RMAX; ++c) w[c] = c < R ? Hs[tid * RP + c] * lamf[c] : 0.0f;
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        const float si = sinv[r];
+        const float mr = Ms[tid * RP + r];
+        const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
+        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < RMAX; c += 4) {
+          const float4 sv = col[c >> 2];
+          d0 = fmaf(w[c], sv.x, d0);
+          d1 = fmaf(w[c + 1], sv.y, d1);
+          d2 = fmaf(w[c + 2], sv.z, d2);
+          d3 = fmaf(w[c + 3], sv.w, d3);
+        }
+        const float dot = (d0 + d1) + (d2 + d3);
+        const float upd = fmaxf(0.0f, w[r] + (mr - dot) * si);
+        w[r] = si != 0.0f ? upd : w[r];  // S_rr = 0: column left as it is
       }
+#pragma unroll
+      for (int c = 0; c < RMAX; ++c) {
+        if (c < R) {
+          b = fmaf(Ms[tid * RP + c], w[c], b);
+          Hs[tid * RP + c] = w[c];
+        }
+      }
+    } else {
+      float* wrow = Hs + tid * RP;
+#pragma unroll
+      for (int c = 0; c < RMAX; ++c) wrow[c] = c < R ? wrow[c] * lamf[c] : 0.0f;
+      const float4* wv = reinterpret_cast<const float4*>(wrow);
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const float si = sinv[r];
+        const float mr = Ms[tid * RP + r];
+        const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
+        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < RMAX / 4; ++c) {
+          const float4 sv = col[c];
+          const float4 w4 = wv[c];
+          d0 = fmaf(w4.x, sv.x, d0);
+          d1 = fmaf(w4.y, sv.y, d1);
+          d2 = fmaf(w4.z, sv.z, d2);
+          d3 = fmaf(w4.w, sv.w, d3);
+        }
+        const float dot = (d0 + d1) + (d2 + d3);
+        const float wr = wrow[r];
+        const float upd = fmaxf(0.0f, wr + (mr - dot) * si);
+        wrow[r] = si != 0.0f ? upd : wr;
+      }
+      for (int c = 0; c < R; ++c) b = fmaf(Ms[tid * RP + c], wrow[c], b);
     }
     bp = (double)b;
   }
   for (int o = 16; o > 0; o >>= 1) bp += __shfl_xor_sync(0xffffffffu, bp, o);
   if ((tid & 31) == 0) red[tid >> 5] = bp;
   __syncthreads();
-  float* Hw = H + (long long)row0 * R;
-  for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R];
+  if (!single) {
+    float* Hw = H + (long long)row0 * R;
+    for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R];
+  }
 
   // ---- partial W^T W: thread = (4x4 tile, row group), register tiles
-  {
-    const int nb = (R + 3) / 4;
-    const int tiles = nb * nb;
-    const int groups = min(GROUPS, max(1, T / tiles));
-    if (tid < tiles * groups) {
-      const int tile = tid % tiles, g = tid / tiles;
-      const int a0 = (tile / nb) * 4, b0 = (tile % nb) * 4;
-      float acc[4][4];
+  const int nb4 = (R + 3) / 4;
+  const int tiles = nb4 * nb4;
+  const int groups = min(GROUPS, max(1, T / tiles));
+  if (tid < tiles * groups) {
+    const int tile = tid % tiles, g = tid / tiles;
+    const int a0 = (tile / nb4) * 4, b0 = (tile % nb4) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+    for (int rr = g; rr < nrows; rr += groups) {
+      const float4 qa = *reinterpret_cast<const float4*>(Hs + rr * RP + a0);
+      const float4 qb = *reinterpret_cast<const float4*>(Hs + rr * RP + b0);
+      const float va[4] = {qa.x, qa.y, qa.z, qa.w};
+      const float vb[4] = {qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
-      for (int rr = g; rr < nrows; rr += groups) {
-        const float4 qa = *reinterpret_cast<const float4*>(Hs + rr * RP + a0);
-        const float4 qb = *reinterpret_cast<const float4*>(Hs + rr * RP + b0);
-        const float va[4] = {qa.x, qa.y, qa.z, qa.w};
-        const float vb[4] = {qb.x, qb.y, qb.z, qb.w};
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(va[x], vb[y], acc[x][y]);
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y)
-          if (a0 + x < R && b0 + y < R) gpart[(g * R + a0 + x) * R + b0 + y] = acc[x][y];
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(va[x], vb[y], acc[x][y]);
     }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (a0 + x < R && b0 + y < R) gpart[(g * R + a0 + x) * R + b0 + y] = acc[x][y];
+  }
+  __syncthreads();
+  // W^T W summed over the row groups (float32, group order)
+  constexpr int EPT = (RMAX * RMAX + T - 1) / T;
+  float gsum[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    gsum[q] = 0.0f;
+    if (e < R2)
+      for (int g = 0; g < groups; ++g) gsum[q] += gpart[g * R2 + e];
+  }
+  double* GW = reinterpret_cast<double*>(gpart);  // R2 doubles, after the sums are read
+  if (single) {
     __syncthreads();
-    float* pb = part + (long long)blockIdx.x * (R2 + 1);
-    for (int e = tid; e < R2; e += T) {
-      float sum = 0.0f;
-      for (int g = 0; g < groups; ++g) sum += gpart[g * R2 + e];
-      pb[e] = sum;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * T;
+      if (e < R2) GW[e] = (double)gsum[q];
     }
     if (tid == 0) {
       double b = 0.0;
-      for (int w = 0; w < T / 32; ++w) b += red[w];
+      for (int k = 0; k < T / 32; ++k) b += red[k];
+      scal_sh[0] = b;
+    }
+  } else {
+    float* pb = part + (long long)blockIdx.x * (R2 + 1);
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * T;
+      if (e < R2) pb[e] = gsum[q];
+    }
+    if (tid == 0) {
+      double b = 0.0;
+      for (int k = 0; k < T / 32; ++k) b += red[k];
       pb[R2] = (float)b;
     }
+    // ---- the last CTA finishes the update
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int ticket = atomicAdd(&st.flags[8], 1);
+      last_sh = ticket == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_sh) return;
+    __threadfence();
+    const int nbk = gridDim.x;
+#pragma unroll 4
+    for (int e = tid; e < R2; e += T) {
+      float v[8];
+      float sum = 0.0f;
+      int b = 0;
+      for (; b + 8 <= nbk; b += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = part[(long long)(b + q) * (R2 + 1) + e];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sum += v[q];
+      }
+      for (; b < nbk; ++b) sum += part[(long long)b * (R2 + 1) + e];
+      GW[e] = (double)sum;
+    }
+    if (tid == 0) {
+      double b = 0.0;
+      for (int k = 0; k < nbk; ++k) b += (double)part[(long long)k * (R2 + 1) + R2];
+      scal_sh[0] = b;
+      st.flags[8] = 0;  // ticket reset for the next launch
+    }
   }
-
-  // ---- the last CTA finishes the update
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const int ticket = atomicAdd(&st.flags[8], 1);
-    last_sh = ticket == (int)gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last_sh) return;
-  __threadfence();
-  const int nb = gridDim.x;
-  // the H/M staging area is free now: W^T W and S (float64) live there
-  double* GW = reinterpret_cast<double*>(Hs);
-  double* Sd = GW + R2;
   if (tid == 0) {
     scal_sh[1] = st.scalars[0];
     const int it = st.flags[2];
     scal_sh[2] = (it >= 1 && it <= kFitCapacity) ? st.fits[it - 1] : 0.0;
-  }
-  for (int e = tid; e < R2; e += T) {
-    float v[8];
-    float sum = 0.0f;
-    int b = 0;
-    for (; b + 8 <= nb; b += 8) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = part[(long long)(b + q) * (R2 + 1) + e];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) sum += v[q];
-    }
-    for (; b < nb; ++b) sum += part[(long long)b * (R2 + 1) + e];
-    GW[e] = (double)sum;
-    Sd[e] = st.S[e];
-  }
-  if (tid == 0) {
-    double b = 0.0;
-    for (int k = 0; k < nb; ++k) b += (double)part[(long long)k * (R2 + 1) + R2];
-    scal_sh[0] = b;
-    st.flags[8] = 0;  // ticket reset for the next launch
   }
   __syncthreads();
   for (int r = tid; r < R; r += T) {
@@ -408,48 +471,64 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     const int a = e / R, b = e % R;
     Gn[e] = GW[e] * cinv_sh[a] * cinv_sh[b];
   }
-  // H = W / lambda (multiplication by the float32 reciprocal); loads in one batch
-  const long long tot = (long long)In * R;
-  for (long long e0 = tid; e0 < tot; e0 += 16LL * T) {
-    float v[16];
+  // H = W / lambda (multiplication by the float32 reciprocal)
+  if (single) {
+    for (int e = tid; e < nrows * R; e += T) H[e] = Hs[(e / R) * RP + e % R] * lamf[e % R];
+  } else {
+    const int tot = In * R;  // <= kMultiMaxRows * 64: 32-bit index arithmetic
+    for (int e0 = tid; e0 < tot; e0 += 16 * T) {
+      float v[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const long long e = e0 + (long long)q * T;
-      v[q] = e < tot ? H[e] : 0.0f;
-    }
+      for (int q = 0; q < 16; ++q) {
+        const int e = e0 + q * T;
+        v[q] = e < tot ? H[e] : 0.0f;
+      }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const long long e = e0 + (long long)q * T;
-      if (e < tot) H[e] = v[q] * lamf[(int)(e % R)];
+      for (int q = 0; q < 16; ++q) {
+        const int e = e0 + q * T;
+        if (e < tot) H[e] = v[q] * lamf[e % R];
+      }
     }
   }
   if (is_last) {
     double g = 0.0;
-    for (int e = tid; e < R2; e += T) g += Sd[e] * GW[e];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * T;
+      if (e < R2) g += st.S[e] * GW[e];
+    }
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
     __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = g;
     __syncthreads();
     if (tid == 0) {
       double gamma = 0.0;
-      for (int w = 0; w < T / 32; ++w) gamma += red[w];
+      for (int k = 0; k < T / 32; ++k) gamma += red[k];
       record_fit_known(st, scal_sh[0], gamma, scal_sh[1], scal_sh[2]);
     }
   }
   __syncthreads();
-  // S for the next mode: Hadamard of every Gram but next_mode's (mode n's is new)
-  for (int e = tid; e < R2; e += T) {
-    double g[kMaxModes];
+  // S for the next mode: Hadamard of every Gram but next_mode's (mode n's is
+  // new); all of a thread's Gram loads first
+  double sv[EPT];
 #pragma unroll
-    for (int k = 0; k < kMaxModes; ++k)
-      g[k] = (k < N && k != next_mode) ? (k == n ? GW[e] * cinv_sh[e / R] * cinv_sh[e % R]
-                                                 : st.G[(long long)k * R2 + e])
-                                       : 1.0;
-    double sv = 1.0;
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    sv[q] = 1.0;
+    if (e < R2) {
 #pragma unroll
-    for (int k = 0; k < kMaxModes; ++k) sv *= g[k];
-    st.S[e] = sv;
-    st.S32[e] = (float)sv;
+      for (int k = 0; k < kMaxModes; ++k)
+        if (k < N && k != next_mode)
+          sv[q] *= (k == n ? GW[e] * cinv_sh[e / R] * cinv_sh[e % R] : st.G[(long long)k * R2 + e]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    if (e < R2) {
+      st.S[e] = sv[q];
+      st.S32[e] = (float)sv[q];
+    }
   }
 }
 
@@ -457,7 +536,7 @@ template <int RMAX>
 size_t multi_smem() {
   using C = MultiCfg<RMAX>;
   const size_t grams = (size_t)C::GROUPS * RMAX * RMAX;
-  return (size_t)(RMAX * RMAX + 2 * kMultiRows * C::RP) * sizeof(float) + grams * sizeof(float);
+  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP) * sizeof(float) + grams * sizeof(float);
 }
 
 __global__ void k_solve_reset(SolveState st, int R, double tol) {
@@ -599,14 +678,14 @@ bool multi_update_ok(int64_t In, int R) { return In <= kMultiMaxRows && R <= 64;
 
 // partial scratch needed by the multi-CTA update (floats)
 size_t multi_update_scratch(int64_t In, int R) {
-  const int64_t nb = (In + kMultiRows - 1) / kMultiRows;
+  const int64_t nb = (In + multi_rows(R) - 1) / multi_rows(R);
   return (size_t)(nb + 1) * (R * R + 1) + 2 * (size_t)R * R + 4;
 }
 
 cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
                                 int next_mode, int is_last, SolveState st, float* part,
                                 cudaStream_t stream) {
-  const int nb = (int)((In + kMultiRows - 1) / kMultiRows);
+  const int nb = (int)((In + multi_rows(R) - 1) / multi_rows(R));
   const int rmax = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
   switch (rmax) {
     case 16:

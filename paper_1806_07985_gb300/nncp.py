@@ -72,8 +72,10 @@ _SIGNATURES = [
     ("nncp_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_batch_destroy", None, [ctypes.c_void_p]),
     ("nncp_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
-    ("nncp_server_footprint", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.c_int,
-                                             ctypes.POINTER(ctypes.c_size_t)]),
+    ("nncp_server_create_ex", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+    ("nncp_server_footprint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i64p, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     ("nncp_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     ("nncp_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]),
@@ -317,7 +319,8 @@ class Batch:
 class _Request(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dims", _c_i64p), ("R", ctypes.c_int),
                 ("X_host", ctypes.c_void_p), ("H_init_host", _c_vpp),
-                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
+                ("precision", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -334,13 +337,6 @@ class _Stats(ctypes.Structure):
                 ("bytes_in_use", ctypes.c_size_t), ("peak_bytes_in_use", ctypes.c_size_t)]
 
 
-def nncp_server_footprint(dims, R, max_iters):
-    n = ctypes.c_size_t()
-    _check(load().nncp_server_footprint(len(dims), _dims(dims), int(R), int(max_iters),
-                                        ctypes.byref(n)))
-    return n.value
-
-
 class Server:
     """Serving loop over host numpy arrays (argument marshalling only).
 
@@ -349,20 +345,35 @@ class Server:
     then a dict with the status, iterations, fit, lambda, factors (numpy
     copies) and the submit/admit/done times on the server clock."""
 
-    def __init__(self, hbm_budget_bytes, max_slots):
+    def __init__(self, hbm_budget_bytes, max_slots, solo_elems=None):
         self.s = ctypes.c_void_p()
-        _scheck(load().nncp_server_create(int(hbm_budget_bytes), int(max_slots),
-                                          ctypes.byref(self.s)), None)
+        if solo_elems is None:
+            _scheck(load().nncp_server_create(int(hbm_budget_bytes), int(max_slots),
+                                              ctypes.byref(self.s)), None)
+        else:
+            _scheck(load().nncp_server_create_ex(int(hbm_budget_bytes), int(max_slots),
+                                                 int(solo_elems), ctypes.byref(self.s)), None)
         self._shapes = {}
 
-    def submit(self, dims, R, X, H, max_iters, tol):
+    def footprint(self, dims, R, max_iters, precision=NNCP_FP32_SIMT):
+        """Device bytes the request would take from the pool (its lane's layout)."""
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        n = ctypes.c_size_t()
+        _scheck(load().nncp_server_footprint(self.s, len(dims), _dims(dims), int(R), int(max_iters),
+                                             int(precision), ctypes.byref(n)), self.s)
+        return n.value
+
+    def submit(self, dims, R, X, H, max_iters, tol, precision=NNCP_FP32_SIMT):
         import numpy as np
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
         X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1)
         H = [np.ascontiguousarray(h, dtype=np.float32) for h in H]
         d = _dims(dims)
         hp = (ctypes.c_void_p * len(H))(*[h.ctypes.data for h in H])
         req = _Request(len(dims), ctypes.cast(d, _c_i64p), int(R), X.ctypes.data,
-                       ctypes.cast(hp, _c_vpp), int(max_iters), float(tol))
+                       ctypes.cast(hp, _c_vpp), int(max_iters), float(tol), int(precision))
         t = ctypes.c_uint64()
         _scheck(load().nncp_server_submit(self.s, ctypes.byref(req), ctypes.byref(t)), self.s)
         self._shapes[t.value] = (tuple(int(x) for x in dims), int(R))
@@ -449,6 +460,7 @@ class Context:
             nncp_set_workspace(self.ctx, self.ws)
         except Exception:
             nncp_destroy(self.ctx)
+            self.ctx = None
             raise
 
     def set_tensor(self, X):

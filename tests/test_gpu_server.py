@@ -1,8 +1,10 @@
 """GPU tests of the serving loop (continuous batching of solve requests).
 
-Each request is one NNCP-HALS problem (root split 1); results are checked
-against the FP64 oracle, against the batched solver (the same kernels, so the
-same bits), and for independence from whatever else the server is running.
+Each request is one NNCP-HALS problem.  Small requests share the batched
+iteration (root split 1): they are checked against the FP64 oracle, against
+the batched solver (the same kernels, so the same bits) and for independence
+from whatever else the server is running.  Large requests run the
+single-problem solver: the same bits as nncp_solve_host.
 """
 
 import numpy as np
@@ -104,7 +106,9 @@ def test_server_bits_match_batch_and_do_not_depend_on_the_mix(nn):
 
 def test_server_admission_respects_budget_and_slots(nn):
     reqs = [_request(900 + q, 3, 30, 40, (8,)) for q in range(6)]
-    need = max(nn.nncp_server_footprint(d, R, 5) for d, R, _, _ in reqs)
+    probe = nn.Server(1 << 30, 1)
+    need = max(probe.footprint(d, R, 5) for d, R, _, _ in reqs)
+    probe.close()
     out, stats = _solve_all(nn, reqs, 5, budget=2 * need + 4096)
     assert stats["completed"] == 6
     assert stats["peak_bytes_in_use"] <= stats["budget"]
@@ -150,3 +154,65 @@ def test_server_poll_and_bounded_wait(nn):
             srv.release(t)
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_simt", "split_bf16x3"])
+def test_server_solo_lane_is_the_single_problem_solver(nn, precision):
+    # a request of >= NNCP_SERVER_SOLO_ELEMS elements runs the single-problem
+    # solver on its own stream: same bits as nncp_solve_host with root_split 0
+    if precision != "fp32_simt" and "tcgen05" not in nn.nncp_version():
+        pytest.skip("no tensor-core path in this build")
+    dims, R = (160, 160, 170), 16
+    assert dims[0] * dims[1] * dims[2] >= (1 << 22)
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=71, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=72)
+    small = _mix()[:3]
+    srv = nn.Server(1 << 32, 8)
+    try:
+        tk = [srv.submit(d, r, xx, h, 6, 0.0) for d, r, xx, h in small[:2]]
+        big = srv.submit(dims, R, x, H0, 6, 0.0, precision=precision)
+        tk.append(srv.submit(*small[2][:2], small[2][2], small[2][3], 6, 0.0))
+        res = srv.wait(big, 120000)
+        others = [srv.wait(t, 120000) for t in tk]
+    finally:
+        srv.close()
+    assert res["status"] == 0 and res["iters"] == 6
+    assert all(o["status"] == 0 and o["iters"] == 6 for o in others)
+    Hh = [h.copy() for h in H0]
+    lam, k, fit = nn.nncp_solve_host(dims, R, x, Hh, precision, 0, 6, 0.0)
+    assert k == res["iters"] and fit == res["fit"]
+    assert np.array_equal(np.array(lam), res["lambda"])
+    for a, b in zip(Hh, res["H"]):
+        assert np.array_equal(a, b)
+    if precision == "fp32_simt":
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=6, use_dimtree=True, s=nn.nncp_default_split(dims))
+        assert abs(res["fit"] - ref["fits"][-1]) <= 1e-4
+        for n in range(3):
+            assert rel_fro(res["H"][n], ref["H"][n]) <= 1e-3
+
+
+def test_server_solo_lane_pads_like_solve_host(nn):
+    # no root split of (161, 163, 165) tiles for tensor cores: the solo lane
+    # pads mode 1 to 164 exactly as nncp_solve_host does (same bits)
+    if "tcgen05" not in nn.nncp_version():
+        pytest.skip("no tensor-core path in this build")
+    dims, R = (161, 163, 165), 12
+    assert dims[0] * dims[1] * dims[2] >= (1 << 22)
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=81, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=82)
+    srv = nn.Server(1 << 32, 4)
+    try:
+        res = srv.wait(srv.submit(dims, R, x, H0, 5, 0.0, precision="split_bf16x3"), 120000)
+    finally:
+        srv.close()
+    Hh = [h.copy() for h in H0]
+    lam, k, fit = nn.nncp_solve_host(dims, R, x, Hh, "split_bf16x3", 0, 5, 0.0)
+    assert res["iters"] == k == 5 and res["fit"] == fit
+    for a, b in zip(Hh, res["H"]):
+        assert a.shape == b.shape and np.array_equal(a, b)
+    ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                           max_iters=5, use_dimtree=True, s=nn.nncp_default_split((164, 163, 165)))
+    assert abs(res["fit"] - ref["fits"][-1]) <= 1e-4
+    for n in range(3):
+        assert rel_fro(res["H"][n], ref["H"][n]) <= 1e-3

@@ -160,3 +160,31 @@ def test_unsupported_shapes_are_refused(nn):
             nn.nncp_set_options(ctx, nn.NNCP_TF32, 0, None)
     finally:
         nn.nncp_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,fit_tol,h_tol", [("split_bf16x3", 1e-4, 1e-3), ("tf32", 2e-2, 5e-2)])
+def test_solve_host_pads_mode1_for_tensor_cores(nn, prec, fit_tol, h_tol):
+    # (37, 23, 29): no root split gives I_1...I_s a multiple of 4, so the
+    # context refuses tensor cores (test above); the host call stores mode 1
+    # padded to 40 with zero slices and zero H_1 rows, which HALS keeps zero.
+    dims, R = (37, 23, 29), 5
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=61, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=62)
+    ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                           max_iters=15, use_dimtree=True, s=nn.nncp_default_split((40, 23, 29)))
+    H = [h.copy() for h in H0]
+    lam, k, fit = nn.nncp_solve_host(dims, R, x, H, prec, 0, 15, 0.0)
+    assert k == 15 and H[0].shape == (37, R)
+    assert abs(fit - ref["fits"][-1]) <= fit_tol, (prec, fit, ref["fits"][-1])
+    for n in range(3):
+        assert rel_fro(H[n], ref["H"][n]) <= h_tol, (prec, n)
+    assert rel_fro(np.array(lam), ref["lam"]) <= h_tol
+
+
+def test_refused_context_cleans_up_once(nn):
+    # a Context whose options are refused is destroyed exactly once
+    for _ in range(3):
+        with pytest.raises(nn.NNCPError):
+            nn.Context((37, 23, 29), 5, precision=nn.NNCP_SPLIT_BF16X3)
+    import gc
+    gc.collect()
