@@ -56,13 +56,18 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=None,
                    choices=["fp32_simt", "tf32", "split_bf16x3", "bf16_stored"])
-    p.add_argument("--mode", default="step", choices=["step", "pm"],
-                   help="pm: only the two root partial MTTKRPs, for kernel profiling")
+    p.add_argument("--mode", default="step", choices=["step", "pm", "batched", "serving"],
+                   help="pm: only the two root partial MTTKRPs (kernel profiling); batched / "
+                        "serving: only that line")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 4096-tensor batched solve (context line 'batched')")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--batch-iters", type=int, default=None,
+                   help="cap the batched solve at this many iterations (profiling)")
+    p.add_argument("--no-plain", action="store_true",
+                   help="skip the one-at-a-time comparison of --mode batched/serving (profiling)")
     p.add_argument("--no-serving", action="store_true",
                    help="skip the serving-loop sample (context line 'serving')")
     p.add_argument("--serve-requests", type=int, default=32)
@@ -180,6 +185,13 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     nncp.load()
+    if args.mode in ("batched", "serving"):
+        if rank == 0:
+            out = (run_batched(nncp, torch, args.batch_count, args.batch_iters, args.no_plain)
+                   if args.mode == "batched" else
+                   run_serving(nncp, torch, args.serve_requests, args.no_plain))
+            print(json.dumps({"mode": args.mode, args.mode: out}), flush=True)
+        return
     prec_name = args.precision or default_precision(nncp)
     prec = nncp.PRECISIONS[prec_name]
 
@@ -341,7 +353,7 @@ BATCH_ITERS, BATCH_TOL = 200, 1e-5      # stopping rule of the 4096-tensor workl
 SERVE_ITERS, SERVE_TOL = 150, 1e-4      # stopping rule of the serving workload
 
 
-def run_batched(nncp, torch, count):
+def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
     """4096 uneven 3-way tensors (I_n log-uniform in [16, 128], R in {4, 8, 16})
     solved together to |dfit| < 1e-5 or 200 iterations, against the plain
     one-problem-at-a-time solver on an evenly spaced sample of 32 of them."""
@@ -352,6 +364,7 @@ def run_batched(nncp, torch, count):
     X = [torch.from_numpy(p[2]).cuda() for p in probs]
     H0 = [[torch.from_numpy(h).cuda() for h in p[3]] for p in probs]
     H = [[h.clone() for h in hs] for hs in H0]
+    iters_cap = max_iters or BATCH_ITERS
     b = nncp.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=BATCH_ITERS)
     b.set_data(X, H)
     b.solve(3, 0.0)                      # graph capture and warm-up
@@ -361,13 +374,20 @@ def run_batched(nncp, torch, count):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    iters, fits, _ = b.solve(BATCH_ITERS, BATCH_TOL)
+    iters, fits, _ = b.solve(iters_cap, BATCH_TOL)
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3
     b.close()
     elems = [int(np.prod(p[0])) for p in probs]
     tensor_bytes = sum(2 * 4 * e * k for e, k in zip(elems, iters))
+    out = {"workload": f"{count} 3-way tensors, I_n log-uniform [16,128], R in {{4,8,16}}, "
+                       f"|dfit|<{BATCH_TOL:g} or {iters_cap} iters, FP32",
+           "solves_per_s": round(count / t, 1), "seconds": round(t, 4),
+           "iters_mean": round(float(np.mean(iters)), 1), "iters_max": int(max(iters)),
+           "tensor_GBps": round(tensor_bytes / t / 1e9, 1)}
+    if no_plain:
+        return out
     sample = list(range(0, count, max(1, count // 32)))[:32]
     ctxs = []
     for q in sample:
@@ -391,14 +411,10 @@ def run_batched(nncp, torch, count):
     for c in ctxs:
         c.close()
     dfit = max(abs(plain[i][2] - fits[q]) for i, q in enumerate(sample))
-    return {"workload": f"{count} 3-way tensors, I_n log-uniform [16,128], R in {{4,8,16}}, "
-                        f"|dfit|<{BATCH_TOL:g} or {BATCH_ITERS} iters, FP32",
-            "solves_per_s": round(count / t, 1), "seconds": round(t, 4),
-            "iters_mean": round(float(np.mean(iters)), 1), "iters_max": int(max(iters)),
-            "tensor_GBps": round(tensor_bytes / t / 1e9, 1),
-            "plain_solves_per_s": round(len(sample) / tp, 2),
-            "plain_sample": len(sample), "speedup": round(count / t / (len(sample) / tp), 1),
-            "max_abs_fit_diff_vs_plain": float(f"{dfit:.3g}")}
+    out.update({"plain_solves_per_s": round(len(sample) / tp, 2),
+                "plain_sample": len(sample), "speedup": round(count / t / (len(sample) / tp), 1),
+                "max_abs_fit_diff_vs_plain": float(f"{dfit:.3g}")})
+    return out
 
 
 def _percentiles(v):
@@ -407,7 +423,7 @@ def _percentiles(v):
             "p99_ms": round(1e3 * float(np.percentile(v, 99)), 2)}
 
 
-def run_serving(nncp, torch, count):
+def run_serving(nncp, torch, count, no_plain=False):
     """Sample of the serving workload: requests 0..count-1 (order 3-5, I_n
     log-uniform [16, 256], at most 64 Mi elements, R in {8, 16, 32, 64},
     |dfit| < 1e-4 or 150 iterations) through the server: (i) saturation, all
@@ -457,6 +473,16 @@ def run_serving(nncp, torch, count):
         out = submit_all(srv, arr)
         loads[rho] = (arr, [r["t_done"] - r["t_submit"] for r in out])
     srv.close()
+    out = {"workload": f"serving requests 0..{count - 1}: order 3-5, I_n log-uniform [16,256], "
+                       f"<= 64Mi elements, R in {{8,16,32,64}}, |dfit|<{SERVE_TOL:g} or "
+                       f"{SERVE_ITERS} iters; batched lane FP32, solo lane (>= 4Mi elements) {prec}",
+           "requests": count, "elements_total": int(sum(elems)),
+           "hbm_budget_bytes": budget, "peak_bytes_in_use": stats["peak_bytes_in_use"],
+           "saturation_solves_per_s": round(cap, 2)}
+    for rho, (arr, lat) in loads.items():
+        out[f"load_{rho}"] = {"rate_per_s": round(rho * cap, 2), "server": _percentiles(lat)}
+    if no_plain:
+        return out
     # the plain path: one request at a time, its best precision per request
     service, plain_fit, plain_prec = [], [], {}
     for dims, R, x, H0 in reqs:
@@ -476,15 +502,10 @@ def run_serving(nncp, torch, count):
         service.append(time.perf_counter() - t0)
         plain_fit.append(f)
         plain_prec[name] = plain_prec.get(name, 0) + 1
-    out = {"workload": f"serving requests 0..{count - 1}: order 3-5, I_n log-uniform [16,256], "
-                       f"<= 64Mi elements, R in {{8,16,32,64}}, |dfit|<{SERVE_TOL:g} or "
-                       f"{SERVE_ITERS} iters, FP32",
-           "requests": count, "elements_total": int(sum(elems)),
-           "hbm_budget_bytes": budget, "peak_bytes_in_use": stats["peak_bytes_in_use"],
-           "saturation_solves_per_s": round(cap, 2),
-           "plain_solves_per_s": round(count / sum(service), 2),
-           "plain_precisions": plain_prec,
-           "max_abs_fit_diff_vs_plain": float(f"{max(abs(a['fit'] - b) for a, b in zip(sat, plain_fit)):.3g}")}
+    out.update({"plain_solves_per_s": round(count / sum(service), 2),
+                "plain_precisions": plain_prec,
+                "max_abs_fit_diff_vs_plain":
+                    float(f"{max(abs(a['fit'] - b) for a, b in zip(sat, plain_fit)):.3g}")})
     for rho, (arr, lat) in loads.items():
         # plain path as a FIFO single server under the same arrivals
         wait_q, plain_lat = 0.0, []
@@ -492,8 +513,7 @@ def run_serving(nncp, torch, count):
             if q:
                 wait_q = max(0.0, wait_q + service[q - 1] - (arr[q] - arr[q - 1]))
             plain_lat.append(wait_q + service[q])
-        out[f"load_{rho}"] = {"rate_per_s": round(rho * cap, 2), "server": _percentiles(lat),
-                              "plain_fifo": _percentiles(plain_lat)}
+        out[f"load_{rho}"]["plain_fifo"] = _percentiles(plain_lat)
     return out
 
 

@@ -19,7 +19,7 @@
 //                (three products, float32 accumulation in TMEM);
 //   BF16_STORED  the tensor is bf16 in HBM: D = X*[Khi|Klo].
 //
-// Warp roles (12 warps, one CTA per SM, persistent over work units):
+// Warp roles (16 warps, one CTA per SM, persistent over work units):
 //   warp 0      TMA producer          warp 1      TMEM owner + MMA issuer
 //   warps 2-7   Khatri-Rao B builders, two per B stage slot (each half of the
 //               stage's 64 contraction elements), so three stages are formed
