@@ -61,6 +61,8 @@ def parse():
                         "serving: only that line")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-4way", action="store_true",
+                   help="skip the 512x512x32x16 R=24 split-2 step (context line 'hsi_4way')")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 4096-tensor batched solve (context line 'batched')")
     p.add_argument("--batch-count", type=int, default=4096)
@@ -79,6 +81,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value, device):
+    """The largest of every rank's `value` (each rank's own when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, bytes_per_rank_step, ms_per_step):
+    """Whole-job GB/s: every rank's bytes over the slowest rank's step time."""
+    return world * bytes_per_rank_step / (ms_per_step * 1e-3) / 1e9
 
 
 # ---------------------------------------------------------------- clocks ----
@@ -241,12 +259,9 @@ def run_ours(args):
         torch.distributed.barrier()
     ms_total = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, "cuda")
     ms_step = ms_total / args.steps
-    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(world, bytes_step, ms_step)
     kernels_per_iter = ctx.iteration_kernels()
 
     # dominant kernel: the root partial MTTKRPs, timed with events on their stream
@@ -296,6 +311,8 @@ def run_ours(args):
         result["e2e"] = run_e2e(nncp, torch, x, H0, prec, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(x, H0)
+    if rank == 0 and world == 1 and not args.no_4way:
+        result["hsi_4way"] = run_4way(nncp, torch, prec_name, max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_batched:
         result["batched"] = run_batched(nncp, torch, args.batch_count)
     if rank == 0 and world == 1 and not args.no_serving:
@@ -322,7 +339,7 @@ def run_e2e(nncp, torch, x, H0, prec, world):
         t0 = time.perf_counter()
         nncp.nncp_solve_host(DIMS, RANK, Xh, Hrun, prec, 1, ITERS_CONFIG, 0.0)
         times.append(time.perf_counter() - t0)
-    t = float(np.median(times))
+    t = max_over_ranks(float(np.median(times)), "cuda")
     bytes_solve = ITERS_CONFIG * tensor_bytes_per_iter(DIMS, 2 if prec == nncp.NNCP_BF16_STORED else 4)
     h2d = x.nbytes + sum(h.nbytes for h in H0)
     d2h = sum(h.nbytes for h in H0) + RANK * 8 + 8
@@ -345,6 +362,52 @@ def cpu_baseline(x, H0):
             "sample": "one outer iteration (with initialisation) of the 512^3 R=32 solve, "
                       "FP64 numpy oracle, dimension tree split 1",
             "seconds": round(t, 2)}
+
+
+# ----------------------------------------------------------- 4-way line --
+
+def run_4way(nncp, torch, prec_name, warmup, steps=50):
+    """The 4-way HSI-like workload (512 x 512 x 32 x 16, R = 24, root split 2):
+    outer-iteration time and each root partial MTTKRP, events on its stream."""
+    from paper_1806_07985_gb300 import synth
+    dims, R, split = (512, 512, 32, 16), 24, 2
+    x, _ = synth.hsi_timelapse(dims, R, seed=0)
+    H0 = synth.init_factors(dims, R, seed=1)
+    X = torch.from_numpy(x).cuda()
+    ctx = nncp.Context(dims, R, precision=nncp.PRECISIONS[prec_name], root_split=split)
+    ctx.set_tensor(X)
+    ctx.set_factors([torch.from_numpy(h.copy()).cuda() for h in H0])
+    ctx.solve_begin()
+    ctx.iterate(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.iterate(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / steps
+    pm = {}
+    for side, rows in ((0, dims[0] * dims[1]), (1, dims[2] * dims[3])):
+        out = torch.empty((rows, R), device="cuda")
+        for _ in range(3):
+            ctx.partial_mttkrp(side, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            ctx.partial_mttkrp(side, out)
+        b.record()
+        torch.cuda.synchronize()
+        pm[side] = a.elapsed_time(b) / 20
+    ctx.close()
+    xb = X.numel() * 4
+    peak, _ = measured_peaks()
+    return {"workload": "hsi_4way_512x512x32x16_R24_split2", "precision": prec_name,
+            "ms_per_step": round(ms_step, 4),
+            "value": round(tensor_bytes_per_iter(dims) / (ms_step * 1e-3) / 1e9, 1), "unit": UNIT,
+            "pm_ms": {"root_to_left": round(pm[0], 4), "root_to_right": round(pm[1], 4)},
+            "pm_frac_of_measured_peak": round(xb / (max(pm.values()) * 1e-3) / 1e9 / peak, 4),
+            "steps": steps}
 
 
 # ------------------------------------------------- batched and serving lines --

@@ -238,18 +238,24 @@ nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* 
  * (|fit_k - fit_{k-1}| < tol, or max_iters), its factors and lambda are
  * copied back and its pool space is freed.  A request's results are the same
  * bits whatever else is active.
- * Two lanes: requests of fewer than NNCP_SERVER_SOLO_ELEMS elements (or the
- * threshold given to nncp_server_create_ex) share
+ * Two lanes, each admitted in submission order: requests of fewer than
+ * NNCP_SERVER_SOLO_ELEMS elements (or the threshold given to
+ * nncp_server_create_ex) share
  * the batched FP32 iteration of their order (root split 1, the same bits as
  * nncp_batch_solve); larger ones, which fill the GPU alone, each run the
  * single-problem solver of nncp_solve on their own stream -- root split by
  * nncp_default_split, the request's precision (mode 1 padded as in
  * nncp_solve_host where that lets the tensor-core path tile the shape, FP32
  * SIMT where nothing does), the same bits as nncp_solve_host with that
- * precision and root_split 0.
+ * precision and root_split 0 -- launched in chunks of 4, 8, then 16
+ * iterations and polled without blocking the batched lane.  At most
+ * NNCP_SERVER_MAX_SOLO of those run at once (two: one's latency-bound mode
+ * updates overlap the other's bandwidth-bound partial MTTKRPs, and neither
+ * is slowed much), while small requests keep being admitted beside them.
  * No call blocks without a bound: submit copies and returns, wait gives up
  * after timeout_ms. */
 #define NNCP_SERVER_SOLO_ELEMS (1LL << 22)
+#define NNCP_SERVER_MAX_SOLO 2
 typedef struct nncp_server nncp_server;
 typedef struct {
   int N;                            /* order */
@@ -276,10 +282,12 @@ typedef struct {
 } nncp_server_stats;
 /* max_slots >= 1: most requests active at once. */
 nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_server** out);
-/* As nncp_server_create, with the lane threshold: requests of at least
- * solo_elems elements (>= 1) take the solo lane. */
+/* As nncp_server_create, with the lane settings: requests of at least
+ * solo_elems elements (>= 1) take the solo lane, and at most max_solo (>= 1)
+ * of them run at once (the others wait in submission order; small requests
+ * are admitted meanwhile). */
 nncp_status nncp_server_create_ex(size_t hbm_budget_bytes, int max_slots, int64_t solo_elems,
-                                  nncp_server** out);
+                                  int max_solo, nncp_server** out);
 /* Device bytes a request takes from the pool (NNCP_ERR_INVALID_ARG if its
  * shape is outside the limits). */
 nncp_status nncp_server_footprint(const nncp_server* s, int N, const int64_t* dims, int R,

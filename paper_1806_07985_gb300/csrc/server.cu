@@ -90,7 +90,12 @@ struct Request {
   nncp_ctx* ctx = nullptr;            // solo lane: a single-problem context
   size_t ws_bytes = 0;
   int64_t I1p = 0;                    // solo lane: stored mode-1 length (padded)
+  bool ctx_was_solo = false;          // took the solo lane (ctx is gone once retired)
   int* h_flags = nullptr;             // solo lane: pinned copy of the context's flags
+  cudaStream_t sst = nullptr;         // solo lane: the request's own stream
+  cudaEvent_t sev = nullptr;          //   marks the end of its launched chunk
+  int launched = 0, chunk = 4;        //   iterations launched, next chunk size
+  bool inflight = false;
   bool done = false;
   nncp_status status = NNCP_OK;
   int iters = 0;
@@ -187,8 +192,7 @@ struct nncp_server {
   int max_slots = 1, device = 0;
   char* pool_base = nullptr;
   Pool pool;
-  cudaStream_t st = nullptr;   // batched lane
-  cudaStream_t st2 = nullptr;  // solo lane (each context also has its own work stream)
+  cudaStream_t st = nullptr;   // batched lane (each solo-lane request has its own stream)
   std::vector<Request*> solo;  // active solo-lane requests
   // scratch for admissions (init) and the done counter the update kernel bumps
   BTensor* d_init_ts = nullptr;
@@ -201,7 +205,8 @@ struct nncp_server {
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Request*> queue;
+  std::deque<Request*> queue_b, queue_s;  // waiting requests of the batched / solo lane
+  int max_solo = NNCP_SERVER_MAX_SOLO, solo_active = 0;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
   int active = 0;
   uint64_t next_ticket = 1;
@@ -261,19 +266,21 @@ cudaError_t admit_one(nncp_server* s, Request* r) {
   for (int n = 1; n < r->N; ++n) H[n] = reinterpret_cast<float*>(take((size_t)r->dims[n] * r->R * sizeof(float)));
   if (r->ctx) {
     char* ws = take(0);
+    cudaStream_t st = r->sst;
     cudaError_t e = cudaSuccess;
     if (I1 != r->dims[0]) {  // zero slices of mode 1 and zero rows of H_1
-      e = cudaMemsetAsync(X, 0, (size_t)(rows * I1) * sizeof(float), s->st2);
+      e = cudaMemsetAsync(X, 0, (size_t)(rows * I1) * sizeof(float), st);
       if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(X, (size_t)I1 * sizeof(float), r->X.data(), (size_t)r->dims[0] * sizeof(float),
-                              (size_t)r->dims[0] * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice, s->st2);
-      if (e == cudaSuccess) e = cudaMemsetAsync(H[0], 0, (size_t)I1 * r->R * sizeof(float), s->st2);
+                              (size_t)r->dims[0] * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(H[0], 0, (size_t)I1 * r->R * sizeof(float), st);
     } else {
-      e = cudaMemcpyAsync(X, r->X.data(), r->X.size() * sizeof(float), cudaMemcpyHostToDevice, s->st2);
+      e = cudaMemcpyAsync(X, r->X.data(), r->X.size() * sizeof(float), cudaMemcpyHostToDevice, st);
     }
     for (int n = 0; n < r->N && e == cudaSuccess; ++n)
-      e = cudaMemcpyAsync(H[n], r->H[n].data(), r->H[n].size() * sizeof(float), cudaMemcpyHostToDevice, s->st2);
+      e = cudaMemcpyAsync(H[n], r->H[n].data(), r->H[n].size() * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMallocHost(&r->h_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->sev, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
     for (int n = 0; n < r->N; ++n) r->desc.H[n] = H[n];
     if (nncp_set_workspace(r->ctx, ws, r->ws_bytes) != NNCP_OK || nncp_set_tensor(r->ctx, X) != NNCP_OK ||
@@ -362,33 +369,92 @@ cudaError_t retire(nncp_server* s, Request* r, int iters, double fit, int state)
   return e;
 }
 
-// Solo lane: flags {done, -, iterations, non-finite} were read after the sweep.
+// Frees a solo-lane request's context, stream, event and pinned flags.
+void release_solo(Request* r) {
+  if (r->ctx) nncp_destroy(r->ctx);
+  r->ctx = nullptr;
+  if (r->sev) cudaEventDestroy(r->sev);
+  r->sev = nullptr;
+  if (r->sst) cudaStreamDestroy(r->sst);
+  r->sst = nullptr;
+  if (r->h_flags) cudaFreeHost(r->h_flags);
+  r->h_flags = nullptr;
+}
+
+// Solo lane: its flags {done, -, iterations, non-finite} were read back.
 cudaError_t retire_solo(nncp_server* s, Request* r) {
   const int* dflags;
   const double *dlam, *dfits;
   const int* dtc;
   ctx_device_state(r->ctx, &dflags, &dlam, &dfits, &dtc);
   const int iters = r->h_flags[2];
+  cudaStream_t st = r->sst;
   cudaError_t e = cudaSuccess;
   for (int n = 0; n < r->N && e == cudaSuccess; ++n)
     e = cudaMemcpyAsync(r->H[n].data(), r->desc.H[n], r->H[n].size() * sizeof(float),
-                        cudaMemcpyDeviceToHost, s->st2);
+                        cudaMemcpyDeviceToHost, st);
   r->lam.resize(r->R);
   double fit = 0.0;
   int tc_err = 0;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(r->lam.data(), dlam, r->R * sizeof(double), cudaMemcpyDeviceToHost, s->st2);
+    e = cudaMemcpyAsync(r->lam.data(), dlam, r->R * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && iters > 0)
-    e = cudaMemcpyAsync(&fit, dfits + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost, s->st2);
-  if (e == cudaSuccess && dtc) e = cudaMemcpyAsync(&tc_err, dtc, sizeof(int), cudaMemcpyDeviceToHost, s->st2);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st2);
+    e = cudaMemcpyAsync(&fit, dfits + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && dtc) e = cudaMemcpyAsync(&tc_err, dtc, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   r->iters = iters;
   r->fit = fit;
   r->status = tc_err ? NNCP_ERR_TIMEOUT : (r->h_flags[3] ? NNCP_ERR_NUMERIC : NNCP_OK);
-  nncp_destroy(r->ctx);
-  r->ctx = nullptr;
-  cudaFreeHost(r->h_flags);
-  r->h_flags = nullptr;
+  release_solo(r);
+  return e;
+}
+
+// Solo lane, without waiting: a request whose chunk has completed is retired
+// if its rule fired (device flags: done, iterations, non-finite) and gets its
+// next chunk otherwise (4, 8, then 16 iterations, never past max_iters; the
+// device flag makes iterations launched after convergence no-ops, as in
+// nncp_solve).  Finished requests are appended to `finished`.
+cudaError_t solo_step(nncp_server* s, std::vector<Request*>* finished) {
+  cudaError_t e = cudaSuccess;
+  std::vector<Request*> keep;
+  for (Request* r : s->solo) {
+    if (e != cudaSuccess) {
+      keep.push_back(r);
+      continue;
+    }
+    if (r->inflight) {
+      const cudaError_t q = cudaEventQuery(r->sev);
+      if (q == cudaErrorNotReady) {
+        keep.push_back(r);
+        continue;
+      }
+      if (q != cudaSuccess) {
+        e = q;
+        keep.push_back(r);
+        continue;
+      }
+      r->inflight = false;
+      if (r->h_flags[0] || r->h_flags[3] || r->h_flags[2] >= r->max_iters) {
+        e = retire_solo(s, r);
+        finished->push_back(r);
+        continue;
+      }
+    }
+    const int n = std::min(r->chunk, r->max_iters - r->launched);
+    const int* dflags;
+    const double *dlam, *dfits;
+    const int* dtc;
+    ctx_device_state(r->ctx, &dflags, &dlam, &dfits, &dtc);
+    if (n > 0 && nncp_iterate(r->ctx, n) != NNCP_OK) e = cudaErrorUnknown;
+    r->launched += std::max(n, 0);
+    r->chunk = std::min(2 * r->chunk, 16);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->h_flags, dflags, 4 * sizeof(int), cudaMemcpyDeviceToHost, r->sst);
+    if (e == cudaSuccess) e = cudaEventRecord(r->sev, r->sst);
+    r->inflight = true;
+    keep.push_back(r);
+  }
+  s->solo.swap(keep);
   return e;
 }
 
@@ -408,7 +474,9 @@ void fail_all(nncp_server* s, const char* what, cudaError_t e) {
       r->t_done = t;
     }
   }
-  s->queue.clear();
+  s->queue_b.clear();
+  s->queue_s.clear();
+  s->solo_active = 0;
   for (auto& grp : s->groups) grp.members.clear();
   s->solo.clear();
   s->active = 0;
@@ -421,17 +489,28 @@ void worker_main(nncp_server* s) {
     std::vector<Request*> fresh;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || s->active > 0 || !s->queue.empty(); });
+      s->cv_work.wait(lk, [&] {
+        return s->stop || s->active > 0 || !s->queue_b.empty() || !s->queue_s.empty();
+      });
       if (s->stop) return;
-      // FIFO admission while the head fits
-      while (!s->queue.empty() && s->active + (int)fresh.size() < s->max_slots) {
-        Request* r = s->queue.front();
-        size_t off = 0;
-        if (!s->pool.alloc(r->bytes, &off)) break;
-        r->off = off;
-        r->t_admit = s->now();
-        s->queue.pop_front();
-        fresh.push_back(r);
+      // admission in submission order within each lane while the head fits;
+      // at most max_solo solo-lane requests run at once
+      for (bool progress = true; progress;) {
+        progress = false;
+        std::deque<Request*>* lanes[2] = {&s->queue_b, &s->queue_s};
+        for (std::deque<Request*>* q : lanes) {
+          if (q->empty() || s->active + (int)fresh.size() >= s->max_slots) continue;
+          if (q == &s->queue_s && s->solo_active >= s->max_solo) continue;
+          Request* r = q->front();
+          size_t off = 0;
+          if (!s->pool.alloc(r->bytes, &off)) continue;
+          r->off = off;
+          r->t_admit = s->now();
+          q->pop_front();
+          fresh.push_back(r);
+          if (r->ctx) ++s->solo_active;
+          progress = true;
+        }
       }
       s->stats.bytes_in_use = s->pool.used();
       s->stats.peak_bytes_in_use = std::max(s->stats.peak_bytes_in_use, s->pool.used());
@@ -466,13 +545,18 @@ void worker_main(nncp_server* s) {
       }
       s->active += (int)fresh.size();
       s->stats.active = s->active;
-      s->stats.queued = (int)s->queue.size();
+      s->stats.queued = (int)(s->queue_b.size() + s->queue_s.size());
       s->stats.peak_active = std::max(s->stats.peak_active, s->active);
     }
-    // one sweep: an outer iteration of every active request
+    // solo lane: retire finished chunks' requests, launch the next chunks
+    std::vector<Request*> finished;
+    if (e == cudaSuccess) e = solo_step(s, &finished);
+    // batched lane: one sweep, an outer iteration of every active request
+    bool swept = false;
     for (int N = 2; N <= kMaxModes && e == cudaSuccess; ++N) {
       Group& g = s->groups[N];
       if (g.members.empty()) continue;
+      swept = true;
       if (g.dirty) e = upload_group(s, g, N);
       if (e == cudaSuccess) e = b_launch_iteration(g.plan, g.d_ts, g.d_items, s->d_done, s->st);
       if (e == cudaSuccess)
@@ -483,27 +567,21 @@ void worker_main(nncp_server* s) {
       if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_fits.data(), g.d_fits, C * sizeof(double), cudaMemcpyDeviceToHost, s->st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_state.data(), g.d_state, C * sizeof(int), cudaMemcpyDeviceToHost, s->st);
     }
-    for (Request* r : s->solo) {
-      if (e != cudaSuccess) break;
-      const int* dflags;
-      const double *dlam, *dfits;
-      const int* dtc;
-      ctx_device_state(r->ctx, &dflags, &dlam, &dfits, &dtc);
-      if (nncp_iterate(r->ctx, 1) != NNCP_OK) {
-        e = cudaErrorUnknown;
-        break;
-      }
-      e = cudaMemcpyAsync(r->h_flags, dflags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s->st2);
+    if (e == cudaSuccess && swept) e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess && !swept && finished.empty() && !s->solo.empty()) {
+      // only solo chunks in flight: block on one of them rather than spin
+      for (Request* r : s->solo)
+        if (r->inflight) {
+          e = cudaEventSynchronize(r->sev);
+          break;
+        }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st2);
     if (e != cudaSuccess) {
       fail_all(s, "sweep", e);
       return;
     }
-    // retire the requests that stopped
-    std::vector<Request*> finished;
-    for (int N = 2; N <= kMaxModes && e == cudaSuccess; ++N) {
+    // retire the batched requests that stopped
+    for (int N = 2; N <= kMaxModes && e == cudaSuccess && swept; ++N) {
       Group& g = s->groups[N];
       if (g.members.empty()) continue;
       std::vector<Request*> keep;
@@ -522,18 +600,6 @@ void worker_main(nncp_server* s) {
         g.dirty = true;
       }
     }
-    if (e == cudaSuccess) {
-      std::vector<Request*> keep;
-      for (Request* r : s->solo) {
-        if (e == cudaSuccess && (r->h_flags[0] || r->h_flags[3] || r->h_flags[2] >= r->max_iters)) {
-          e = retire_solo(s, r);
-          finished.push_back(r);
-        } else {
-          keep.push_back(r);
-        }
-      }
-      s->solo.swap(keep);
-    }
     if (e != cudaSuccess) {
       fail_all(s, "retire", e);
       return;
@@ -545,10 +611,11 @@ void worker_main(nncp_server* s) {
         s->pool.release(r->off, r->bytes);
         r->done = true;
         r->t_done = t;
+        if (r->ctx_was_solo) --s->solo_active;
       }
       s->active -= (int)finished.size();
       s->stats.completed += finished.size();
-      s->stats.sweeps += 1;
+      s->stats.sweeps += swept ? 1 : 0;
       s->stats.active = s->active;
       s->stats.bytes_in_use = s->pool.used();
     }
@@ -591,25 +658,27 @@ nncp_status nncp_server_footprint(const nncp_server* s, int N, const int64_t* di
 }
 
 nncp_status nncp_server_create(size_t hbm_budget_bytes, int max_slots, nncp_server** out) {
-  return nncp_server_create_ex(hbm_budget_bytes, max_slots, NNCP_SERVER_SOLO_ELEMS, out);
+  return nncp_server_create_ex(hbm_budget_bytes, max_slots, NNCP_SERVER_SOLO_ELEMS,
+                               NNCP_SERVER_MAX_SOLO, out);
 }
 
 nncp_status nncp_server_create_ex(size_t hbm_budget_bytes, int max_slots, int64_t solo_elems,
-                                  nncp_server** out) {
+                                  int max_solo, nncp_server** out) {
   if (!out) return sfail(nullptr, NNCP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (hbm_budget_bytes < 4096 || max_slots < 1 || solo_elems < 1)
-    return sfail(nullptr, NNCP_ERR_INVALID_ARG, "budget below 4 KiB, max_slots < 1 or solo_elems < 1");
+  if (hbm_budget_bytes < 4096 || max_slots < 1 || solo_elems < 1 || max_solo < 1)
+    return sfail(nullptr, NNCP_ERR_INVALID_ARG,
+                 "budget below 4 KiB, or max_slots, solo_elems or max_solo below 1");
   std::unique_ptr<nncp_server> s(new (std::nothrow) nncp_server());
   if (!s) return sfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "host allocation failed");
   s->solo_elems = solo_elems;
+  s->max_solo = max_solo;
   s->budget = al(hbm_budget_bytes - 255);
   s->max_slots = max_slots;
   s->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = batch_attributes_init();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_done, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s->d_done, 0, sizeof(int));
   if (e == cudaSuccess) {
@@ -618,7 +687,6 @@ nncp_status nncp_server_create_ex(size_t hbm_budget_bytes, int max_slots, int64_
       s->pool_base = nullptr;
       cudaGetLastError();
       if (s->st) cudaStreamDestroy(s->st);
-      if (s->st2) cudaStreamDestroy(s->st2);
       if (s->d_done) cudaFree(s->d_done);
       return sfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "pool of %zu bytes: %s", s->budget,
                    cudaGetErrorString(e));
@@ -626,7 +694,6 @@ nncp_status nncp_server_create_ex(size_t hbm_budget_bytes, int max_slots, int64_
   }
   if (e != cudaSuccess) {
     if (s->st) cudaStreamDestroy(s->st);
-    if (s->st2) cudaStreamDestroy(s->st2);
     if (s->d_done) cudaFree(s->d_done);
     return sfail(nullptr, NNCP_ERR_CUDA, "nncp_server_create: %s", cudaGetErrorString(e));
   }
@@ -650,13 +717,18 @@ nncp_status nncp_server_submit(nncp_server* s, const nncp_request* q, uint64_t* 
   if (!r) return sfail(s, NNCP_ERR_OUT_OF_MEMORY, "host allocation failed");
   const bool solo = solo_lane(q->N, q->dims, s->solo_elems);
   if (solo) {
-    nncp_status e = make_solo_ctx(q->N, q->dims, q->R, q->precision, s->st2, &r->ctx, &r->ws_bytes,
+    if (cudaStreamCreateWithFlags(&r->sst, cudaStreamNonBlocking) != cudaSuccess)
+      return sfail(s, NNCP_ERR_CUDA, "solo-lane stream");
+    nncp_status e = make_solo_ctx(q->N, q->dims, q->R, q->precision, r->sst, &r->ctx, &r->ws_bytes,
                                   &r->I1p);
-    if (e != NNCP_OK) return sfail(s, e, "solo-lane context: %s", nncp_global_error());
+    if (e != NNCP_OK) {
+      release_solo(r.get());
+      return sfail(s, e, "solo-lane context: %s", nncp_global_error());
+    }
   }
   const size_t bytes = footprint(q->N, q->dims, q->R, q->max_iters, solo, r->ws_bytes, r->I1p);
   if (bytes > s->budget) {
-    if (r->ctx) nncp_destroy(r->ctx);
+    release_solo(r.get());
     return sfail(s, NNCP_ERR_INVALID_ARG, "request needs %zu bytes, budget is %zu", bytes, s->budget);
   }
   r->N = q->N;
@@ -675,22 +747,23 @@ nncp_status nncp_server_submit(nncp_server* s, const nncp_request* q, uint64_t* 
     for (int n = 0; n < q->N; ++n)
       r->H[n].assign(q->H_init_host[n], q->H_init_host[n] + r->dims[n] * r->R);
   } catch (...) {
-    if (r->ctx) nncp_destroy(r->ctx);
+    release_solo(r.get());
     return sfail(s, NNCP_ERR_OUT_OF_MEMORY, "host copy of the request failed");
   }
   {
     std::lock_guard<std::mutex> g(s->mu);
     if (s->broken) {
-      if (r->ctx) nncp_destroy(r->ctx);
+      release_solo(r.get());
       return NNCP_ERR_CUDA;
     }
     r->ticket = s->next_ticket++;
     r->t_submit = t_submit;
     *ticket = r->ticket;
-    s->queue.push_back(r.get());
+    r->ctx_was_solo = r->ctx != nullptr;
+    (r->ctx ? s->queue_s : s->queue_b).push_back(r.get());
     s->reqs.emplace(r->ticket, std::move(r));
     s->stats.submitted += 1;
-    s->stats.queued = (int)s->queue.size();
+    s->stats.queued = (int)(s->queue_b.size() + s->queue_s.size());
   }
   s->cv_work.notify_one();
   return NNCP_OK;
@@ -749,11 +822,10 @@ void nncp_server_destroy(nncp_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   if (s->st) cudaStreamSynchronize(s->st);
-  if (s->st2) cudaStreamSynchronize(s->st2);
   for (auto& kv : s->reqs) {
     Request* r = kv.second.get();
-    if (r->ctx) nncp_destroy(r->ctx);
-    if (r->h_flags) cudaFreeHost(r->h_flags);
+    if (r->sst) cudaStreamSynchronize(r->sst);
+    release_solo(r);
   }
   for (auto& g : s->groups) {
     if (g.d_ts) cudaFree(g.d_ts);
@@ -769,7 +841,6 @@ void nncp_server_destroy(nncp_server* s) {
   if (s->d_done) cudaFree(s->d_done);
   if (s->pool_base) cudaFree(s->pool_base);
   if (s->st) cudaStreamDestroy(s->st);
-  if (s->st2) cudaStreamDestroy(s->st2);
   delete s;
 }
 

@@ -73,7 +73,7 @@ _SIGNATURES = [
     ("nncp_batch_destroy", None, [ctypes.c_void_p]),
     ("nncp_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("nncp_server_create_ex", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int64,
-                                             ctypes.POINTER(ctypes.c_void_p)]),
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("nncp_server_footprint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i64p, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
@@ -345,14 +345,19 @@ class Server:
     then a dict with the status, iterations, fit, lambda, factors (numpy
     copies) and the submit/admit/done times on the server clock."""
 
-    def __init__(self, hbm_budget_bytes, max_slots, solo_elems=None):
+    SOLO_ELEMS = 1 << 22   # NNCP_SERVER_SOLO_ELEMS
+    MAX_SOLO = 2           # NNCP_SERVER_MAX_SOLO
+
+    def __init__(self, hbm_budget_bytes, max_slots, solo_elems=None, max_solo=None):
         self.s = ctypes.c_void_p()
-        if solo_elems is None:
+        if solo_elems is None and max_solo is None:
             _scheck(load().nncp_server_create(int(hbm_budget_bytes), int(max_slots),
                                               ctypes.byref(self.s)), None)
         else:
-            _scheck(load().nncp_server_create_ex(int(hbm_budget_bytes), int(max_slots),
-                                                 int(solo_elems), ctypes.byref(self.s)), None)
+            _scheck(load().nncp_server_create_ex(
+                int(hbm_budget_bytes), int(max_slots),
+                int(self.SOLO_ELEMS if solo_elems is None else solo_elems),
+                int(self.MAX_SOLO if max_solo is None else max_solo), ctypes.byref(self.s)), None)
         self._shapes = {}
 
     def footprint(self, dims, R, max_iters, precision=NNCP_FP32_SIMT):
