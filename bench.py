@@ -61,6 +61,8 @@ def parse():
                         "serving: only that line")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-dimtree-compare", action="store_true",
+                   help="skip the with / without dimension tree comparison (context line)")
     p.add_argument("--no-4way", action="store_true",
                    help="skip the 512x512x32x16 R=24 split-2 step (context line 'hsi_4way')")
     p.add_argument("--no-batched", action="store_true",
@@ -311,6 +313,8 @@ def run_ours(args):
         result["e2e"] = run_e2e(nncp, torch, x, H0, prec, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(x, H0)
+    if rank == 0 and world == 1 and not args.no_dimtree_compare:
+        result["dimtree_vs_direct"] = run_dimtree_compare(nncp, torch)
     if rank == 0 and world == 1 and not args.no_4way:
         result["hsi_4way"] = run_4way(nncp, torch, prec_name, max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_batched:
@@ -362,6 +366,48 @@ def cpu_baseline(x, H0):
             "sample": "one outer iteration (with initialisation) of the 512^3 R=32 solve, "
                       "FP64 numpy oracle, dimension tree split 1",
             "seconds": round(t, 2)}
+
+
+# --------------------------------------------- with / without dimension tree --
+
+def run_dimtree_compare(nncp, torch, steps=4):
+    """Outer-iteration time with the dimension tree (two tensor passes) and
+    without it (a full MTTKRP per mode, N passes; Sec. V-C), FP32 SIMT both,
+    plus the tree on tensor cores, for 512^3 and the 5-way 64^5 at R = 32.
+    Timing-only inputs: U[0,1) tensor and factors from a seeded torch
+    generator on the device (kernel time does not depend on the values)."""
+    out = {}
+    for dims in ((512, 512, 512), (64, 64, 64, 64, 64)):
+        R = 32
+        g = torch.Generator(device="cuda")
+        g.manual_seed(7)
+        n_el = 1
+        for d in dims:
+            n_el *= d
+        X = torch.rand(n_el, device="cuda", generator=g)
+        H0 = [torch.rand((d, R), device="cuda", generator=g) for d in dims]
+        row = {}
+        for name, prec, tree in (("tree_fp32", nncp.NNCP_FP32_SIMT, True),
+                                 ("direct_fp32", nncp.NNCP_FP32_SIMT, False),
+                                 ("tree_" + default_precision(nncp), nncp.PRECISIONS[default_precision(nncp)], True)):
+            ctx = nncp.Context(dims, R, precision=prec)
+            ctx.set_dimtree(tree)
+            ctx.set_tensor(X)
+            ctx.set_factors([h.clone() for h in H0])
+            ctx.solve_begin()
+            ctx.iterate(2)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.iterate(steps)
+            b.record()
+            torch.cuda.synchronize()
+            row[name + "_ms"] = round(a.elapsed_time(b) / steps, 3)
+            ctx.close()
+        row["tree_speedup_fp32"] = round(row["direct_fp32_ms"] / row["tree_fp32_ms"], 2)
+        out["x".join(str(d) for d in dims) + "_R32"] = row
+        del X
+    return out
 
 
 # ----------------------------------------------------------- 4-way line --

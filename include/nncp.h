@@ -77,6 +77,14 @@ int nncp_default_split(int N, const int64_t* dims);
 nncp_status nncp_set_options(nncp_ctx* ctx, nncp_precision precision, int root_split,
                              void* stream);
 
+/* Solve with or without the dimension tree (enabled = 1, the default).
+ * Without it every outer iteration computes each M(n) by a full MTTKRP over
+ * the whole tensor (N passes per iteration instead of two) -- the
+ * implementation without the optimization that Sec. V-C benchmarks (results
+ * in Sec. V-D) and the third line of the cost table in Sec. IV-C.  FP32 SIMT only:
+ * NNCP_ERR_UNSUPPORTED for a tensor-core precision.  Takes effect at the
+ * next solve or iteration. */
+nncp_status nncp_set_dimtree(nncp_ctx* ctx, int enabled);
 /* Bytes of device scratch the context needs for its current options
  * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
 nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);

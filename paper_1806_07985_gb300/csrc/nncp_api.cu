@@ -38,6 +38,7 @@ struct nncp_ctx {
   int64_t I = 1;
   int precision = NNCP_FP32_SIMT;
   int split = 1;
+  int dimtree = 1;  // 0: every M(n) by a direct MTTKRP (N tensor passes per iteration)
   cudaStream_t user_stream = nullptr;
   cudaStream_t work = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -273,6 +274,18 @@ cudaError_t visit(nncp_ctx* c, const float* T, int a, int last, int h, int base,
 
 cudaError_t run_iteration(nncp_ctx* c, cudaStream_t st) {
   const int s = c->split, N = c->N;
+  if (!c->dimtree) {
+    // without the tree: a full MTTKRP per mode, each over the whole tensor
+    for (int n = 0; n < N; ++n) {
+      KrpDesc KL = krp(c, 0, n - 1), KQ = krp(c, n + 1, N - 1);
+      cudaError_t e = launch_simt_mttkrp(static_cast<const float*>(c->X), prod(c->dims, 0, n - 1),
+                                         c->dims[n], prod(c->dims, n + 1, N - 1), KL, KQ, c->R,
+                                         c->Mbuf, c->partials, c->part_cap, c->num_sms, st);
+      if (e == cudaSuccess) e = update_mode(c, n, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   float* TL = (s == 1) ? c->Mbuf : c->node[0][0];
   cudaError_t e = pm_right(c, TL, st);
   if (e != cudaSuccess) return e;
@@ -458,6 +471,15 @@ nncp_status nncp_create(int N, const int64_t* dims, int R, nncp_ctx** out) {
   return NNCP_OK;
 }
 
+nncp_status nncp_set_dimtree(nncp_ctx* c, int enabled) {
+  if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
+  if (!enabled && c->precision != NNCP_FP32_SIMT)
+    return fail(c, NNCP_ERR_UNSUPPORTED, "the solve without the dimension tree is FP32 SIMT only");
+  c->dimtree = enabled ? 1 : 0;
+  drop_graph(c);
+  return NNCP_OK;
+}
+
 nncp_status nncp_set_options(nncp_ctx* c, nncp_precision precision, int root_split, void* stream) {
   if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
   if (precision < NNCP_FP32_SIMT || precision > NNCP_BF16_STORED)
@@ -466,6 +488,8 @@ nncp_status nncp_set_options(nncp_ctx* c, nncp_precision precision, int root_spl
     return fail(c, NNCP_ERR_INVALID_ARG, "root_split %d not in [0, N-1]", root_split);
   if (precision != NNCP_FP32_SIMT && !tc_available())
     return fail(c, NNCP_ERR_UNSUPPORTED, "tensor-core kernels not compiled in");
+  if (precision != NNCP_FP32_SIMT && !c->dimtree)
+    return fail(c, NNCP_ERR_UNSUPPORTED, "the solve without the dimension tree is FP32 SIMT only");
   const int split = root_split ? root_split : nncp_default_split(c->N, c->dims);
   if (precision != NNCP_FP32_SIMT) {
     const char* why = tc_unsupported_reason(precision, c->N, c->dims, c->R, split);

@@ -44,6 +44,7 @@ _SIGNATURES = [
     ("nncp_default_split", ctypes.c_int, [ctypes.c_int, _c_i64p]),
     ("nncp_create", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("nncp_set_options", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_set_dimtree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("nncp_set_tensor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -159,6 +160,10 @@ def nncp_set_options(ctx, precision=NNCP_FP32_SIMT, root_split=0, stream=None):
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     _check(load().nncp_set_options(ctx, int(precision), int(root_split), _stream(stream)), ctx)
+
+
+def nncp_set_dimtree(ctx, enabled):
+    _check(load().nncp_set_dimtree(ctx, 1 if enabled else 0), ctx)
 
 
 def nncp_workspace_size(ctx):
@@ -486,6 +491,9 @@ class Context:
 
     def iteration_kernels(self):
         return nncp_iteration_kernels(self.ctx)
+
+    def set_dimtree(self, enabled):
+        nncp_set_dimtree(self.ctx, enabled)
 
     def solve(self, max_iters, tol=0.0):
         return nncp_solve(self.ctx, self.R, max_iters, tol)

@@ -210,3 +210,34 @@ def test_full_size_512cubed_sampled_rows(nn):
                 assert err <= MTTKRP_TOL, (n, tree, err)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("dims,R", [((20, 17, 13), 5), ((9, 7, 8, 6), 4)])
+def test_solve_without_dimension_tree_matches_oracle(nn, dims, R):
+    # every M(n) by a full MTTKRP (Sec. V-C's comparison): same iteration,
+    # checked against the oracle's own direct path
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=31, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=32)
+    ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                           max_iters=8, use_dimtree=False)
+    c, X, Hd = _ctx(nn, dims, R, x, [h.copy() for h in H0])
+    try:
+        c.set_dimtree(False)
+        lam, k, fit = c.solve(8)
+        assert k == 8 and abs(fit - ref["fits"][-1]) <= FIT_TOL
+        for n in range(len(dims)):
+            assert rel_fro(Hd[n].cpu().numpy(), ref["H"][n]) <= 1e-3, n
+    finally:
+        c.close()
+
+
+def test_without_dimension_tree_is_fp32_only(nn):
+    if "tcgen05" not in nn.nncp_version():
+        pytest.skip("no tensor-core path in this build")
+    c = nn.Context((32, 16, 8), 4, precision=nn.NNCP_SPLIT_BF16X3)
+    try:
+        with pytest.raises(nn.NNCPError) as info:
+            c.set_dimtree(False)
+        assert info.value.status == nn.NNCP_ERR_UNSUPPORTED
+    finally:
+        c.close()
