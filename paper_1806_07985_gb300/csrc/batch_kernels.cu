@@ -119,62 +119,50 @@ constexpr int kThreads = 256;
 // summation order of an output depends only on its tensor's shape.
 constexpr int kGroupThreads = 256;
 
-// floats [0, L) of src (16-byte aligned), streamed (X is read once per pass)
-template <int NT, int V4>
-__device__ __forceinline__ void tile_fetch(const float* __restrict__ src, int L, float4 (&r)[V4]) {
-#pragma unroll
-  for (int k = 0; k < V4; ++k) {
-    const int e = 4 * ((int)threadIdx.x + NT * k);
-    if (e + 3 < L) {
-      r[k] = __ldcs(reinterpret_cast<const float4*>(src + e));
-    } else {
-      r[k].x = e < L ? __ldcs(src + e) : 0.0f;
-      r[k].y = e + 1 < L ? __ldcs(src + e + 1) : 0.0f;
-      r[k].z = e + 2 < L ? __ldcs(src + e + 2) : 0.0f;
-      r[k].w = 0.0f;
-    }
-  }
+// Tiles are copied global -> shared with cp.async (no registers held while
+// in flight) into a two-stage ring, so tile k+1 streams in while tile k is
+// formed and contracted; X is read once per pass.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING) : "memory");
 }
 
-// the tile as fetched: Xs[e] = src[e]
-template <int NT, int V4>
-__device__ __forceinline__ void tile_store_dense(float* Xs, int L, const float4 (&r)[V4]) {
-#pragma unroll
-  for (int k = 0; k < V4; ++k) {
-    const int e = 4 * ((int)threadIdx.x + NT * k);
-    if (e + 3 < L) {
-      *reinterpret_cast<float4*>(Xs + e) = r[k];
-    } else {
-      if (e < L) Xs[e] = r[k].x;
-      if (e + 1 < L) Xs[e + 1] = r[k].y;
-      if (e + 2 < L) Xs[e + 2] = r[k].z;
-    }
-  }
+// floats [0, L) of src (16-byte aligned) to Xs[0, L)
+__device__ __forceinline__ void tile_copy_dense(float* Xs, const float* __restrict__ src, int L) {
+  const int L4 = L & ~3;
+  for (int e = 4 * (int)threadIdx.x; e < L4; e += 4 * kThreads) cp_async16(Xs + e, src + e);
+  const int tail = L4 + (int)threadIdx.x;
+  if (tail < L) cp_async4(Xs + tail, src + tail);
 }
 
-// rows of I1 floats at an odd stride S (so threads reading one column of
+// rows of I1 floats to an odd stride S (threads reading one column of
 // consecutive rows hit distinct banks): Xs[row * S + col] = src[row * I1 + col]
-template <int NT, int V4>
-__device__ __forceinline__ void tile_store_rows(float* Xs, int L, int I1, int S,
-                                                const float4 (&r)[V4]) {
+__device__ __forceinline__ void tile_copy_rows(float* Xs, const float* __restrict__ src, int L,
+                                               int I1, int S) {
   if (S == I1) {
-    tile_store_dense<NT, V4>(Xs, L, r);
+    tile_copy_dense(Xs, src, L);
     return;
   }
-#pragma unroll
-  for (int k = 0; k < V4; ++k) {
-    const int e = 4 * ((int)threadIdx.x + NT * k);
-    if (e < L) {
-      int row = e / I1, col = e - row * I1;
-      const float v[4] = {r[k].x, r[k].y, r[k].z, r[k].w};
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        if (e + b < L) Xs[row * S + col] = v[b];
-        if (++col == I1) {
-          col = 0;
-          ++row;
-        }
-      }
+  int e = threadIdx.x;
+  int row = e / I1, col = e - row * I1;
+  const int drow = kThreads / I1, dcol = kThreads - drow * I1;
+  for (; e < L; e += kThreads) {
+    cp_async4(Xs + row * S + col, src + e);
+    row += drow;
+    col += dcol;
+    if (col >= I1) {
+      col -= I1;
+      ++row;
     }
   }
 }
@@ -205,10 +193,11 @@ __device__ __forceinline__ void fma4(float (&a)[4], float x, const float4& w) {
 // Item (tensor, chunk).  Thread = row i with all RQB = b_rq(R) rank groups;
 // 256 / I1 column groups split each tile's rows (j = g, g + G, ...) and are
 // added in group order at the end of the chunk.
-template <int RQB, bool PF>
-__device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float* Xs, float* Ws) {
-  constexpr int V4 = kTileFloats / 4 / kThreads;
+template <int RQB>
+__device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float* smem) {
   constexpr int WU = kWsFloats / 4 / kThreads;
+  float* Xbuf[2] = {smem, smem + kTileFloats};
+  float* Ws = smem + 2 * kTileFloats;  // kWsFloats: rows x padded rank
   const int tid = threadIdx.x;
   const int R = t.R, N = t.N;
   const int I1 = (int)t.dims[0];
@@ -225,19 +214,20 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[u][b] = 0.0f;
   const int ntile = (j1 - j0 + nj - 1) / nj;
-  float4 xr[V4];
-  if (PF) tile_fetch<kThreads, V4>(t.X + (long long)j0 * I1, min(nj, j1 - j0) * I1, xr);
   const float4* W4 = reinterpret_cast<const float4*>(Ws);
+  tile_copy_dense(Xbuf[0], t.X + (long long)j0 * I1, min(nj, j1 - j0) * I1);
+  cp_async_commit();
   for (int k = 0; k < ntile; ++k) {
     const int jt = j0 + k * nj, njk = min(nj, j1 - jt);
-    __syncthreads();
-    if (!PF) tile_fetch<kThreads, V4>(t.X + (long long)jt * I1, njk * I1, xr);
-    tile_store_dense<kThreads, V4>(Xs, njk * I1, xr);
-    if (PF && k + 1 < ntile) {
+    if (k + 1 < ntile) {
       const int jn = jt + nj;
-      tile_fetch<kThreads, V4>(t.X + (long long)jn * I1, min(nj, j1 - jn) * I1, xr);
+      tile_copy_dense(Xbuf[(k + 1) & 1], t.X + (long long)jn * I1, min(nj, j1 - jn) * I1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
-    // Khatri-Rao rows of the tile: float4 entries (row, rank group), nj * RQB <= 1024
+    // Khatri-Rao rows of the tile: float4 entries (row, rank group), nj * RQB <= kWsFloats / 4
     {
       float4 w[WU];
       int rem[WU];
@@ -271,7 +261,7 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
     }
     __syncthreads();
     if (act) {
-      const float* xp = Xs + i;
+      const float* xp = Xbuf[k & 1] + i;
 #pragma unroll 2
       for (int jj = g; jj < njk; jj += G) {
         const float x = xp[jj * I1];
@@ -279,13 +269,13 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
         for (int u = 0; u < RQB; ++u) fma4(acc[u], x, W4[jj * RQB + u]);
       }
     }
+    __syncthreads();
   }
   float* out = t.part + (long long)chunk * I1 * R;
   if (G > 1) {
-    float4* red = reinterpret_cast<float4*>(Xs);  // G * I1 <= 256 float4
+    float4* red = reinterpret_cast<float4*>(Xbuf[0]);  // G * I1 <= 256 float4
 #pragma unroll
     for (int u = 0; u < RQB; ++u) {
-      __syncthreads();
       if (act) red[tid] = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
       __syncthreads();
       if (tid < I1) {
@@ -301,6 +291,7 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
         for (int b = 0; b < 4; ++b)
           if (4 * u + b < R) out[tid * R + 4 * u + b] = s4[b];
       }
+      __syncthreads();
     }
   } else if (act) {
 #pragma unroll
@@ -312,20 +303,18 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
 }
 
 template <int RMAX>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, RMAX <= 16 ? 4 : (RMAX <= 32 ? 3 : 2))
 k_b_pm_right(const BTensor* __restrict__ ts, const int4* __restrict__ items) {
   extern __shared__ __align__(16) float smem[];
   const int4 it = items[blockIdx.x];
   const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
-  float* Xs = smem;                // kTileFloats
-  float* Ws = smem + kTileFloats;  // kWsFloats: rows x padded rank
   switch (b_rq(t.R)) {
-    case 1: pm_right_item<1, true>(t, it.y, Xs, Ws); break;
-    case 2: pm_right_item<2, true>(t, it.y, Xs, Ws); break;
-    case 4: pm_right_item<4, true>(t, it.y, Xs, Ws); break;
-    case 8: if constexpr (RMAX >= 32) pm_right_item<8, true>(t, it.y, Xs, Ws); break;
-    default: if constexpr (RMAX >= 64) pm_right_item<16, false>(t, it.y, Xs, Ws); break;
+    case 1: pm_right_item<1>(t, it.y, smem); break;
+    case 2: pm_right_item<2>(t, it.y, smem); break;
+    case 4: pm_right_item<4>(t, it.y, smem); break;
+    case 8: if constexpr (RMAX >= 32) pm_right_item<8>(t, it.y, smem); break;
+    default: if constexpr (RMAX >= 64) pm_right_item<16>(t, it.y, smem); break;
   }
 }
 
@@ -351,10 +340,10 @@ __global__ void __launch_bounds__(kReduceBlock) k_b_reduce(const BTensor* __rest
 }
 
 constexpr int kLeftRedFloats = 4 * kThreads;
-constexpr int kLeftV4 = kTileFloats / 4 / kThreads;
+constexpr int kLeftStageFloats = kTileFloats + kLeftMaxRows;  // rows at odd stride
 
 __host__ __device__ constexpr int left_fixed_floats() {
-  return kTileFloats + kLeftMaxRows + kLeftRedFloats;
+  return 2 * kLeftStageFloats + kLeftRedFloats;
 }
 
 // root -> node {2..N}: T(j, r) = sum_i X[i + I1 j] H_1(i, r).  Item (tensor,
@@ -362,9 +351,11 @@ __host__ __device__ constexpr int left_fixed_floats() {
 // zeros) sits in shared memory.  Thread = (row j, block of RQB rank groups);
 // when a tile has fewer than 256 such pairs (then RQB = 1) the i range is
 // split over groups added in group order.
-template <int RQB, bool PF>
-__device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* Xs, float* red,
-                                             float* Hs) {
+template <int RQB>
+__device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* smem) {
+  float* Xbuf[2] = {smem, smem + kLeftStageFloats};
+  float* red = smem + 2 * kLeftStageFloats;  // kLeftRedFloats
+  float* Hs = red + kLeftRedFloats;          // I1 x padded rank
   const int tid = threadIdx.x;
   const int R = t.R, Rq = b_rq(R), Rp = 4 * Rq;
   const int I1 = (int)t.dims[0], S = I1 | 1;
@@ -378,8 +369,8 @@ __device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* 
   const int npass = (P + kThreads - 1) / kThreads;
   const int g = G > 1 ? tid / P : 0;
   const int ia = g * I1 / G, ib = (g + 1) * I1 / G;
-  float4 xr[kLeftV4];
-  if (PF) tile_fetch<kThreads, kLeftV4>(t.X + (long long)jb0 * I1, min(nj, jb1 - jb0) * I1, xr);
+  tile_copy_rows(Xbuf[0], t.X + (long long)jb0 * I1, min(nj, jb1 - jb0) * I1, I1, S);
+  cp_async_commit();
   {
     const float* H1 = t.H[0];
     if (R == Rp) {
@@ -409,14 +400,16 @@ __device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* 
   const int ntile = (jb1 - jb0 + nj - 1) / nj;
   for (int k = 0; k < ntile; ++k) {
     const int jt = jb0 + k * nj, njk = min(nj, jb1 - jt);
-    __syncthreads();
-    if (!PF) tile_fetch<kThreads, kLeftV4>(t.X + (long long)jt * I1, njk * I1, xr);
-    tile_store_rows<kThreads, kLeftV4>(Xs, njk * I1, I1, S, xr);
-    if (PF && k + 1 < ntile) {
+    if (k + 1 < ntile) {
       const int jn = jt + nj;
-      tile_fetch<kThreads, kLeftV4>(t.X + (long long)jn * I1, min(nj, jb1 - jn) * I1, xr);
+      tile_copy_rows(Xbuf[(k + 1) & 1], t.X + (long long)jn * I1, min(nj, jb1 - jn) * I1, I1, S);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float* Xs = Xbuf[k & 1];
     for (int p = 0; p < npass; ++p) {
       const int pair = G > 1 ? tid - g * P : tid + kThreads * p;
       const int jl = pair / NB, qb = pair - jl * NB;
@@ -466,25 +459,23 @@ __device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* 
           }
       }
     }
+    __syncthreads();
   }
 }
 
 template <int RMAX>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, RMAX <= 16 ? 3 : 2)
 k_b_pm_left(const BTensor* __restrict__ ts, const int4* __restrict__ items) {
   extern __shared__ __align__(16) float smem[];
   const int4 it = items[blockIdx.x];
   const BTensor& t = ts[it.x];
   if (tensor_done(t)) return;
-  float* Xs = smem;                                // rows at odd stride
-  float* red = smem + kTileFloats + kLeftMaxRows;  // kLeftRedFloats
-  float* Hs = red + kLeftRedFloats;                // I1 x padded rank
   switch (b_rqb_left((int)t.dims[0], t.R)) {
-    case 1: pm_left_item<1, true>(t, it.y, Xs, red, Hs); break;
-    case 2: pm_left_item<2, true>(t, it.y, Xs, red, Hs); break;
-    case 4: pm_left_item<4, true>(t, it.y, Xs, red, Hs); break;
-    case 8: if constexpr (RMAX >= 32) pm_left_item<8, true>(t, it.y, Xs, red, Hs); break;
-    default: if constexpr (RMAX >= 64) pm_left_item<16, false>(t, it.y, Xs, red, Hs); break;
+    case 1: pm_left_item<1>(t, it.y, smem); break;
+    case 2: pm_left_item<2>(t, it.y, smem); break;
+    case 4: pm_left_item<4>(t, it.y, smem); break;
+    case 8: if constexpr (RMAX >= 32) pm_left_item<8>(t, it.y, smem); break;
+    default: if constexpr (RMAX >= 64) pm_left_item<16>(t, it.y, smem); break;
   }
 }
 
@@ -767,7 +758,7 @@ cudaError_t batch_attributes_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_b_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)update_smem<64>());
-  const int right = (kTileFloats + kWsFloats) * (int)sizeof(float);
+  const int right = (2 * kTileFloats + kWsFloats) * (int)sizeof(float);
   const int left = (left_fixed_floats() + kBatchMaxI * kBatchMaxRank) * (int)sizeof(float);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
@@ -781,7 +772,7 @@ cudaError_t batch_attributes_init() {
 namespace {
 
 cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, cudaStream_t st) {
-  const size_t sm = (size_t)(kTileFloats + kWsFloats) * sizeof(float);
+  const size_t sm = (size_t)(2 * kTileFloats + kWsFloats) * sizeof(float);
   const int n = p.pmr.count;
   const int4* it = items + p.pmr.off;
   if (n > 0) {

@@ -17,12 +17,13 @@ constexpr long long kBatchMaxElems = (1LL << 31) - 1;  // per tensor (32-bit ind
 
 // Tiles of the two root partial MTTKRPs.  X_(1) of a tensor is read as rows j
 // of I_1 contiguous floats; a tile is a run of whole rows (a multiple of four
-// rows, so every tile starts 16-byte aligned), at most kTileFloats floats.
-constexpr int kTileFloats = 8192;
-constexpr int kWsFloats = 4096;       // Khatri-Rao tile (rows x padded rank)
-constexpr int kLeftMaxRows = 2048;    // padded X tile <= kTileFloats + kLeftMaxRows
+// rows, so every tile starts 16-byte aligned), at most kTileFloats floats,
+// double-buffered in shared memory.
+constexpr int kTileFloats = 4096;
+constexpr int kWsFloats = 2048;       // Khatri-Rao tile (rows x padded rank)
+constexpr int kLeftMaxRows = 512;     // padded X tile <= kTileFloats + kLeftMaxRows
 constexpr int kRightTileTarget = 32768;  // elements per root -> {1} chunk
-constexpr int kLeftItemTiles = 4;        // tiles per root -> {2..N} item
+constexpr int kLeftItemTiles = 8;        // tiles per root -> {2..N} item
 // rank groups of four, rounded up to a power of two (1 .. 16), and the padded rank
 __host__ __device__ inline int b_rq(int R) {
   int q = 1;
