@@ -223,6 +223,7 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
 //   1 / lambda.  The finishing CTA forms lambda, G_n, the fit at n = N and S
 //   for the next mode.  Results do not depend on arrival order.
 constexpr int kMultiThreads = 512;
+constexpr int kGpreDoubles = 3072;  // other modes' Grams prefetched for the next S (24 KB)
 constexpr int kMultiMaxRows = 16384;
 
 template <int RMAX>
@@ -251,12 +252,12 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   float* Hs = St + RMAX * RMAX;         // ROWS x RP: H, then W
   float* Ms = Hs + ROWS * RP;           // ROWS x RP
   float* gpart = Ms + ROWS * RP;        // GROUPS x R x R, then W^T W in float64
-  __shared__ float lamf[RMAX];
+  __shared__ __align__(16) float lamf[RMAX];
   __shared__ float sinv[RMAX];
   __shared__ double red[T / 32];
   __shared__ double cinv_sh[RMAX];
-  __shared__ double scal_sh[4];  // beta, alpha, previous fit
-  __shared__ int last_sh;
+  __shared__ double scal_sh[4];  // beta, alpha, previous fit, tol
+  __shared__ int last_sh, it_sh;
   const int tid = threadIdx.x;
   const int R2 = R * R;
   const int row0 = blockIdx.x * ROWS;
@@ -280,6 +281,38 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     const int rr = e / R, c = e % R;
     Hs[rr * RP + c] = Hg[e];
     Ms[rr * RP + c] = Mg[e];
+  }
+  // everything the finishing CTA reads from global memory after the HALS
+  // sweep that is already known now is fetched with the staging loads: S of
+  // this mode (the fit's gamma at n = N), the other modes' Grams (the next
+  // S, when they fit in kGpreDoubles), alpha, the iteration count, the
+  // previous fit and the tolerance
+  constexpr int EPT = (RMAX * RMAX + T - 1) / T;
+  double sfit[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    sfit[q] = (is_last && e < R2) ? st.S[e] : 0.0;
+  }
+  double* Gpre = reinterpret_cast<double*>(gpart + GROUPS * RMAX * RMAX);
+  const int ng = N - (next_mode == n ? 1 : 2);
+  const bool gpre = ng > 0 && ng * R2 <= kGpreDoubles;
+  if (gpre) {
+#pragma unroll 4
+    for (int x = tid; x < ng * R2; x += T) {
+      const int slot = x / R2, e = x - slot * R2;
+      int k = -1;
+      for (int m = 0, seen = 0; m < N; ++m)
+        if (m != n && m != next_mode && seen++ == slot) k = m;
+      Gpre[x] = st.G[(long long)k * R2 + e];
+    }
+  }
+  if (tid == 0) {
+    const int it = st.flags[2];
+    it_sh = it;
+    scal_sh[1] = st.scalars[0];
+    scal_sh[2] = (it >= 1 && it <= kFitCapacity) ? st.fits[it - 1] : 0.0;
+    scal_sh[3] = st.scalars[4];
   }
   __syncthreads();
 
@@ -387,7 +420,6 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   }
   __syncthreads();
   // W^T W summed over the row groups (float32, group order)
-  constexpr int EPT = (RMAX * RMAX + T - 1) / T;
   float gsum[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
@@ -453,17 +485,13 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
       st.flags[8] = 0;  // ticket reset for the next launch
     }
   }
-  if (tid == 0) {
-    scal_sh[1] = st.scalars[0];
-    const int it = st.flags[2];
-    scal_sh[2] = (it >= 1 && it <= kFitCapacity) ? st.fits[it - 1] : 0.0;
-  }
   __syncthreads();
   for (int r = tid; r < R; r += T) {
-    const double v = sqrt(GW[r * R + r]);
-    st.lam[r] = v;
-    cinv_sh[r] = v > 0.0 ? 1.0 / v : 0.0;
-    lamf[r] = v > 0.0 ? (float)(1.0 / v) : 0.0f;  // from here on: 1 / lambda
+    const double g = GW[r * R + r];
+    const double ci = g > 0.0 ? rsqrt(g) : 0.0;  // 1 / lambda
+    st.lam[r] = g * ci;
+    cinv_sh[r] = ci;
+    lamf[r] = (float)ci;  // from here on: 1 / lambda
   }
   __syncthreads();
   double* Gn = st.G + (long long)n * R2;
@@ -472,8 +500,36 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     Gn[e] = GW[e] * cinv_sh[a] * cinv_sh[b];
   }
   // H = W / lambda (multiplication by the float32 reciprocal)
-  if (single) {
+  if (single && (R & 3) == 0) {
+    const float4* l4 = reinterpret_cast<const float4*>(lamf);
+    for (int v = tid; v < nrows * R / 4; v += T) {
+      const int e = 4 * v, rr = e / R, c = e - rr * R;
+      const float4 w = *reinterpret_cast<const float4*>(Hs + rr * RP + c);
+      const float4 l = l4[c >> 2];
+      reinterpret_cast<float4*>(H)[v] = make_float4(w.x * l.x, w.y * l.y, w.z * l.z, w.w * l.w);
+    }
+  } else if (single) {
     for (int e = tid; e < nrows * R; e += T) H[e] = Hs[(e / R) * RP + e % R] * lamf[e % R];
+  } else if ((R & 3) == 0) {
+    const int tot4 = In * R / 4;
+    const float4* l4 = reinterpret_cast<const float4*>(lamf);
+    float4* H4 = reinterpret_cast<float4*>(H);
+    for (int v0 = tid; v0 < tot4; v0 += 8 * T) {
+      float4 w[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int v = v0 + q * T;
+        if (v < tot4) w[q] = H4[v];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int v = v0 + q * T;
+        if (v < tot4) {
+          const float4 l = l4[(4 * v % R) >> 2];
+          H4[v] = make_float4(w[q].x * l.x, w[q].y * l.y, w[q].z * l.z, w[q].w * l.w);
+        }
+      }
+    }
   } else {
     const int tot = In * R;  // <= kMultiMaxRows * 64: 32-bit index arithmetic
     for (int e0 = tid; e0 < tot; e0 += 16 * T) {
@@ -495,7 +551,7 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * T;
-      if (e < R2) g += st.S[e] * GW[e];
+      if (e < R2) g += sfit[q] * GW[e];
     }
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
     __syncthreads();
@@ -504,7 +560,21 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     if (tid == 0) {
       double gamma = 0.0;
       for (int k = 0; k < T / 32; ++k) gamma += red[k];
-      record_fit_known(st, scal_sh[0], gamma, scal_sh[1], scal_sh[2]);
+      const double beta = scal_sh[0], alpha = scal_sh[1], prev = scal_sh[2], tol = scal_sh[3];
+      const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
+      const double fit = 1.0 - eps;
+      const int it = it_sh;
+      st.scalars[1] = beta;
+      st.scalars[2] = gamma;
+      st.scalars[3] = eps;
+      if (it < kFitCapacity) st.fits[it] = fit;
+      st.flags[2] = it + 1;
+      if (!isfinite(fit)) {
+        st.flags[3] = 1;
+        st.flags[0] = 1;
+      } else if (it >= 1 && it < kFitCapacity && fabs(fit - prev) < tol) {
+        st.flags[0] = 1;
+      }
     }
   }
   __syncthreads();
@@ -516,10 +586,17 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     const int e = tid + q * T;
     sv[q] = 1.0;
     if (e < R2) {
+      int slot = 0;
 #pragma unroll
       for (int k = 0; k < kMaxModes; ++k)
-        if (k < N && k != next_mode)
-          sv[q] *= (k == n ? GW[e] * cinv_sh[e / R] * cinv_sh[e % R] : st.G[(long long)k * R2 + e]);
+        if (k < N && k != next_mode) {
+          if (k == n) {
+            sv[q] *= GW[e] * cinv_sh[e / R] * cinv_sh[e % R];
+          } else {
+            sv[q] *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
+            ++slot;
+          }
+        }
     }
   }
 #pragma unroll
@@ -536,7 +613,8 @@ template <int RMAX>
 size_t multi_smem() {
   using C = MultiCfg<RMAX>;
   const size_t grams = (size_t)C::GROUPS * RMAX * RMAX;
-  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP) * sizeof(float) + grams * sizeof(float);
+  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP) * sizeof(float) + grams * sizeof(float) +
+         (size_t)kGpreDoubles * sizeof(double);
 }
 
 __global__ void k_solve_reset(SolveState st, int R, double tol) {
