@@ -61,7 +61,8 @@ constexpr long long kWaitCycles = 4000000000LL;
 
 constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;  // B builder row offsets
 // barriers: raw full/empty/converted per A stage, B full/empty, acc full/empty x2, drain
-constexpr int kNumBars = 3 * kMaxSF + 2 * kSB + 4 + 1;
+constexpr int kSA = 4;     // A stages in tensor memory (split-BF16x3), 64 columns each
+constexpr int kNumBars = 3 * kMaxSF + 2 * kSB + 4 + kSA + 1;
 constexpr int kMiscBytes = kNumBars * 8 + 256;
 constexpr int kSmemMax = 232448;  // 227 KB per CTA on sm_103a
 
@@ -202,6 +203,37 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       : "memory");
 }
 
+// A operand in tensor memory (lane = row of A, 32-bit column = two bf16
+// contraction elements, the lower one in the low half), B in shared memory.
+__device__ __forceinline__ void mma_f16_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                           uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    bar)
@@ -317,6 +349,10 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   auto b_empty = [&](int i) { return bar0 + 8u * (3 * kMaxSF + kSB + i); };
   auto acc_full = [&](int i) { return bar0 + 8u * (3 * kMaxSF + 2 * kSB + i); };
   auto acc_empty = [&](int i) { return bar0 + 8u * (3 * kMaxSF + 2 * kSB + 2 + i); };
+  // split-BF16x3: the converters write A (hi and lo) to tensor memory; conv_full(i)
+  // then marks A stage i written, a_empty(i) its MMAs done
+  auto a_empty = [&](int i) { return bar0 + 8u * (3 * kMaxSF + 2 * kSB + 4 + i); };
+  const bool a_tmem = p.mode == NNCP_SPLIT_BF16X3;
   const uint32_t drain_bar = bar0 + 8u * (kNumBars - 1);
   uint8_t* misc = gbase + p.sm.off_bar + kNumBars * 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);
@@ -327,15 +363,18 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
 
   const int Rp = p.Rp;
   const uint32_t acc_cols = 2u * Rp;  // per accumulator buffer
+  const uint32_t a_col0 = 2u * acc_cols;  // A stages (split-BF16x3) after the accumulators
   uint32_t tmem_cols = 32;
-  while (tmem_cols < 2 * acc_cols) tmem_cols <<= 1;
+  while (tmem_cols < a_col0 + (a_tmem ? 64u * kSA : 0u)) tmem_cols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kSF; ++i) {
       mbar_init(raw_full(i), 1);
-      mbar_init(raw_empty(i), 1);
+      // split-BF16x3: every converter warp releases the stage once it has read it
+      mbar_init(raw_empty(i), a_tmem ? kConvThreads / 32 : 1);
       mbar_init(conv_full(i), kConvThreads / 32);
     }
+    for (int i = 0; i < kSA; ++i) mbar_init(a_empty(i), 1);
     for (int i = 0; i < kSB; ++i) {
       mbar_init(b_full(i), (p.b_resident && i == 0) ? 2 * kSB : 2);
       mbar_init(b_empty(i), 1);
@@ -427,7 +466,28 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         if (!mbar_wait(acc_empty(bsel), (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, p.err)) break;
         tc_fence_after();
         const uint32_t d = tmem_base + bsel * acc_cols;
-        for (int s = 0; s < w.nk; ++s) {
+        for (int s = 0; s < w.nk && a_tmem; ++s) {
+          // A (hi, lo) in tensor memory stage sa, B in shared memory
+          if (!mbar_wait(conv_full(sa), pha, abort_flag, p.err) ||
+              (!p.b_resident && !mbar_wait(b_full(sb), phb, abort_flag, p.err))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ahi = tmem_base + a_col0 + 64u * sa;
+          const uint32_t b = b0 + (p.b_resident ? s : sb) * kBBytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t bd = sw128_desc(b + kk * 32);
+            mma_f16_ta(d, ahi + kk * 8, bd, idesc_full, (s > 0 || kk > 0) ? 1u : 0u);
+            mma_f16_ta(d, ahi + 32 + kk * 8, bd, idesc_hi, 1u);
+          }
+          mma_commit(a_empty(sa));
+          if (!p.b_resident) mma_commit(b_empty(sb));
+          if (++sa == kSA) { sa = 0; pha ^= 1u; }
+          if (++sb == kSB) { sb = 0; phb ^= 1u; }
+        }
+        for (int s = 0; s < w.nk && !a_tmem; ++s) {
           const uint32_t afull = p.direct ? raw_full(sa) : conv_full(sa);
           const uint32_t aempty = raw_empty(sa);
           if (!mbar_wait(afull, pha, abort_flag, p.err) ||
@@ -614,8 +674,10 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     // sources: the two halves of a row in lanes l and l + 16 of one warp, eight
     // consecutive rows per quarter-warp (conflict-free 16-byte reads).  MN-major
     // sources: 32 consecutive rows per warp (conflict-free 4-byte reads).
-    const int m = p.contract_fast ? ((ct >> 5) * 16 + (ct & 15)) : (ct & 127);
-    const int kh = p.contract_fast ? ((ct >> 4) & 1) : (ct >> 7);
+    // (split-BF16x3 writes A to tensor memory: row m must sit in this warp's lane
+    // quarter, so 32 consecutive rows per warp for both sources)
+    const int m = (p.contract_fast && !a_tmem) ? ((ct >> 5) * 16 + (ct & 15)) : (ct & 127);
+    const int kh = (p.contract_fast && !a_tmem) ? ((ct >> 4) & 1) : (ct >> 7);
     const bool epi_warp = warp < kWarpConv + 4;   // warps 8-11 also run the epilogue
     const int q = warp & 3;                       // TMEM lane quarter of this warp
     const bool two = p.mode != NNCP_TF32;
@@ -660,9 +722,51 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       if (lane == 0) mbar_arrive(acc_empty(bsel));
       return true;
     };
+    int sa = 0;
+    uint32_t pha = 0;
     for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
       const Unit w = get_unit(p, u);
-      for (int s = 0; s < w.nk && !p.direct; ++s) {
+      for (int s = 0; s < w.nk && a_tmem; ++s) {
+        // wait for the TMA stage and the tensor-memory A stage, then, eight
+        // elements of row m (half kh) at a time, read, split into hi + lo and
+        // write both to A stage sa; release the TMA stage after the last read
+        bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err);
+        got = got && mbar_wait(a_empty(sa), pha ^ 1u, abort_flag, p.err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = raw0 + sf * kRawBytes;
+        const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + a_col0 + 64u * sa + 16u * kh;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          float x[8];
+          if (p.contract_fast) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const float4 a = lds128(sw128_chunk(st + kh * 16384, m, 2 * g + c));
+              x[4 * c] = a.x; x[4 * c + 1] = a.y; x[4 * c + 2] = a.z; x[4 * c + 3] = a.w;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = lds32(st + (32 * kh + 8 * g + e) * 512 + m * 4);
+          }
+          uint32_t hi[4], lo[4];
+          split8(x, hi, lo);
+          tmem_st4(ta + 4 * g, hi);
+          tmem_st4(ta + 32 + 4 * g, lo);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(raw_empty(sf));
+        if (++sf == kSF) { sf = 0; phf ^= 1u; }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(conv_full(sa));
+        if (++sa == kSA) { sa = 0; pha ^= 1u; }
+      }
+      for (int s = 0; s < w.nk && !p.direct && !a_tmem; ++s) {
         const bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err);
         const uint32_t st = raw0 + sf * kRawBytes;
         // read phase: this thread's 32 source elements of row m, half kh
