@@ -7,13 +7,17 @@
 // memory already is.  Two contractions:
 //   contract_fast: out(j, r) = sum_i X[i + IL*j] K(i, r)   (M = IR rows, K = IL)
 //   contract_slow: out(i, r) = sum_j X[i + IL*j] K(j, r)   (M = IL rows, K = IR)
-// A (128 output rows x 64 contraction elements per stage) is always handed to
-// the MMA K-major with the 128-byte swizzle.  contract_fast tiles arrive
-// K-major from TMA; contract_slow tiles arrive MN-major (no swizzle) and the
-// converter warps transpose them.  Conversion is done in place: the converted
-// tile (bf16 hi + lo, or a transposed copy) has the size of its source, so each
-// converter thread reads its share into registers, a named barrier separates
-// the reads from the writes, and the result overwrites the TMA stage.  Precision modes:
+// contract_fast tiles (128 output rows x 64 contraction elements per stage)
+// arrive K-major from TMA with the 128-byte swizzle; contract_slow tiles arrive
+// MN-major (no swizzle).  SPLIT_BF16X3 converter threads read one row of A each
+// and write its bf16 hi and lo parts into a ring of A stages in tensor memory
+// (tcgen05.st, one TMEM lane per row), from which the MMA takes A; the TMA stage
+// is released as soon as it has been read.  The other modes hand A to the MMA
+// from shared memory, K-major with the 128-byte swizzle: TF32 K-major tiles
+// directly, everything else converted in place (the converted tile has the size
+// of its source, so each converter thread reads its share into registers, a
+// named barrier separates the reads from the writes, and the result overwrites
+// the TMA stage).  Precision modes:
 //   TF32         kind::tf32 on the float32 tensor (direct when K-major);
 //   SPLIT_BF16X3 x = hi + lo in bf16, K = Khi + Klo: D = hi*[Khi|Klo] + lo*Khi
 //                (three products, float32 accumulation in TMEM);
