@@ -112,7 +112,7 @@ KrpDesc krp(const nncp_ctx* c, int first, int last) {
 struct Plan {
   size_t node_off[2][kMaxModes];
   size_t node_bytes[2][kMaxModes];
-  size_t M_off, upd_off, part_off, part_cap, gram_off, G_off, S_off, S32_off, lam_off, scal_off,
+  size_t M_off, upd_off, part_off, part_cap, gram_off, G_off, S_off, lam_off, scal_off,
       fits_off, flags_off, red_off;
   int red_nparts;
   size_t tc_off, tc_bytes;
@@ -172,9 +172,8 @@ Plan make_plan(const nncp_ctx* c) {
   int maxblocks = 0;
   for (int n = 0; n < N; ++n) maxblocks = std::max(maxblocks, hals_gram_blocks(c->dims[n]));
   p.gram_off = take((size_t)maxblocks * (R * R + 1) * sizeof(double));
-  p.G_off = take((size_t)N * R * R * sizeof(double));
-  p.S_off = take((size_t)R * R * sizeof(double));
-  p.S32_off = take((size_t)R * R * sizeof(float));
+  p.G_off = take((size_t)N * R * R * sizeof(float));
+  p.S_off = take((size_t)R * R * sizeof(float));
   p.lam_off = take((size_t)R * sizeof(double));
   p.scal_off = take(16 * sizeof(double));
   p.fits_off = take((size_t)kFitCapacity * sizeof(double));
@@ -198,9 +197,8 @@ void bind_workspace(nncp_ctx* c) {
   c->partials = reinterpret_cast<float*>(w + p.part_off);
   c->part_cap = p.part_cap;
   c->st.gram_part = reinterpret_cast<double*>(w + p.gram_off);
-  c->st.G = reinterpret_cast<double*>(w + p.G_off);
-  c->st.S = reinterpret_cast<double*>(w + p.S_off);
-  c->st.S32 = reinterpret_cast<float*>(w + p.S32_off);
+  c->st.G = reinterpret_cast<float*>(w + p.G_off);
+  c->st.S = reinterpret_cast<float*>(w + p.S_off);
   c->st.lam = reinterpret_cast<double*>(w + p.lam_off);
   c->st.scalars = reinterpret_cast<double*>(w + p.scal_off);
   c->st.fits = reinterpret_cast<double*>(w + p.fits_off);
@@ -245,6 +243,9 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st) {
 }
 
 cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
+  if (cluster_update_ok(c->dims[n], c->R))
+    return launch_update_cluster(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                                 n == c->N - 1, c->st, st);
   if (multi_update_ok(c->dims[n], c->R))
     return launch_update_multi(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
                                n == c->N - 1, c->st, c->upd_part, st);

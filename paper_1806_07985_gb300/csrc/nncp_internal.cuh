@@ -4,7 +4,65 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace nncp {
+
+// ---- programmatic dependent launch --------------------------------------------
+// The kernels of one outer iteration are captured into a CUDA graph with
+// programmatic stream serialization, so a kernel may be scheduled while its
+// predecessor in the iteration is still running.  Every kernel launched that way
+// calls pdl_wait() before its first access to memory that an earlier kernel
+// writes, or that a later one writes while an earlier one may still read it.  pdl_wait() returns
+// once every predecessor grid has completed and its writes are visible, so the
+// chain stays ordered transitively.  Small kernels then call pdl_trigger(), which
+// lets their successor be scheduled on the SMs they leave free; large grids do
+// not, so their successor is scheduled as their CTAs exit.  Outside such a
+// launch both return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches k(args...) on st: with programmatic stream serialization while st is
+// being captured into a graph, as an ordinary launch otherwise.  Only kernels
+// that follow the pdl_wait() rule above are launched through this.
+// cluster_x > 0 launches the grid as thread-block clusters of cluster_x CTAs.
+template <typename... P, typename... A>
+cudaError_t launch_kernel_cluster(void (*k)(P...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t st, int cluster_x, A&&... args) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute at[2];
+  unsigned na = 0;
+  if (cluster_x > 0) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = (unsigned)cluster_x;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (cs == cudaStreamCaptureStatusActive) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
+template <typename... P, typename... A>
+cudaError_t launch_kernel(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          A&&... args) {
+  return launch_kernel_cluster(k, grid, block, smem, st, 0, std::forward<A>(args)...);
+}
 
 constexpr int kMaxModes = 8;
 constexpr int kMaxRank = 128;
@@ -22,12 +80,12 @@ struct KrpDesc {
 
 // Per-solve device state (lives in the caller's workspace).
 struct SolveState {
-  double* G;        // N x R x R, Gram of each normalised factor
-  double* S;        // R x R, Hadamard of Grams for the mode being updated
-  float* S32;       // R x R, S rounded to float32 (HALS arithmetic)
+  float* G;         // N x R x R, Gram of each normalised factor
+  float* S;         // R x R, Hadamard of the Grams for the mode being updated
   double* lam;      // R
   double* gram_part;  // blocks x (R*R + 1): per-block W^T W and <M, W>
-  double* scalars;  // [0] alpha = ||X||^2, [1] beta, [2] gamma, [3] eps, [4] tol
+  double* scalars;  // [0] alpha = ||X||^2, [1] beta, [2] gamma, [3] eps, [4] tol,
+                    // [5] the last recorded fit, [8..9] explicit residual and ||X||^2
   double* fits;     // kFitCapacity
   int* flags;       // [0] done, [1] status, [2] iteration count, [3] nonfinite, [8] CTA ticket
 };
@@ -108,10 +166,16 @@ cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveS
 int hals_gram_blocks(int64_t In);
 
 // Whole mode update (HALS, Gram, normalisation, fit, next S) in one launch over
-// CTAs of 32 rows, used when multi_update_ok(In, R); `part` is device scratch of
-// multi_update_scratch(In, R) floats.
+// CTAs of up to 512 rows (R <= 32) or 128 rows (R <= 64), used when
+// multi_update_ok(In, R); `part` is device scratch of multi_update_scratch(In, R)
+// floats.
 bool multi_update_ok(int64_t In, int R);
 size_t multi_update_scratch(int64_t In, int R);
+// The same update on one thread-block cluster (cluster_update_ok(In, R):
+// I_n <= 1024, R <= 64), preferred where it applies; needs no scratch.
+bool cluster_update_ok(int64_t In, int R);
+cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, int N, int n,
+                                  int next_mode, int is_last, SolveState st, cudaStream_t stream);
 cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
                                 int next_mode, int is_last, SolveState st, float* part,
                                 cudaStream_t stream);

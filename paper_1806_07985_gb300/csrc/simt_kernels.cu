@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kThreads)
 k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q, KrpDesc KL,
               KrpDesc KQ, int R, long long kchunk, float* __restrict__ out,
               long long out_chunk_stride) {
+  pdl_wait();  // no early trigger: a large grid; its successor spreads as CTAs exit
   __shared__ __align__(16) float Xs[kBK][kBI + 4];
   __shared__ __align__(16) float Ws[kBK][kRT];
   __shared__ TileRows rows[kBK];
@@ -140,6 +141,8 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
 // sums over c = 0, 4, 8, ... / 1, 5, 9, ... combined in a fixed order).
 __global__ void k_reduce_chunks(const float* __restrict__ part, long long E, int C,
                                 float* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E;
        e += (long long)gridDim.x * blockDim.x) {
     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
@@ -163,6 +166,8 @@ template <int V>
 __global__ void __launch_bounds__(kThreads)
 k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, int R,
             long long kchunk, float* __restrict__ out, long long out_chunk_stride) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ float smem[];
   float* Ws = smem;  // kBK x R
   __shared__ int offs[kBK][kMaxModes];
@@ -218,6 +223,8 @@ k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, i
 template <int V>
 __global__ void k_mttv_first(const float* __restrict__ T, long long I, const float* __restrict__ H,
                              int R, int G, float* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ float red[];  // G x R
   const long long j = blockIdx.x;
   const int RV = R / V;
@@ -351,18 +358,11 @@ cudaError_t launch_simt_mttkrp(const float* X, int64_t L, int64_t I, int64_t Q,
     dst = partials;
   }
   dim3 grid((unsigned)gx, (unsigned)C, (unsigned)gz);
-  if (L == 1)
-    k_simt_mttkrp<true><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
-                                                   (long long)I * R);
-  else
-    k_simt_mttkrp<false><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
-                                                    (long long)I * R);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_kernel(L == 1 ? k_simt_mttkrp<true> : k_simt_mttkrp<false>, grid,
+                                dim3(kThreads), 0, st, X, (long long)L, (long long)I,
+                                (long long)Q, KL, KQ, R, kchunk, dst, (long long)I * R);
   if (e != cudaSuccess || C == 1) return e;
-  long long E = (long long)I * R;
-  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
-  k_reduce_chunks<<<blocks, 256, 0, st>>>(partials, E, C, out);
-  return cudaGetLastError();
+  return launch_reduce_chunks(partials, (long long)I * R, C, out, num_sms, st);
 }
 
 // Same MTTKRP with the split-K chunk count capped so the partials fit in
@@ -383,26 +383,18 @@ cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int6
     dst = partials;
   }
   dim3 grid((unsigned)gx, (unsigned)C, (unsigned)gz);
-  if (L == 1)
-    k_simt_mttkrp<true><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
-                                                   (long long)I * R);
-  else
-    k_simt_mttkrp<false><<<grid, kThreads, 0, st>>>(X, L, I, Q, KL, KQ, R, kchunk, dst,
-                                                    (long long)I * R);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_kernel(L == 1 ? k_simt_mttkrp<true> : k_simt_mttkrp<false>, grid,
+                                dim3(kThreads), 0, st, X, (long long)L, (long long)I,
+                                (long long)Q, KL, KQ, R, kchunk, dst, (long long)I * R);
   if (e != cudaSuccess || C == 1) return e;
-  long long E = (long long)I * R;
-  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
-  k_reduce_chunks<<<blocks, 256, 0, st>>>(partials, E, C, out);
-  return cudaGetLastError();
+  return launch_reduce_chunks(partials, (long long)I * R, C, out, num_sms, st);
 }
 
 cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out, int num_sms,
                                  cudaStream_t st) {
   int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
   if (blocks < 1) blocks = 1;
-  k_reduce_chunks<<<blocks, 256, 0, st>>>(part, E, C, out);
-  return cudaGetLastError();
+  return launch_kernel(k_reduce_chunks, dim3(blocks), dim3(256), 0, st, part, (long long)E, C, out);
 }
 
 size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
@@ -427,13 +419,9 @@ cudaError_t launch_mttv_leaf(const float* T, int64_t I, int64_t K, const KrpDesc
     dst = partials;
   }
   size_t smem = (size_t)kBK * R * sizeof(float);
-  if (V == 4)
-    k_mttv_leaf<4><<<dim3((unsigned)gx, (unsigned)C), kThreads, smem, st>>>(T, I, K, KK, R, kchunk,
-                                                                           dst, E);
-  else
-    k_mttv_leaf<1><<<dim3((unsigned)gx, (unsigned)C), kThreads, smem, st>>>(T, I, K, KK, R, kchunk,
-                                                                           dst, E);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_kernel(V == 4 ? k_mttv_leaf<4> : k_mttv_leaf<1>,
+                                dim3((unsigned)gx, (unsigned)C), dim3(kThreads), smem, st, T,
+                                (long long)I, (long long)K, KK, R, kchunk, dst, E);
   if (e != cudaSuccess || C == 1) return e;
   return launch_reduce_chunks(partials, E, C, out, num_sms, st);
 }
@@ -446,11 +434,8 @@ cudaError_t launch_mttv_first(const float* T, int64_t I, int64_t J, const float*
   if (G > I) G = (int)I;
   const int threads = G * RV;
   size_t smem = (size_t)G * R * sizeof(float);
-  if (V == 4)
-    k_mttv_first<4><<<(unsigned)J, threads, smem, st>>>(T, I, H, R, G, out);
-  else
-    k_mttv_first<1><<<(unsigned)J, threads, smem, st>>>(T, I, H, R, G, out);
-  return cudaGetLastError();
+  return launch_kernel(V == 4 ? k_mttv_first<4> : k_mttv_first<1>, dim3((unsigned)J),
+                       dim3(threads), smem, st, T, (long long)I, H, R, G, out);
 }
 
 cudaError_t launch_sumsq(const void* X, int bf16, int64_t n, double* partials, int nparts,

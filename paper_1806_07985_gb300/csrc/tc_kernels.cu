@@ -331,6 +331,14 @@ __device__ __forceinline__ Unit get_unit(const TcParams& p, long long u) {
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
+  // Launched in a graph with programmatic serialization, the kernel may start
+  // while its predecessor runs: only the B builders (factor rows) and the
+  // epilogue (output) touch memory that other kernels of the iteration write or
+  // read, so only they wait for it (pdl_wait); the producer streams the tensor,
+  // which nothing in the iteration writes, and the converters fill the tensor-
+  // memory A stages from it in the meantime.  The kernel does not trigger its
+  // successor early: that one is scheduled as CTAs exit, and CTAs placed on the
+  // first SMs to free up would crowd there instead of spreading over the GPU.
   extern __shared__ uint8_t smem_dyn[];
   const uint32_t sbase_raw = smem_u32(smem_dyn);
   const uint32_t sbase = (sbase_raw + 1023u) & ~1023u;
@@ -535,6 +543,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     }
   } else if (warp < kWarpConv) {
     // ---------------------------------------------- Khatri-Rao B builders --
+    pdl_wait();
     // Builder warps 2w and 2w+1 form, for every stage t with t % kSB == w,
     // contraction elements [32 h, 32 h + 32) of B slot w (h = warp parity).
     const int bw = (warp - kWarpB) >> 1;
@@ -692,6 +701,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     Unit prev;
     prev.mt = -1;
     auto epilogue = [&](const Unit& w, long long lj) -> bool {
+      pdl_wait();
       const int bsel = (int)(lj & 1);
       const bool got = mbar_wait(acc_full(bsel), (uint32_t)((lj >> 1) & 1), abort_flag, p.err);
       if (!__all_sync(0xffffffffu, got)) return false;
@@ -1023,8 +1033,8 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
   p.sm = plan_smem(precision, contract_fast, p.direct, bf16x, pl.Rp, pl.K, pl.nsplit, &p.b_resident);
   if (p.sm.nsf < 2) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(pl.n_units, num_sms);
-  k_tc_partial_mttkrp<<<grid, kThreads, p.sm.total, st>>>(map, p);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_kernel(k_tc_partial_mttkrp, dim3(grid), dim3(kThreads), p.sm.total, st,
+                                map, p);
   if (e != cudaSuccess || pl.nsplit == 1) return e;
   return launch_reduce_chunks(partials, pl.M * R, (int)pl.nsplit, out, num_sms, st);
 }

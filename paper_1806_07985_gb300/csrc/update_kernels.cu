@@ -4,8 +4,11 @@
 //   a single-CTA finalise: lambda = column norms, G_n = H_n^T H_n,
 //   H_n = W diag(lambda)^-1, the fit from the Sec. IV-B identity at n = N,
 //   and S = Hadamard of the other Grams for the next mode.
-// FP64 is used for S, lambda, the Gram sums and the fit; the HALS arithmetic
-// and the factors are float32.
+// The factors, the HALS arithmetic, the Grams and S are float32.  The sums the
+// fit needs to more than float32 precision (<M, W> and lambda^T (S * G) lambda)
+// are float-float (unevaluated hi + lo pairs added with the error-free TwoSum),
+// and only the fit's last few scalar steps are float64: float64 issues about
+// 60x slower than float32 on this GPU, so it is kept off every per-element path.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -30,8 +33,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 // and partial <M, W>.
 __global__ void __launch_bounds__(kHalsThreads)
 k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, int R,
-            const float* __restrict__ S32, const double* __restrict__ lam,
+            const float* __restrict__ S, const double* __restrict__ lam,
             double* __restrict__ gram_part, const int* __restrict__ flags, int do_hals) {
+  pdl_wait();
+  pdl_trigger();
   if (flags && flags[0]) return;
   extern __shared__ float sm[];
   float* Ss = sm;                        // R x R
@@ -43,7 +48,7 @@ k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, in
   const int nrows = (int)min((long long)kRowsPerBlock, In - row0);
 
   if (do_hals)
-    for (int t = threadIdx.x; t < R * R; t += blockDim.x) Ss[t] = S32[t];
+    for (int t = threadIdx.x; t < R * R; t += blockDim.x) Ss[t] = S[t];
   __syncthreads();
 
   double beta_acc = 0.0;
@@ -118,41 +123,26 @@ __device__ void record_fit(SolveState st, double beta, double gamma) {
   st.scalars[2] = gamma;
   st.scalars[3] = eps;
   const int it = st.flags[2];
+  const double prev = st.scalars[5];
   if (it < kFitCapacity) st.fits[it] = fit;
   st.flags[2] = it + 1;
+  st.scalars[5] = fit;
   const double tol = st.scalars[4];
   if (!isfinite(fit)) {
     st.flags[3] = 1;
     st.flags[0] = 1;
-  } else if (it >= 1 && it < kFitCapacity && fabs(fit - st.fits[it - 1]) < tol) {
+  } else if (it >= 1 && fabs(fit - prev) < tol) {
     st.flags[0] = 1;
   }
 }
 
-// record_fit with alpha and the previous fit already loaded.
-__device__ void record_fit_known(SolveState st, double beta, double gamma, double alpha,
-                                 double prev_fit) {
-  const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
-  const double fit = 1.0 - eps;
-  st.scalars[1] = beta;
-  st.scalars[2] = gamma;
-  st.scalars[3] = eps;
-  const int it = st.flags[2];
-  if (it < kFitCapacity) st.fits[it] = fit;
-  st.flags[2] = it + 1;
-  const double tol = st.scalars[4];
-  if (!isfinite(fit)) {
-    st.flags[3] = 1;
-    st.flags[0] = 1;
-  } else if (it >= 1 && it < kFitCapacity && fabs(fit - prev_fit) < tol) {
-    st.flags[0] = 1;
-  }
-}
 
 // Single CTA (1024 threads).  Shared: GW (R*R doubles) + c (R doubles).
 __global__ void __launch_bounds__(1024)
 k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mode,
            int nblocks, int is_last, int init, SolveState st) {
+  pdl_wait();
+  pdl_trigger();
   if (st.flags[0]) return;
   extern __shared__ double dsm[];
   double* GW = dsm;          // R x R
@@ -177,10 +167,10 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   __shared__ double cinv[kMaxRank];
   for (int r = tid; r < R; r += blockDim.x) cinv[r] = c[r] > 0.0 ? 1.0 / c[r] : 0.0;
   __syncthreads();
-  double* Gn = st.G + (long long)n * R2;
+  float* Gn = st.G + (long long)n * R2;
   for (int t = tid; t < R2; t += blockDim.x) {
     const int a = t / R, b = t % R;
-    Gn[t] = GW[t] * cinv[a] * cinv[b];
+    Gn[t] = (float)(GW[t] * cinv[a] * cinv[b]);
   }
   for (long long t = tid; t < In * R; t += blockDim.x) {
     const int r = (int)(t % R);
@@ -189,7 +179,7 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   if (is_last) {
     // gamma = lam^T (S * G_N) lam = sum_ab S_ab (W^T W)_ab
     double g = 0.0;
-    for (int t = tid; t < R2; t += blockDim.x) g += st.S[t] * GW[t];
+    for (int t = tid; t < R2; t += blockDim.x) g += (double)st.S[t] * GW[t];
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
     if ((tid & 31) == 0) red[tid >> 5] = g;
     __syncthreads();
@@ -205,25 +195,54 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   // S for the next mode: Hadamard of every Gram but next_mode's
   if (next_mode >= 0) {
     for (int t = tid; t < R2; t += blockDim.x) {
-      double s = 1.0;
+      float s = 1.0f;
       for (int k = 0; k < N; ++k)
         if (k != next_mode) s *= st.G[(long long)k * R2 + t];
       st.S[t] = s;
-      st.S32[t] = (float)s;
     }
   }
+}
+
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// float-float: the unevaluated sum hi + lo of two float32 values.  ff_add is
+// the TwoSum-based addition (Knuth): the rounding error of hi_a + hi_b is
+// recovered exactly and carried in lo, so a sum of float32 terms keeps about
+// 44 bits.  Its result does not depend on the operand order, so butterfly
+// reductions leave the same bits in every lane.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  const float t = e + (a.lo + b.lo);
+  const float hi = s + t;
+  return {hi, t - (hi - s)};
+}
+
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
 }
 
 // Mode update spread over CTAs of MultiCfg<RMAX>::ROWS rows (I_n <= kMultiMaxRows, R <= 64):
 //   every CTA stages its rows of H and M in shared memory (coalesced), runs the
 //   HALS sweep (Sec. II-B) with one thread per row, and forms its partial W^T W
-//   (float32) and <M, W>.  A single CTA finishes on its own from shared
-//   memory; otherwise every CTA writes W and its partials and the last CTA to
-//   finish (atomic ticket) sums the partials in CTA order and scales H by
-//   1 / lambda.  The finishing CTA forms lambda, G_n, the fit at n = N and S
-//   for the next mode.  Results do not depend on arrival order.
+//   and <M, W>.  A single CTA finishes on its own from shared memory;
+//   otherwise every CTA writes W and its partials and the last CTA to finish
+//   (atomic ticket) sums the partials in CTA order and scales H by 1 / lambda.
+//   The finishing CTA forms lambda, G_n, the fit at n = N and S for the next
+//   mode.  Results do not depend on arrival order.
 constexpr int kMultiThreads = 512;
-constexpr int kGpreDoubles = 3072;  // other modes' Grams prefetched for the next S (24 KB)
+constexpr int kGpreFloats = 6144;  // other modes' Grams staged for the next S (24 KB)
 constexpr int kMultiMaxRows = 16384;
 
 template <int RMAX>
@@ -234,7 +253,7 @@ struct MultiCfg {
   static constexpr int ROWS = 128;
   static constexpr int RP = RMAX + 4;        // padded row stride (16-byte multiple) in shared memory
   static constexpr int NB = RMAX / 4;
-  static constexpr int GROUPS = T / (NB * NB);  // Gram row groups (>= 2)
+  static constexpr int GROUPS = T / (NB * NB);  // Gram row groups
 };
 
 int multi_rows(int R) { return R <= 32 ? MultiCfg<32>::ROWS : MultiCfg<64>::ROWS; }  // all 128
@@ -243,77 +262,79 @@ template <int RMAX>
 __global__ void __launch_bounds__(kMultiThreads, 1)
 k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
                int next_mode, int is_last, SolveState st, float* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   if (st.flags[0]) return;
   using C = MultiCfg<RMAX>;
   constexpr int T = C::T, ROWS = C::ROWS, RP = C::RP, GROUPS = C::GROUPS;
-  static_assert(GROUPS >= 2, "W^T W in float64 reuses the Gram partial area");
+  constexpr int EPT = (RMAX * RMAX + T - 1) / T;  // R x R elements per thread
   extern __shared__ __align__(16) float usm[];
   float* St = usm;                      // RMAX x RMAX, St[r][c] = S[c][r], zero padded
   float* Hs = St + RMAX * RMAX;         // ROWS x RP: H, then W
   float* Ms = Hs + ROWS * RP;           // ROWS x RP
-  float* gpart = Ms + ROWS * RP;        // GROUPS x R x R, then W^T W in float64
+  float* gpart = Ms + ROWS * RP;        // GROUPS x R x R, then W^T W
+  float* Gn = gpart + GROUPS * RMAX * RMAX;  // R x R: the new G_n
+  float* Gpre = Gn + RMAX * RMAX;       // the other modes' Grams for the next S
   __shared__ __align__(16) float lamf[RMAX];
   __shared__ float sinv[RMAX];
-  __shared__ double red[T / 32];
-  __shared__ double cinv_sh[RMAX];
-  __shared__ double scal_sh[4];  // beta, alpha, previous fit, tol
+  __shared__ FF red[T / 32];
+  __shared__ FF beta_sh;
+  __shared__ double scal_sh[3];  // alpha, previous fit, tol
   __shared__ int last_sh, it_sh;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int R2 = R * R;
   const int row0 = blockIdx.x * ROWS;
   const int nrows = min(ROWS, In - row0);
   const bool single = gridDim.x == 1;
-  // staging: every loop issues its global loads in batches
+
+  // ---- staging: every load the update needs is issued here, in one batch
 #pragma unroll
   for (int e = tid; e < RMAX * RMAX; e += T) {
     const int r = e / RMAX, c = e % RMAX;
-    St[e] = (r < R && c < R) ? st.S32[c * R + r] : 0.0f;
+    St[e] = (r < R && c < R) ? st.S[c * R + r] : 0.0f;
   }
   for (int r = tid; r < RMAX; r += T) {
     lamf[r] = r < R ? (float)st.lam[r] : 0.0f;
-    const float srr = r < R ? st.S32[r * R + r] : 0.0f;
+    const float srr = r < R ? st.S[r * R + r] : 0.0f;
     sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
   }
   const float* Hg = H + (long long)row0 * R;
   const float* Mg = M + (long long)row0 * R;
+  if ((R & 3) == 0) {
+    // 16-byte asynchronous copies straight into the padded rows (R % 4 == 0:
+    // every source row and destination row starts on a 16-byte boundary)
+    const int n4 = nrows * R / 4;
+    for (int v = tid; v < n4; v += T) {
+      const int rr = 4 * v / R, c = 4 * v - rr * R;
+      cp_async16(Hs + rr * RP + c, Hg + 4 * v);
+      cp_async16(Ms + rr * RP + c, Mg + 4 * v);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  } else {
 #pragma unroll 4
-  for (int e = tid; e < nrows * R; e += T) {
-    const int rr = e / R, c = e % R;
-    Hs[rr * RP + c] = Hg[e];
-    Ms[rr * RP + c] = Mg[e];
+    for (int e = tid; e < nrows * R; e += T) {
+      const int rr = e / R, c = e % R;
+      Hs[rr * RP + c] = Hg[e];
+      Ms[rr * RP + c] = Mg[e];
+    }
   }
-  // everything the finishing CTA reads from global memory after the HALS
-  // sweep that is already known now is fetched with the staging loads: S of
-  // this mode (the fit's gamma at n = N), the other modes' Grams (the next
-  // S, when they fit in kGpreDoubles), alpha, the iteration count, the
-  // previous fit and the tolerance
-  constexpr int EPT = (RMAX * RMAX + T - 1) / T;
-  double sfit[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * T;
-    sfit[q] = (is_last && e < R2) ? st.S[e] : 0.0;
-  }
-  double* Gpre = reinterpret_cast<double*>(gpart + GROUPS * RMAX * RMAX);
+  // the other modes' Grams for the next S, when they fit (slots in mode order)
   const int ng = N - (next_mode == n ? 1 : 2);
-  const bool gpre = ng > 0 && ng * R2 <= kGpreDoubles;
+  const bool gpre = ng > 0 && ng * R2 <= kGpreFloats;
   if (gpre) {
-#pragma unroll 4
-    for (int x = tid; x < ng * R2; x += T) {
-      const int slot = x / R2, e = x - slot * R2;
-      int k = -1;
-      for (int m = 0, seen = 0; m < N; ++m)
-        if (m != n && m != next_mode && seen++ == slot) k = m;
-      Gpre[x] = st.G[(long long)k * R2 + e];
+    for (int k = 0, slot = 0; k < N; ++k) {
+      if (k == n || k == next_mode) continue;
+      for (int e = tid; e < R2; e += T) Gpre[slot * R2 + e] = st.G[(long long)k * R2 + e];
+      ++slot;
     }
   }
   if (tid == 0) {
-    const int it = st.flags[2];
-    it_sh = it;
-    scal_sh[1] = st.scalars[0];
-    scal_sh[2] = (it >= 1 && it <= kFitCapacity) ? st.fits[it - 1] : 0.0;
-    scal_sh[3] = st.scalars[4];
+    it_sh = st.flags[2];
+    scal_sh[0] = st.scalars[0];
+    scal_sh[1] = st.scalars[5];
+    scal_sh[2] = st.scalars[4];
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
 
   // ---- HALS sweep (Sec. II-B): thread = row, columns in order.  Up to 32
@@ -321,7 +342,7 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   // straight-line code is too long to fetch once per warp, so the row is
   // updated in place in its shared-memory row by a rolled column loop.  Both
   // form each dot product in the same order, so they give the same bits.
-  double bp = 0.0;
+  FF bp{0.0f, 0.0f};
   if (tid < nrows) {
     float b = 0.0f;
     if constexpr (RMAX <= 32) {
@@ -380,11 +401,17 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
       }
       for (int c = 0; c < R; ++c) b = fmaf(Ms[tid * RP + c], wrow[c], b);
     }
-    bp = (double)b;
+    bp.hi = b;
   }
-  for (int o = 16; o > 0; o >>= 1) bp += __shfl_xor_sync(0xffffffffu, bp, o);
-  if ((tid & 31) == 0) red[tid >> 5] = bp;
+  // <M, W> of this CTA: float-float over the rows (warp, then warps in order)
+  if (warp * 32 < nrows) bp = ff_warp_sum(bp);
+  if (lane == 0) red[warp] = bp;
   __syncthreads();
+  if (tid == 0) {
+    FF s{0.0f, 0.0f};
+    for (int k = 0; k < T / 32; ++k) s = ff_add(s, red[k]);
+    beta_sh = s;
+  }
   if (!single) {
     float* Hw = H + (long long)row0 * R;
     for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R];
@@ -419,7 +446,7 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
         if (a0 + x < R && b0 + y < R) gpart[(g * R + a0 + x) * R + b0 + y] = acc[x][y];
   }
   __syncthreads();
-  // W^T W summed over the row groups (float32, group order)
+  // W^T W summed over the row groups (group order)
   float gsum[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
@@ -428,30 +455,24 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     if (e < R2)
       for (int g = 0; g < groups; ++g) gsum[q] += gpart[g * R2 + e];
   }
-  double* GW = reinterpret_cast<double*>(gpart);  // R2 doubles, after the sums are read
+  float* GW = gpart;  // R x R, after the group sums are read
   if (single) {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * T;
-      if (e < R2) GW[e] = (double)gsum[q];
-    }
-    if (tid == 0) {
-      double b = 0.0;
-      for (int k = 0; k < T / 32; ++k) b += red[k];
-      scal_sh[0] = b;
+      if (e < R2) GW[e] = gsum[q];
     }
   } else {
-    float* pb = part + (long long)blockIdx.x * (R2 + 1);
+    float* pb = part + (long long)blockIdx.x * (R2 + 2);
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * T;
       if (e < R2) pb[e] = gsum[q];
     }
     if (tid == 0) {
-      double b = 0.0;
-      for (int k = 0; k < T / 32; ++k) b += red[k];
-      pb[R2] = (float)b;
+      pb[R2] = beta_sh.hi;
+      pb[R2 + 1] = beta_sh.lo;
     }
     // ---- the last CTA finishes the update
     __threadfence();
@@ -471,33 +492,39 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
       int b = 0;
       for (; b + 8 <= nbk; b += 8) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = part[(long long)(b + q) * (R2 + 1) + e];
+        for (int q = 0; q < 8; ++q) v[q] = part[(long long)(b + q) * (R2 + 2) + e];
 #pragma unroll
         for (int q = 0; q < 8; ++q) sum += v[q];
       }
-      for (; b < nbk; ++b) sum += part[(long long)b * (R2 + 1) + e];
-      GW[e] = (double)sum;
+      for (; b < nbk; ++b) sum += part[(long long)b * (R2 + 2) + e];
+      GW[e] = sum;
     }
     if (tid == 0) {
-      double b = 0.0;
-      for (int k = 0; k < nbk; ++k) b += (double)part[(long long)k * (R2 + 1) + R2];
-      scal_sh[0] = b;
+      FF s{0.0f, 0.0f};
+      for (int k = 0; k < nbk; ++k)
+        s = ff_add(s, FF{part[(long long)k * (R2 + 2) + R2], part[(long long)k * (R2 + 2) + R2 + 1]});
+      beta_sh = s;
       st.flags[8] = 0;  // ticket reset for the next launch
     }
   }
   __syncthreads();
+  // lambda = column norms of W; from here on lamf holds 1 / lambda
   for (int r = tid; r < R; r += T) {
-    const double g = GW[r * R + r];
-    const double ci = g > 0.0 ? rsqrt(g) : 0.0;  // 1 / lambda
-    st.lam[r] = g * ci;
-    cinv_sh[r] = ci;
-    lamf[r] = (float)ci;  // from here on: 1 / lambda
+    const float g = GW[r * R + r];
+    const float l = sqrtf(g);
+    st.lam[r] = (double)l;
+    lamf[r] = g > 0.0f ? 1.0f / l : 0.0f;
   }
   __syncthreads();
-  double* Gn = st.G + (long long)n * R2;
-  for (int e = tid; e < R2; e += T) {
-    const int a = e / R, b = e % R;
-    Gn[e] = GW[e] * cinv_sh[a] * cinv_sh[b];
+  float* Gng = st.G + (long long)n * R2;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    if (e < R2) {
+      const float v = GW[e] * lamf[e / R] * lamf[e % R];
+      Gn[e] = v;
+      Gng[e] = v;
+    }
   }
   // H = W / lambda (multiplication by the float32 reciprocal)
   if (single && (R & 3) == 0) {
@@ -547,64 +574,59 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     }
   }
   if (is_last) {
-    double g = 0.0;
+    // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
+    // float-float over the thread's terms, the warp, then the warps in order
+    FF g{0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * T;
-      if (e < R2) g += sfit[q] * GW[e];
+      if (e < R2) g = ff_add(g, FF{St[(e % R) * RMAX + e / R] * GW[e], 0.0f});
     }
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    g = ff_warp_sum(g);
     __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = g;
+    if (lane == 0) red[warp] = g;
     __syncthreads();
     if (tid == 0) {
-      double gamma = 0.0;
-      for (int k = 0; k < T / 32; ++k) gamma += red[k];
-      const double beta = scal_sh[0], alpha = scal_sh[1], prev = scal_sh[2], tol = scal_sh[3];
+      FF gs{0.0f, 0.0f};
+      for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
+      const double gamma = (double)gs.hi + (double)gs.lo;
+      const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
+      const double alpha = scal_sh[0], prev = scal_sh[1], tol = scal_sh[2];
       const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
       const double fit = 1.0 - eps;
       const int it = it_sh;
       st.scalars[1] = beta;
       st.scalars[2] = gamma;
       st.scalars[3] = eps;
+      st.scalars[5] = fit;
       if (it < kFitCapacity) st.fits[it] = fit;
       st.flags[2] = it + 1;
       if (!isfinite(fit)) {
         st.flags[3] = 1;
         st.flags[0] = 1;
-      } else if (it >= 1 && it < kFitCapacity && fabs(fit - prev) < tol) {
+      } else if (it >= 1 && fabs(fit - prev) < tol) {
         st.flags[0] = 1;
       }
     }
   }
   __syncthreads();
-  // S for the next mode: Hadamard of every Gram but next_mode's (mode n's is
-  // new); all of a thread's Gram loads first
-  double sv[EPT];
+  // S for the next mode: Hadamard of every Gram but next_mode's, in mode order
+  // (mode n's is the new one)
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
     const int e = tid + q * T;
-    sv[q] = 1.0;
     if (e < R2) {
-      int slot = 0;
-#pragma unroll
-      for (int k = 0; k < kMaxModes; ++k)
-        if (k < N && k != next_mode) {
-          if (k == n) {
-            sv[q] *= GW[e] * cinv_sh[e / R] * cinv_sh[e % R];
-          } else {
-            sv[q] *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
-            ++slot;
-          }
+      float s = 1.0f;
+      for (int k = 0, slot = 0; k < N; ++k) {
+        if (k == next_mode) continue;
+        if (k == n) {
+          s *= Gn[e];
+        } else {
+          s *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
+          ++slot;
         }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * T;
-    if (e < R2) {
-      st.S[e] = sv[q];
-      st.S32[e] = (float)sv[q];
+      }
+      st.S[e] = s;
     }
   }
 }
@@ -612,9 +634,410 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
 template <int RMAX>
 size_t multi_smem() {
   using C = MultiCfg<RMAX>;
-  const size_t grams = (size_t)C::GROUPS * RMAX * RMAX;
-  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP) * sizeof(float) + grams * sizeof(float) +
-         (size_t)kGpreDoubles * sizeof(double);
+  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP + C::GROUPS * RMAX * RMAX + RMAX * RMAX +
+                  kGpreFloats) *
+         sizeof(float);
+}
+
+// ---- thread-block cluster helpers (distributed shared memory) ---------------
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// address of `p` (this CTA's shared memory) in the shared memory of CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float ld_cluster(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+// every thread of every CTA of the cluster arrives; wait returns once all have
+// (release / acquire: shared-memory writes before the arrive are visible after the wait)
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Mode update on one thread-block cluster (I_n <= kClusterMaxRows, R <= 64):
+// CTA k of the cluster owns rows [k * rows, (k + 1) * rows).  Every CTA stages
+// its rows of H and M, runs the HALS sweep (Sec. II-B) with one thread per row,
+// and forms its partial W^T W and <M, W> in its own shared memory.  After a
+// cluster barrier each CTA reads every CTA's partials through distributed
+// shared memory, in CTA order, so all of them hold the same W^T W bits, forms
+// lambda and writes its own rows of H = W / lambda; CTA 0 also writes lambda,
+// G_n, the fit at n = N and S for the next mode.  No global round trip
+// between the phases, no atomics; the hardware schedules the cluster's CTAs
+// together, so the barrier needs no co-residency assumption.
+//
+// Launched in the iteration graph with programmatic serialization, the kernel
+// may start while its predecessor runs.  Everything it reads except M (H_n, S,
+// G, lambda, the scalars and flags) is written two or more kernels earlier and
+// never by the kernel just before an update (a partial MTTKRP, a multi-TTV or a
+// reduction), and every kernel of the iteration lets its successor start only
+// after its own pdl_wait(): those loads are issued before pdl_wait(), M after.
+constexpr int kClusterThreads = 256;
+constexpr int kClusterMax = 8;      // portable cluster size
+constexpr int kClusterRowsMax = 128;
+constexpr int kClusterMaxRows = kClusterMax * kClusterRowsMax;
+
+template <int RMAX>
+struct ClusterCfg {
+  static constexpr int T = kClusterThreads;
+  static constexpr int RP = RMAX + 4;   // padded row stride (16-byte multiple)
+  static constexpr int NB = RMAX / 4;
+  static constexpr int GROUPS = T / (NB * NB) > 0 ? T / (NB * NB) : 1;  // Gram row groups
+  static constexpr int EPT = (RMAX * RMAX + T - 1) / T;                // R x R elements per thread
+};
+
+// rows per CTA: I_n spread over at most kClusterMax CTAs, a multiple of 32
+int cluster_rows(int64_t In) {
+  int r = (int)((In + kClusterMax - 1) / kClusterMax);
+  r = (r + 31) / 32 * 32;
+  return std::max(32, r);
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(kClusterThreads, 1)
+k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
+                 int next_mode, int is_last, int rows, SolveState st) {
+  using C = ClusterCfg<RMAX>;
+  constexpr int T = C::T, RP = C::RP, GROUPS = C::GROUPS, EPT = C::EPT;
+  extern __shared__ __align__(16) float csm[];
+  float* St = csm;                             // RMAX x RMAX, St[r][c] = S[c][r], zero padded
+  float* Hs = St + RMAX * RMAX;                // rows x RP: H, then W
+  float* Ms = Hs + kClusterRowsMax * RP;       // rows x RP
+  float* gpart = Ms + kClusterRowsMax * RP;    // GROUPS x R x R
+  float* Gown = gpart + GROUPS * RMAX * RMAX;  // this CTA's W^T W (read by the cluster)
+  float* GW = Gown + RMAX * RMAX;              // the cluster's W^T W
+  float* Gn = GW + RMAX * RMAX;                // G_n (CTA 0)
+  float* Gpre = Gn + RMAX * RMAX;              // the other modes' Grams (CTA 0)
+  __shared__ __align__(16) float lamf[RMAX];
+  __shared__ float sinv[RMAX];
+  __shared__ FF red[T / 32];
+  __shared__ FF beta_own, beta_sh;
+  __shared__ double scal_sh[3];  // alpha, previous fit, tol
+  __shared__ int it_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned rank = cluster_rank(), nrank = cluster_size();
+  const bool lead = rank == 0;
+  const int R2 = R * R;
+  const int row0 = (int)rank * rows;
+  const int nrows = min(rows, In - row0);
+
+  // the stop flag is the same for every CTA (written by an earlier kernel only)
+  if (st.flags[0]) return;
+
+  // ---- staging, first everything an earlier kernel than the predecessor wrote
+#pragma unroll
+  for (int e = tid; e < RMAX * RMAX; e += T) {
+    const int r = e / RMAX, c = e % RMAX;
+    St[e] = (r < R && c < R) ? st.S[c * R + r] : 0.0f;
+  }
+  for (int r = tid; r < RMAX; r += T) {
+    lamf[r] = r < R ? (float)st.lam[r] : 0.0f;
+    const float srr = r < R ? st.S[r * R + r] : 0.0f;
+    sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
+  }
+  const float* Hg = H + (long long)row0 * R;
+  const float* Mg = M + (long long)row0 * R;
+  const bool vec = (R & 3) == 0;
+  if (vec) {
+    for (int v = tid; v < nrows * R / 4; v += T) {
+      const int rr = 4 * v / R, c = 4 * v - rr * R;
+      cp_async16(Hs + rr * RP + c, Hg + 4 * v);
+    }
+  } else {
+    for (int e = tid; e < nrows * R; e += T) Hs[(e / R) * RP + e % R] = Hg[e];
+  }
+  const int ng = N - (next_mode == n ? 1 : 2);
+  const bool gpre = ng > 0 && ng * R2 <= kGpreFloats;
+  if (lead && gpre) {
+    for (int k = 0, slot = 0; k < N; ++k) {
+      if (k == n || k == next_mode) continue;
+      for (int e = tid; e < R2; e += T) Gpre[slot * R2 + e] = st.G[(long long)k * R2 + e];
+      ++slot;
+    }
+  }
+  if (lead && tid == 0) {
+    it_sh = st.flags[2];
+    scal_sh[0] = st.scalars[0];
+    scal_sh[1] = st.scalars[5];
+    scal_sh[2] = st.scalars[4];
+  }
+  // ---- then M, which the predecessor writes
+  pdl_wait();
+  pdl_trigger();
+  if (vec) {
+    for (int v = tid; v < nrows * R / 4; v += T) {
+      const int rr = 4 * v / R, c = 4 * v - rr * R;
+      cp_async16(Ms + rr * RP + c, Mg + 4 * v);
+    }
+  } else {
+    for (int e = tid; e < nrows * R; e += T) Ms[(e / R) * RP + e % R] = Mg[e];
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+
+  // ---- HALS sweep (Sec. II-B): thread = row, columns in order; the row and
+  // its M in registers up to 32 columns (fully unrolled), in the shared-memory
+  // row with a rolled column loop at 64.  Both form each dot product in the
+  // same order (eight partial sums), so they give the same bits.
+  FF bp{0.0f, 0.0f};
+  if (tid < nrows) {
+    float b = 0.0f;
+    if constexpr (RMAX <= 32) {
+      float w[RMAX], m[RMAX];
+#pragma unroll
+      for (int c = 0; c < RMAX; ++c) {
+        w[c] = c < R ? Hs[tid * RP + c] * lamf[c] : 0.0f;
+        m[c] = c < R ? Ms[tid * RP + c] : 0.0f;
+      }
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        const float si = sinv[r];
+        const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
+        float d[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < RMAX; c += 4) {
+          const float4 sv = col[c >> 2];
+          const int h = (c >> 2) & 1;
+          d[4 * h] = fmaf(w[c], sv.x, d[4 * h]);
+          d[4 * h + 1] = fmaf(w[c + 1], sv.y, d[4 * h + 1]);
+          d[4 * h + 2] = fmaf(w[c + 2], sv.z, d[4 * h + 2]);
+          d[4 * h + 3] = fmaf(w[c + 3], sv.w, d[4 * h + 3]);
+        }
+        const float dot = ((d[0] + d[4]) + (d[1] + d[5])) + ((d[2] + d[6]) + (d[3] + d[7]));
+        const float upd = fmaxf(0.0f, w[r] + (m[r] - dot) * si);
+        w[r] = si != 0.0f ? upd : w[r];  // S_rr = 0: column left as it is
+      }
+#pragma unroll
+      for (int c = 0; c < RMAX; ++c) {
+        if (c < R) {
+          b = fmaf(m[c], w[c], b);
+          Hs[tid * RP + c] = w[c];
+        }
+      }
+    } else {
+      float* wrow = Hs + tid * RP;
+#pragma unroll
+      for (int c = 0; c < RMAX; ++c) wrow[c] = c < R ? wrow[c] * lamf[c] : 0.0f;
+      const float4* wv = reinterpret_cast<const float4*>(wrow);
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const float si = sinv[r];
+        const float mr = Ms[tid * RP + r];
+        const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
+        float d[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c4 = 0; c4 < RMAX / 4; ++c4) {
+          const float4 sv = col[c4];
+          const float4 w4 = wv[c4];
+          const int h = c4 & 1;
+          d[4 * h] = fmaf(w4.x, sv.x, d[4 * h]);
+          d[4 * h + 1] = fmaf(w4.y, sv.y, d[4 * h + 1]);
+          d[4 * h + 2] = fmaf(w4.z, sv.z, d[4 * h + 2]);
+          d[4 * h + 3] = fmaf(w4.w, sv.w, d[4 * h + 3]);
+        }
+        const float dot = ((d[0] + d[4]) + (d[1] + d[5])) + ((d[2] + d[6]) + (d[3] + d[7]));
+        const float wr = wrow[r];
+        const float upd = fmaxf(0.0f, wr + (mr - dot) * si);
+        wrow[r] = si != 0.0f ? upd : wr;
+      }
+      for (int c = 0; c < R; ++c) b = fmaf(Ms[tid * RP + c], wrow[c], b);
+    }
+    bp.hi = b;
+  }
+  // <M, W> of this CTA: float-float over its rows (warp, then warps in order)
+  if (warp * 32 < nrows) bp = ff_warp_sum(bp);
+  if (lane == 0) red[warp] = bp;
+  __syncthreads();
+  if (tid == 0) {
+    FF s{0.0f, 0.0f};
+    for (int k = 0; k < T / 32; ++k) s = ff_add(s, red[k]);
+    beta_own = s;
+  }
+
+  // ---- partial W^T W: thread = (4x4 tile, row group), register tiles
+  const int nb4 = (R + 3) / 4;
+  const int tiles = nb4 * nb4;
+  const int groups = min(GROUPS, max(1, T / tiles));
+  for (int t0 = tid; t0 < tiles * groups; t0 += T) {
+    const int tile = t0 % tiles, g = t0 / tiles;
+    const int a0 = (tile / nb4) * 4, b0 = (tile % nb4) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+    for (int rr = g; rr < nrows; rr += groups) {
+      const float4 qa = *reinterpret_cast<const float4*>(Hs + rr * RP + a0);
+      const float4 qb = *reinterpret_cast<const float4*>(Hs + rr * RP + b0);
+      const float va[4] = {qa.x, qa.y, qa.z, qa.w};
+      const float vb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(va[x], vb[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (a0 + x < R && b0 + y < R) gpart[(g * R + a0 + x) * R + b0 + y] = acc[x][y];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    if (e < R2) {
+      float s = 0.0f;
+      for (int g = 0; g < groups; ++g) s += gpart[g * R2 + e];
+      Gown[e] = s;
+    }
+  }
+  cluster_arrive();
+  cluster_wait();
+
+  // ---- the cluster's W^T W and <M, W>, summed in CTA order (same bits in every CTA)
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * T;
+    if (e < R2) {
+      float v[kClusterMax];
+#pragma unroll
+      for (int k = 0; k < kClusterMax; ++k)
+        v[k] = k < (int)nrank ? ld_cluster(cluster_addr(Gown + e, k)) : 0.0f;
+      float s = v[0];
+#pragma unroll
+      for (int k = 1; k < kClusterMax; ++k)
+        if (k < (int)nrank) s += v[k];
+      GW[e] = s;
+    }
+  }
+  if (tid == 0) {
+    FF s{0.0f, 0.0f};
+    for (unsigned k = 0; k < nrank; ++k)
+      s = ff_add(s, FF{ld_cluster(cluster_addr(&beta_own.hi, k)),
+                       ld_cluster(cluster_addr(&beta_own.lo, k))});
+    beta_sh = s;
+  }
+  // done reading the other CTAs' shared memory; they may leave once all have
+  cluster_arrive();
+  __syncthreads();
+
+  // ---- lambda = column norms of W; from here on lamf holds 1 / lambda
+  for (int r = tid; r < R; r += T) {
+    const float g = GW[r * R + r];
+    const float l = sqrtf(g);
+    if (lead) st.lam[r] = (double)l;
+    lamf[r] = g > 0.0f ? 1.0f / l : 0.0f;
+  }
+  __syncthreads();
+  // this CTA's rows of H = W / lambda (multiplication by the float32 reciprocal)
+  float* Hw = H + (long long)row0 * R;
+  if (vec) {
+    const float4* l4 = reinterpret_cast<const float4*>(lamf);
+    for (int v = tid; v < nrows * R / 4; v += T) {
+      const int e = 4 * v, rr = e / R, c = e - rr * R;
+      const float4 w = *reinterpret_cast<const float4*>(Hs + rr * RP + c);
+      const float4 l = l4[c >> 2];
+      reinterpret_cast<float4*>(Hw)[v] = make_float4(w.x * l.x, w.y * l.y, w.z * l.z, w.w * l.w);
+    }
+  } else {
+    for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R] * lamf[e % R];
+  }
+  if (lead) {
+    float* Gng = st.G + (long long)n * R2;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * T;
+      if (e < R2) {
+        const float v = GW[e] * lamf[e / R] * lamf[e % R];
+        Gn[e] = v;
+        Gng[e] = v;
+      }
+    }
+    if (is_last) {
+      // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
+      // float-float over the thread's terms, the warp, then the warps in order
+      FF g{0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + q * T;
+        if (e < R2) g = ff_add(g, FF{St[(e % R) * RMAX + e / R] * GW[e], 0.0f});
+      }
+      g = ff_warp_sum(g);
+      __syncthreads();
+      if (lane == 0) red[warp] = g;
+      __syncthreads();
+      if (tid == 0) {
+        FF gs{0.0f, 0.0f};
+        for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
+        const double gamma = (double)gs.hi + (double)gs.lo;
+        const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
+        const double alpha = scal_sh[0], prev = scal_sh[1], tol = scal_sh[2];
+        const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
+        const double fit = 1.0 - eps;
+        const int it = it_sh;
+        st.scalars[1] = beta;
+        st.scalars[2] = gamma;
+        st.scalars[3] = eps;
+        st.scalars[5] = fit;
+        if (it < kFitCapacity) st.fits[it] = fit;
+        st.flags[2] = it + 1;
+        if (!isfinite(fit)) {
+          st.flags[3] = 1;
+          st.flags[0] = 1;
+        } else if (it >= 1 && fabs(fit - prev) < tol) {
+          st.flags[0] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    // S for the next mode: Hadamard of every Gram but next_mode's, in mode
+    // order (mode n's is the new one)
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * T;
+      if (e < R2) {
+        float s = 1.0f;
+        for (int k = 0, slot = 0; k < N; ++k) {
+          if (k == next_mode) continue;
+          if (k == n) {
+            s *= Gn[e];
+          } else {
+            s *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
+            ++slot;
+          }
+        }
+        st.S[e] = s;
+      }
+    }
+  }
+  // the other CTAs have read this CTA's partials before it leaves
+  cluster_wait();
+}
+
+template <int RMAX>
+size_t cluster_smem() {
+  using C = ClusterCfg<RMAX>;
+  return (size_t)(RMAX * RMAX + 2 * kClusterRowsMax * C::RP + C::GROUPS * RMAX * RMAX +
+                  3 * RMAX * RMAX + kGpreFloats) *
+         sizeof(float);
 }
 
 __global__ void k_solve_reset(SolveState st, int R, double tol) {
@@ -626,17 +1049,17 @@ __global__ void k_solve_reset(SolveState st, int R, double tol) {
     st.flags[3] = 0;
     st.flags[8] = 0;
     st.scalars[4] = tol;
+    st.scalars[5] = 0.0;
   }
 }
 
 __global__ void k_compute_S(SolveState st, int N, int R, int mode) {
   const int R2 = R * R;
   for (int t = threadIdx.x; t < R2; t += blockDim.x) {
-    double s = 1.0;
+    float s = 1.0f;
     for (int k = 0; k < N; ++k)
       if (k != mode) s *= st.G[(long long)k * R2 + t];
     st.S[t] = s;
-    st.S32[t] = (float)s;
   }
 }
 
@@ -730,6 +1153,15 @@ cudaError_t kernel_attributes_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_update_multi<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)multi_smem<64>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_cluster<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cluster_smem<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_cluster<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cluster_smem<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_update_cluster<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cluster_smem<64>());
   if (e == cudaSuccess) e = tc_attributes_init();
   return e;
 }
@@ -739,16 +1171,16 @@ int hals_gram_blocks(int64_t In) { return (int)((In + kRowsPerBlock - 1) / kRows
 cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveState st,
                              cudaStream_t stream) {
   size_t smem = hals_smem(R);
-  k_hals_gram<<<hals_gram_blocks(In), kHalsThreads, smem, stream>>>(
-      H, M, In, R, st.S32, st.lam, st.gram_part, st.flags, 1);
-  return cudaGetLastError();
+  return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), smem, stream,
+                       H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       st.gram_part, (const int*)st.flags, 1);
 }
 
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream) {
   size_t smem = hals_smem(R);
   k_hals_gram<<<hals_gram_blocks(In), kHalsThreads, smem, stream>>>(
-      const_cast<float*>(H), nullptr, In, R, st.S32, st.lam, st.gram_part, st.flags, 0);
+      const_cast<float*>(H), nullptr, In, R, st.S, st.lam, st.gram_part, st.flags, 0);
   return cudaGetLastError();
 }
 
@@ -757,7 +1189,7 @@ bool multi_update_ok(int64_t In, int R) { return In <= kMultiMaxRows && R <= 64;
 // partial scratch needed by the multi-CTA update (floats)
 size_t multi_update_scratch(int64_t In, int R) {
   const int64_t nb = (In + multi_rows(R) - 1) / multi_rows(R);
-  return (size_t)(nb + 1) * (R * R + 1) + 2 * (size_t)R * R + 4;
+  return (size_t)(nb + 1) * (R * R + 2) + 2 * (size_t)R * R + 4;
 }
 
 cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
@@ -767,19 +1199,38 @@ cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int
   const int rmax = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
   switch (rmax) {
     case 16:
-      k_update_multi<16><<<nb, MultiCfg<16>::T, multi_smem<16>(), stream>>>(
-          H, M, (int)In, R, N, n, next_mode, is_last, st, part);
-      break;
+      return launch_kernel(k_update_multi<16>, dim3(nb), dim3(MultiCfg<16>::T), multi_smem<16>(),
+                           stream, H, M, (int)In, R, N, n, next_mode, is_last, st, part);
     case 32:
-      k_update_multi<32><<<nb, MultiCfg<32>::T, multi_smem<32>(), stream>>>(
-          H, M, (int)In, R, N, n, next_mode, is_last, st, part);
-      break;
+      return launch_kernel(k_update_multi<32>, dim3(nb), dim3(MultiCfg<32>::T), multi_smem<32>(),
+                           stream, H, M, (int)In, R, N, n, next_mode, is_last, st, part);
     default:
-      k_update_multi<64><<<nb, MultiCfg<64>::T, multi_smem<64>(), stream>>>(
-          H, M, (int)In, R, N, n, next_mode, is_last, st, part);
-      break;
+      return launch_kernel(k_update_multi<64>, dim3(nb), dim3(MultiCfg<64>::T), multi_smem<64>(),
+                           stream, H, M, (int)In, R, N, n, next_mode, is_last, st, part);
   }
-  return cudaGetLastError();
+}
+
+bool cluster_update_ok(int64_t In, int R) { return In >= 1 && In <= kClusterMaxRows && R <= 64; }
+
+cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, int N, int n,
+                                  int next_mode, int is_last, SolveState st, cudaStream_t stream) {
+  const int rows = cluster_rows(In);
+  const int nb = (int)((In + rows - 1) / rows);
+  const int rmax = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
+  switch (rmax) {
+    case 16:
+      return launch_kernel_cluster(k_update_cluster<16>, dim3(nb), dim3(kClusterThreads),
+                                   cluster_smem<16>(), stream, nb, H, M, (int)In, R, N, n,
+                                   next_mode, is_last, rows, st);
+    case 32:
+      return launch_kernel_cluster(k_update_cluster<32>, dim3(nb), dim3(kClusterThreads),
+                                   cluster_smem<32>(), stream, nb, H, M, (int)In, R, N, n,
+                                   next_mode, is_last, rows, st);
+    default:
+      return launch_kernel_cluster(k_update_cluster<64>, dim3(nb), dim3(kClusterThreads),
+                                   cluster_smem<64>(), stream, nb, H, M, (int)In, R, N, n,
+                                   next_mode, is_last, rows, st);
+  }
 }
 
 cudaError_t launch_finalize(float* H, int64_t In, int R, int N, int n, int next_mode,
@@ -787,8 +1238,8 @@ cudaError_t launch_finalize(float* H, int64_t In, int R, int N, int n, int next_
                             cudaStream_t stream) {
   (void)tol;
   size_t smem = ((size_t)R * R + R) * sizeof(double);
-  k_finalize<<<1, 1024, smem, stream>>>(H, In, R, N, n, next_mode, nblocks, is_last, init, st);
-  return cudaGetLastError();
+  return launch_kernel(k_finalize, dim3(1), dim3(1024), smem, stream, H, (long long)In, R, N, n,
+                       next_mode, nblocks, is_last, init, st);
 }
 
 cudaError_t launch_solve_reset(SolveState st, int R, double tol, cudaStream_t stream) {
