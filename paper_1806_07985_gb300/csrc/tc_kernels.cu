@@ -155,13 +155,23 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// `policy` is an L2 cache policy (createpolicy): the tensor is read once per
+// partial MTTKRP, so its lines are marked evict-first and the streamed half
+// gigabyte does not flush what the other kernels of the iteration keep in L2
+// (their code, the factors, M, the node temporaries).
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t bar) {
+                                            uint32_t bar, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
       : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -426,6 +436,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       uint32_t ph = 0;
       int issued[kMaxSF] = {0, 0, 0, 0, 0, 0, 0, 0};
       const uint32_t tx = p.bf16x ? 16384u : 32768u;
+      const uint64_t pol = l2_evict_first_policy();
       bool ok = true;
       for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
         const Unit w = get_unit(p, u);
@@ -437,13 +448,13 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
           const uint32_t dst = raw0 + sf * kRawBytes;
           if (p.contract_fast) {
             if (p.bf16x) {
-              tma_load_2d(dst, &tmap, k0, m0, raw_full(sf));
+              tma_load_2d(dst, &tmap, k0, m0, raw_full(sf), pol);
             } else {
-              tma_load_2d(dst, &tmap, k0, m0, raw_full(sf));
-              tma_load_2d(dst + 16384, &tmap, k0 + 32, m0, raw_full(sf));
+              tma_load_2d(dst, &tmap, k0, m0, raw_full(sf), pol);
+              tma_load_2d(dst + 16384, &tmap, k0 + 32, m0, raw_full(sf), pol);
             }
           } else {
-            tma_load_2d(dst, &tmap, m0, k0, raw_full(sf));
+            tma_load_2d(dst, &tmap, m0, k0, raw_full(sf), pol);
           }
           ++issued[sf];
           if (++sf == kSF) { sf = 0; ph ^= 1u; }

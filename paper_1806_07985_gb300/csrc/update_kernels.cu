@@ -207,6 +207,14 @@ __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gmem_sr
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 
 // float-float: the unevaluated sum hi + lo of two float32 values.  ff_add is
 // the TwoSum-based addition (Knuth): the rounding error of hi_a + hi_b is
@@ -699,7 +707,6 @@ struct ClusterCfg {
   static constexpr int RP = RMAX + 4;   // padded row stride (16-byte multiple)
   static constexpr int NB = RMAX / 4;
   static constexpr int GROUPS = T / (NB * NB) > 0 ? T / (NB * NB) : 1;  // Gram row groups
-  static constexpr int EPT = (RMAX * RMAX + T - 1) / T;                // R x R elements per thread
 };
 
 // rows per CTA: I_n spread over at most kClusterMax CTAs, a multiple of 32
@@ -714,10 +721,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
 k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
                  int next_mode, int is_last, int rows, SolveState st) {
   using C = ClusterCfg<RMAX>;
-  constexpr int T = C::T, RP = C::RP, GROUPS = C::GROUPS, EPT = C::EPT;
+  constexpr int T = C::T, RP = C::RP, GROUPS = C::GROUPS;
   extern __shared__ __align__(16) float csm[];
-  float* St = csm;                             // RMAX x RMAX, St[r][c] = S[c][r], zero padded
-  float* Hs = St + RMAX * RMAX;                // rows x RP: H, then W
+  // Srot[j][c] = S[(4 floor(j / 4) + c) mod RMAX][j], zero outside R x R: row j
+  // holds column j of S in the rotated order in which the HALS sweep keeps W
+  float* Srot = csm;
+  float* Hs = Srot + RMAX * RMAX;              // rows x RP: H, then W
   float* Ms = Hs + kClusterRowsMax * RP;       // rows x RP
   float* gpart = Ms + kClusterRowsMax * RP;    // GROUPS x R x R
   float* Gown = gpart + GROUPS * RMAX * RMAX;  // this CTA's W^T W (read by the cluster)
@@ -725,139 +734,139 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   float* Gn = GW + RMAX * RMAX;                // G_n (CTA 0)
   float* Gpre = Gn + RMAX * RMAX;              // the other modes' Grams (CTA 0)
   __shared__ __align__(16) float lamf[RMAX];
+  __shared__ __align__(8) double lamd[RMAX];
   __shared__ float sinv[RMAX];
   __shared__ FF red[T / 32];
   __shared__ FF beta_own, beta_sh;
-  __shared__ double scal_sh[3];  // alpha, previous fit, tol
-  __shared__ int it_sh;
+  __shared__ __align__(8) double scal_sh[4];  // alpha, tol, previous fit
+  __shared__ int flag_sh[2];                  // stop flag, iteration count
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned rank = cluster_rank(), nrank = cluster_size();
   const bool lead = rank == 0;
   const int R2 = R * R;
   const int row0 = (int)rank * rows;
   const int nrows = min(rows, In - row0);
+  const bool vec = (R & 3) == 0;
 
-  // the stop flag is the same for every CTA (written by an earlier kernel only)
-  if (st.flags[0]) return;
-
-  // ---- staging, first everything an earlier kernel than the predecessor wrote
-#pragma unroll
+  // ---- staging: asynchronous copies, one round trip.  First everything an
+  // earlier kernel than the predecessor wrote ...
+#pragma unroll 1
   for (int e = tid; e < RMAX * RMAX; e += T) {
-    const int r = e / RMAX, c = e % RMAX;
-    St[e] = (r < R && c < R) ? st.S[c * R + r] : 0.0f;
+    const int j = e / RMAX, c = e % RMAX;
+    const int a = ((j & ~3) + c) & (RMAX - 1);
+    if (j < R && a < R) cp_async4(Srot + e, st.S + a * R + j);
+    else Srot[e] = 0.0f;
   }
-  for (int r = tid; r < RMAX; r += T) {
-    lamf[r] = r < R ? (float)st.lam[r] : 0.0f;
-    const float srr = r < R ? st.S[r * R + r] : 0.0f;
-    sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
-  }
+  for (int r = tid; r < R; r += T) cp_async8(lamd + r, st.lam + r);
   const float* Hg = H + (long long)row0 * R;
   const float* Mg = M + (long long)row0 * R;
-  const bool vec = (R & 3) == 0;
   if (vec) {
+#pragma unroll 1
     for (int v = tid; v < nrows * R / 4; v += T) {
       const int rr = 4 * v / R, c = 4 * v - rr * R;
       cp_async16(Hs + rr * RP + c, Hg + 4 * v);
     }
   } else {
-    for (int e = tid; e < nrows * R; e += T) Hs[(e / R) * RP + e % R] = Hg[e];
+#pragma unroll 1
+    for (int e = tid; e < nrows * R; e += T) cp_async4(Hs + (e / R) * RP + e % R, Hg + e);
   }
   const int ng = N - (next_mode == n ? 1 : 2);
   const bool gpre = ng > 0 && ng * R2 <= kGpreFloats;
   if (lead && gpre) {
+#pragma unroll 1
     for (int k = 0, slot = 0; k < N; ++k) {
       if (k == n || k == next_mode) continue;
-      for (int e = tid; e < R2; e += T) Gpre[slot * R2 + e] = st.G[(long long)k * R2 + e];
+#pragma unroll 1
+      for (int e = tid; e < R2; e += T) cp_async4(Gpre + slot * R2 + e, st.G + (long long)k * R2 + e);
       ++slot;
     }
   }
-  if (lead && tid == 0) {
-    it_sh = st.flags[2];
-    scal_sh[0] = st.scalars[0];
-    scal_sh[1] = st.scalars[5];
-    scal_sh[2] = st.scalars[4];
+  if (tid == 0) {
+    cp_async4(reinterpret_cast<float*>(flag_sh), reinterpret_cast<const float*>(st.flags));
+    cp_async4(reinterpret_cast<float*>(flag_sh + 1), reinterpret_cast<const float*>(st.flags + 2));
+    cp_async8(scal_sh, st.scalars);
+    cp_async8(scal_sh + 1, st.scalars + 4);
+    cp_async8(scal_sh + 2, st.scalars + 5);
   }
-  // ---- then M, which the predecessor writes
+  // ... then M, which the predecessor writes
   pdl_wait();
   pdl_trigger();
   if (vec) {
+#pragma unroll 1
     for (int v = tid; v < nrows * R / 4; v += T) {
       const int rr = 4 * v / R, c = 4 * v - rr * R;
       cp_async16(Ms + rr * RP + c, Mg + 4 * v);
     }
   } else {
-    for (int e = tid; e < nrows * R; e += T) Ms[(e / R) * RP + e % R] = Mg[e];
+#pragma unroll 1
+    for (int e = tid; e < nrows * R; e += T) cp_async4(Ms + (e / R) * RP + e % R, Mg + e);
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
+  // the stop flag is the same for every CTA (written by an earlier kernel only):
+  // every CTA of the cluster leaves here, before any cluster barrier
+  if (flag_sh[0]) return;
+  for (int r = tid; r < RMAX; r += T) {
+    lamf[r] = r < R ? (float)lamd[r] : 0.0f;
+    const float srr = r < R ? Srot[r * RMAX + (r & 3)] : 0.0f;  // S_rr
+    sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
+  }
+  __syncthreads();
 
-  // ---- HALS sweep (Sec. II-B): thread = row, columns in order; the row and
-  // its M in registers up to 32 columns (fully unrolled), in the shared-memory
-  // row with a rolled column loop at 64.  Both form each dot product in the
-  // same order (eight partial sums), so they give the same bits.
+  // ---- HALS sweep (Sec. II-B): thread = row, columns in order.  The row of
+  // W sits in registers, rotated so that column j is w[j mod 4] while columns
+  // 4 floor(j / 4) .. + 3 are swept; the sweep is a rolled loop over those
+  // blocks (a 4-column body, then a rotation by 4), which keeps the code small
+  // enough to stay in the instruction cache.  Columns R .. R rounded up to 4
+  // are zero padding (S_rr = 0 leaves them as they are).
   FF bp{0.0f, 0.0f};
   if (tid < nrows) {
-    float b = 0.0f;
-    if constexpr (RMAX <= 32) {
-      float w[RMAX], m[RMAX];
+    const float* hrow = Hs + tid * RP;
+    const float* mrow = Ms + tid * RP;
+    float w[RMAX];
 #pragma unroll
-      for (int c = 0; c < RMAX; ++c) {
-        w[c] = c < R ? Hs[tid * RP + c] * lamf[c] : 0.0f;
-        m[c] = c < R ? Ms[tid * RP + c] : 0.0f;
-      }
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r) {
-        const float si = sinv[r];
-        const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
-        float d[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int c = 0; c < RMAX; c += 4) {
-          const float4 sv = col[c >> 2];
-          const int h = (c >> 2) & 1;
-          d[4 * h] = fmaf(w[c], sv.x, d[4 * h]);
-          d[4 * h + 1] = fmaf(w[c + 1], sv.y, d[4 * h + 1]);
-          d[4 * h + 2] = fmaf(w[c + 2], sv.z, d[4 * h + 2]);
-          d[4 * h + 3] = fmaf(w[c + 3], sv.w, d[4 * h + 3]);
-        }
-        const float dot = ((d[0] + d[4]) + (d[1] + d[5])) + ((d[2] + d[6]) + (d[3] + d[7]));
-        const float upd = fmaxf(0.0f, w[r] + (m[r] - dot) * si);
-        w[r] = si != 0.0f ? upd : w[r];  // S_rr = 0: column left as it is
-      }
-#pragma unroll
-      for (int c = 0; c < RMAX; ++c) {
-        if (c < R) {
-          b = fmaf(m[c], w[c], b);
-          Hs[tid * RP + c] = w[c];
-        }
-      }
-    } else {
-      float* wrow = Hs + tid * RP;
-#pragma unroll
-      for (int c = 0; c < RMAX; ++c) wrow[c] = c < R ? wrow[c] * lamf[c] : 0.0f;
-      const float4* wv = reinterpret_cast<const float4*>(wrow);
+    for (int c = 0; c < RMAX; ++c) w[c] = c < R ? hrow[c] * lamf[c] : 0.0f;
+    const int Rpad = (R + 3) & ~3;
 #pragma unroll 1
-      for (int r = 0; r < R; ++r) {
-        const float si = sinv[r];
-        const float mr = Ms[tid * RP + r];
-        const float4* col = reinterpret_cast<const float4*>(St + r * RMAX);
+    for (int j0 = 0; j0 < Rpad; j0 += 4) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = j0 + t;
+        const float4* srow = reinterpret_cast<const float4*>(Srot + j * RMAX);
         float d[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int c4 = 0; c4 < RMAX / 4; ++c4) {
-          const float4 sv = col[c4];
-          const float4 w4 = wv[c4];
-          const int h = c4 & 1;
-          d[4 * h] = fmaf(w4.x, sv.x, d[4 * h]);
-          d[4 * h + 1] = fmaf(w4.y, sv.y, d[4 * h + 1]);
-          d[4 * h + 2] = fmaf(w4.z, sv.z, d[4 * h + 2]);
-          d[4 * h + 3] = fmaf(w4.w, sv.w, d[4 * h + 3]);
+          const float4 sv = srow[c4];
+          const int h = 4 * (c4 & 1);
+          d[h] = fmaf(w[4 * c4], sv.x, d[h]);
+          d[h + 1] = fmaf(w[4 * c4 + 1], sv.y, d[h + 1]);
+          d[h + 2] = fmaf(w[4 * c4 + 2], sv.z, d[h + 2]);
+          d[h + 3] = fmaf(w[4 * c4 + 3], sv.w, d[h + 3]);
         }
         const float dot = ((d[0] + d[4]) + (d[1] + d[5])) + ((d[2] + d[6]) + (d[3] + d[7]));
-        const float wr = wrow[r];
-        const float upd = fmaxf(0.0f, wr + (mr - dot) * si);
-        wrow[r] = si != 0.0f ? upd : wr;
+        const float si = sinv[j];
+        const float upd = fmaxf(0.0f, w[t] + (mrow[j] - dot) * si);
+        w[t] = si != 0.0f ? upd : w[t];  // S_jj = 0: column left as it is
       }
-      for (int c = 0; c < R; ++c) b = fmaf(Ms[tid * RP + c], wrow[c], b);
+      const float r0 = w[0], r1 = w[1], r2 = w[2], r3 = w[3];
+#pragma unroll
+      for (int c = 0; c < RMAX - 4; ++c) w[c] = w[c + 4];
+      w[RMAX - 4] = r0;
+      w[RMAX - 3] = r1;
+      w[RMAX - 2] = r2;
+      w[RMAX - 1] = r3;
+    }
+    // w[c] is now column (Rpad + c) mod RMAX
+    float b = 0.0f;
+    float* wrow = Hs + tid * RP;
+#pragma unroll
+    for (int c = 0; c < RMAX; ++c) {
+      const int col = (Rpad + c) & (RMAX - 1);
+      if (col < R) {
+        b = fmaf(mrow[col], w[c], b);
+        wrow[col] = w[c];
+      }
     }
     bp.hi = b;
   }
@@ -875,6 +884,7 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   const int nb4 = (R + 3) / 4;
   const int tiles = nb4 * nb4;
   const int groups = min(GROUPS, max(1, T / tiles));
+#pragma unroll 1
   for (int t0 = tid; t0 < tiles * groups; t0 += T) {
     const int tile = t0 % tiles, g = t0 / tiles;
     const int a0 = (tile / nb4) * 4, b0 = (tile % nb4) * 4;
@@ -883,6 +893,7 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+#pragma unroll 2
     for (int rr = g; rr < nrows; rr += groups) {
       const float4 qa = *reinterpret_cast<const float4*>(Hs + rr * RP + a0);
       const float4 qb = *reinterpret_cast<const float4*>(Hs + rr * RP + b0);
@@ -900,33 +911,27 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
         if (a0 + x < R && b0 + y < R) gpart[(g * R + a0 + x) * R + b0 + y] = acc[x][y];
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * T;
-    if (e < R2) {
-      float s = 0.0f;
-      for (int g = 0; g < groups; ++g) s += gpart[g * R2 + e];
-      Gown[e] = s;
-    }
+#pragma unroll 1
+  for (int e = tid; e < R2; e += T) {
+    float s = 0.0f;
+    for (int g = 0; g < groups; ++g) s += gpart[g * R2 + e];
+    Gown[e] = s;
   }
   cluster_arrive();
   cluster_wait();
 
   // ---- the cluster's W^T W and <M, W>, summed in CTA order (same bits in every CTA)
+#pragma unroll 1
+  for (int e = tid; e < R2; e += T) {
+    float v[kClusterMax];
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * T;
-    if (e < R2) {
-      float v[kClusterMax];
+    for (int k = 0; k < kClusterMax; ++k)
+      v[k] = k < (int)nrank ? ld_cluster(cluster_addr(Gown + e, k)) : 0.0f;
+    float s = v[0];
 #pragma unroll
-      for (int k = 0; k < kClusterMax; ++k)
-        v[k] = k < (int)nrank ? ld_cluster(cluster_addr(Gown + e, k)) : 0.0f;
-      float s = v[0];
-#pragma unroll
-      for (int k = 1; k < kClusterMax; ++k)
-        if (k < (int)nrank) s += v[k];
-      GW[e] = s;
-    }
+    for (int k = 1; k < kClusterMax; ++k)
+      if (k < (int)nrank) s += v[k];
+    GW[e] = s;
   }
   if (tid == 0) {
     FF s{0.0f, 0.0f};
@@ -951,6 +956,7 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   float* Hw = H + (long long)row0 * R;
   if (vec) {
     const float4* l4 = reinterpret_cast<const float4*>(lamf);
+#pragma unroll 1
     for (int v = tid; v < nrows * R / 4; v += T) {
       const int e = 4 * v, rr = e / R, c = e - rr * R;
       const float4 w = *reinterpret_cast<const float4*>(Hs + rr * RP + c);
@@ -958,30 +964,27 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
       reinterpret_cast<float4*>(Hw)[v] = make_float4(w.x * l.x, w.y * l.y, w.z * l.z, w.w * l.w);
     }
   } else {
+#pragma unroll 1
     for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R] * lamf[e % R];
   }
   if (lead) {
     float* Gng = st.G + (long long)n * R2;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * T;
-      if (e < R2) {
-        const float v = GW[e] * lamf[e / R] * lamf[e % R];
-        Gn[e] = v;
-        Gng[e] = v;
-      }
+#pragma unroll 1
+    for (int e = tid; e < R2; e += T) {
+      const float v = GW[e] * lamf[e / R] * lamf[e % R];
+      Gn[e] = v;
+      Gng[e] = v;
     }
     if (is_last) {
       // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
       // float-float over the thread's terms, the warp, then the warps in order
       FF g{0.0f, 0.0f};
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * T;
-        if (e < R2) g = ff_add(g, FF{St[(e % R) * RMAX + e / R] * GW[e], 0.0f});
+#pragma unroll 1
+      for (int e = tid; e < R2; e += T) {
+        const int a = e / R, b = e % R;
+        g = ff_add(g, FF{Srot[b * RMAX + ((a - (b & ~3)) & (RMAX - 1))] * GW[e], 0.0f});
       }
       g = ff_warp_sum(g);
-      __syncthreads();
       if (lane == 0) red[warp] = g;
       __syncthreads();
       if (tid == 0) {
@@ -989,10 +992,10 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
         for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
         const double gamma = (double)gs.hi + (double)gs.lo;
         const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
-        const double alpha = scal_sh[0], prev = scal_sh[1], tol = scal_sh[2];
+        const double alpha = scal_sh[0], tol = scal_sh[1], prev = scal_sh[2];
         const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
         const double fit = 1.0 - eps;
-        const int it = it_sh;
+        const int it = flag_sh[1];
         st.scalars[1] = beta;
         st.scalars[2] = gamma;
         st.scalars[3] = eps;
@@ -1010,22 +1013,19 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
     __syncthreads();
     // S for the next mode: Hadamard of every Gram but next_mode's, in mode
     // order (mode n's is the new one)
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * T;
-      if (e < R2) {
-        float s = 1.0f;
-        for (int k = 0, slot = 0; k < N; ++k) {
-          if (k == next_mode) continue;
-          if (k == n) {
-            s *= Gn[e];
-          } else {
-            s *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
-            ++slot;
-          }
+#pragma unroll 1
+    for (int e = tid; e < R2; e += T) {
+      float s = 1.0f;
+      for (int k = 0, slot = 0; k < N; ++k) {
+        if (k == next_mode) continue;
+        if (k == n) {
+          s *= Gn[e];
+        } else {
+          s *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
+          ++slot;
         }
-        st.S[e] = s;
       }
+      st.S[e] = s;
     }
   }
   // the other CTAs have read this CTA's partials before it leaves
