@@ -60,7 +60,8 @@ struct nncp_ctx {
   SolveState st = {};
   TcScratch tc = {};
 
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;   // one outer iteration
+  cudaGraphExec_t graph4 = nullptr;  // kGraphIters outer iterations, back to back
   int graph_kernels = 0;
   int* host_flags = nullptr;  // pinned
   double* host_dbl = nullptr; // pinned
@@ -211,7 +212,9 @@ void bind_workspace(nncp_ctx* c) {
 
 void drop_graph(nncp_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph4) cudaGraphExecDestroy(c->graph4);
   c->graph = nullptr;
+  c->graph4 = nullptr;
 }
 
 // ---- one partial MTTKRP from the root (precision-dependent) ----------------
@@ -335,37 +338,62 @@ nncp_status solve_init(nncp_ctx* c, double tol) {
   return NNCP_OK;
 }
 
-nncp_status ensure_graph(nncp_ctx* c) {
-  if (c->graph) return NNCP_OK;
+// Captures the outer iteration into a graph, once as one iteration and once as
+// kGraphIters iterations back to back.  Inside a graph the kernels are launched
+// with programmatic serialization, so a kernel can start (and, for the partial
+// MTTKRP, stream tensor tiles) while its predecessor finishes; between two
+// graph launches the dependency is a full one, so longer graphs leave fewer
+// such boundaries.  Iterations after the stop flag is set do no work.
+constexpr int kGraphIters = 4;
+
+nncp_status capture_iterations(nncp_ctx* c, int iters, cudaGraphExec_t* out, int* kernels) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = run_iteration(c, c->work);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < iters && e == cudaSuccess; ++k) e = run_iteration(c, c->work);
   cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
   if (e != cudaSuccess) {
     if (e2 == cudaSuccess) cudaGraphDestroy(g);
     return cuda_fail(c, e, "capturing the outer iteration");
   }
   if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-  {
+  if (kernels) {
     size_t nn = 0;
-    c->graph_kernels = 0;
+    *kernels = 0;
     if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn) {
       std::vector<cudaGraphNode_t> nodes(nn);
       if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
         for (size_t i = 0; i < nn; ++i) {
           cudaGraphNodeType t;
           if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
-            ++c->graph_kernels;
+            ++*kernels;
         }
     }
   }
-  e = cudaGraphInstantiate(&c->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    c->graph = nullptr;
+    *out = nullptr;
     return cuda_fail(c, e, "cudaGraphInstantiate");
   }
   return NNCP_OK;
+}
+
+nncp_status ensure_graph(nncp_ctx* c) {
+  if (c->graph && c->graph4) return NNCP_OK;
+  nncp_status s = NNCP_OK;
+  if (!c->graph) s = capture_iterations(c, 1, &c->graph, &c->graph_kernels);
+  if (s == NNCP_OK && !c->graph4) s = capture_iterations(c, kGraphIters, &c->graph4, nullptr);
+  return s;
+}
+
+// `iters` outer iterations on the work stream
+cudaError_t launch_iterations(nncp_ctx* c, int iters) {
+  cudaError_t e = cudaSuccess;
+  for (; iters >= kGraphIters && e == cudaSuccess; iters -= kGraphIters)
+    e = cudaGraphLaunch(c->graph4, c->work);
+  for (; iters > 0 && e == cudaSuccess; --iters) e = cudaGraphLaunch(c->graph, c->work);
+  return e;
 }
 
 }  // namespace
@@ -627,7 +655,7 @@ nncp_status nncp_iterate(nncp_ctx* c, int iters) {
   if (!c->initialised) return fail(c, NNCP_ERR_INVALID_ARG, "call nncp_solve_begin first");
   if ((s = ensure_graph(c)) != NNCP_OK) return s;
   if ((s = begin_on_work(c)) != NNCP_OK) return s;
-  for (int k = 0; k < iters; ++k) CK(cudaGraphLaunch(c->graph, c->work));
+  CK(launch_iterations(c, iters));
   return end_on_work(c);
 }
 
@@ -643,7 +671,7 @@ nncp_status nncp_solve(nncp_ctx* c, int max_iters, double tol, double* lambda_ou
   int launched = 0, check_every = 4;
   while (launched < max_iters) {
     int batch = std::min(check_every, max_iters - launched);
-    for (int k = 0; k < batch; ++k) CK(cudaGraphLaunch(c->graph, c->work));
+    CK(launch_iterations(c, batch));
     launched += batch;
     CK(cudaMemcpyAsync(c->host_flags, c->st.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost,
                        c->work));

@@ -670,6 +670,14 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
   asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
   return v;
 }
+__device__ __forceinline__ float4 ld_cluster4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
 // every thread of every CTA of the cluster arrives; wait returns once all have
 // (release / acquire: shared-memory writes before the arrive are visible after the wait)
 __device__ __forceinline__ void cluster_arrive() {
@@ -685,8 +693,8 @@ __device__ __forceinline__ void cluster_wait() {
 // and forms its partial W^T W and <M, W> in its own shared memory.  After a
 // cluster barrier each CTA reads every CTA's partials through distributed
 // shared memory, in CTA order, so all of them hold the same W^T W bits, forms
-// lambda and writes its own rows of H = W / lambda; CTA 0 also writes lambda,
-// G_n, the fit at n = N and S for the next mode.  No global round trip
+// lambda and writes its own rows of H = W / lambda and its slice of G_n and of
+// S for the next mode; CTA 0 also writes lambda and the fit at n = N.  No global round trip
 // between the phases, no atomics; the hardware schedules the cluster's CTAs
 // together, so the barrier needs no co-residency assumption.
 //
@@ -731,8 +739,7 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   float* gpart = Ms + kClusterRowsMax * RP;    // GROUPS x R x R
   float* Gown = gpart + GROUPS * RMAX * RMAX;  // this CTA's W^T W (read by the cluster)
   float* GW = Gown + RMAX * RMAX;              // the cluster's W^T W
-  float* Gn = GW + RMAX * RMAX;                // G_n (CTA 0)
-  float* Gpre = Gn + RMAX * RMAX;              // the other modes' Grams (CTA 0)
+  float* Gpre = GW + RMAX * RMAX;              // the other modes' Grams, this CTA's slice
   __shared__ __align__(16) float lamf[RMAX];
   __shared__ __align__(8) double lamd[RMAX];
   __shared__ float sinv[RMAX];
@@ -770,14 +777,18 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
 #pragma unroll 1
     for (int e = tid; e < nrows * R; e += T) cp_async4(Hs + (e / R) * RP + e % R, Hg + e);
   }
+  // this CTA's slice [s0, s0 + ssz) of the R x R outputs G_n and the next S
+  const int ssz = (R2 + (int)nrank - 1) / (int)nrank;
+  const int s0 = min(R2, (int)rank * ssz), s1 = min(R2, s0 + ssz);
   const int ng = N - (next_mode == n ? 1 : 2);
-  const bool gpre = ng > 0 && ng * R2 <= kGpreFloats;
-  if (lead && gpre) {
+  const bool gpre = ng > 0 && ng * ssz <= kGpreFloats;
+  if (gpre) {
 #pragma unroll 1
     for (int k = 0, slot = 0; k < N; ++k) {
       if (k == n || k == next_mode) continue;
 #pragma unroll 1
-      for (int e = tid; e < R2; e += T) cp_async4(Gpre + slot * R2 + e, st.G + (long long)k * R2 + e);
+      for (int e = s0 + tid; e < s1; e += T)
+        cp_async4(Gpre + slot * ssz + (e - s0), st.G + (long long)k * R2 + e);
       ++slot;
     }
   }
@@ -833,18 +844,22 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int j = j0 + t;
-        const float4* srow = reinterpret_cast<const float4*>(Srot + j * RMAX);
+        // the column swept last (rotated index p) enters the dot product last,
+        // so the other terms do not wait for its update
+        const int p = t == 0 ? RMAX - 1 : t - 1;
+        const float* srow = Srot + j * RMAX;
         float d[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int c4 = 0; c4 < RMAX / 4; ++c4) {
-          const float4 sv = srow[c4];
+          const float4 sv = reinterpret_cast<const float4*>(srow)[c4];
+          const float sa[4] = {sv.x, sv.y, sv.z, sv.w};
           const int h = 4 * (c4 & 1);
-          d[h] = fmaf(w[4 * c4], sv.x, d[h]);
-          d[h + 1] = fmaf(w[4 * c4 + 1], sv.y, d[h + 1]);
-          d[h + 2] = fmaf(w[4 * c4 + 2], sv.z, d[h + 2]);
-          d[h + 3] = fmaf(w[4 * c4 + 3], sv.w, d[h + 3]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (4 * c4 + k != p) d[h + k] = fmaf(w[4 * c4 + k], sa[k], d[h + k]);
         }
-        const float dot = ((d[0] + d[4]) + (d[1] + d[5])) + ((d[2] + d[6]) + (d[3] + d[7]));
+        float dot = ((d[0] + d[4]) + (d[1] + d[5])) + ((d[2] + d[6]) + (d[3] + d[7]));
+        dot = fmaf(w[p], srow[p], dot);
         const float si = sinv[j];
         const float upd = fmaxf(0.0f, w[t] + (mrow[j] - dot) * si);
         w[t] = si != 0.0f ? upd : w[t];  // S_jj = 0: column left as it is
@@ -893,7 +908,7 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
-#pragma unroll 2
+#pragma unroll 4
     for (int rr = g; rr < nrows; rr += groups) {
       const float4 qa = *reinterpret_cast<const float4*>(Hs + rr * RP + a0);
       const float4 qb = *reinterpret_cast<const float4*>(Hs + rr * RP + b0);
@@ -920,25 +935,49 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   cluster_arrive();
   cluster_wait();
 
-  // ---- the cluster's W^T W and <M, W>, summed in CTA order (same bits in every CTA)
+  // ---- the cluster's W^T W and <M, W>, summed in CTA order (same bits in
+  // every CTA); four elements per remote load, every CTA's loads in flight at once
 #pragma unroll 1
-  for (int e = tid; e < R2; e += T) {
-    float v[kClusterMax];
+  for (int e4 = tid; e4 < (R2 + 3) / 4; e4 += T) {
+    const int e = 4 * e4;
+    float4 v[kClusterMax];
+    if (e + 4 <= R2) {
 #pragma unroll
-    for (int k = 0; k < kClusterMax; ++k)
-      v[k] = k < (int)nrank ? ld_cluster(cluster_addr(Gown + e, k)) : 0.0f;
-    float s = v[0];
+      for (int k = 0; k < kClusterMax; ++k)
+        if (k < (int)nrank) v[k] = ld_cluster4(cluster_addr(Gown + e, k));
+    } else {
+#pragma unroll
+      for (int k = 0; k < kClusterMax; ++k)
+        if (k < (int)nrank) {
+          v[k].x = ld_cluster(cluster_addr(Gown + e, k));
+          v[k].y = e + 1 < R2 ? ld_cluster(cluster_addr(Gown + e + 1, k)) : 0.0f;
+          v[k].z = e + 2 < R2 ? ld_cluster(cluster_addr(Gown + e + 2, k)) : 0.0f;
+          v[k].w = 0.0f;
+        }
+    }
+    float4 sum = v[0];
 #pragma unroll
     for (int k = 1; k < kClusterMax; ++k)
-      if (k < (int)nrank) s += v[k];
-    GW[e] = s;
+      if (k < (int)nrank) {
+        sum.x += v[k].x;
+        sum.y += v[k].y;
+        sum.z += v[k].z;
+        sum.w += v[k].w;
+      }
+    const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (e + i < R2) GW[e + i] = sv[i];
   }
-  if (tid == 0) {
+  if (warp == 0) {
+    // lane k fetches CTA k's <M, W>; lane 0 adds them in CTA order
+    FF bk{0.0f, 0.0f};
+    if (lane < (int)nrank)
+      bk = FF{ld_cluster(cluster_addr(&beta_own.hi, lane)), ld_cluster(cluster_addr(&beta_own.lo, lane))};
     FF s{0.0f, 0.0f};
-    for (unsigned k = 0; k < nrank; ++k)
-      s = ff_add(s, FF{ld_cluster(cluster_addr(&beta_own.hi, k)),
-                       ld_cluster(cluster_addr(&beta_own.lo, k))});
-    beta_sh = s;
+    for (int k = 0; k < (int)nrank; ++k)
+      s = ff_add(s, FF{__shfl_sync(0xffffffffu, bk.hi, k), __shfl_sync(0xffffffffu, bk.lo, k)});
+    if (lane == 0) beta_sh = s;
   }
   // done reading the other CTAs' shared memory; they may leave once all have
   cluster_arrive();
@@ -967,65 +1006,58 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
 #pragma unroll 1
     for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R] * lamf[e % R];
   }
-  if (lead) {
-    float* Gng = st.G + (long long)n * R2;
+  // this CTA's slice of G_n and of S for the next mode: Hadamard of every Gram
+  // but next_mode's, in mode order (mode n's is the new one)
+  float* Gng = st.G + (long long)n * R2;
+#pragma unroll 1
+  for (int e = s0 + tid; e < s1; e += T) {
+    const float gn = GW[e] * lamf[e / R] * lamf[e % R];
+    Gng[e] = gn;
+    float s = 1.0f;
+    for (int k = 0, slot = 0; k < N; ++k) {
+      if (k == next_mode) continue;
+      if (k == n) {
+        s *= gn;
+      } else {
+        s *= gpre ? Gpre[slot * ssz + (e - s0)] : st.G[(long long)k * R2 + e];
+        ++slot;
+      }
+    }
+    st.S[e] = s;
+  }
+  if (lead && is_last) {
+    // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
+    // float-float over the thread's terms, the warp, then the warps in order
+    FF g{0.0f, 0.0f};
 #pragma unroll 1
     for (int e = tid; e < R2; e += T) {
-      const float v = GW[e] * lamf[e / R] * lamf[e % R];
-      Gn[e] = v;
-      Gng[e] = v;
+      const int a = e / R, b = e % R;
+      g = ff_add(g, FF{Srot[b * RMAX + ((a - (b & ~3)) & (RMAX - 1))] * GW[e], 0.0f});
     }
-    if (is_last) {
-      // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
-      // float-float over the thread's terms, the warp, then the warps in order
-      FF g{0.0f, 0.0f};
-#pragma unroll 1
-      for (int e = tid; e < R2; e += T) {
-        const int a = e / R, b = e % R;
-        g = ff_add(g, FF{Srot[b * RMAX + ((a - (b & ~3)) & (RMAX - 1))] * GW[e], 0.0f});
-      }
-      g = ff_warp_sum(g);
-      if (lane == 0) red[warp] = g;
-      __syncthreads();
-      if (tid == 0) {
-        FF gs{0.0f, 0.0f};
-        for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
-        const double gamma = (double)gs.hi + (double)gs.lo;
-        const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
-        const double alpha = scal_sh[0], tol = scal_sh[1], prev = scal_sh[2];
-        const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
-        const double fit = 1.0 - eps;
-        const int it = flag_sh[1];
-        st.scalars[1] = beta;
-        st.scalars[2] = gamma;
-        st.scalars[3] = eps;
-        st.scalars[5] = fit;
-        if (it < kFitCapacity) st.fits[it] = fit;
-        st.flags[2] = it + 1;
-        if (!isfinite(fit)) {
-          st.flags[3] = 1;
-          st.flags[0] = 1;
-        } else if (it >= 1 && fabs(fit - prev) < tol) {
-          st.flags[0] = 1;
-        }
-      }
-    }
+    g = ff_warp_sum(g);
+    if (lane == 0) red[warp] = g;
     __syncthreads();
-    // S for the next mode: Hadamard of every Gram but next_mode's, in mode
-    // order (mode n's is the new one)
-#pragma unroll 1
-    for (int e = tid; e < R2; e += T) {
-      float s = 1.0f;
-      for (int k = 0, slot = 0; k < N; ++k) {
-        if (k == next_mode) continue;
-        if (k == n) {
-          s *= Gn[e];
-        } else {
-          s *= gpre ? Gpre[slot * R2 + e] : st.G[(long long)k * R2 + e];
-          ++slot;
-        }
+    if (tid == 0) {
+      FF gs{0.0f, 0.0f};
+      for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
+      const double gamma = (double)gs.hi + (double)gs.lo;
+      const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
+      const double alpha = scal_sh[0], tol = scal_sh[1], prev = scal_sh[2];
+      const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
+      const double fit = 1.0 - eps;
+      const int it = flag_sh[1];
+      st.scalars[1] = beta;
+      st.scalars[2] = gamma;
+      st.scalars[3] = eps;
+      st.scalars[5] = fit;
+      if (it < kFitCapacity) st.fits[it] = fit;
+      st.flags[2] = it + 1;
+      if (!isfinite(fit)) {
+        st.flags[3] = 1;
+        st.flags[0] = 1;
+      } else if (it >= 1 && fabs(fit - prev) < tol) {
+        st.flags[0] = 1;
       }
-      st.S[e] = s;
     }
   }
   // the other CTAs have read this CTA's partials before it leaves
@@ -1036,7 +1068,7 @@ template <int RMAX>
 size_t cluster_smem() {
   using C = ClusterCfg<RMAX>;
   return (size_t)(RMAX * RMAX + 2 * kClusterRowsMax * C::RP + C::GROUPS * RMAX * RMAX +
-                  3 * RMAX * RMAX + kGpreFloats) *
+                  2 * RMAX * RMAX + kGpreFloats) *
          sizeof(float);
 }
 
