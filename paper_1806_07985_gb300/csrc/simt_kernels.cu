@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "nncp_internal.cuh"
 
@@ -138,23 +139,57 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
 }
 
 // out[e] = sum_{c < C} part[c * E + e] (deterministic: four interleaved partial
-// sums over c = 0, 4, 8, ... / 1, 5, 9, ... combined in a fixed order).
+// sums over c = 0, 4, 8, ... / 1, 5, 9, ... combined in a fixed order).  The
+// loads of eight chunks are issued before any is added; V = 4 sums four
+// consecutive elements per thread with 16-byte loads (large E only).
+template <int V>
 __global__ void k_reduce_chunks(const float* __restrict__ part, long long E, int C,
                                 float* __restrict__ out) {
   pdl_wait();
   pdl_trigger();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E;
+  using VT = typename std::conditional<V == 4, float4, float>::type;
+  const VT* pv = reinterpret_cast<const VT*>(part);
+  VT* ov = reinterpret_cast<VT*>(out);
+  const long long Ev = E / V;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Ev;
        e += (long long)gridDim.x * blockDim.x) {
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    float s[4][V];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int i = 0; i < V; ++i) s[q][i] = 0.0f;
     int c = 0;
-    for (; c + 4 <= C; c += 4) {
-      s0 += __ldg(part + (long long)c * E + e);
-      s1 += __ldg(part + (long long)(c + 1) * E + e);
-      s2 += __ldg(part + (long long)(c + 2) * E + e);
-      s3 += __ldg(part + (long long)(c + 3) * E + e);
+    for (; c + 8 <= C; c += 8) {
+      VT v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = __ldg(pv + (long long)(c + q) * Ev + e);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float* f = reinterpret_cast<const float*>(&v[q]);
+#pragma unroll
+        for (int i = 0; i < V; ++i) s[q & 3][i] += f[i];
+      }
     }
-    for (; c < C; ++c) s0 += __ldg(part + (long long)c * E + e);
-    out[e] = (s0 + s1) + (s2 + s3);
+    for (; c + 4 <= C; c += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const VT v = __ldg(pv + (long long)(c + q) * Ev + e);
+        const float* f = reinterpret_cast<const float*>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) s[q][i] += f[i];
+      }
+    }
+    for (; c < C; ++c) {
+      const VT v = __ldg(pv + (long long)c * Ev + e);
+      const float* f = reinterpret_cast<const float*>(&v);
+#pragma unroll
+      for (int i = 0; i < V; ++i) s[0][i] += f[i];
+    }
+    VT r;
+    float* rf = reinterpret_cast<float*>(&r);
+#pragma unroll
+    for (int i = 0; i < V; ++i) rf[i] = (s[0][i] + s[1][i]) + (s[2][i] + s[3][i]);
+    ov[e] = r;
   }
 }
 
@@ -194,8 +229,24 @@ k_mttv_leaf(const float* __restrict__ T, long long I, long long K, KrpDesc KK, i
       const int kn = (int)min((long long)kBK, kend - k0);
       const float* Tp = T + (I * k0) * R + e;
       if (V == 4) {
+        // eight node rows in flight, then their products in k order
+        int kk = 0;
+        for (; kk + 8 <= kn; kk += 8) {
+          float4 tv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            tv[q] = __ldg(reinterpret_cast<const float4*>(Tp + I * R * (kk + q)));
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 wv = *reinterpret_cast<const float4*>(Ws + (kk + q) * R + r);
+            acc[0] = fmaf(tv[q].x, wv.x, acc[0]);
+            acc[V > 1 ? 1 : 0] = fmaf(tv[q].y, wv.y, acc[V > 1 ? 1 : 0]);
+            acc[V > 2 ? 2 : 0] = fmaf(tv[q].z, wv.z, acc[V > 2 ? 2 : 0]);
+            acc[V > 3 ? 3 : 0] = fmaf(tv[q].w, wv.w, acc[V > 3 ? 3 : 0]);
+          }
+        }
 #pragma unroll 4
-        for (int kk = 0; kk < kn; ++kk) {
+        for (; kk < kn; ++kk) {
           const float4 tv = __ldg(reinterpret_cast<const float4*>(Tp + I * R * kk));
           const float4 wv = *reinterpret_cast<const float4*>(Ws + kk * R + r);
           acc[0] = fmaf(tv.x, wv.x, acc[0]);
@@ -392,9 +443,16 @@ cudaError_t launch_simt_mttkrp_capped(const float* X, int64_t L, int64_t I, int6
 
 cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out, int num_sms,
                                  cudaStream_t st) {
-  int blocks = (int)min(ceil_div(E, 256), (long long)num_sms * 8);
+  // four elements per thread only when that still leaves a full wave of CTAs:
+  // the reduction is bound by how many SMs pull the partials
+  const bool v4 = E % 4 == 0 && E / 4 >= (int64_t)num_sms * 8 * 256 &&
+                  reinterpret_cast<uintptr_t>(part) % 16 == 0 &&
+                  reinterpret_cast<uintptr_t>(out) % 16 == 0;
+  const long long Ev = v4 ? E / 4 : E;
+  int blocks = (int)min(ceil_div(Ev, 256), (long long)num_sms * 8);
   if (blocks < 1) blocks = 1;
-  return launch_kernel(k_reduce_chunks, dim3(blocks), dim3(256), 0, st, part, (long long)E, C, out);
+  return launch_kernel(v4 ? k_reduce_chunks<4> : k_reduce_chunks<1>, dim3(blocks), dim3(256), 0,
+                       st, part, (long long)E, C, out);
 }
 
 size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
