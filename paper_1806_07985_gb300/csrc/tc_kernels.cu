@@ -592,6 +592,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     bool ok = true;
     // resident B: one pass over the whole contraction, tile s into slot s
     const long long n_pass = p.b_resident ? (blockIdx.x < n_units ? 1 : 0) : n_units;
+    const uint32_t kd0 = kdim[0];
     for (long long u = blockIdx.x, pass = 0; pass < n_pass && ok; u += gridDim.x, ++pass) {
       Unit w = get_unit(p, p.b_resident ? 0 : u);
       if (p.b_resident) {
@@ -600,6 +601,14 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         w.nk = (int)((p.K + kKC - 1) / kKC);
       }
       if (!p.b_resident && u >= n_units) break;
+      // lead-aligned position of this half's first element, kept incrementally:
+      // k = kbeg + 64 s + 32 half = lq * kd0 + lk (one 64-bit division per unit)
+      const long long kb = w.kbeg + half * 32;
+      long long lq = kb / kd0;
+      uint32_t lk = (uint32_t)(kb - lq * kd0);
+      int ls = 0;                 // stage the position refers to
+      long long cst_q = -1;       // slow index the cached constant belongs to
+      float cst = 1.0f;
       for (int s = 0; s < w.nk; ++s, ++t) {
         if ((int)(t % kSB) != bw) continue;
         if (p.b_resident) bt_base = b0 + s * kBBytes;
@@ -640,20 +649,37 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
           if (lead_aligned) {
             // modes after the first are constant over the stage:
             // v(e) = H_0(k0 + e, r) * prod_{m>=1} H_m(k_m, r)
-            const int k0 = (int)(kst % kdim[0]);
-            const float* h0 = kH[0] + (long long)k0 * R + rs;
+            if (it == 0) {
+              // advance the position to stage s (64 elements per stage)
+              lk += (uint32_t)(s - ls) * kKC;
+              ls = s;
+              while (lk >= kd0) {
+                lk -= kd0;
+                ++lq;
+              }
+            }
+            const float* h0 = kH[0] + (long long)lk * R + rs;
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = __ldg(h0 + e * R);
-            uint32_t rem = (uint32_t)(kst / kdim[0]);
-            float cst = 1.0f;
-            for (int m = 1; m < nm; ++m) {
-              const uint32_t dm = kdim[m];
-              cst *= __ldg(kH[m] + (rem % dm) * (uint32_t)R + rs);
-              rem /= dm;
+            if (lq != cst_q || iters > 1) {
+              long long rem = lq;
+              cst = 1.0f;
+              for (int m = 1; m < nm; ++m) {
+                const uint32_t dm = kdim[m];
+                const long long q = rem / dm;
+                cst *= __ldg(kH[m] + (uint32_t)(rem - q * dm) * (uint32_t)R + rs);
+                rem = q;
+              }
+              cst_q = lq;
             }
+            if (rr < R && kst + 32 <= w.kend) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
-              v[e] = (rr < R && kst + e < w.kend) ? v[e] * cst : 0.0f;
+              for (int e = 0; e < 32; ++e) v[e] *= cst;
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e)
+                v[e] = (rr < R && kst + e < w.kend) ? v[e] * cst : 0.0f;
+            }
           } else {
 #pragma unroll
             for (int m = 0; m < kMaxModes; ++m) {
