@@ -85,6 +85,17 @@ nncp_status nncp_set_options(nncp_ctx* ctx, nncp_precision precision, int root_s
  * NNCP_ERR_UNSUPPORTED for a tensor-core precision.  Takes effect at the
  * next solve or iteration. */
 nncp_status nncp_set_dimtree(nncp_ctx* ctx, int enabled);
+
+/* Fuse the first multi-TTV out of the right root node into that node's
+ * partial MTTKRP (enabled = 1, the default; Sec. IV-A, Fig. 2b): the leaf of
+ * the node's first mode is accumulated from the tensor-core kernel's
+ * accumulators while the node is written, instead of by a separate pass over
+ * the node.  Applies to the tensor-core precisions when the node has two or
+ * more modes, its first mode is a multiple of 128, its rows fill the GPU (no
+ * split contraction) and R <= 32; otherwise, and with enabled = 0, the leaf is
+ * a separate multi-TTV.  Results agree to rounding (a different summation
+ * order).  Takes effect at the next solve or iteration. */
+nncp_status nncp_set_leaf_fusion(nncp_ctx* ctx, int enabled);
 /* Bytes of device scratch the context needs for its current options
  * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
 nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);

@@ -60,6 +60,7 @@ struct nncp_ctx {
   SolveState st = {};
   TcScratch tc = {};
 
+  bool fuse_leaf = true;              // fuse first leaf multi-TTVs into partial MTTKRPs
   cudaGraphExec_t graph = nullptr;   // one outer iteration
   cudaGraphExec_t graph4 = nullptr;  // kGraphIters outer iterations, back to back
   int graph_kernels = 0;
@@ -219,7 +220,7 @@ void drop_graph(nncp_ctx* c) {
 
 // ---- one partial MTTKRP from the root (precision-dependent) ----------------
 
-cudaError_t pm_right(nncp_ctx* c, float* out, cudaStream_t st) {
+cudaError_t pm_right(nncp_ctx* c, float* out, cudaStream_t st, const TcLeaf* leaf = nullptr) {
   const int s = c->split, N = c->N;
   const int64_t IL = prod(c->dims, 0, s - 1), IR = prod(c->dims, s, N - 1);
   KrpDesc none;
@@ -227,12 +228,12 @@ cudaError_t pm_right(nncp_ctx* c, float* out, cudaStream_t st) {
   KrpDesc KQ = krp(c, s, N - 1);
   if (c->precision != NNCP_FP32_SIMT)
     return tc_partial_mttkrp(c->precision, /*contract_fast=*/0, c->X, IL, IR, KQ, c->R, out,
-                             c->tc, c->num_sms, st);
+                             c->tc, c->num_sms, st, leaf);
   return launch_simt_mttkrp(static_cast<const float*>(c->X), 1, IL, IR, none, KQ, c->R, out,
                             c->partials, c->part_cap, c->num_sms, st);
 }
 
-cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st) {
+cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st, const TcLeaf* leaf = nullptr) {
   const int s = c->split, N = c->N;
   const int64_t IL = prod(c->dims, 0, s - 1), IR = prod(c->dims, s, N - 1);
   KrpDesc none;
@@ -240,7 +241,7 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st) {
   KrpDesc KL = krp(c, 0, s - 1);
   if (c->precision != NNCP_FP32_SIMT)
     return tc_partial_mttkrp(c->precision, /*contract_fast=*/1, c->X, IL, IR, KL, c->R, out,
-                             c->tc, c->num_sms, st);
+                             c->tc, c->num_sms, st, leaf);
   return launch_simt_mttkrp(static_cast<const float*>(c->X), IL, IR, 1, KL, none, c->R, out,
                             c->partials, c->part_cap, c->num_sms, st);
 }
@@ -259,15 +260,18 @@ cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
 }
 
 // Node {a..last} held in T (half h, depth d): leaf M(a), update, child node.
+// leaf_done: M(a) is in Mbuf already (fused into the partial MTTKRP).
 cudaError_t visit(nncp_ctx* c, const float* T, int a, int last, int h, int base,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool leaf_done = false) {
   const int R = c->R;
   cudaError_t e;
   if (a == last) return update_mode(c, a, st);  // T is Mbuf already
   KrpDesc rest = krp(c, a + 1, last);
-  e = launch_mttv_leaf(T, c->dims[a], prod(c->dims, a + 1, last), rest, R, c->Mbuf,
-                       c->partials, c->part_cap, c->num_sms, st);
-  if (e != cudaSuccess) return e;
+  if (!leaf_done) {
+    e = launch_mttv_leaf(T, c->dims[a], prod(c->dims, a + 1, last), rest, R, c->Mbuf,
+                         c->partials, c->part_cap, c->num_sms, st);
+    if (e != cudaSuccess) return e;
+  }
   e = update_mode(c, a, st);
   if (e != cudaSuccess) return e;
   float* child = (a + 1 == last) ? c->Mbuf : c->node[h][a + 1 - base];
@@ -290,15 +294,24 @@ cudaError_t run_iteration(nncp_ctx* c, cudaStream_t st) {
     }
     return cudaSuccess;
   }
+  // a node of two or more modes gets its first leaf M(a) from the partial
+  // MTTKRP's epilogue when the tensor-core kernel can fuse it
+  const int64_t IL = prod(c->dims, 0, s - 1), IR = prod(c->dims, s, N - 1);
+  TcLeaf lf{c->dims[0], krp(c, 1, s - 1), c->Mbuf};
+  TcLeaf rf{c->dims[s], krp(c, s + 1, N - 1), c->Mbuf};
+  const bool fuse_l = c->fuse_leaf && s >= 2 &&
+                      tc_leaf_ok(c->precision, 0, IL, IR, c->R, lf.I, c->num_sms);
+  const bool fuse_r = c->fuse_leaf && N - s >= 2 &&
+                      tc_leaf_ok(c->precision, 1, IL, IR, c->R, rf.I, c->num_sms);
   float* TL = (s == 1) ? c->Mbuf : c->node[0][0];
-  cudaError_t e = pm_right(c, TL, st);
+  cudaError_t e = pm_right(c, TL, st, fuse_l ? &lf : nullptr);
   if (e != cudaSuccess) return e;
-  e = visit(c, TL, 0, s - 1, 0, 0, st);
+  e = visit(c, TL, 0, s - 1, 0, 0, st, fuse_l);
   if (e != cudaSuccess) return e;
   float* TR = (N - s == 1) ? c->Mbuf : c->node[1][0];
-  e = pm_left(c, TR, st);
+  e = pm_left(c, TR, st, fuse_r ? &rf : nullptr);
   if (e != cudaSuccess) return e;
-  return visit(c, TR, s, N - 1, 1, s, st);
+  return visit(c, TR, s, N - 1, 1, s, st, fuse_r);
 }
 
 nncp_status check_ready(nncp_ctx* c) {
@@ -505,6 +518,13 @@ nncp_status nncp_set_dimtree(nncp_ctx* c, int enabled) {
   if (!enabled && c->precision != NNCP_FP32_SIMT)
     return fail(c, NNCP_ERR_UNSUPPORTED, "the solve without the dimension tree is FP32 SIMT only");
   c->dimtree = enabled ? 1 : 0;
+  drop_graph(c);
+  return NNCP_OK;
+}
+
+nncp_status nncp_set_leaf_fusion(nncp_ctx* c, int enabled) {
+  if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
+  c->fuse_leaf = enabled != 0;
   drop_graph(c);
   return NNCP_OK;
 }

@@ -89,6 +89,17 @@ struct TcParams {
   KrpDesc krp;
   float* out;
   int* err;
+  // Fused first multi-TTV of the output node (leaf_I > 0; Sec. IV-A, Fig. 2b):
+  // output rows are node rows (the node's first mode fastest, then its other
+  // modes), so tile mt holds rows i_lead in [128 (mt mod nblk), +128) of slice
+  // rest = mt / nblk, nblk = leaf_I / 128.  The epilogue adds
+  // row(r) * q(rest, r), q the Khatri-Rao row of the node's other modes, into
+  // the CTA's partial leaf kept in tensor memory (a CTA's tiles share
+  // mt mod nblk because the grid is a multiple of nblk); at the end every CTA
+  // writes its partial to leaf_part[blockIdx / nblk][i_lead][r].
+  long long leaf_I;
+  KrpDesc leaf_krp;
+  float* leaf_part;
 };
 
 // ------------------------------------------------------------ PTX helpers --
@@ -238,6 +249,19 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16f(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* r) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
@@ -339,6 +363,9 @@ __device__ __forceinline__ Unit get_unit(const TcParams& p, long long u) {
 
 // ------------------------------------------------------------------ kernel --
 
+// LEAF: the fused first multi-TTV (TcParams::leaf_I > 0), a separate
+// instantiation so that the plain kernel carries none of its code.
+template <bool LEAF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   // Launched in a graph with programmatic serialization, the kernel may start
@@ -403,7 +430,8 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(acc_full(i), 1);
-      mbar_init(acc_empty(i), 4);
+      // the four epilogue warps, and with the fused leaf its four warps too
+      mbar_init(acc_empty(i), LEAF ? 8 : 4);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -717,6 +745,65 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       __syncwarp();
       if (lane == 0) mbar_arrive(b_full(0));
     }
+    if constexpr (LEAF) {
+      if (warp >= 4) {
+        // ---------------------------------------- fused leaf multi-TTV --
+        // Warps 4-7 (TMEM lane quarters 0-3; idle once the resident B is
+        // built) read every unit's accumulator beside the epilogue warps and
+        // add row(r) * q(rest, r) into the CTA's partial leaf, one row per
+        // thread, in registers; q (the Khatri-Rao row of the tile's slice of
+        // the node's other modes, lane l holding column l) is loaded before
+        // the accumulator wait.
+        const int lq = warp & 3;
+        const uint32_t nblk = (uint32_t)(p.leaf_I >> 7);
+        float lacc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) lacc[i] = 0.0f;
+        long long li = 0;
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
+          const Unit w = get_unit(p, u);
+          uint32_t rest = (uint32_t)w.mt / nblk;  // the host fuses only below 2^31 tiles
+          float qv = lane < R ? 1.0f : 0.0f;
+          for (int m = 0; m < p.leaf_krp.nm; ++m) {
+            const uint32_t dm = (uint32_t)p.leaf_krp.dim[m];
+            const uint32_t qm = rest / dm;
+            if (lane < R) qv *= __ldg(p.leaf_krp.H[m] + (size_t)(rest - qm * dm) * R + lane);
+            rest = qm;
+          }
+          const int bsel = (int)(li & 1);
+          const bool got = mbar_wait(acc_full(bsel), (uint32_t)((li >> 1) & 1), abort_flag, p.err);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tbase = tmem_base + ((uint32_t)(lq * 32) << 16) + bsel * acc_cols;
+#pragma unroll
+          for (int c = 0; c < 32; c += 16) {
+            if (c < Rp) {
+              float v[16], v2[16];
+              tmem_ld16(tbase + c, v);
+              if (p.mode != NNCP_TF32) tmem_ld16(tbase + Rp + c, v2);
+              tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const float x = p.mode != NNCP_TF32 ? v[i] + v2[i] : v[i];
+                lacc[c + i] = fmaf(x, __shfl_sync(0xffffffffu, qv, c + i), lacc[c + i]);
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty(bsel));
+        }
+        // this CTA's partial of the leaf: rows [128 (blockIdx mod nblk), +128)
+        const long long i_lead = (long long)(blockIdx.x % nblk) * 128 + lq * 32 + lane;
+        float* dst = p.leaf_part + ((long long)(blockIdx.x / nblk) * p.leaf_I + i_lead) * R;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < R) dst[i] = lacc[i];
+      }
+    }
   } else {
     // ---------------------------------------- converters + epilogue --
     const int ct = threadIdx.x - kWarpConv * 32;  // 0..255
@@ -1004,19 +1091,50 @@ size_t tc_scratch_bytes(int N, const int64_t* dims, int R, int split, int precis
     Plan pl = plan_for(cf, IL, IR, R, num_sms);
     if (pl.nsplit > 1) need = std::max<size_t>(need, (size_t)pl.nsplit * pl.M * R * sizeof(float));
   }
+  // fused leaf partials: 128 rows per CTA
+  need = std::max<size_t>(need, (size_t)num_sms * 128 * R * sizeof(float));
   return 256 + need;
+}
+
+// grid of a fused-leaf launch: a multiple of the leaf's 128-row blocks
+static int leaf_grid(const Plan& pl, int64_t leaf_I, int num_sms) {
+  const int nblk = (int)(leaf_I / 128);
+  const int g = num_sms - num_sms % nblk;
+  return (int)std::min<long long>(g, pl.n_units);
+}
+
+bool tc_leaf_ok(int precision, int contract_fast, int64_t IL, int64_t IR, int R, int64_t leaf_I,
+                int num_sms) {
+  // the leaf runs on builder warps that are idle once a resident B is built:
+  // the contract-fast (root -> right) kernel, up to 32 rank columns
+  if (precision == NNCP_FP32_SIMT || !contract_fast || leaf_I <= 0 || leaf_I % 128 != 0 || R > 32)
+    return false;
+  const Plan pl = plan_for(contract_fast, IL, IR, R, num_sms);
+  if (pl.nsplit != 1 || pl.M % leaf_I != 0 || leaf_I / 128 > num_sms || pl.n_mt >= (1LL << 31))
+    return false;
+  const bool bf16x = precision == NNCP_BF16_STORED;
+  const bool direct = precision != NNCP_SPLIT_BF16X3;
+  int resident = 0;
+  plan_smem(precision, contract_fast, direct, bf16x, pl.Rp, pl.K, pl.nsplit, &resident);
+  if (!resident) return false;
+  const int g = leaf_grid(pl, leaf_I, num_sms);
+  return g >= 1 && g % (leaf_I / 128) == 0;
 }
 
 int* tc_error_word(const TcScratch& s) { return static_cast<int*>(s.base); }
 
 cudaError_t tc_attributes_init() {
-  return cudaFuncSetAttribute(k_tc_partial_mttkrp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_tc_partial_mttkrp<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tc_partial_mttkrp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kSmemMax);
 }
 
 cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, int64_t IL,
                               int64_t IR, const KrpDesc& K, int R, float* out,
-                              const TcScratch& scratch, int num_sms, cudaStream_t st) {
+                              const TcScratch& scratch, int num_sms, cudaStream_t st,
+                              const TcLeaf* leaf) {
   if (!load_encode()) return cudaErrorNotSupported;
   if (R > kMaxRp || !scratch.base) return cudaErrorInvalidValue;
   const bool bf16x = precision == NNCP_BF16_STORED;
@@ -1069,10 +1187,28 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
 
   p.sm = plan_smem(precision, contract_fast, p.direct, bf16x, pl.Rp, pl.K, pl.nsplit, &p.b_resident);
   if (p.sm.nsf < 2) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>(pl.n_units, num_sms);
-  cudaError_t e = launch_kernel(k_tc_partial_mttkrp, dim3(grid), dim3(kThreads), p.sm.total, st,
-                                map, p);
-  if (e != cudaSuccess || pl.nsplit == 1) return e;
+  int grid = (int)std::min<long long>(pl.n_units, num_sms);
+  if (leaf) {
+    if (!tc_leaf_ok(precision, contract_fast, IL, IR, R, leaf->I, num_sms) || !leaf->out)
+      return cudaErrorInvalidValue;
+    grid = leaf_grid(pl, leaf->I, num_sms);
+    p.leaf_I = leaf->I;
+    p.leaf_krp = leaf->rest;
+    p.leaf_part = partials;
+    if (256 + (size_t)grid * 128 * R * sizeof(float) > scratch.bytes) return cudaErrorInvalidValue;
+  }
+  cudaError_t e =
+      leaf ? launch_kernel(k_tc_partial_mttkrp<true>, dim3(grid), dim3(kThreads), p.sm.total, st,
+                           map, p)
+           : launch_kernel(k_tc_partial_mttkrp<false>, dim3(grid), dim3(kThreads), p.sm.total,
+                           st, map, p);
+  if (e != cudaSuccess) return e;
+  if (leaf) {
+    // the CTAs' partial leaves, summed in CTA order
+    const int nblk = (int)(leaf->I / 128);
+    return launch_reduce_chunks(partials, leaf->I * R, grid / nblk, leaf->out, num_sms, st);
+  }
+  if (pl.nsplit == 1) return e;
   return launch_reduce_chunks(partials, pl.M * R, (int)pl.nsplit, out, num_sms, st);
 }
 

@@ -45,6 +45,7 @@ _SIGNATURES = [
     ("nncp_create", ctypes.c_int, [ctypes.c_int, _c_i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("nncp_set_options", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("nncp_set_dimtree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("nncp_set_leaf_fusion", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("nncp_set_tensor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -164,6 +165,10 @@ def nncp_set_options(ctx, precision=NNCP_FP32_SIMT, root_split=0, stream=None):
 
 def nncp_set_dimtree(ctx, enabled):
     _check(load().nncp_set_dimtree(ctx, 1 if enabled else 0), ctx)
+
+
+def nncp_set_leaf_fusion(ctx, enabled):
+    _check(load().nncp_set_leaf_fusion(ctx, 1 if enabled else 0), ctx)
 
 
 def nncp_workspace_size(ctx):
@@ -494,6 +499,9 @@ class Context:
 
     def set_dimtree(self, enabled):
         nncp_set_dimtree(self.ctx, enabled)
+
+    def set_leaf_fusion(self, enabled):
+        nncp_set_leaf_fusion(self.ctx, enabled)
 
     def solve(self, max_iters, tol=0.0):
         return nncp_solve(self.ctx, self.R, max_iters, tol)

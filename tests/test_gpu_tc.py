@@ -188,3 +188,53 @@ def test_refused_context_cleans_up_once(nn):
             nn.Context((37, 23, 29), 5, precision=nn.NNCP_SPLIT_BF16X3)
     import gc
     gc.collect()
+
+
+# Shapes whose first multi-TTV out of the right root node is fused into its
+# partial MTTKRP (lead mode a multiple of 128, node rows filling the GPU):
+# a 3-way tensor, a 3-mode right node, and a 2-mode right node at split 2.
+FUSED = [((16, 128, 160), 8, 1), ((8, 256, 20, 6), 16, 1), ((4, 4, 128, 200), 24, 2)]
+
+
+@pytest.mark.parametrize("prec", ["split_bf16x3", "tf32", "bf16_stored"])
+@pytest.mark.parametrize("dims,R,split", FUSED)
+def test_fused_leaf_matches_unfused_and_oracle(nn, prec, dims, R, split):
+    iters = 5
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=7, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=8)
+    out = {}
+    for fused in (True, False):
+        c = nn.Context(dims, R, precision=prec, root_split=split)
+        try:
+            c.set_leaf_fusion(fused)
+            X = torch.from_numpy(x).cuda()
+            Xuse = X
+            if prec == "bf16_stored":
+                Xuse = torch.empty(X.numel(), dtype=torch.bfloat16, device="cuda")
+                nn.nncp_tensor_to_bf16(X, Xuse)
+            Hd = [torch.from_numpy(h.copy()).cuda() for h in H0]
+            c.set_tensor(Xuse)
+            c.set_factors(Hd)
+            kernels = c.iteration_kernels()
+            lam, k, fit = c.solve(iters)
+            assert k == iters
+            out[fused] = (fit, [h.cpu().numpy() for h in Hd], kernels)
+        finally:
+            c.close()
+    (ff, Hf, kf), (fu, Hu, ku) = out[True], out[False]
+    # the fused node drops its leaf multi-TTV (and that multi-TTV's split sum)
+    # for the fused kernel's own sum of the CTAs' partial leaves
+    assert kf == ku - 1, (kf, ku)
+    # fused and unfused differ only in the leaf's summation order; the fit
+    # identity amplifies that by ~1/eps^2 (and, with TF32 or bf16 operands,
+    # through HALS clamps the noisier M puts near zero), hence per-mode bounds
+    fit_tol, h_tol = (1e-5, 1e-4) if prec == "split_bf16x3" else (1e-3, 1e-2)
+    assert abs(ff - fu) <= fit_tol, (ff, fu)
+    for a, b in zip(Hf, Hu):
+        assert rel_fro(a, b) <= h_tol
+    if prec == "split_bf16x3":
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=iters, use_dimtree=True, s=split)
+        assert abs(ff - ref["fits"][-1]) <= 1e-4, (ff, ref["fits"][-1])
+        for n in range(len(dims)):
+            assert rel_fro(Hf[n], ref["H"][n]) <= 1e-3, n
