@@ -271,8 +271,8 @@ nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* 
  * NNCP_SERVER_MAX_SOLO of those run at once (two: one's latency-bound mode
  * updates overlap the other's bandwidth-bound partial MTTKRPs, and neither
  * is slowed much), while small requests keep being admitted beside them.
- * No call blocks without a bound: submit copies and returns, wait gives up
- * after timeout_ms. */
+ * No call blocks without a bound: submit copies the request (or borrows the
+ * tensor, borrow_x) and returns, wait gives up after timeout_ms. */
 #define NNCP_SERVER_SOLO_ELEMS (1LL << 22)
 #define NNCP_SERVER_MAX_SOLO 2
 typedef struct nncp_server nncp_server;
@@ -280,11 +280,17 @@ typedef struct {
   int N;                            /* order */
   const int64_t* dims;              /* N mode lengths */
   int R;                            /* rank */
-  const float* X_host;              /* I_1...I_N floats, mode-1 fastest; copied by submit */
+  const float* X_host;              /* I_1...I_N floats, mode-1 fastest; copied by submit
+                                       unless borrow_x */
   const float* const* H_init_host;  /* N pointers, I_n x R row-major; copied by submit */
   int max_iters;                    /* 1..65536 */
   double tol;                       /* stop when |fit_k - fit_{k-1}| < tol */
   nncp_precision precision;         /* solo lane: NNCP_FP32_SIMT, NNCP_TF32 or NNCP_SPLIT_BF16X3 */
+  int borrow_x;                     /* 0: submit copies X_host.  1: the server keeps the pointer
+                                       and uploads from it at admission; the caller keeps it
+                                       valid and unchanged until the request is done (poll or
+                                       wait returned its result).  From page-locked memory the
+                                       upload is an asynchronous copy with no host-side copy. */
 } nncp_request;
 typedef struct {
   nncp_status status;       /* NNCP_OK, NNCP_ERR_NUMERIC (non-finite fit) or NNCP_ERR_CUDA */

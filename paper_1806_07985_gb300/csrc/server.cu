@@ -81,7 +81,9 @@ struct Request {
   int64_t dims[kMaxModes] = {0};
   int64_t I = 0;
   double tol = 0.0;
-  std::vector<float> X;               // host copy until admission
+  std::vector<float> X;               // host copy until admission (empty when borrowed)
+  const float* Xb = nullptr;          // the caller's tensor when borrowed (borrow_x)
+  const float* x_host() const { return Xb ? Xb : X.data(); }
   std::vector<std::vector<float>> H;  // initial factors, then the results
   std::vector<const float*> Hp;
   std::vector<double> lam;
@@ -271,11 +273,11 @@ cudaError_t admit_one(nncp_server* s, Request* r) {
     if (I1 != r->dims[0]) {  // zero slices of mode 1 and zero rows of H_1
       e = cudaMemsetAsync(X, 0, (size_t)(rows * I1) * sizeof(float), st);
       if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(X, (size_t)I1 * sizeof(float), r->X.data(), (size_t)r->dims[0] * sizeof(float),
+        e = cudaMemcpy2DAsync(X, (size_t)I1 * sizeof(float), r->x_host(), (size_t)r->dims[0] * sizeof(float),
                               (size_t)r->dims[0] * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(H[0], 0, (size_t)I1 * r->R * sizeof(float), st);
     } else {
-      e = cudaMemcpyAsync(X, r->X.data(), r->X.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(X, r->x_host(), (size_t)r->I * sizeof(float), cudaMemcpyHostToDevice, st);
     }
     for (int n = 0; n < r->N && e == cudaSuccess; ++n)
       e = cudaMemcpyAsync(H[n], r->H[n].data(), r->H[n].size() * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -293,7 +295,7 @@ cudaError_t admit_one(nncp_server* s, Request* r) {
   for (int n = 0; n < r->N; ++n) r->desc.H[n] = H[n];
   r->desc.max_iters = r->max_iters;
   r->desc.tol = r->tol;
-  cudaError_t e = cudaMemcpyAsync(X, r->X.data(), r->X.size() * sizeof(float), cudaMemcpyHostToDevice, s->st);
+  cudaError_t e = cudaMemcpyAsync(X, r->x_host(), (size_t)r->I * sizeof(float), cudaMemcpyHostToDevice, s->st);
   for (int n = 0; n < r->N && e == cudaSuccess; ++n)
     e = cudaMemcpyAsync(H[n], r->H[n].data(), r->H[n].size() * sizeof(float), cudaMemcpyHostToDevice, s->st);
   return e;
@@ -742,7 +744,10 @@ nncp_status nncp_server_submit(nncp_server* s, const nncp_request* q, uint64_t* 
   }
   r->bytes = bytes;
   try {
-    r->X.assign(q->X_host, q->X_host + r->I);
+    if (q->borrow_x)
+      r->Xb = q->X_host;
+    else
+      r->X.assign(q->X_host, q->X_host + r->I);
     r->H.resize(q->N);
     for (int n = 0; n < q->N; ++n)
       r->H[n].assign(q->H_init_host[n], q->H_init_host[n] + r->dims[n] * r->R);

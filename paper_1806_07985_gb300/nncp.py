@@ -330,7 +330,7 @@ class _Request(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dims", _c_i64p), ("R", ctypes.c_int),
                 ("X_host", ctypes.c_void_p), ("H_init_host", _c_vpp),
                 ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("borrow_x", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -369,6 +369,7 @@ class Server:
                 int(self.SOLO_ELEMS if solo_elems is None else solo_elems),
                 int(self.MAX_SOLO if max_solo is None else max_solo), ctypes.byref(self.s)), None)
         self._shapes = {}
+        self._borrowed = {}  # ticket -> X the server may still read (borrow=True)
 
     def footprint(self, dims, R, max_iters, precision=NNCP_FP32_SIMT):
         """Device bytes the request would take from the pool (its lane's layout)."""
@@ -379,23 +380,37 @@ class Server:
                                              int(precision), ctypes.byref(n)), self.s)
         return n.value
 
-    def submit(self, dims, R, X, H, max_iters, tol, precision=NNCP_FP32_SIMT):
+    def submit(self, dims, R, X, H, max_iters, tol, precision=NNCP_FP32_SIMT, borrow=False):
+        """X: host float32 tensor (numpy array or CPU torch tensor).  borrow=True
+        passes borrow_x: the server uploads from X itself at admission (page-locked
+        memory makes that an asynchronous copy); X is kept referenced here until
+        the request's result has been returned or released."""
         import numpy as np
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1)
+        if hasattr(X, "data_ptr"):
+            if X.device.type != "cpu" or not X.is_contiguous() or X.element_size() != 4:
+                raise ValueError("X must be a contiguous float32 CPU tensor")
+            xptr = X.data_ptr()
+        else:
+            X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1)
+            xptr = X.ctypes.data
         H = [np.ascontiguousarray(h, dtype=np.float32) for h in H]
         d = _dims(dims)
         hp = (ctypes.c_void_p * len(H))(*[h.ctypes.data for h in H])
-        req = _Request(len(dims), ctypes.cast(d, _c_i64p), int(R), X.ctypes.data,
-                       ctypes.cast(hp, _c_vpp), int(max_iters), float(tol), int(precision))
+        req = _Request(len(dims), ctypes.cast(d, _c_i64p), int(R), xptr,
+                       ctypes.cast(hp, _c_vpp), int(max_iters), float(tol), int(precision),
+                       1 if borrow else 0)
         t = ctypes.c_uint64()
         _scheck(load().nncp_server_submit(self.s, ctypes.byref(req), ctypes.byref(t)), self.s)
         self._shapes[t.value] = (tuple(int(x) for x in dims), int(R))
+        if borrow:
+            self._borrowed[t.value] = X
         return t.value
 
     def _result(self, ticket, res):
         import numpy as np
+        self._borrowed.pop(ticket, None)  # done: the server no longer reads X
         dims, R = self._shapes[ticket]
         H = [np.ctypeslib.as_array(res.H[n], shape=(dims[n], R)).copy() for n in range(len(dims))]
         lam = np.ctypeslib.as_array(res.lam, shape=(R,)).copy() if res.lam else None
@@ -421,6 +436,7 @@ class Server:
     def release(self, ticket):
         _scheck(load().nncp_server_release(self.s, ticket), self.s)
         self._shapes.pop(ticket, None)
+        self._borrowed.pop(ticket, None)
 
     def stats(self):
         st = _Stats()

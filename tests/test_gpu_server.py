@@ -216,3 +216,28 @@ def test_server_solo_lane_pads_like_solve_host(nn):
     assert abs(res["fit"] - ref["fits"][-1]) <= 1e-4
     for n in range(3):
         assert rel_fro(res["H"][n], ref["H"][n]) <= 1e-3
+
+
+def test_server_borrowed_tensor_gives_the_same_bits(nn):
+    # borrow_x: the server uploads from the caller's (page-locked) tensor at
+    # admission instead of copying it at submit; results are the same bits
+    small = _mix()[:3]
+    dims, R = (160, 160, 170), 16
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=91, noise=0.01)
+    big = (dims, R, x, synth.init_factors(dims, R, seed=92))
+    reqs = small + [big]
+    outs = []
+    for borrow in (False, True):
+        srv = nn.Server(1 << 32, 8)
+        try:
+            xs = [torch.from_numpy(q[2]).pin_memory() if borrow else q[2] for q in reqs]
+            tk = [srv.submit(q[0], q[1], xx, q[3], 6, 0.0, precision="split_bf16x3", borrow=borrow)
+                  for q, xx in zip(reqs, xs)]
+            outs.append([srv.wait(t, 120000) for t in tk])
+        finally:
+            srv.close()
+    for a, b in zip(*outs):
+        assert a["status"] == b["status"] == 0 and a["iters"] == b["iters"] == 6
+        assert a["fit"] == b["fit"]
+        for u, v in zip(a["H"], b["H"]):
+            assert np.array_equal(u, v)
