@@ -241,3 +241,34 @@ def test_without_dimension_tree_is_fp32_only(nn):
         assert info.value.status == nn.NNCP_ERR_UNSUPPORTED
     finally:
         c.close()
+
+
+# Mode-update configurations: the cluster update (I_n <= 1024) with 1-8 CTAs
+# of 32, 64 or 128 rows (ragged last CTA), every RMAX variant (R <= 16, <= 32,
+# <= 64; R = 1; odd R takes the scalar staging path; R = 33 rotates 64 register
+# columns of which 31 are padding), its largest case (1024 rows) and the
+# multi-CTA kernel just above it (1025 rows).  FP32 SIMT, so the update is the
+# only tensor-core-independent difference from the FP64 oracle.
+UPDATE_SHAPES = [
+    ((3, 40, 30), 5),       # a 3-row mode: one CTA of 32 rows, 3 used
+    ((31, 33, 20), 7),      # odd R, 31- and 33-row modes (1 and 2 CTAs)
+    ((100, 64, 10), 16),    # 4 CTAs of 32 rows
+    ((512, 20, 8), 24),     # 8 CTAs of 64 rows, R in the 32-column variant
+    ((1000, 12, 8), 32),    # 8 CTAs of 128 rows, the last one partial
+    ((1024, 10, 6), 33),    # 64-column variant at the largest cluster mode
+    ((1025, 10, 6), 8),     # one row more: the multi-CTA kernel
+    ((40, 30, 20), 64),     # the maximum rank
+    ((64, 48, 20), 1),      # rank one
+]
+
+
+@pytest.mark.parametrize("dims,R", UPDATE_SHAPES)
+def test_update_configurations_match_oracle(nn, dims, R):
+    x, _ = synth.lowrank_plus_noise(dims, min(R, 8), seed=31, noise=0.02)
+    H0 = synth.init_factors(dims, R, seed=32)
+    ref, (lam, k, fit, hist, exact, Hg) = _solve_both(nn, dims, R, 3, x, H0, split=1)
+    assert k == 3
+    assert np.max(np.abs(np.array(hist) - np.array(ref["fits"]))) <= FIT_TOL
+    for n in range(len(dims)):
+        assert rel_fro(Hg[n], ref["H"][n]) <= 1e-4, n
+    assert rel_fro(lam, ref["lam"]) <= 1e-4
