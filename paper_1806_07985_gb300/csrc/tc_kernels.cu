@@ -65,7 +65,13 @@ constexpr long long kWaitCycles = 4000000000LL;
 
 constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;  // B builder row offsets
 // barriers: raw full/empty/converted per A stage, B full/empty, acc full/empty x2, drain
-constexpr int kSA = 4;     // A stages in tensor memory (split-BF16x3), 64 columns each
+// A stages in tensor memory (split-BF16x3), 64 columns each: at most kSA, and
+// no more than fit beside the two accumulators (4 Rp columns) in the 512
+// columns.  Their full barriers are the conv_full slots, initialised for every
+// A stage even where there are fewer TMA stages.  (Six stages, which fit for
+// R <= 32, measured slower on the 512^3 root -> left contraction.)
+constexpr int kSA = 4;
+static_assert(kSA <= kMaxSF, "A stages use conv_full barrier slots");
 constexpr int kNumBars = 3 * kMaxSF + 2 * kSB + 4 + kSA + 1;
 constexpr int kMiscBytes = kNumBars * 8 + 256;
 constexpr int kSmemMax = 232448;  // 227 KB per CTA on sm_103a
@@ -414,7 +420,8 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   const uint32_t acc_cols = 2u * Rp;  // per accumulator buffer
   const uint32_t a_col0 = 2u * acc_cols;  // A stages (split-BF16x3) after the accumulators
   uint32_t tmem_cols = 32;
-  while (tmem_cols < a_col0 + (a_tmem ? 64u * kSA : 0u)) tmem_cols <<= 1;
+  const int nsa = min(kSA, (int)(512u - a_col0) / 64);  // A stages (a_tmem)
+  while (tmem_cols < a_col0 + (a_tmem ? 64u * nsa : 0u)) tmem_cols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kSF; ++i) {
@@ -423,7 +430,9 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       mbar_init(raw_empty(i), a_tmem ? kConvThreads / 32 : 1);
       mbar_init(conv_full(i), kConvThreads / 32);
     }
-    for (int i = 0; i < kSA; ++i) mbar_init(a_empty(i), 1);
+    // a_tmem: conv_full(i) marks A stage i written (i < nsa), which may exceed kSF
+    for (int i = kSF; i < nsa; ++i) mbar_init(conv_full(i), kConvThreads / 32);
+    for (int i = 0; i < nsa; ++i) mbar_init(a_empty(i), 1);
     for (int i = 0; i < kSB; ++i) {
       mbar_init(b_full(i), (p.b_resident && i == 0) ? 2 * kSB : 2);
       mbar_init(b_empty(i), 1);
@@ -535,7 +544,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
           }
           mma_commit(a_empty(sa));
           if (!p.b_resident) mma_commit(b_empty(sb));
-          if (++sa == kSA) { sa = 0; pha ^= 1u; }
+          if (++sa == nsa) { sa = 0; pha ^= 1u; }
           if (++sb == kSB) { sb = 0; phb ^= 1u; }
         }
         for (int s = 0; s < w.nk && !a_tmem; ++s) {
@@ -902,7 +911,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(conv_full(sa));
-        if (++sa == kSA) { sa = 0; pha ^= 1u; }
+        if (++sa == nsa) { sa = 0; pha ^= 1u; }
       }
       for (int s = 0; s < w.nk && !p.direct && !a_tmem; ++s) {
         const bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err);
