@@ -299,8 +299,9 @@ def run_ours(args):
               "dtype": PRECISION_DTYPE[prec_name], "data": "synthetic",
               "config": {"workload": "nncp_hals_512x512x512_R32_dimtree_split1",
                          "dims": list(DIMS), "rank": RANK, "precision": prec_name,
-                         "step": "one outer BCD iteration (2 root partial MTTKRPs, 2 multi-TTVs, "
-                                 "3 HALS updates, fit)",
+                         "step": "one outer BCD iteration (2 root partial MTTKRPs, the mode-2 "
+                                 "leaf multi-TTV fused into the second where the tensor-core "
+                                 "path allows, the mode-3 multi-TTV, 3 HALS updates, fit)",
                          "bytes_per_step": bytes_step,
                          "l2": "inputs larger than L2 (512 MiB tensor), no flush",
                          "parallelism": f"replicas x{world}"},
