@@ -174,11 +174,20 @@ nncp_status nncp_tensor_to_bf16(const float* X_dev, uint16_t* Xb_dev, int64_t n,
  * NNCP_BF16_STORED) and H_1 given matching zero rows: a HALS row update with
  * m = 0 and w = 0 yields 0, so those rows stay zero, add nothing to the Grams,
  * lambda or the fit, and the iteration is that of the unpadded problem up to
- * rounding (Sec. II-B update rule).  Only the first I_1 rows are returned. */
+ * rounding (Sec. II-B update rule).  Only the first I_1 rows are returned.
+ * The call keeps one plan per process -- the context, its captured graphs and
+ * the device buffers of the last (stored shape, R, precision, root_split,
+ * device) -- and reuses it when the next call matches, so repeated solves of
+ * one shape allocate nothing and capture nothing; a call made while another
+ * thread holds the plan runs without it.  The plan's device memory stays
+ * allocated until nncp_solve_host_release or process exit. */
 nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_host,
                             float* const* H_host, nncp_precision precision, int root_split,
                             int max_iters, double tol, double* lambda_out, int* iters_out,
                             double* fit_out);
+
+/* Frees the plan nncp_solve_host keeps (a no-op if there is none). */
+void nncp_solve_host_release(void);
 
 /* ---- Batched solver: many independent problems of one order N ----------
  * `count` tensors, tensor t with mode lengths dims[t*N .. t*N+N-1] (each in

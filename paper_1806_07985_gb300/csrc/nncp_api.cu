@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -771,7 +772,7 @@ nncp_status nncp_tensor_to_bf16(const float* X_dev, uint16_t* Xb_dev, int64_t n,
   return NNCP_OK;
 }
 
-nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_host,
+static nncp_status solve_host_uncached(int N, const int64_t* dims, int R, const float* X_host,
                             float* const* H_host, nncp_precision precision, int root_split,
                             int max_iters, double tol, double* lambda_out, int* iters_out,
                             double* fit_out) {
@@ -852,6 +853,136 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
   cleanup();
   return NNCP_OK;
 #undef CKH
+}
+
+namespace {
+// The plan nncp_solve_host keeps between calls: the context of the last shape
+// solved (with its captured graphs) and its device buffers.  A call with the
+// same stored shape, rank, precision and split on the same device reuses them:
+// no allocation, no graph capture -- the graphs stay valid because the
+// buffers do not move.  Held on the heap and never destroyed at exit (the
+// driver reclaims it); nncp_solve_host_release frees it earlier.
+struct HostPlan {
+  std::mutex mu;
+  int device = -1, N = 0, R = 0, precision = -1, split = -1;
+  int64_t dims[nncp::kMaxModes] = {};
+  nncp_ctx* c = nullptr;
+  void* dX = nullptr;
+  void* dXb = nullptr;
+  float* dH[nncp::kMaxModes] = {};
+  void* dws = nullptr;
+  bool matches(int dev, int n, const int64_t* d, int r, int prec, int sp) const {
+    if (!c || dev != device || n != N || r != R || prec != precision || sp != split) return false;
+    for (int k = 0; k < n; ++k)
+      if (d[k] != dims[k]) return false;
+    return true;
+  }
+  void release() {
+    if (c && c->work) cudaStreamSynchronize(c->work);
+    cudaFree(dX);
+    cudaFree(dXb);
+    for (int k = 0; k < nncp::kMaxModes; ++k) cudaFree(dH[k]);
+    cudaFree(dws);
+    nncp_destroy(c);
+    c = nullptr;
+    dX = dXb = dws = nullptr;
+    for (int k = 0; k < nncp::kMaxModes; ++k) dH[k] = nullptr;
+    device = -1;
+  }
+};
+HostPlan* g_host_plan = new HostPlan;
+}  // namespace
+
+nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_host,
+                            float* const* H_host, nncp_precision precision, int root_split,
+                            int max_iters, double tol, double* lambda_out, int* iters_out,
+                            double* fit_out) {
+  if (!X_host || !H_host) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null host buffer");
+  if (N < 2 || N > kMaxModes || !dims) return fail(nullptr, NNCP_ERR_INVALID_ARG, "N=%d not in [2,8]", N);
+  for (int n = 0; n < N; ++n)
+    if (dims[n] < 1 || !H_host[n]) return fail(nullptr, NNCP_ERR_INVALID_ARG, "invalid mode %d", n + 1);
+  if (R < 1) return fail(nullptr, NNCP_ERR_INVALID_ARG, "R=%d", R);
+  std::unique_lock<std::mutex> lk(g_host_plan->mu, std::try_to_lock);
+  if (!lk.owns_lock())  // another thread holds the plan: solve without it
+    return solve_host_uncached(N, dims, R, X_host, H_host, precision, root_split, max_iters, tol,
+                               lambda_out, iters_out, fit_out);
+  HostPlan& P = *g_host_plan;
+  int64_t pd[kMaxModes];
+  for (int n = 0; n < N; ++n) pd[n] = dims[n];
+  pd[0] = tc_padded_mode1(precision, N, dims, R, root_split);
+  const bool padded = pd[0] != dims[0];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, NNCP_ERR_CUDA, "cudaGetDevice");
+  nncp_status s = NNCP_OK;
+#define CKP(call)                                        \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) {                             \
+      s = cuda_fail(nullptr, e_, #call);                 \
+      P.release();                                       \
+      return s;                                          \
+    }                                                    \
+  } while (0)
+  if (!P.matches(dev, N, pd, R, precision, root_split)) {
+    P.release();
+    if ((s = nncp_create(N, pd, R, &P.c)) != NNCP_OK) return s;
+    if ((s = nncp_set_options(P.c, precision, root_split, P.c->work)) != NNCP_OK) {
+      g_error = P.c->err;
+      P.release();
+      return s;
+    }
+    const size_t I = (size_t)P.c->I;
+    CKP(cudaMalloc(&P.dX, I * sizeof(float)));
+    if (padded) CKP(cudaMemsetAsync(P.dX, 0, I * sizeof(float), P.c->work));  // zero slices stay zero
+    if (precision == NNCP_BF16_STORED) CKP(cudaMalloc(&P.dXb, I * 2));
+    for (int n = 0; n < N; ++n) CKP(cudaMalloc(&P.dH[n], (size_t)pd[n] * R * sizeof(float)));
+    size_t wsb = 0;
+    nncp_workspace_size(P.c, &wsb);
+    CKP(cudaMalloc(&P.dws, wsb));
+    if ((s = nncp_set_workspace(P.c, P.dws, wsb)) != NNCP_OK ||
+        (s = nncp_set_tensor(P.c, P.dXb ? P.dXb : P.dX)) != NNCP_OK ||
+        (s = nncp_set_factors(P.c, P.dH)) != NNCP_OK) {
+      g_error = P.c->err;
+      P.release();
+      return s;
+    }
+    P.device = dev;
+    P.N = N;
+    P.R = R;
+    P.precision = precision;
+    P.split = root_split;
+    for (int n = 0; n < N; ++n) P.dims[n] = pd[n];
+  }
+  cudaStream_t st = P.c->work;
+  const size_t rows = (size_t)(P.c->I / pd[0]);
+  if (padded)
+    CKP(cudaMemcpy2DAsync(P.dX, (size_t)pd[0] * sizeof(float), X_host, (size_t)dims[0] * sizeof(float),
+                          (size_t)dims[0] * sizeof(float), rows, cudaMemcpyHostToDevice, st));
+  else
+    CKP(cudaMemcpyAsync(P.dX, X_host, (size_t)P.c->I * sizeof(float), cudaMemcpyHostToDevice, st));
+  if (P.dXb)
+    CKP(launch_to_bf16(static_cast<float*>(P.dX), static_cast<uint16_t*>(P.dXb), P.c->I, st));
+  for (int n = 0; n < N; ++n) {
+    if (pd[n] != dims[n]) CKP(cudaMemsetAsync(P.dH[n], 0, (size_t)pd[n] * R * sizeof(float), st));
+    CKP(cudaMemcpyAsync(P.dH[n], H_host[n], (size_t)dims[n] * R * sizeof(float),
+                        cudaMemcpyHostToDevice, st));
+  }
+  if ((s = nncp_solve(P.c, max_iters, tol, lambda_out, iters_out, fit_out)) != NNCP_OK) {
+    g_error = P.c->err;
+    P.release();
+    return s;
+  }
+  for (int n = 0; n < N; ++n)
+    CKP(cudaMemcpyAsync(H_host[n], P.dH[n], (size_t)dims[n] * R * sizeof(float),
+                        cudaMemcpyDeviceToHost, st));
+  CKP(cudaStreamSynchronize(st));
+  return NNCP_OK;
+#undef CKP
+}
+
+void nncp_solve_host_release(void) {
+  std::lock_guard<std::mutex> lk(g_host_plan->mu);
+  g_host_plan->release();
 }
 
 const char* nncp_last_error(const nncp_ctx* c) { return c ? c->err.c_str() : g_error.c_str(); }

@@ -46,6 +46,7 @@ _SIGNATURES = [
     ("nncp_set_options", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("nncp_set_dimtree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_set_leaf_fusion", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("nncp_solve_host_release", None, []),
     ("nncp_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("nncp_set_tensor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -236,6 +237,11 @@ def nncp_iterate(ctx, iters):
 
 def nncp_tensor_to_bf16(X, Xb, stream=None):
     _check(load().nncp_tensor_to_bf16(_ptr(X), _ptr(Xb), X.numel(), _stream(stream)))
+
+
+def nncp_solve_host_release():
+    """Frees the plan (context, graphs, device buffers) nncp_solve_host keeps."""
+    load().nncp_solve_host_release()
 
 
 def nncp_solve_host(dims, R, X_host, H_host, precision=NNCP_FP32_SIMT, root_split=0,

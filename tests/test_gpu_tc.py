@@ -238,3 +238,33 @@ def test_fused_leaf_matches_unfused_and_oracle(nn, prec, dims, R, split):
         assert abs(ff - ref["fits"][-1]) <= 1e-4, (ff, ref["fits"][-1])
         for n in range(len(dims)):
             assert rel_fro(Hf[n], ref["H"][n]) <= 1e-3, n
+
+
+@pytest.mark.parametrize("prec,dims", [("fp32_simt", (48, 40, 36)), ("split_bf16x3", (48, 40, 36)),
+                                       ("split_bf16x3", (41, 23, 29))])
+def test_solve_host_plan_reuse_gives_the_same_bits(nn, prec, dims):
+    # nncp_solve_host keeps its plan (context, graphs, device buffers) for the
+    # next call of the same shape: built, reused, and rebuilt after another
+    # shape replaced it, the results are the same bits ((41, 23, 29) stores
+    # mode 1 padded for the tensor cores)
+    R = 6
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=41, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=42)
+
+    def run():
+        Hh = [h.copy() for h in H0]
+        lam, k, fit = nn.nncp_solve_host(dims, R, x, Hh, prec, 0, 7, 0.0)
+        return np.array(lam), k, fit, Hh
+
+    nn.nncp_solve_host_release()
+    built = run()
+    reused = run()
+    xo, _ = synth.lowrank_plus_noise((20, 30, 12), 4, seed=43, noise=0.01)
+    nn.nncp_solve_host((20, 30, 12), 4, xo, synth.init_factors((20, 30, 12), 4, seed=44), prec, 0, 3, 0.0)
+    rebuilt = run()
+    nn.nncp_solve_host_release()
+    for other in (reused, rebuilt):
+        assert other[1] == built[1] and other[2] == built[2]
+        assert np.array_equal(other[0], built[0])
+        for a, b in zip(other[3], built[3]):
+            assert np.array_equal(a, b)
