@@ -154,7 +154,8 @@ nncp_status nncp_fit(nncp_ctx* ctx, int exact, double* fit_out);
 
 /* Run exactly `iters` outer iterations on the device state left by a previous
  * nncp_solve (or nncp_solve_begin), without host synchronisation: the unit
- * that the benchmark times.  Uses a captured CUDA graph per iteration. */
+ * that the benchmark times.  Launches captured CUDA graphs of four iterations
+ * (whole batches of four) and of one (the rest). */
 nncp_status nncp_solve_begin(nncp_ctx* ctx);
 nncp_status nncp_iterate(nncp_ctx* ctx, int iters);
 

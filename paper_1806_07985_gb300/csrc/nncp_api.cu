@@ -6,8 +6,11 @@
 // {a..b} yields the leaf M(a) by a multi-TTV over modes a+1..b and its child
 // {a+1..b} by a multi-TTV over mode a with the freshly updated H(a).  Each
 // leaf is followed by the factor update of Alg. 1/Alg. 3 (HALS sweep,
-// normalisation, Gram), and the fit of Sec. IV-B closes the iteration.  One
-// outer iteration is captured once as a CUDA graph and relaunched.
+// normalisation, Gram), and the fit of Sec. IV-B closes the iteration.  The
+// right node's first leaf comes out of its partial MTTKRP's epilogue where the
+// tensor-core kernel can fuse it.  The outer iteration is captured into CUDA
+// graphs of one and of four iterations (programmatic dependent launches inside)
+// and relaunched.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>

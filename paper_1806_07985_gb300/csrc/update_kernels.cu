@@ -1,9 +1,13 @@
-// Factor-update kernels of one BCD inner iteration (Alg. 1 / Alg. 3):
-//   HALS sweep (Sec. II-B) on W = H_n diag(lambda), row-parallel;
-//   per-block partials of W^T W and <M, W>;
-//   a single-CTA finalise: lambda = column norms, G_n = H_n^T H_n,
-//   H_n = W diag(lambda)^-1, the fit from the Sec. IV-B identity at n = N,
-//   and S = Hadamard of the other Grams for the next mode.
+// Factor-update kernels of one BCD inner iteration (Alg. 1 / Alg. 3): the
+// HALS sweep (Sec. II-B) on W = H_n diag(lambda), row-parallel; W^T W and
+// <M, W>; lambda = column norms, G_n = H_n^T H_n, H_n = W diag(lambda)^-1,
+// the fit from the Sec. IV-B identity at n = N, and S = Hadamard of the other
+// Grams for the next mode.  Three forms by mode length:
+//   k_update_cluster  I_n <= 1024: one launch on a thread-block cluster that
+//                     exchanges its partials through distributed shared memory;
+//   k_update_multi    I_n <= 16384: CTAs of 128 rows, the last CTA (atomic
+//                     ticket) finishes;
+//   k_hals_gram + k_finalize  otherwise (and for the solve's initialisation).
 // The factors, the HALS arithmetic, the Grams and S are float32.  The sums the
 // fit needs to more than float32 precision (<M, W> and lambda^T (S * G) lambda)
 // are float-float (unevaluated hi + lo pairs added with the error-free TwoSum),
