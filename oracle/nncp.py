@@ -33,6 +33,8 @@ __all__ = [
     "gram",
     "hadamard_of_grams",
     "hals_sweep",
+    "nnls_bpp",
+    "bpp_update",
     "normalize_columns",
     "fit_identity",
     "reconstruct",
@@ -279,6 +281,61 @@ def hals_sweep(W, M, S):
     return W
 
 
+def nnls_bpp(S, m, max_steps=None):
+    """min_{x >= 0} x^T S x / 2 - m^T x for symmetric positive (semi)definite S,
+    by block principal pivoting (the NLS solver the paper names, Sec. II-B).
+
+    The solution is the x with x >= 0, y = S x - m >= 0 and x_i y_i = 0 (the
+    KKT conditions; unique when S is positive definite).  Block principal
+    pivoting keeps a passive set F (x_F free, x elsewhere 0), solves
+    S_FF x_F = m_F, and moves every infeasible index (x_i < 0 in F, or
+    y_i < 0 outside it) to the other set at once.  While the number of
+    infeasible indices does not fall below its best value, at most three
+    more full exchanges are tried, after which only the infeasible index of
+    largest position moves (the backup rule that guarantees termination).
+    Columns with S_rr = 0 stay at x_r = 0 (their step is undefined, as in the
+    HALS sweep).
+    """
+    S = np.asarray(S, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    R = m.shape[0]
+    usable = np.diag(S) > 0.0
+    F = np.zeros(R, dtype=bool)
+    x = np.zeros(R)
+    y = -m.copy()
+    y[~usable] = 0.0
+    best, backups = R + 1, 3
+    for _ in range(max_steps or 50 * R + 50):
+        infeasible = ((F & (x < 0.0)) | (~F & (y < 0.0))) & usable
+        count = int(np.count_nonzero(infeasible))
+        if count == 0:
+            return x
+        if count < best:
+            best, backups = count, 3
+            flip = infeasible
+        elif backups > 0:
+            backups -= 1
+            flip = infeasible
+        else:
+            flip = np.zeros(R, dtype=bool)
+            flip[np.flatnonzero(infeasible)[-1]] = True
+        F = F ^ flip
+        x = np.zeros(R)
+        if F.any():
+            x[F] = np.linalg.solve(S[np.ix_(F, F)], m[F])
+        y = S @ x - m
+        y[F] = 0.0
+        y[~usable] = 0.0
+    raise RuntimeError("block principal pivoting did not terminate")
+
+
+def bpp_update(M, S):
+    """W = argmin_{W >= 0} ||M - W S||-style NLS of every row: row i of W is
+    nnls_bpp(S, M(i, :)) (the exact block solve of Alg. 1's NLS-Update)."""
+    M = np.asarray(M, dtype=np.float64)
+    return np.stack([nnls_bpp(S, M[i]) for i in range(M.shape[0])]) if M.shape[0] else M.copy()
+
+
 def normalize_columns(W):
     """lambda_r = ||W(:, r)||_2 and H = W diag(lambda)^-1 (Alg. 3, column norms).
 
@@ -332,8 +389,13 @@ def hals_objective(W, M, S):
 
 
 def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
-              callback=None):
+              callback=None, nls="hals"):
     """NNCP by block coordinate descent with one HALS sweep per block (Alg. 1, Alg. 3).
+
+    nls selects Alg. 1's NLS-Update: "hals" (one HALS sweep from W = H_n
+    diag(lam), the default) or "bpp" (the exact nonnegative least-squares
+    solve of every row by block principal pivoting, ``bpp_update``; its
+    result does not depend on the starting W).
 
     Steps, in the paper's order:
       init   : normalise every initial factor, fold the norms into lam,
@@ -369,8 +431,11 @@ def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
 
     def update(n, M):
         S = hadamard_of_grams(G, n)
-        W = H[n] * state["lam"]
-        hals_sweep(W, M, S)
+        if nls == "bpp":
+            W = bpp_update(M, S)
+        else:
+            W = H[n] * state["lam"]
+            hals_sweep(W, M, S)
         H[n], state["lam"] = normalize_columns(W)
         G[n] = gram(H[n])
         if n == N - 1:

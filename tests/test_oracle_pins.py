@@ -324,3 +324,87 @@ def test_planted_fit_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(oracle.nncp, "fit_identity", wrong_fit)
     with pytest.raises(AssertionError):
         test_fit_identity_matches_explicit_residual()
+
+
+# ---- block principal pivoting (Alg. 1's NLS-Update solved exactly) --------
+
+@pytest.mark.parametrize("R", [1, 2, 3, 5, 8, 16, 32])
+def test_bpp_satisfies_kkt_and_matches_library_nnls(R):
+    # the NNLS solution is unique for positive definite S: KKT conditions,
+    # scipy's Lawson-Hanson NNLS on the equivalent least squares, and (small
+    # R) the brute-force enumeration of active sets must all agree
+    scipy_optimize = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(70 + R)
+    for _ in range(20):
+        A = rng.standard_normal((2 * R + 3, R))
+        b = rng.standard_normal(2 * R + 3)
+        S, m = A.T @ A, A.T @ b
+        x = oracle.nnls_bpp(S, m)
+        y = S @ x - m
+        scale = max(1.0, float(np.abs(m).max()))
+        assert x.min() >= 0.0
+        assert y.min() >= -1e-9 * scale
+        assert np.abs(x * y).max() <= 1e-9 * scale * scale
+        x_ref, _ = scipy_optimize.nnls(A, b)
+        assert np.allclose(x, x_ref, atol=1e-8)
+        if R <= 5:
+            assert np.allclose(x, _nnls_by_active_sets(S, m), atol=1e-8)
+
+
+def test_bpp_special_cases():
+    rng = np.random.default_rng(81)
+    A = rng.random((12, 6)) + np.eye(12, 6)
+    S = A.T @ A
+    # m <= 0: x = 0 satisfies KKT (y = -m >= 0)
+    assert np.array_equal(oracle.nnls_bpp(S, -rng.random(6)), np.zeros(6))
+    # an interior unconstrained minimiser is the solution
+    x_int = rng.random(6) + 0.5
+    assert np.allclose(oracle.nnls_bpp(S, S @ x_int), x_int, atol=1e-10)
+    # a zero-curvature column (S_rr = 0) stays at zero, the rest is solved
+    S0 = S.copy()
+    S0[2, :] = 0.0
+    S0[:, 2] = 0.0
+    m = S @ x_int
+    x = oracle.nnls_bpp(S0, m)
+    assert x[2] == 0.0
+    keep = [0, 1, 3, 4, 5]
+    assert np.allclose(x[keep], oracle.nnls_bpp(S0[np.ix_(keep, keep)], m[keep]), atol=1e-12)
+
+
+def test_bpp_is_the_fixed_point_of_hals_sweeps():
+    # repeated HALS sweeps (each a descent step on the same objective)
+    # converge to the exact row-wise NNLS solution that BPP computes directly
+    rng = np.random.default_rng(83)
+    R = 5
+    A0 = rng.random((3 * R, R)) + 0.3 * np.eye(3 * R, R)
+    S = A0.T @ A0
+    M = rng.standard_normal((7, R)) * 2
+    W = rng.random((7, R))
+    for _ in range(4000):
+        oracle.hals_sweep(W, M, S)
+    assert np.allclose(oracle.bpp_update(M, S), W, atol=1e-8)
+
+
+def test_bpp_solve_fit_never_decreases():
+    # BCD with exact block minimisation: the objective never increases, so
+    # the fit never decreases (up to rounding), unlike a single HALS sweep
+    # which is only a descent step
+    dims, R = (12, 10, 9), 4
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=85, noise=0.05)
+    H0 = synth.init_factors(dims, R, seed=86)
+    ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                           max_iters=15, nls="bpp")
+    fits = np.array(ref["fits"])
+    assert np.all(np.diff(fits) >= -1e-10)
+    exact = 1.0 - oracle.explicit_residual(x.astype(np.float64), dims, ref["lam"], ref["H"])
+    assert abs(exact - fits[-1]) <= 1e-10
+
+
+def test_planted_bpp_mistake_is_caught(monkeypatch):
+    # clipping the unconstrained minimiser is a plausible wrong NNLS
+    def wrong(S, m, max_steps=None):
+        return np.maximum(0.0, np.linalg.solve(S, m))
+
+    monkeypatch.setattr(oracle, "nnls_bpp", wrong)
+    with pytest.raises(AssertionError):
+        test_bpp_satisfies_kkt_and_matches_library_nnls(8)
