@@ -96,6 +96,16 @@ nncp_status nncp_set_dimtree(nncp_ctx* ctx, int enabled);
  * a separate multi-TTV.  Results agree to rounding (a different summation
  * order).  Takes effect at the next solve or iteration. */
 nncp_status nncp_set_leaf_fusion(nncp_ctx* ctx, int enabled);
+
+/* NLS-Update of Alg. 1 (Sec. II-B): NNCP_NLS_HALS (the default) makes one
+ * HALS sweep from W = H_n diag(lambda); NNCP_NLS_BPP solves each row's
+ * nonnegative least squares exactly by block principal pivoting (the solver
+ * the paper benchmarks), whatever the starting W, then normalises as HALS
+ * does.  BPP supports R <= 32 (NNCP_ERR_UNSUPPORTED above) and any precision
+ * of the MTTKRPs.  Takes effect at the next solve or iteration. */
+#define NNCP_NLS_HALS 0
+#define NNCP_NLS_BPP  1
+nncp_status nncp_set_nls(nncp_ctx* ctx, int nls);
 /* Bytes of device scratch the context needs for its current options
  * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
 nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);

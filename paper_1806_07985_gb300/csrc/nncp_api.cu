@@ -65,6 +65,7 @@ struct nncp_ctx {
   TcScratch tc = {};
 
   bool fuse_leaf = true;              // fuse first leaf multi-TTVs into partial MTTKRPs
+  int nls = NNCP_NLS_HALS;            // NLS-Update: HALS sweep or block principal pivoting
   cudaGraphExec_t graph = nullptr;   // one outer iteration
   cudaGraphExec_t graph4 = nullptr;  // kGraphIters outer iterations, back to back
   int graph_kernels = 0;
@@ -251,6 +252,12 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st, const TcLeaf* leaf
 }
 
 cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
+  if (c->nls == NNCP_NLS_BPP) {
+    cudaError_t e = launch_bpp_update(c->H[n], c->Mbuf, c->dims[n], c->R, c->st, c->num_sms, st);
+    if (e != cudaSuccess) return e;
+    return launch_finalize(c->H[n], c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                           hals_gram_blocks(c->dims[n]), n == c->N - 1, 0, 0.0, c->st, st);
+  }
   if (cluster_update_ok(c->dims[n], c->R))
     return launch_update_cluster(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
                                  n == c->N - 1, c->st, st);
@@ -522,6 +529,17 @@ nncp_status nncp_set_dimtree(nncp_ctx* c, int enabled) {
   if (!enabled && c->precision != NNCP_FP32_SIMT)
     return fail(c, NNCP_ERR_UNSUPPORTED, "the solve without the dimension tree is FP32 SIMT only");
   c->dimtree = enabled ? 1 : 0;
+  drop_graph(c);
+  return NNCP_OK;
+}
+
+nncp_status nncp_set_nls(nncp_ctx* c, int nls) {
+  if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
+  if (nls != NNCP_NLS_HALS && nls != NNCP_NLS_BPP)
+    return fail(c, NNCP_ERR_INVALID_ARG, "unknown NLS update %d", nls);
+  if (nls == NNCP_NLS_BPP && c->R > 32)
+    return fail(c, NNCP_ERR_UNSUPPORTED, "block principal pivoting supports R <= 32");
+  c->nls = nls;
   drop_graph(c);
   return NNCP_OK;
 }

@@ -180,6 +180,13 @@ cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int
                                 int next_mode, int is_last, SolveState st, float* part,
                                 cudaStream_t stream);
 
+// Block principal pivoting NLS update (R <= 32): W = argmin_{W >= 0} of the
+// row-wise least squares with S = st.S and M, written to H unnormalised,
+// followed by the Gram partials and <M, W> into st.gram_part (then
+// launch_finalize, as after launch_hals_gram).
+cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, SolveState st,
+                              int num_sms, cudaStream_t stream);
+
 // Gram partials of H as given (initialisation: W = H).
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream);

@@ -39,6 +39,9 @@ __global__ void __launch_bounds__(kHalsThreads)
 k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, int R,
             const float* __restrict__ S, const double* __restrict__ lam,
             double* __restrict__ gram_part, const int* __restrict__ flags, int do_hals) {
+  // do_hals: 1 = HALS sweep on W = H diag(lam), then the partials; 0 = the
+  // partials of W = H alone (no <M, W>); 2 = W given in H (the block
+  // principal pivoting update): the partials and <M, W>, no sweep
   pdl_wait();
   pdl_trigger();
   if (flags && flags[0]) return;
@@ -67,12 +70,12 @@ k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, in
       if (c < R) {
         w[j] = H[i * R + c];
         if (do_hals) {
-          w[j] = w[j] * (float)lam[c];
+          if (do_hals == 1) w[j] = w[j] * (float)lam[c];
           m[j] = M[i * R + c];
         }
       }
     }
-    if (do_hals) {
+    if (do_hals == 1) {
       for (int r = 0; r < R; ++r) {
         const float srr = Ss[r * R + r];
         if (srr == 0.0f) continue;  // warp-uniform
@@ -87,6 +90,8 @@ k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, in
         for (int j = 0; j < 4; ++j)
           if (lane + 32 * j == r) w[j] = fmaxf(0.0f, w[j] + (m[j] - dot) / srr);
       }
+    }
+    if (do_hals) {
       float bp = 0.0f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) bp = fmaf(m[j], w[j], bp);
@@ -96,7 +101,7 @@ k_hals_gram(float* __restrict__ H, const float* __restrict__ M, long long In, in
     for (int j = 0; j < 4; ++j) {
       int c = lane + 32 * j;
       if (c < R) {
-        if (do_hals) H[i * R + c] = w[j];
+        if (do_hals == 1) H[i * R + c] = w[j];
         Ws[rr * RP + c] = w[j];
       }
     }
@@ -1076,6 +1081,104 @@ size_t cluster_smem() {
          sizeof(float);
 }
 
+// ---- block principal pivoting NLS update -----------------------------------
+// Alg. 1's NLS-Update solved exactly, one warp per row of W (R <= 32): lane j
+// owns variable j.  For the row's m (its row of M) it finds x >= 0 with
+// y = S x - m >= 0 and x_j y_j = 0 by block principal pivoting: the passive
+// set F is a lane bit; S_FF x_F = m_F is solved by a Cholesky factorisation of
+// S with the rows and columns outside F replaced by the identity (the system
+// keeps its R x R shape and x stays 0 outside F), in the warp's own tile of
+// shared memory, lanes parallel over rows; every infeasible index (x_j < 0 in
+// F, y_j < 0 outside it: a warp ballot) changes sides at once while their
+// count falls, up to three more times otherwise, then only the last one (the
+// backup rule).  Columns with S_jj = 0 stay at 0.  The step count is bounded
+// as in the FP64 oracle (50 R + 50).  W is written to H, unnormalised.
+constexpr int kBppWarps = 8;
+
+__global__ void __launch_bounds__(kBppWarps * 32)
+k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
+           const float* __restrict__ S, const int* __restrict__ flags) {
+  pdl_wait();
+  pdl_trigger();
+  if (flags[0]) return;
+  __shared__ float Ss[32][33];
+  __shared__ float Ls[kBppWarps][32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int a = e >> 5, b = e & 31;
+    Ss[a][b] = (a < R && b < R) ? S[a * R + b] : 0.0f;
+  }
+  __syncthreads();
+  float(*A)[33] = Ls[warp];
+  const bool usable = lane < R && Ss[lane][lane] > 0.0f;
+  for (int row = blockIdx.x * kBppWarps + warp; row < In; row += gridDim.x * kBppWarps) {
+    const float m = lane < R ? M[(long long)row * R + lane] : 0.0f;
+    bool inF = false;
+    float x = 0.0f, y = usable ? -m : 0.0f;
+    int best = R + 1, backups = 3;
+#pragma unroll 1
+    for (int step = 0; step < 50 * R + 50; ++step) {
+      const unsigned V = __ballot_sync(0xffffffffu, usable && (inF ? x < 0.0f : y < 0.0f));
+      if (V == 0u) break;
+      const int count = __popc(V);
+      unsigned flip;
+      if (count < best) {
+        best = count;
+        backups = 3;
+        flip = V;
+      } else if (backups > 0) {
+        --backups;
+        flip = V;
+      } else {
+        flip = 1u << (31 - __clz(V));
+      }
+      if ((flip >> lane) & 1u) inF = !inF;
+      const unsigned Fm = __ballot_sync(0xffffffffu, inF);
+      // A = S_FF, identity outside F (lane = row)
+      for (int j = 0; j < R; ++j)
+        A[lane][j] = (inF && ((Fm >> j) & 1u)) ? Ss[lane][j] : (lane == j ? 1.0f : 0.0f);
+      __syncwarp();
+      // Cholesky A = L L^T, lower triangle in place, one column at a time
+#pragma unroll 1
+      for (int k = 0; k < R; ++k) {
+        const float d = sqrtf(A[k][k]);
+        float lik = 0.0f;
+        if (lane > k && lane < R) {
+          lik = A[lane][k] / d;
+          A[lane][k] = lik;
+        }
+        __syncwarp();
+        if (lane > k && lane < R)
+          for (int j = k + 1; j <= lane; ++j) A[lane][j] = fmaf(-lik, A[j][k], A[lane][j]);
+        if (lane == k) A[k][k] = d;
+        __syncwarp();
+      }
+      // L z = b (b = m on F, 0 elsewhere), then L^T x = z
+      float z = (inF && lane < R) ? m : 0.0f;
+#pragma unroll 1
+      for (int k = 0; k < R; ++k) {
+        const float zk = __shfl_sync(0xffffffffu, z, k) / A[k][k];
+        if (lane == k) z = zk;
+        if (lane > k && lane < R) z = fmaf(-A[lane][k], zk, z);
+      }
+#pragma unroll 1
+      for (int k = R - 1; k >= 0; --k) {
+        const float xk = __shfl_sync(0xffffffffu, z, k) / A[k][k];
+        if (lane == k) z = xk;
+        if (lane < k) z = fmaf(-A[k][lane], xk, z);
+      }
+      __syncwarp();
+      x = (inF && lane < R) ? z : 0.0f;
+      // y = S x - m outside F
+      float yy = -m;
+#pragma unroll 1
+      for (int k = 0; k < R; ++k) yy = fmaf(Ss[lane][k], __shfl_sync(0xffffffffu, x, k), yy);
+      y = (inF || !usable) ? 0.0f : yy;
+    }
+    if (lane < R) W[(long long)row * R + lane] = x;
+  }
+}
+
 __global__ void k_solve_reset(SolveState st, int R, double tol) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) st.lam[r] = 1.0;
   if (threadIdx.x == 0) {
@@ -1210,6 +1313,20 @@ cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveS
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), smem, stream,
                        H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
                        st.gram_part, (const int*)st.flags, 1);
+}
+
+cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, SolveState st,
+                              int num_sms, cudaStream_t stream) {
+  if (R > 32) return cudaErrorInvalidValue;
+  const long long warps = (In + kBppWarps - 1) / kBppWarps;
+  const int grid = (int)std::max(1LL, std::min(warps, (long long)num_sms * 4));
+  cudaError_t e = launch_kernel(k_bpp_rows, dim3(grid), dim3(kBppWarps * 32), 0, stream, H, M,
+                                (int)In, R, (const float*)st.S, (const int*)st.flags);
+  if (e != cudaSuccess) return e;
+  // Gram partials and <M, W> of the new W (no sweep)
+  return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
+                       stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       st.gram_part, (const int*)st.flags, 2);
 }
 
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,

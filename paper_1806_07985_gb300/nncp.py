@@ -46,6 +46,7 @@ _SIGNATURES = [
     ("nncp_set_options", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("nncp_set_dimtree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_set_leaf_fusion", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("nncp_set_nls", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_solve_host_release", None, []),
     ("nncp_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -170,6 +171,16 @@ def nncp_set_dimtree(ctx, enabled):
 
 def nncp_set_leaf_fusion(ctx, enabled):
     _check(load().nncp_set_leaf_fusion(ctx, 1 if enabled else 0), ctx)
+
+
+NNCP_NLS_HALS, NNCP_NLS_BPP = 0, 1
+NLS = {"hals": NNCP_NLS_HALS, "bpp": NNCP_NLS_BPP}
+
+
+def nncp_set_nls(ctx, nls):
+    if isinstance(nls, str):
+        nls = NLS[nls]
+    _check(load().nncp_set_nls(ctx, int(nls)), ctx)
 
 
 def nncp_workspace_size(ctx):
@@ -524,6 +535,9 @@ class Context:
 
     def set_leaf_fusion(self, enabled):
         nncp_set_leaf_fusion(self.ctx, enabled)
+
+    def set_nls(self, nls):
+        nncp_set_nls(self.ctx, nls)
 
     def solve(self, max_iters, tol=0.0):
         return nncp_solve(self.ctx, self.R, max_iters, tol)
