@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-dimtree-compare", action="store_true",
                    help="skip the with / without dimension tree comparison (context line)")
+    p.add_argument("--no-nls-compare", action="store_true",
+                   help="skip the HALS vs block principal pivoting NLS comparison")
     p.add_argument("--no-4way", action="store_true",
                    help="skip the 512x512x32x16 R=24 split-2 step (context line 'hsi_4way')")
     p.add_argument("--no-batched", action="store_true",
@@ -314,6 +316,8 @@ def run_ours(args):
         result["cpu_baseline"] = cpu_baseline(x, H0)
     if rank == 0 and world == 1 and not args.no_dimtree_compare:
         result["dimtree_vs_direct"] = run_dimtree_compare(nncp, torch)
+    if rank == 0 and world == 1 and not args.no_nls_compare:
+        result["nls_hals_vs_bpp"] = run_nls_compare(nncp, torch, Xuse, H0, prec)
     if rank == 0 and world == 1 and not args.no_4way:
         result["hsi_4way"] = run_4way(nncp, torch, prec_name, max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_batched:
@@ -406,6 +410,39 @@ def run_dimtree_compare(nncp, torch, steps=4):
         row["tree_speedup_fp32"] = round(row["direct_fp32_ms"] / row["tree_fp32_ms"], 2)
         out["x".join(str(d) for d in dims) + "_R32"] = row
         del X
+    return out
+
+
+def run_nls_compare(nncp, torch, X, H0, prec, steps=20, max_iters=400, tol=1e-6):
+    """The two NLS updates of Alg. 1 on the step's workload: HALS (one sweep
+    over the columns per mode update) and block principal pivoting (each
+    row's NNLS solved exactly).  Per-iteration time of back-to-back graphs,
+    then one solve each from the same start to the relative fit-change
+    tolerance `tol`: iterations, device time and final fit."""
+    out = {"tol": tol, "max_iters": max_iters}
+    for nls in ("hals", "bpp"):
+        ctx = nncp.Context(DIMS, RANK, precision=prec, root_split=1)
+        ctx.set_nls(nls)
+        ctx.set_tensor(X)
+        ctx.set_factors([torch.from_numpy(h.copy()).cuda() for h in H0])
+        ctx.solve_begin()
+        ctx.iterate(3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.iterate(steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms_iter = a.elapsed_time(b) / steps
+        ctx.set_factors([torch.from_numpy(h.copy()).cuda() for h in H0])
+        torch.cuda.synchronize()
+        a.record()
+        _, k, fit = ctx.solve(max_iters, tol)
+        b.record()
+        torch.cuda.synchronize()
+        out[nls] = {"ms_per_iter": round(ms_iter, 4), "iters": int(k),
+                    "solve_ms": round(a.elapsed_time(b), 3), "fit": round(float(fit), 7)}
+        ctx.close()
     return out
 
 

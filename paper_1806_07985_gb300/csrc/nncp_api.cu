@@ -253,6 +253,12 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st, const TcLeaf* leaf
 
 cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
   if (c->nls == NNCP_NLS_BPP) {
+    if (cluster_update_ok(c->dims[n], c->R)) {
+      cudaError_t e = launch_bpp_rows(c->H[n], c->Mbuf, c->dims[n], c->R, c->st, c->num_sms, st);
+      if (e != cudaSuccess) return e;
+      return launch_update_cluster(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                                   n == c->N - 1, c->st, st, 0);
+    }
     cudaError_t e = launch_bpp_update(c->H[n], c->Mbuf, c->dims[n], c->R, c->st, c->num_sms, st);
     if (e != cudaSuccess) return e;
     return launch_finalize(c->H[n], c->dims[n], c->R, c->N, n, (n + 1) % c->N,

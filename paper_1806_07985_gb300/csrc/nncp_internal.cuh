@@ -173,9 +173,12 @@ bool multi_update_ok(int64_t In, int R);
 size_t multi_update_scratch(int64_t In, int R);
 // The same update on one thread-block cluster (cluster_update_ok(In, R):
 // I_n <= 1024, R <= 64), preferred where it applies; needs no scratch.
+// sweep = 0: H holds W already (written by the kernel just before), no HALS
+// sweep; the rest of the update as above.
 bool cluster_update_ok(int64_t In, int R);
 cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, int N, int n,
-                                  int next_mode, int is_last, SolveState st, cudaStream_t stream);
+                                  int next_mode, int is_last, SolveState st, cudaStream_t stream,
+                                  int sweep = 1);
 cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
                                 int next_mode, int is_last, SolveState st, float* part,
                                 cudaStream_t stream);
@@ -186,6 +189,9 @@ cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int
 // launch_finalize, as after launch_hals_gram).
 cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, SolveState st,
                               int num_sms, cudaStream_t stream);
+// The row solves alone (W into H, unnormalised), for launch_update_cluster(sweep = 0).
+cudaError_t launch_bpp_rows(float* H, const float* M, int64_t In, int R, SolveState st,
+                            int num_sms, cudaStream_t stream);
 
 // Gram partials of H as given (initialisation: W = H).
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,

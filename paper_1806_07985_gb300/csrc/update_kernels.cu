@@ -713,6 +713,8 @@ __device__ __forceinline__ void cluster_wait() {
 // never by the kernel just before an update (a partial MTTKRP, a multi-TTV or a
 // reduction), and every kernel of the iteration lets its successor start only
 // after its own pdl_wait(): those loads are issued before pdl_wait(), M after.
+// With sweep = 0 the kernel just before wrote W into H (an exact NLS solve of
+// the rows), so H is staged after pdl_wait() as well and taken as W as it is.
 constexpr int kClusterThreads = 256;
 constexpr int kClusterMax = 8;      // portable cluster size
 constexpr int kClusterRowsMax = 128;
@@ -736,7 +738,7 @@ int cluster_rows(int64_t In) {
 template <int RMAX>
 __global__ void __launch_bounds__(kClusterThreads, 1)
 k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
-                 int next_mode, int is_last, int rows, SolveState st) {
+                 int next_mode, int is_last, int rows, int sweep, SolveState st) {
   using C = ClusterCfg<RMAX>;
   constexpr int T = C::T, RP = C::RP, GROUPS = C::GROUPS;
   extern __shared__ __align__(16) float csm[];
@@ -776,16 +778,21 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   for (int r = tid; r < R; r += T) cp_async8(lamd + r, st.lam + r);
   const float* Hg = H + (long long)row0 * R;
   const float* Mg = M + (long long)row0 * R;
-  if (vec) {
+  // rows x R from global into a padded tile
+  auto stage_rows = [&](float* dst, const float* src) {
+    if (vec) {
 #pragma unroll 1
-    for (int v = tid; v < nrows * R / 4; v += T) {
-      const int rr = 4 * v / R, c = 4 * v - rr * R;
-      cp_async16(Hs + rr * RP + c, Hg + 4 * v);
+      for (int v = tid; v < nrows * R / 4; v += T) {
+        const int rr = 4 * v / R, c = 4 * v - rr * R;
+        cp_async16(dst + rr * RP + c, src + 4 * v);
+      }
+    } else {
+#pragma unroll 1
+      for (int e = tid; e < nrows * R; e += T) cp_async4(dst + (e / R) * RP + e % R, src + e);
     }
-  } else {
-#pragma unroll 1
-    for (int e = tid; e < nrows * R; e += T) cp_async4(Hs + (e / R) * RP + e % R, Hg + e);
-  }
+  };
+  // without the sweep H holds W, which the predecessor writes
+  if (sweep) stage_rows(Hs, Hg);
   // this CTA's slice [s0, s0 + ssz) of the R x R outputs G_n and the next S
   const int ssz = (R2 + (int)nrank - 1) / (int)nrank;
   const int s0 = min(R2, (int)rank * ssz), s1 = min(R2, s0 + ssz);
@@ -811,16 +818,8 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   // ... then M, which the predecessor writes
   pdl_wait();
   pdl_trigger();
-  if (vec) {
-#pragma unroll 1
-    for (int v = tid; v < nrows * R / 4; v += T) {
-      const int rr = 4 * v / R, c = 4 * v - rr * R;
-      cp_async16(Ms + rr * RP + c, Mg + 4 * v);
-    }
-  } else {
-#pragma unroll 1
-    for (int e = tid; e < nrows * R; e += T) cp_async4(Ms + (e / R) * RP + e % R, Mg + e);
-  }
+  if (!sweep) stage_rows(Hs, Hg);
+  stage_rows(Ms, Mg);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
@@ -841,7 +840,14 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   // enough to stay in the instruction cache.  Columns R .. R rounded up to 4
   // are zero padding (S_rr = 0 leaves them as they are).
   FF bp{0.0f, 0.0f};
-  if (tid < nrows) {
+  if (tid < nrows && !sweep) {
+    // W given (an exact NLS solve wrote it): only <M, W>
+    const float* wrow = Hs + tid * RP;
+    const float* mrow = Ms + tid * RP;
+    float b = 0.0f;
+    for (int c = 0; c < R; ++c) b = fmaf(mrow[c], wrow[c], b);
+    bp.hi = b;
+  } else if (tid < nrows) {
     const float* hrow = Hs + tid * RP;
     const float* mrow = Ms + tid * RP;
     float w[RMAX];
@@ -1084,16 +1090,23 @@ size_t cluster_smem() {
 // ---- block principal pivoting NLS update -----------------------------------
 // Alg. 1's NLS-Update solved exactly, one warp per row of W (R <= 32): lane j
 // owns variable j.  For the row's m (its row of M) it finds x >= 0 with
-// y = S x - m >= 0 and x_j y_j = 0 by block principal pivoting: the passive
-// set F is a lane bit; S_FF x_F = m_F is solved by a Cholesky factorisation of
-// S with the rows and columns outside F replaced by the identity (the system
-// keeps its R x R shape and x stays 0 outside F), in the warp's own tile of
-// shared memory, lanes parallel over rows; every infeasible index (x_j < 0 in
-// F, y_j < 0 outside it: a warp ballot) changes sides at once while their
-// count falls, up to three more times otherwise, then only the last one (the
-// backup rule).  Columns with S_jj = 0 stay at 0.  The step count is bounded
-// as in the FP64 oracle (50 R + 50).  W is written to H, unnormalised.
-constexpr int kBppWarps = 8;
+// y = S x - m >= 0 and x_j y_j = 0 by block principal pivoting.  The passive
+// set F is a lane bit, started from the support of the row's previous value
+// in H (the solution is unique for positive definite S, so the start changes
+// only the number of steps; near convergence the first solve is feasible).
+// Each step solves S_FF x_F = m_F with a Cholesky factor of S whose rows and
+// columns outside F are replaced by the identity (x stays 0 there): lane i
+// holds row i of the factor in registers, columns broadcast by shuffles; the
+// forward substitution runs on the rows, the backward one on L^T read back
+// from a transpose in the warp's tile of shared memory.  Then every
+// infeasible index (x_j < 0 in F, y_j < 0 outside it: a warp ballot) changes
+// sides at once while their count falls, up to three more times otherwise,
+// then only the largest one (the backup rule).  Columns with S_jj = 0 stay at
+// 0.  At most 50 R + 50 solves, as in the FP64 oracle.  W is written to H,
+// unnormalised.  An index that the single-index rule would flip straight back
+// (possible only through rounding, see below) is left as it is, and x is
+// clamped at 0 on exit.
+constexpr int kBppWarps = 4;
 
 __global__ void __launch_bounds__(kBppWarps * 32)
 k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
@@ -1102,23 +1115,78 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
   pdl_trigger();
   if (flags[0]) return;
   __shared__ float Ss[32][33];
-  __shared__ float Ls[kBppWarps][32][33];
+  __shared__ float Lt[kBppWarps][32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned full = 0xffffffffu;
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int a = e >> 5, b = e & 31;
     Ss[a][b] = (a < R && b < R) ? S[a * R + b] : 0.0f;
   }
   __syncthreads();
-  float(*A)[33] = Ls[warp];
+  float(*T)[33] = Lt[warp];
   const bool usable = lane < R && Ss[lane][lane] > 0.0f;
   for (int row = blockIdx.x * kBppWarps + warp; row < In; row += gridDim.x * kBppWarps) {
-    const float m = lane < R ? M[(long long)row * R + lane] : 0.0f;
-    bool inF = false;
-    float x = 0.0f, y = usable ? -m : 0.0f;
-    int best = R + 1, backups = 3;
+    const long long off = (long long)row * R + lane;
+    const float m = lane < R ? M[off] : 0.0f;
+    bool inF = usable && W[off] > 0.0f;
+    float x = 0.0f;
+    int best = R + 1, backups = 3, last = -1;
 #pragma unroll 1
     for (int step = 0; step < 50 * R + 50; ++step) {
-      const unsigned V = __ballot_sync(0xffffffffu, usable && (inF ? x < 0.0f : y < 0.0f));
+      const unsigned Fm = __ballot_sync(full, inF);
+      // a = row `lane` of S_FF, identity outside F
+      float a[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        a[j] = (inF && ((Fm >> j) & 1u)) ? Ss[lane][j] : (lane == j ? 1.0f : 0.0f);
+      // right-looking Cholesky: after column k, a[k] = L(lane, k) for lane >= k
+      float dinv = 1.0f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float dkk = __shfl_sync(full, a[k], k);
+        const float inv = rsqrtf(dkk);
+        const float l = a[k] * inv;
+        if (lane == k) {
+          a[k] = dkk * inv;
+          dinv = inv;
+        } else if (lane > k) {
+          a[k] = l;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j > k) {
+            const float ljk = __shfl_sync(full, l, j);
+            if (lane >= j) a[j] = fmaf(-l, ljk, a[j]);
+          }
+        }
+      }
+      // L z = b (b = m on F, 0 elsewhere)
+      float z = inF ? m : 0.0f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float zk = __shfl_sync(full, z * dinv, k);
+        if (lane == k) z = zk;
+        else if (lane > k) z = fmaf(-a[k], zk, z);
+      }
+      // L^T x = z, column k of L^T (row k of L) from the transpose
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j <= lane) T[lane][j] = a[j];
+      __syncwarp();
+#pragma unroll
+      for (int k = 31; k >= 0; --k) {
+        const float xk = __shfl_sync(full, z * dinv, k);
+        if (lane == k) z = xk;
+        else if (lane < k) z = fmaf(-T[k][lane], xk, z);
+      }
+      __syncwarp();
+      x = inF ? z : 0.0f;
+      // y = S x - m outside F
+      float y = -m;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) y = fmaf(Ss[lane][k], __shfl_sync(full, x, k), y);
+      if (inF || !usable) y = 0.0f;
+      const unsigned V = __ballot_sync(full, usable && (inF ? x < 0.0f : y < 0.0f));
       if (V == 0u) break;
       const int count = __popc(V);
       unsigned flip;
@@ -1126,56 +1194,23 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
         best = count;
         backups = 3;
         flip = V;
+        last = -1;
       } else if (backups > 0) {
         --backups;
         flip = V;
+        last = -1;
       } else {
-        flip = 1u << (31 - __clz(V));
+        // a single pivot on a positive definite S reverses the sign of its
+        // variable, so the index flipped just before is infeasible again only
+        // by rounding: it is left as it is
+        const unsigned Vb = last >= 0 ? V & ~(1u << last) : V;
+        if (Vb == 0u) break;
+        last = 31 - __clz(Vb);
+        flip = 1u << last;
       }
       if ((flip >> lane) & 1u) inF = !inF;
-      const unsigned Fm = __ballot_sync(0xffffffffu, inF);
-      // A = S_FF, identity outside F (lane = row)
-      for (int j = 0; j < R; ++j)
-        A[lane][j] = (inF && ((Fm >> j) & 1u)) ? Ss[lane][j] : (lane == j ? 1.0f : 0.0f);
-      __syncwarp();
-      // Cholesky A = L L^T, lower triangle in place, one column at a time
-#pragma unroll 1
-      for (int k = 0; k < R; ++k) {
-        const float d = sqrtf(A[k][k]);
-        float lik = 0.0f;
-        if (lane > k && lane < R) {
-          lik = A[lane][k] / d;
-          A[lane][k] = lik;
-        }
-        __syncwarp();
-        if (lane > k && lane < R)
-          for (int j = k + 1; j <= lane; ++j) A[lane][j] = fmaf(-lik, A[j][k], A[lane][j]);
-        if (lane == k) A[k][k] = d;
-        __syncwarp();
-      }
-      // L z = b (b = m on F, 0 elsewhere), then L^T x = z
-      float z = (inF && lane < R) ? m : 0.0f;
-#pragma unroll 1
-      for (int k = 0; k < R; ++k) {
-        const float zk = __shfl_sync(0xffffffffu, z, k) / A[k][k];
-        if (lane == k) z = zk;
-        if (lane > k && lane < R) z = fmaf(-A[lane][k], zk, z);
-      }
-#pragma unroll 1
-      for (int k = R - 1; k >= 0; --k) {
-        const float xk = __shfl_sync(0xffffffffu, z, k) / A[k][k];
-        if (lane == k) z = xk;
-        if (lane < k) z = fmaf(-A[k][lane], xk, z);
-      }
-      __syncwarp();
-      x = (inF && lane < R) ? z : 0.0f;
-      // y = S x - m outside F
-      float yy = -m;
-#pragma unroll 1
-      for (int k = 0; k < R; ++k) yy = fmaf(Ss[lane][k], __shfl_sync(0xffffffffu, x, k), yy);
-      y = (inF || !usable) ? 0.0f : yy;
     }
-    if (lane < R) W[(long long)row * R + lane] = x;
+    if (lane < R) W[off] = fmaxf(x, 0.0f);
   }
 }
 
@@ -1315,13 +1350,18 @@ cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveS
                        st.gram_part, (const int*)st.flags, 1);
 }
 
+cudaError_t launch_bpp_rows(float* H, const float* M, int64_t In, int R, SolveState st,
+                            int num_sms, cudaStream_t stream) {
+  if (R > 32) return cudaErrorInvalidValue;
+  const long long ctas = (In + kBppWarps - 1) / kBppWarps;
+  const int grid = (int)std::max(1LL, std::min(ctas, (long long)num_sms * 4));
+  return launch_kernel(k_bpp_rows, dim3(grid), dim3(kBppWarps * 32), 0, stream, H, M, (int)In, R,
+                       (const float*)st.S, (const int*)st.flags);
+}
+
 cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, SolveState st,
                               int num_sms, cudaStream_t stream) {
-  if (R > 32) return cudaErrorInvalidValue;
-  const long long warps = (In + kBppWarps - 1) / kBppWarps;
-  const int grid = (int)std::max(1LL, std::min(warps, (long long)num_sms * 4));
-  cudaError_t e = launch_kernel(k_bpp_rows, dim3(grid), dim3(kBppWarps * 32), 0, stream, H, M,
-                                (int)In, R, (const float*)st.S, (const int*)st.flags);
+  cudaError_t e = launch_bpp_rows(H, M, In, R, st, num_sms, stream);
   if (e != cudaSuccess) return e;
   // Gram partials and <M, W> of the new W (no sweep)
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
@@ -1366,7 +1406,8 @@ cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int
 bool cluster_update_ok(int64_t In, int R) { return In >= 1 && In <= kClusterMaxRows && R <= 64; }
 
 cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, int N, int n,
-                                  int next_mode, int is_last, SolveState st, cudaStream_t stream) {
+                                  int next_mode, int is_last, SolveState st, cudaStream_t stream,
+                                  int sweep) {
   const int rows = cluster_rows(In);
   const int nb = (int)((In + rows - 1) / rows);
   const int rmax = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
@@ -1374,15 +1415,15 @@ cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, i
     case 16:
       return launch_kernel_cluster(k_update_cluster<16>, dim3(nb), dim3(kClusterThreads),
                                    cluster_smem<16>(), stream, nb, H, M, (int)In, R, N, n,
-                                   next_mode, is_last, rows, st);
+                                   next_mode, is_last, rows, sweep, st);
     case 32:
       return launch_kernel_cluster(k_update_cluster<32>, dim3(nb), dim3(kClusterThreads),
                                    cluster_smem<32>(), stream, nb, H, M, (int)In, R, N, n,
-                                   next_mode, is_last, rows, st);
+                                   next_mode, is_last, rows, sweep, st);
     default:
       return launch_kernel_cluster(k_update_cluster<64>, dim3(nb), dim3(kClusterThreads),
                                    cluster_smem<64>(), stream, nb, H, M, (int)In, R, N, n,
-                                   next_mode, is_last, rows, st);
+                                   next_mode, is_last, rows, sweep, st);
   }
 }
 
