@@ -35,6 +35,7 @@ __all__ = [
     "hals_sweep",
     "nnls_bpp",
     "bpp_update",
+    "admm_update",
     "normalize_columns",
     "fit_identity",
     "reconstruct",
@@ -336,6 +337,37 @@ def bpp_update(M, S):
     return np.stack([nnls_bpp(S, M[i]) for i in range(M.shape[0])]) if M.shape[0] else M.copy()
 
 
+def admm_update(M, S, Z, U, iters):
+    """`iters` iterations of ADMM on every row's NLS (AO-ADMM, one of the
+    alternative NLS-Updates Sec. II-B names), in the scaled form of ADMM.
+
+    Row problem: min_{x >= 0} 1/2 x^T S x - m^T x, split as x = z with the
+    constraint on z and a scaled dual u.  With rho = trace(S) / R, each
+    iteration is, for every row at once (the rows share S + rho I):
+        x <- (S + rho I)^-1 (m + rho (z - u))
+        z <- max(0, x + u)
+        u <- u + x - z
+    Z and U are the starting values (rows of z and u); returns the final
+    (Z, U), Z being the updated factor.  At a fixed point x = z and
+    S z - m = -rho u, which with z >= 0, u <= 0, z_i u_i = 0 are the NNLS
+    KKT conditions.  trace(S) = 0 gives Z = U = 0.
+    """
+    M = np.asarray(M, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    Z = np.array(Z, dtype=np.float64, copy=True)
+    U = np.array(U, dtype=np.float64, copy=True)
+    R = S.shape[0]
+    rho = float(np.trace(S)) / R
+    if rho <= 0.0:
+        return np.zeros_like(Z), np.zeros_like(U)
+    A = S + rho * np.eye(R)
+    for _ in range(iters):
+        X = np.linalg.solve(A, (M + rho * (Z - U)).T).T
+        Z = np.maximum(0.0, X + U)
+        U = U + X - Z
+    return Z, U
+
+
 def normalize_columns(W):
     """lambda_r = ||W(:, r)||_2 and H = W diag(lambda)^-1 (Alg. 3, column norms).
 
@@ -389,13 +421,18 @@ def hals_objective(W, M, S):
 
 
 def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
-              callback=None, nls="hals"):
+              callback=None, nls="hals", admm_iters=5):
     """NNCP by block coordinate descent with one HALS sweep per block (Alg. 1, Alg. 3).
 
     nls selects Alg. 1's NLS-Update: "hals" (one HALS sweep from W = H_n
     diag(lam), the default) or "bpp" (the exact nonnegative least-squares
     solve of every row by block principal pivoting, ``bpp_update``; its
-    result does not depend on the starting W).
+    result does not depend on the starting W) or "admm" (``admm_iters``
+    ADMM iterations, ``admm_update``, from z = H_n diag(lam) and the dual
+    this mode's previous update left; the factor is z).  The dual is kept
+    in the frame of the normalised factor: divided by the new lam when
+    H_n is, multiplied by the current lam when the next update of mode n
+    starts, as z is; it starts at 0.
 
     Steps, in the paper's order:
       init   : normalise every initial factor, fold the norms into lam,
@@ -428,15 +465,23 @@ def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
     alpha = float(np.sum(x * x))
     state = {"lam": lam, "fit": None, "eps": None}
     fits, epss = [], []
+    Uhat = [np.zeros_like(h) for h in H]  # ADMM duals, normalised frame
 
     def update(n, M):
         S = hadamard_of_grams(G, n)
         if nls == "bpp":
             W = bpp_update(M, S)
+        elif nls == "admm":
+            W, U = admm_update(M, S, H[n] * state["lam"], Uhat[n] * state["lam"], admm_iters)
         else:
             W = H[n] * state["lam"]
             hals_sweep(W, M, S)
         H[n], state["lam"] = normalize_columns(W)
+        if nls == "admm":
+            lam_n = state["lam"]
+            Uhat[n] = np.zeros_like(U)
+            nz = lam_n > 0
+            Uhat[n][:, nz] = U[:, nz] / lam_n[nz]
         G[n] = gram(H[n])
         if n == N - 1:
             eps, _, _ = fit_identity(alpha, M, W, state["lam"], S, G[n])

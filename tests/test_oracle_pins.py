@@ -408,3 +408,77 @@ def test_planted_bpp_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "nnls_bpp", wrong)
     with pytest.raises(AssertionError):
         test_bpp_satisfies_kkt_and_matches_library_nnls(8)
+
+
+# ---- ADMM (AO-ADMM's NLS-Update, Sec. II-B's alternatives) ------------------
+
+@pytest.mark.parametrize("R", [1, 3, 8, 16])
+def test_admm_converges_to_library_nnls_with_its_dual(R):
+    # ADMM's fixed point is the NNLS solution (scipy's Lawson-Hanson on the
+    # equivalent least squares), and the scaled dual there is -y / rho with
+    # y = S z - m the KKT multiplier: nonpositive, zero where z > 0
+    scipy_optimize = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(90 + R)
+    rows = 6
+    A = rng.standard_normal((2 * R + 4, R))
+    S = A.T @ A
+    B = rng.standard_normal((rows, 2 * R + 4))
+    M = B @ A
+    Z, U = oracle.admm_update(M, S, rng.random((rows, R)), np.zeros((rows, R)), 6000)
+    rho = np.trace(S) / R
+    for i in range(rows):
+        z_ref, _ = scipy_optimize.nnls(A, B[i])
+        assert np.allclose(Z[i], z_ref, atol=1e-7)
+    scale = max(1.0, float(np.abs(M).max()))
+    assert np.allclose(Z @ S - M, -rho * U, atol=1e-7 * scale)
+    assert U.max() <= 1e-9 * scale
+    assert np.abs(Z * U).max() <= 1e-9 * scale * scale
+
+
+def test_admm_interior_solution_is_a_fixed_point():
+    # M = Z* S with Z* > 0: the unconstrained minimiser is feasible; from
+    # z = Z*, u = 0 every iteration returns the same point
+    rng = np.random.default_rng(95)
+    R = 7
+    A = rng.random((15, R)) + np.eye(15, R)
+    S = A.T @ A
+    Zs = rng.random((5, R)) + 0.1
+    Z, U = oracle.admm_update(Zs @ S, S, Zs, np.zeros_like(Zs), 25)
+    assert np.allclose(Z, Zs, atol=1e-12)
+    assert np.abs(U).max() <= 1e-12
+
+
+def test_admm_solve_limit_is_the_exact_bcd_solve():
+    # with enough inner iterations every NLS-Update is solved exactly, so the
+    # AO-ADMM solve follows the BPP solve whatever dual it carries
+    dims, R = (8, 7, 6), 3
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=96, noise=0.05)
+    H0 = [h.astype(np.float64) for h in synth.init_factors(dims, R, seed=97)]
+    xd = x.astype(np.float64)
+    a = oracle.nncp_hals(xd, dims, H0, max_iters=4, nls="admm", admm_iters=3000)
+    b = oracle.nncp_hals(xd, dims, H0, max_iters=4, nls="bpp")
+    assert np.allclose(a["fits"], b["fits"], atol=1e-9)
+    for n in range(3):
+        assert np.allclose(a["H"][n], b["H"][n], atol=1e-7)
+
+
+def test_planted_admm_mistake_is_caught(monkeypatch):
+    # a dual step with the wrong sign is a plausible slip
+    real = oracle.admm_update
+
+    def wrong(M, S, Z, U, iters):
+        Z = np.array(Z, dtype=np.float64, copy=True)
+        U = np.array(U, dtype=np.float64, copy=True)
+        R = S.shape[0]
+        rho = float(np.trace(S)) / R
+        A = S + rho * np.eye(R)
+        for _ in range(iters):
+            X = np.linalg.solve(A, (M + rho * (Z - U)).T).T
+            Z = np.maximum(0.0, X + U)
+            U = U - X + Z
+        return Z, U
+
+    assert real is not wrong
+    monkeypatch.setattr(oracle, "admm_update", wrong)
+    with pytest.raises(AssertionError), np.errstate(over="ignore", invalid="ignore"):
+        test_admm_converges_to_library_nnls_with_its_dual(8)
