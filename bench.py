@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--no-dimtree-compare", action="store_true",
                    help="skip the with / without dimension tree comparison (context line)")
     p.add_argument("--no-nls-compare", action="store_true",
-                   help="skip the HALS vs block principal pivoting NLS comparison")
+                   help="skip the HALS / block principal pivoting / ADMM NLS comparison")
     p.add_argument("--no-4way", action="store_true",
                    help="skip the 512x512x32x16 R=24 split-2 step (context line 'hsi_4way')")
     p.add_argument("--no-batched", action="store_true",
@@ -317,7 +317,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_dimtree_compare:
         result["dimtree_vs_direct"] = run_dimtree_compare(nncp, torch)
     if rank == 0 and world == 1 and not args.no_nls_compare:
-        result["nls_hals_vs_bpp"] = run_nls_compare(nncp, torch, Xuse, H0, prec)
+        result["nls_compare"] = run_nls_compare(nncp, torch, Xuse, H0, prec)
     if rank == 0 and world == 1 and not args.no_4way:
         result["hsi_4way"] = run_4way(nncp, torch, prec_name, max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_batched:
@@ -413,16 +413,20 @@ def run_dimtree_compare(nncp, torch, steps=4):
     return out
 
 
-def run_nls_compare(nncp, torch, X, H0, prec, steps=20, max_iters=400, tol=1e-6):
-    """The two NLS updates of Alg. 1 on the step's workload: HALS (one sweep
-    over the columns per mode update) and block principal pivoting (each
-    row's NNLS solved exactly).  Per-iteration time of back-to-back graphs,
-    then one solve each from the same start to the relative fit-change
-    tolerance `tol`: iterations, device time and final fit."""
-    out = {"tol": tol, "max_iters": max_iters}
-    for nls in ("hals", "bpp"):
+def run_nls_compare(nncp, torch, X, H0, prec, steps=20, max_iters=400, tol=1e-6,
+                    admm_iters=5):
+    """The NLS updates of Alg. 1 on the step's workload: HALS (one sweep over
+    the columns per mode update), block principal pivoting (each row's NNLS
+    solved exactly) and AO-ADMM (`admm_iters` ADMM iterations per update).
+    Per-iteration time of back-to-back graphs, then one solve each from the
+    same start to the fit-change tolerance `tol`: iterations, device time
+    and final fit."""
+    out = {"tol": tol, "max_iters": max_iters, "admm_iters": admm_iters}
+    for nls in ("hals", "bpp", "admm"):
         ctx = nncp.Context(DIMS, RANK, precision=prec, root_split=1)
         ctx.set_nls(nls)
+        if nls == "admm":
+            ctx.set_admm_iters(admm_iters)
         ctx.set_tensor(X)
         ctx.set_factors([torch.from_numpy(h.copy()).cuda() for h in H0])
         ctx.solve_begin()

@@ -101,11 +101,19 @@ nncp_status nncp_set_leaf_fusion(nncp_ctx* ctx, int enabled);
  * HALS sweep from W = H_n diag(lambda); NNCP_NLS_BPP solves each row's
  * nonnegative least squares exactly by block principal pivoting (the solver
  * the paper benchmarks), whatever the starting W, then normalises as HALS
- * does.  BPP supports R <= 32 (NNCP_ERR_UNSUPPORTED above) and any precision
- * of the MTTKRPs.  Takes effect at the next solve or iteration. */
+ * does; NNCP_NLS_ADMM runs a fixed number of ADMM iterations on every row
+ * (AO-ADMM, one of the alternatives Sec. II-B names; rho = trace(S) / R),
+ * from z = H_n diag(lambda) and the scaled dual its previous update of the
+ * mode left (zero at the start of a solve), and takes z as the new W.  BPP
+ * and ADMM support R <= 32 (NNCP_ERR_UNSUPPORTED above) and any precision of
+ * the MTTKRPs.  Takes effect at the next solve or iteration. */
 #define NNCP_NLS_HALS 0
 #define NNCP_NLS_BPP  1
+#define NNCP_NLS_ADMM 2
 nncp_status nncp_set_nls(nncp_ctx* ctx, int nls);
+/* ADMM iterations per mode update for NNCP_NLS_ADMM: 1 <= iters <= 10000
+ * (NNCP_ERR_INVALID_ARG otherwise); default 5. */
+nncp_status nncp_set_admm_iters(nncp_ctx* ctx, int iters);
 /* Bytes of device scratch the context needs for its current options
  * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
 nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);

@@ -65,7 +65,9 @@ struct nncp_ctx {
   TcScratch tc = {};
 
   bool fuse_leaf = true;              // fuse first leaf multi-TTVs into partial MTTKRPs
-  int nls = NNCP_NLS_HALS;            // NLS-Update: HALS sweep or block principal pivoting
+  int nls = NNCP_NLS_HALS;            // NLS-Update: HALS sweep, block principal pivoting, ADMM
+  int admm_iters = 5;                 // ADMM iterations per mode update
+  float* U[kMaxModes] = {};           // ADMM duals, I_n x R, normalised frame (workspace)
   cudaGraphExec_t graph = nullptr;   // one outer iteration
   cudaGraphExec_t graph4 = nullptr;  // kGraphIters outer iterations, back to back
   int graph_kernels = 0;
@@ -121,6 +123,7 @@ struct Plan {
   size_t node_bytes[2][kMaxModes];
   size_t M_off, upd_off, part_off, part_cap, gram_off, G_off, S_off, lam_off, scal_off,
       fits_off, flags_off, red_off;
+  size_t dual_off[kMaxModes];
   int red_nparts;
   size_t tc_off, tc_bytes;
   size_t total;
@@ -189,6 +192,7 @@ Plan make_plan(const nncp_ctx* c) {
   p.red_off = take((size_t)2 * p.red_nparts * sizeof(double));
   p.tc_bytes = tc_scratch_bytes(c->N, c->dims, c->R, c->split, c->precision, c->num_sms);
   p.tc_off = take(std::max<size_t>(p.tc_bytes, 1));
+  for (int n = 0; n < N; ++n) p.dual_off[n] = take((size_t)c->dims[n] * R * sizeof(float));
   p.total = off;
   return p;
 }
@@ -212,6 +216,8 @@ void bind_workspace(nncp_ctx* c) {
   c->st.flags = reinterpret_cast<int*>(w + p.flags_off);
   c->red_part = reinterpret_cast<double*>(w + p.red_off);
   c->red_nparts = p.red_nparts;
+  for (int n = 0; n < kMaxModes; ++n)
+    c->U[n] = n < c->N ? reinterpret_cast<float*>(w + p.dual_off[n]) : nullptr;
   c->tc.base = w + p.tc_off;
   c->tc.bytes = p.tc_bytes;
 }
@@ -252,6 +258,21 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st, const TcLeaf* leaf
 }
 
 cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
+  if (c->nls == NNCP_NLS_ADMM) {
+    if (cluster_update_ok(c->dims[n], c->R)) {
+      cudaError_t e = launch_admm_rows(c->H[n], c->U[n], c->Mbuf, c->dims[n], c->R,
+                                       c->admm_iters, c->st, st);
+      if (e != cudaSuccess) return e;
+      return launch_update_cluster(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                                   n == c->N - 1, c->st, st, 0, c->U[n]);
+    }
+    cudaError_t e = launch_admm_update(c->H[n], c->U[n], c->Mbuf, c->dims[n], c->R,
+                                       c->admm_iters, c->st, st);
+    if (e != cudaSuccess) return e;
+    return launch_finalize(c->H[n], c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                           hals_gram_blocks(c->dims[n]), n == c->N - 1, 0, 0.0, c->st, st,
+                           c->U[n]);
+  }
   if (c->nls == NNCP_NLS_BPP) {
     if (cluster_update_ok(c->dims[n], c->R)) {
       cudaError_t e = launch_bpp_rows(c->H[n], c->Mbuf, c->dims[n], c->R, c->st, c->num_sms, st);
@@ -356,6 +377,8 @@ nncp_status solve_init(nncp_ctx* c, double tol) {
   cudaStream_t st = c->work;
   const int R = c->R, N = c->N;
   CK(launch_solve_reset(c->st, R, tol, st));
+  for (int n = 0; n < N; ++n)
+    CK(cudaMemsetAsync(c->U[n], 0, (size_t)c->dims[n] * R * sizeof(float), st));
   CK(launch_sumsq(c->X, c->precision == NNCP_BF16_STORED, c->I, c->red_part, c->red_nparts,
                   c->st.scalars, nullptr, st));
   for (int n = 0; n < N; ++n) {
@@ -541,11 +564,22 @@ nncp_status nncp_set_dimtree(nncp_ctx* c, int enabled) {
 
 nncp_status nncp_set_nls(nncp_ctx* c, int nls) {
   if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
-  if (nls != NNCP_NLS_HALS && nls != NNCP_NLS_BPP)
+  if (nls != NNCP_NLS_HALS && nls != NNCP_NLS_BPP && nls != NNCP_NLS_ADMM)
     return fail(c, NNCP_ERR_INVALID_ARG, "unknown NLS update %d", nls);
   if (nls == NNCP_NLS_BPP && c->R > 32)
     return fail(c, NNCP_ERR_UNSUPPORTED, "block principal pivoting supports R <= 32");
+  if (nls == NNCP_NLS_ADMM && c->R > 32)
+    return fail(c, NNCP_ERR_UNSUPPORTED, "the ADMM update supports R <= 32");
   c->nls = nls;
+  drop_graph(c);
+  return NNCP_OK;
+}
+
+nncp_status nncp_set_admm_iters(nncp_ctx* c, int iters) {
+  if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
+  if (iters < 1 || iters > 10000)
+    return fail(c, NNCP_ERR_INVALID_ARG, "ADMM iterations %d outside 1..10000", iters);
+  c->admm_iters = iters;
   drop_graph(c);
   return NNCP_OK;
 }

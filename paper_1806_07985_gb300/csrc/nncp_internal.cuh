@@ -174,11 +174,12 @@ size_t multi_update_scratch(int64_t In, int R);
 // The same update on one thread-block cluster (cluster_update_ok(In, R):
 // I_n <= 1024, R <= 64), preferred where it applies; needs no scratch.
 // sweep = 0: H holds W already (written by the kernel just before), no HALS
-// sweep; the rest of the update as above.
+// sweep; the rest of the update as above.  U (non-null with sweep = 0): the
+// rows' ADMM duals, divided by the new lambda along with H.
 bool cluster_update_ok(int64_t In, int R);
 cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, int N, int n,
                                   int next_mode, int is_last, SolveState st, cudaStream_t stream,
-                                  int sweep = 1);
+                                  int sweep = 1, float* U = nullptr);
 cudaError_t launch_update_multi(float* H, const float* M, int64_t In, int R, int N, int n,
                                 int next_mode, int is_last, SolveState st, float* part,
                                 cudaStream_t stream);
@@ -193,6 +194,15 @@ cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, Solve
 cudaError_t launch_bpp_rows(float* H, const float* M, int64_t In, int R, SolveState st,
                             int num_sms, cudaStream_t stream);
 
+// AO-ADMM NLS update (R <= 32): `iters` ADMM iterations on every row from
+// z = H diag(lam), u = U diag(lam); z into H (unnormalised W), u into U.  The
+// _update form adds the Gram partials and <M, W> (then launch_finalize with
+// U); the _rows form is for launch_update_cluster(sweep = 0, U).
+cudaError_t launch_admm_rows(float* H, float* U, const float* M, int64_t In, int R, int iters,
+                            SolveState st, cudaStream_t stream);
+cudaError_t launch_admm_update(float* H, float* U, const float* M, int64_t In, int R, int iters,
+                               SolveState st, cudaStream_t stream);
+
 // Gram partials of H as given (initialisation: W = H).
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream);
@@ -201,9 +211,10 @@ cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
 //   W^T W = sum of the partials; lam = sqrt(diag); G_n = D^-1 W^T W D^-1;
 //   H_n = W / lam (in place); if is_last: fit from the Sec. IV-B identity;
 //   S for mode next_mode.  init = 1: lam *= column norms instead of replacing.
+//   U non-null: the rows' ADMM duals, divided by the new lambda along with H.
 cudaError_t launch_finalize(float* H, int64_t In, int R, int N, int n, int next_mode,
                             int nblocks, int is_last, int init, double tol, SolveState st,
-                            cudaStream_t stream);
+                            cudaStream_t stream, float* U = nullptr);
 
 // lambda = 1, flags and fit counter cleared, tolerance stored (before initialisation).
 cudaError_t launch_solve_reset(SolveState st, int R, double tol, cudaStream_t stream);

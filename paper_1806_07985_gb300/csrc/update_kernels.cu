@@ -149,7 +149,7 @@ __device__ void record_fit(SolveState st, double beta, double gamma) {
 // Single CTA (1024 threads).  Shared: GW (R*R doubles) + c (R doubles).
 __global__ void __launch_bounds__(1024)
 k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mode,
-           int nblocks, int is_last, int init, SolveState st) {
+           int nblocks, int is_last, int init, SolveState st, float* __restrict__ U) {
   pdl_wait();
   pdl_trigger();
   if (st.flags[0]) return;
@@ -184,6 +184,7 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   for (long long t = tid; t < In * R; t += blockDim.x) {
     const int r = (int)(t % R);
     H[t] = c[r] > 0.0 ? H[t] / (float)c[r] : 0.0f;
+    if (U) U[t] = c[r] > 0.0 ? U[t] / (float)c[r] : 0.0f;  // ADMM dual, same frame as H
   }
   if (is_last) {
     // gamma = lam^T (S * G_N) lam = sum_ab S_ab (W^T W)_ab
@@ -738,7 +739,8 @@ int cluster_rows(int64_t In) {
 template <int RMAX>
 __global__ void __launch_bounds__(kClusterThreads, 1)
 k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int R, int N, int n,
-                 int next_mode, int is_last, int rows, int sweep, SolveState st) {
+                 int next_mode, int is_last, int rows, int sweep, SolveState st,
+                 float* __restrict__ U) {
   using C = ClusterCfg<RMAX>;
   constexpr int T = C::T, RP = C::RP, GROUPS = C::GROUPS;
   extern __shared__ __align__(16) float csm[];
@@ -1021,6 +1023,13 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
 #pragma unroll 1
     for (int e = tid; e < nrows * R; e += T) Hw[e] = Hs[(e / R) * RP + e % R] * lamf[e % R];
   }
+  if (U) {
+    // the ADMM dual of these rows (written by the kernel just before) into
+    // the frame of the normalised factor
+    float* Uw = U + (long long)row0 * R;
+#pragma unroll 1
+    for (int e = tid; e < nrows * R; e += T) Uw[e] *= lamf[e % R];
+  }
   // this CTA's slice of G_n and of S for the next mode: Hadamard of every Gram
   // but next_mode's, in mode order (mode n's is the new one)
   float* Gng = st.G + (long long)n * R2;
@@ -1087,6 +1096,38 @@ size_t cluster_smem() {
          sizeof(float);
 }
 
+// ---- warp Cholesky ------------------------------------------------------------
+// A = L L^T for a 32 x 32 symmetric positive definite A held one row per lane
+// (a[j] = A(lane, j)); on return a[k] = L(lane, k) for k <= lane and
+// dinv = 1 / L(lane, lane).  Right-looking: column k is scaled by the
+// reciprocal square root of its pivot and broadcast by shuffles, and the
+// trailing rows take its rank-one update.  Every register index is static.
+// Called by all 32 lanes of a warp.
+__device__ __forceinline__ void warp_cholesky32(float (&a)[32], float& dinv) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  dinv = 1.0f;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const float dkk = __shfl_sync(full, a[k], k);
+    const float inv = rsqrtf(dkk);
+    const float l = a[k] * inv;
+    if (lane == k) {
+      a[k] = dkk * inv;
+      dinv = inv;
+    } else if (lane > k) {
+      a[k] = l;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j > k) {
+        const float ljk = __shfl_sync(full, l, j);
+        if (lane >= j) a[j] = fmaf(-l, ljk, a[j]);
+      }
+    }
+  }
+}
+
 // ---- block principal pivoting NLS update -----------------------------------
 // Alg. 1's NLS-Update solved exactly, one warp per row of W (R <= 32): lane j
 // owns variable j.  For the row's m (its row of M) it finds x >= 0 with
@@ -1139,27 +1180,8 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         a[j] = (inF && ((Fm >> j) & 1u)) ? Ss[lane][j] : (lane == j ? 1.0f : 0.0f);
-      // right-looking Cholesky: after column k, a[k] = L(lane, k) for lane >= k
-      float dinv = 1.0f;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float dkk = __shfl_sync(full, a[k], k);
-        const float inv = rsqrtf(dkk);
-        const float l = a[k] * inv;
-        if (lane == k) {
-          a[k] = dkk * inv;
-          dinv = inv;
-        } else if (lane > k) {
-          a[k] = l;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j > k) {
-            const float ljk = __shfl_sync(full, l, j);
-            if (lane >= j) a[j] = fmaf(-l, ljk, a[j]);
-          }
-        }
-      }
+      float dinv;
+      warp_cholesky32(a, dinv);
       // L z = b (b = m on F, 0 elsewhere)
       float z = inF ? m : 0.0f;
 #pragma unroll
@@ -1211,6 +1233,140 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
       if ((flip >> lane) & 1u) inF = !inF;
     }
     if (lane < R) W[off] = fmaxf(x, 0.0f);
+  }
+}
+
+// ---- AO-ADMM NLS update ----------------------------------------------------
+// `iters` iterations of ADMM (scaled form) on every row's NNLS, R <= RMAX <= 32:
+// rho = trace(S) / R; x = (S + rho I)^-1 (m + rho (z - u)); z = max(0, x + u);
+// u = u + x - z, starting from z = H diag(lam) and u = U diag(lam) (the dual
+// this mode's previous update left, in the normalised frame).  Every row
+// shares S + rho I: warp 0 of each CTA factors it (warp_cholesky32, identity
+// outside R) and lane j forms column j of its inverse P by two triangular
+// solves against the factor in shared memory.  Then one thread per row keeps
+// z, u and the right-hand side in registers; each x_i is a dot product with
+// row i of P (shared-memory broadcasts).  Rows are staged in and written
+// back through padded shared-memory tiles (coalesced).  z goes to H
+// (unnormalised W), u to U; the update's tail divides both by the new lambda.
+// trace(S) = 0 gives z = u = 0.
+constexpr int kAdmmRows = 64;
+
+template <int RMAX>
+__global__ void __launch_bounds__(kAdmmRows)
+k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restrict__ M, int In,
+            int R, const float* __restrict__ S, const double* __restrict__ lam, int iters,
+            const int* __restrict__ flags) {
+  pdl_wait();
+  pdl_trigger();
+  if (flags[0]) return;
+  __shared__ __align__(16) float P[RMAX][RMAX];
+  __shared__ float Lt[32][33];
+  __shared__ float Y[32][33];
+  __shared__ float dinv_s[32];
+  __shared__ float Zs[kAdmmRows][RMAX + 1], Us[kAdmmRows][RMAX + 1], Ms[kAdmmRows][RMAX + 1];
+  __shared__ float lamf[RMAX];
+  __shared__ float rho_s;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const unsigned full = 0xffffffffu;
+  const long long row0 = (long long)blockIdx.x * kAdmmRows;
+  const int nrows = (int)min((long long)kAdmmRows, (long long)In - row0);
+  for (int e = tid; e < nrows * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    const long long g = row0 * R + e;
+    Zs[r][c] = W[g];
+    Us[r][c] = U[g];
+    Ms[r][c] = M[g];
+  }
+  if (tid < RMAX) lamf[tid] = tid < R ? (float)lam[tid] : 0.0f;
+  if (tid < 32) {
+    const float sll = lane < R ? S[lane * R + lane] : 0.0f;
+    float tr = sll;
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(full, tr, o);
+    const float rho = __shfl_sync(full, tr, 0) / (float)R;
+    if (lane == 0) rho_s = rho;
+    if (rho > 0.0f) {
+      float a[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        a[j] = (lane < R && j < R) ? S[lane * R + j] + (j == lane ? rho : 0.0f)
+                                   : (j == lane ? 1.0f : 0.0f);
+      float dinv;
+      warp_cholesky32(a, dinv);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j <= lane) Lt[lane][j] = a[j];
+      dinv_s[lane] = dinv;
+      __syncwarp();
+      // lane j: L y = e_j, then L^T p = y (p = column j of the inverse), y in
+      // column j of Y (each lane touches only its own column: no conflicts)
+#pragma unroll 1
+      for (int i = 0; i < 32; ++i) {
+        float v = i == lane ? 1.0f : 0.0f;
+#pragma unroll 4
+        for (int k = 0; k < i; ++k) v = fmaf(-Lt[i][k], Y[k][lane], v);
+        Y[i][lane] = v * dinv_s[i];
+      }
+#pragma unroll 1
+      for (int i = 31; i >= 0; --i) {
+        float v = Y[i][lane];
+#pragma unroll 4
+        for (int k = i + 1; k < 32; ++k) v = fmaf(-Lt[k][i], Y[k][lane], v);
+        Y[i][lane] = v * dinv_s[i];
+      }
+#pragma unroll 1
+      for (int i = 0; i < RMAX; ++i)
+        if (lane < RMAX) P[i][lane] = (i < R && lane < R) ? Y[i][lane] : 0.0f;
+    }
+  }
+  __syncthreads();
+  const float rho = rho_s;
+  if (tid < nrows) {
+    float z[RMAX], u[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      z[j] = (j < R && rho > 0.0f) ? Zs[tid][j] * lamf[j] : 0.0f;
+      u[j] = (j < R && rho > 0.0f) ? Us[tid][j] * lamf[j] : 0.0f;
+    }
+    if (rho > 0.0f) {
+#pragma unroll 1
+      for (int it = 0; it < iters; ++it) {
+        // P is reread every iteration rather than held in registers
+        asm volatile("" ::: "memory");
+        float b[RMAX];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) b[j] = j < R ? fmaf(rho, z[j] - u[j], Ms[tid][j]) : 0.0f;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+          const float4* Pi = reinterpret_cast<const float4*>(&P[i][0]);
+          float x0 = 0.0f, x1 = 0.0f;
+#pragma unroll
+          for (int j4 = 0; j4 < RMAX / 4; ++j4) {
+            const float4 pv = Pi[j4];
+            x0 = fmaf(pv.x, b[4 * j4], x0);
+            x1 = fmaf(pv.y, b[4 * j4 + 1], x1);
+            x0 = fmaf(pv.z, b[4 * j4 + 2], x0);
+            x1 = fmaf(pv.w, b[4 * j4 + 3], x1);
+          }
+          const float x = x0 + x1;
+          const float zn = fmaxf(0.0f, x + u[i]);
+          u[i] = u[i] + (x - zn);
+          z[i] = zn;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j)
+      if (j < R) {
+        Zs[tid][j] = z[j];
+        Us[tid][j] = u[j];
+      }
+  }
+  __syncthreads();
+  for (int e = tid; e < nrows * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    const long long g = row0 * R + e;
+    W[g] = Zs[r][c];
+    U[g] = Us[r][c];
   }
 }
 
@@ -1369,6 +1525,25 @@ cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, Solve
                        st.gram_part, (const int*)st.flags, 2);
 }
 
+cudaError_t launch_admm_rows(float* H, float* U, const float* M, int64_t In, int R, int iters,
+                            SolveState st, cudaStream_t stream) {
+  if (R > 32 || In > INT32_MAX) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((In + kAdmmRows - 1) / kAdmmRows)), block(kAdmmRows);
+  const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
+  auto k = rmax == 8 ? k_admm_rows<8> : (rmax == 16 ? k_admm_rows<16> : k_admm_rows<32>);
+  return launch_kernel(k, grid, block, 0, stream, H, U, M, (int)In, R, (const float*)st.S,
+                       (const double*)st.lam, iters, (const int*)st.flags);
+}
+
+cudaError_t launch_admm_update(float* H, float* U, const float* M, int64_t In, int R, int iters,
+                               SolveState st, cudaStream_t stream) {
+  cudaError_t e = launch_admm_rows(H, U, M, In, R, iters, st, stream);
+  if (e != cudaSuccess) return e;
+  return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
+                       stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       st.gram_part, (const int*)st.flags, 2);
+}
+
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream) {
   size_t smem = hals_smem(R);
@@ -1407,7 +1582,7 @@ bool cluster_update_ok(int64_t In, int R) { return In >= 1 && In <= kClusterMaxR
 
 cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, int N, int n,
                                   int next_mode, int is_last, SolveState st, cudaStream_t stream,
-                                  int sweep) {
+                                  int sweep, float* U) {
   const int rows = cluster_rows(In);
   const int nb = (int)((In + rows - 1) / rows);
   const int rmax = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
@@ -1415,25 +1590,25 @@ cudaError_t launch_update_cluster(float* H, const float* M, int64_t In, int R, i
     case 16:
       return launch_kernel_cluster(k_update_cluster<16>, dim3(nb), dim3(kClusterThreads),
                                    cluster_smem<16>(), stream, nb, H, M, (int)In, R, N, n,
-                                   next_mode, is_last, rows, sweep, st);
+                                   next_mode, is_last, rows, sweep, st, U);
     case 32:
       return launch_kernel_cluster(k_update_cluster<32>, dim3(nb), dim3(kClusterThreads),
                                    cluster_smem<32>(), stream, nb, H, M, (int)In, R, N, n,
-                                   next_mode, is_last, rows, sweep, st);
+                                   next_mode, is_last, rows, sweep, st, U);
     default:
       return launch_kernel_cluster(k_update_cluster<64>, dim3(nb), dim3(kClusterThreads),
                                    cluster_smem<64>(), stream, nb, H, M, (int)In, R, N, n,
-                                   next_mode, is_last, rows, sweep, st);
+                                   next_mode, is_last, rows, sweep, st, U);
   }
 }
 
 cudaError_t launch_finalize(float* H, int64_t In, int R, int N, int n, int next_mode,
                             int nblocks, int is_last, int init, double tol, SolveState st,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, float* U) {
   (void)tol;
   size_t smem = ((size_t)R * R + R) * sizeof(double);
   return launch_kernel(k_finalize, dim3(1), dim3(1024), smem, stream, H, (long long)In, R, N, n,
-                       next_mode, nblocks, is_last, init, st);
+                       next_mode, nblocks, is_last, init, st, U);
 }
 
 cudaError_t launch_solve_reset(SolveState st, int R, double tol, cudaStream_t stream) {
