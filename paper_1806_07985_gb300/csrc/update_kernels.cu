@@ -1244,11 +1244,12 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
 // shares S + rho I: warp 0 of each CTA factors it (warp_cholesky32, identity
 // outside R) and lane j forms column j of its inverse P by two triangular
 // solves against the factor in shared memory.  Then one thread per row keeps
-// z, u and the right-hand side in registers; each x_i is a dot product with
-// row i of P (shared-memory broadcasts).  Rows are staged in and written
+// z, u, the right-hand side and x in registers; x accumulates the columns
+// of P (shared-memory broadcasts) times the right-hand side.  Rows are staged in and written
 // back through padded shared-memory tiles (coalesced).  z goes to H
 // (unnormalised W), u to U; the update's tail divides both by the new lambda.
-// trace(S) = 0 gives z = u = 0.
+// trace(S) = 0 gives z = u = 0.  Everything but M is staged, and the inverse
+// formed, before griddepcontrol.wait (see the kernel).
 constexpr int kAdmmRows = 64;
 
 template <int RMAX>
@@ -1256,9 +1257,6 @@ __global__ void __launch_bounds__(kAdmmRows)
 k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restrict__ M, int In,
             int R, const float* __restrict__ S, const double* __restrict__ lam, int iters,
             const int* __restrict__ flags) {
-  pdl_wait();
-  pdl_trigger();
-  if (flags[0]) return;
   __shared__ __align__(16) float P[RMAX][RMAX];
   __shared__ float Lt[32][33];
   __shared__ float Y[32][33];
@@ -1270,12 +1268,14 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
   const unsigned full = 0xffffffffu;
   const long long row0 = (long long)blockIdx.x * kAdmmRows;
   const int nrows = (int)min((long long)kAdmmRows, (long long)In - row0);
+  // H, U, S and lambda are written two or more kernels earlier (this mode's
+  // previous update, the previous mode's): staged, and the inverse formed,
+  // before griddepcontrol.wait, overlapping the predecessor; M after it
+#pragma unroll 1
   for (int e = tid; e < nrows * R; e += blockDim.x) {
     const int r = e / R, c = e - r * R;
-    const long long g = row0 * R + e;
-    Zs[r][c] = W[g];
-    Us[r][c] = U[g];
-    Ms[r][c] = M[g];
+    cp_async4(&Zs[r][c], W + row0 * R + e);
+    cp_async4(&Us[r][c], U + row0 * R + e);
   }
   if (tid < RMAX) lamf[tid] = tid < R ? (float)lam[tid] : 0.0f;
   if (tid < 32) {
@@ -1299,25 +1299,54 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
       __syncwarp();
       // lane j: L y = e_j, then L^T p = y (p = column j of the inverse), y in
       // column j of Y (each lane touches only its own column: no conflicts)
+      // (four partial sums per dot product, off one dependency chain)
 #pragma unroll 1
       for (int i = 0; i < 32; ++i) {
-        float v = i == lane ? 1.0f : 0.0f;
-#pragma unroll 4
-        for (int k = 0; k < i; ++k) v = fmaf(-Lt[i][k], Y[k][lane], v);
-        Y[i][lane] = v * dinv_s[i];
+        float v0 = i == lane ? 1.0f : 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
+        int k = 0;
+#pragma unroll 1
+        for (; k + 4 <= i; k += 4) {
+          v0 = fmaf(-Lt[i][k], Y[k][lane], v0);
+          v1 = fmaf(-Lt[i][k + 1], Y[k + 1][lane], v1);
+          v2 = fmaf(-Lt[i][k + 2], Y[k + 2][lane], v2);
+          v3 = fmaf(-Lt[i][k + 3], Y[k + 3][lane], v3);
+        }
+        for (; k < i; ++k) v0 = fmaf(-Lt[i][k], Y[k][lane], v0);
+        Y[i][lane] = ((v0 + v1) + (v2 + v3)) * dinv_s[i];
       }
 #pragma unroll 1
       for (int i = 31; i >= 0; --i) {
-        float v = Y[i][lane];
-#pragma unroll 4
-        for (int k = i + 1; k < 32; ++k) v = fmaf(-Lt[k][i], Y[k][lane], v);
-        Y[i][lane] = v * dinv_s[i];
+        float v0 = Y[i][lane], v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
+        int k = i + 1;
+#pragma unroll 1
+        for (; k + 4 <= 32; k += 4) {
+          v0 = fmaf(-Lt[k][i], Y[k][lane], v0);
+          v1 = fmaf(-Lt[k + 1][i], Y[k + 1][lane], v1);
+          v2 = fmaf(-Lt[k + 2][i], Y[k + 2][lane], v2);
+          v3 = fmaf(-Lt[k + 3][i], Y[k + 3][lane], v3);
+        }
+        for (; k < 32; ++k) v0 = fmaf(-Lt[k][i], Y[k][lane], v0);
+        Y[i][lane] = ((v0 + v1) + (v2 + v3)) * dinv_s[i];
       }
 #pragma unroll 1
       for (int i = 0; i < RMAX; ++i)
         if (lane < RMAX) P[i][lane] = (i < R && lane < R) ? Y[i][lane] : 0.0f;
     }
   }
+  pdl_wait();
+  pdl_trigger();
+  if (flags[0]) {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
+#pragma unroll 1
+  for (int e = tid; e < nrows * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    cp_async4(&Ms[r][c], M + row0 * R + e);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   const float rho = rho_s;
   if (tid < nrows) {
@@ -1332,24 +1361,30 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
       for (int it = 0; it < iters; ++it) {
         // P is reread every iteration rather than held in registers
         asm volatile("" ::: "memory");
-        float b[RMAX];
+        float b[RMAX], x[RMAX];
 #pragma unroll
-        for (int j = 0; j < RMAX; ++j) b[j] = j < R ? fmaf(rho, z[j] - u[j], Ms[tid][j]) : 0.0f;
+        for (int j = 0; j < RMAX; ++j) {
+          b[j] = j < R ? fmaf(rho, z[j] - u[j], Ms[tid][j]) : 0.0f;
+          x[j] = 0.0f;
+        }
+        // x = P b as a sum of the columns of P times b_j (P is symmetric, so
+        // column j is read as row j): RMAX independent accumulators
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) {
+          const float4* Pj = reinterpret_cast<const float4*>(&P[j][0]);
+#pragma unroll
+          for (int i4 = 0; i4 < RMAX / 4; ++i4) {
+            const float4 pv = Pj[i4];
+            x[4 * i4] = fmaf(pv.x, b[j], x[4 * i4]);
+            x[4 * i4 + 1] = fmaf(pv.y, b[j], x[4 * i4 + 1]);
+            x[4 * i4 + 2] = fmaf(pv.z, b[j], x[4 * i4 + 2]);
+            x[4 * i4 + 3] = fmaf(pv.w, b[j], x[4 * i4 + 3]);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
-          const float4* Pi = reinterpret_cast<const float4*>(&P[i][0]);
-          float x0 = 0.0f, x1 = 0.0f;
-#pragma unroll
-          for (int j4 = 0; j4 < RMAX / 4; ++j4) {
-            const float4 pv = Pi[j4];
-            x0 = fmaf(pv.x, b[4 * j4], x0);
-            x1 = fmaf(pv.y, b[4 * j4 + 1], x1);
-            x0 = fmaf(pv.z, b[4 * j4 + 2], x0);
-            x1 = fmaf(pv.w, b[4 * j4 + 3], x1);
-          }
-          const float x = x0 + x1;
-          const float zn = fmaxf(0.0f, x + u[i]);
-          u[i] = u[i] + (x - zn);
+          const float zn = fmaxf(0.0f, x[i] + u[i]);
+          u[i] = u[i] + (x[i] - zn);
           z[i] = zn;
         }
       }
