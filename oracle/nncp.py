@@ -36,6 +36,7 @@ __all__ = [
     "nnls_bpp",
     "bpp_update",
     "admm_update",
+    "apg_update",
     "normalize_columns",
     "fit_identity",
     "reconstruct",
@@ -368,6 +369,35 @@ def admm_update(M, S, Z, U, iters):
     return Z, U
 
 
+def apg_update(M, S, W0, iters):
+    """`iters` steps of Nesterov's accelerated projected gradient on every
+    row's NLS (the Nesterov-type NLS-Update Sec. II-B names), FISTA form.
+
+    Row problem: min_{x >= 0} f(x) = 1/2 x^T S x - m^T x, gradient S x - m.
+    L = max_i sum_j |S_ij| bounds the largest eigenvalue of S (Gershgorin),
+    so 1/L is a valid step.  From x_0 = y_1 = w0 and t_1 = 1, step k is
+        x_k     = max(0, y_k - (S y_k - m) / L)
+        t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+        y_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1})
+    for all rows at once; returns x after `iters` steps.  L = 0 (S = 0)
+    returns W0 unchanged.
+    """
+    M = np.asarray(M, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    X = np.array(W0, dtype=np.float64, copy=True)
+    L = float(np.max(np.sum(np.abs(S), axis=1))) if S.size else 0.0
+    if L <= 0.0:
+        return X
+    Y = X.copy()
+    t = 1.0
+    for _ in range(iters):
+        Xn = np.maximum(0.0, Y - (Y @ S - M) / L)
+        tn = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        Y = Xn + ((t - 1.0) / tn) * (Xn - X)
+        X, t = Xn, tn
+    return X
+
+
 def normalize_columns(W):
     """lambda_r = ||W(:, r)||_2 and H = W diag(lambda)^-1 (Alg. 3, column norms).
 
@@ -421,7 +451,7 @@ def hals_objective(W, M, S):
 
 
 def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
-              callback=None, nls="hals", admm_iters=5):
+              callback=None, nls="hals", admm_iters=5, apg_iters=None):
     """NNCP by block coordinate descent with one HALS sweep per block (Alg. 1, Alg. 3).
 
     nls selects Alg. 1's NLS-Update: "hals" (one HALS sweep from W = H_n
@@ -432,7 +462,9 @@ def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
     this mode's previous update left; the factor is z).  The dual is kept
     in the frame of the normalised factor: divided by the new lam when
     H_n is, multiplied by the current lam when the next update of mode n
-    starts, as z is; it starts at 0.
+    starts, as z is; it starts at 0), or "apg" (``apg_iters`` steps of
+    the accelerated projected gradient, ``apg_update``, from W = H_n
+    diag(lam); default ``admm_iters`` steps).
 
     Steps, in the paper's order:
       init   : normalise every initial factor, fold the norms into lam,
@@ -473,6 +505,9 @@ def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
             W = bpp_update(M, S)
         elif nls == "admm":
             W, U = admm_update(M, S, H[n] * state["lam"], Uhat[n] * state["lam"], admm_iters)
+        elif nls == "apg":
+            W = apg_update(M, S, H[n] * state["lam"],
+                           admm_iters if apg_iters is None else apg_iters)
         else:
             W = H[n] * state["lam"]
             hals_sweep(W, M, S)

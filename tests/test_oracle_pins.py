@@ -482,3 +482,67 @@ def test_planted_admm_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "admm_update", wrong)
     with pytest.raises(AssertionError), np.errstate(over="ignore", invalid="ignore"):
         test_admm_converges_to_library_nnls_with_its_dual(8)
+
+
+# ---- accelerated projected gradient (the Nesterov-type NLS-Update) ---------
+
+@pytest.mark.parametrize("R", [1, 3, 8, 16])
+def test_apg_converges_to_library_nnls(R):
+    scipy_optimize = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(100 + R)
+    A = rng.standard_normal((2 * R + 4, R))
+    S = A.T @ A
+    B = rng.standard_normal((6, 2 * R + 4))
+    Z = oracle.apg_update(B @ A, S, rng.random((6, R)), 2000)
+    for i in range(6):
+        z_ref, _ = scipy_optimize.nnls(A, B[i])
+        assert np.allclose(Z[i], z_ref, atol=1e-9)
+
+
+def test_apg_scalar_case_is_exact_in_one_step():
+    # R = 1: L = s, so the first projected step is max(0, m / s) exactly
+    rng = np.random.default_rng(105)
+    for _ in range(20):
+        s = float(rng.random() + 0.1)
+        m = rng.standard_normal((4, 1))
+        x = oracle.apg_update(m, np.array([[s]]), rng.random((4, 1)) * 3, 1)
+        assert np.allclose(x, np.maximum(0.0, m / s), rtol=1e-14, atol=1e-15)
+
+
+def test_apg_interior_solution_is_a_fixed_point():
+    rng = np.random.default_rng(106)
+    R = 7
+    A = rng.random((15, R)) + np.eye(15, R)
+    S = A.T @ A
+    Zs = rng.random((5, R)) + 0.1
+    assert np.allclose(oracle.apg_update(Zs @ S, S, Zs, 30), Zs, atol=1e-12)
+
+
+def test_apg_solve_limit_is_the_exact_bcd_solve():
+    dims, R = (8, 7, 6), 3
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=107, noise=0.05)
+    H0 = [h.astype(np.float64) for h in synth.init_factors(dims, R, seed=108)]
+    xd = x.astype(np.float64)
+    a = oracle.nncp_hals(xd, dims, H0, max_iters=4, nls="apg", apg_iters=4000)
+    b = oracle.nncp_hals(xd, dims, H0, max_iters=4, nls="bpp")
+    assert np.allclose(a["fits"], b["fits"], atol=1e-9)
+    for n in range(3):
+        assert np.allclose(a["H"][n], b["H"][n], atol=1e-7)
+
+
+def test_planted_apg_mistake_is_caught(monkeypatch):
+    # a gradient with the wrong sign on m is a plausible slip
+    def wrong(M, S, W0, iters):
+        X = np.array(W0, dtype=np.float64, copy=True)
+        L = float(np.max(np.sum(np.abs(S), axis=1)))
+        Y, t = X.copy(), 1.0
+        for _ in range(iters):
+            Xn = np.maximum(0.0, Y - (Y @ S + M) / L)
+            tn = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
+            Y = Xn + ((t - 1.0) / tn) * (Xn - X)
+            X, t = Xn, tn
+        return X
+
+    monkeypatch.setattr(oracle, "apg_update", wrong)
+    with pytest.raises(AssertionError):
+        test_apg_converges_to_library_nnls(8)
