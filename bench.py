@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--no-dimtree-compare", action="store_true",
                    help="skip the with / without dimension tree comparison (context line)")
     p.add_argument("--no-nls-compare", action="store_true",
-                   help="skip the HALS / block principal pivoting / ADMM NLS comparison")
+                   help="skip the comparison of the NLS updates (HALS, BPP, ADMM, APG)")
     p.add_argument("--no-4way", action="store_true",
                    help="skip the 512x512x32x16 R=24 split-2 step (context line 'hsi_4way')")
     p.add_argument("--no-batched", action="store_true",
@@ -414,19 +414,20 @@ def run_dimtree_compare(nncp, torch, steps=4):
 
 
 def run_nls_compare(nncp, torch, X, H0, prec, steps=20, max_iters=400, tol=1e-6,
-                    admm_iters=5):
+                    nls_iters=5):
     """The NLS updates of Alg. 1 on the step's workload: HALS (one sweep over
     the columns per mode update), block principal pivoting (each row's NNLS
-    solved exactly) and AO-ADMM (`admm_iters` ADMM iterations per update).
+    solved exactly), AO-ADMM and the accelerated projected gradient
+    (`nls_iters` inner iterations per update each).
     Per-iteration time of back-to-back graphs, then one solve each from the
     same start to the fit-change tolerance `tol`: iterations, device time
     and final fit."""
-    out = {"tol": tol, "max_iters": max_iters, "admm_iters": admm_iters}
-    for nls in ("hals", "bpp", "admm"):
+    out = {"tol": tol, "max_iters": max_iters, "nls_iters": nls_iters}
+    for nls in ("hals", "bpp", "admm", "apg"):
         ctx = nncp.Context(DIMS, RANK, precision=prec, root_split=1)
         ctx.set_nls(nls)
-        if nls == "admm":
-            ctx.set_admm_iters(admm_iters)
+        if nls in ("admm", "apg"):
+            ctx.set_nls_iters(nls_iters)
         ctx.set_tensor(X)
         ctx.set_factors([torch.from_numpy(h.copy()).cuda() for h in H0])
         ctx.solve_begin()

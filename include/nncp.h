@@ -104,16 +104,21 @@ nncp_status nncp_set_leaf_fusion(nncp_ctx* ctx, int enabled);
  * does; NNCP_NLS_ADMM runs a fixed number of ADMM iterations on every row
  * (AO-ADMM, one of the alternatives Sec. II-B names; rho = trace(S) / R),
  * from z = H_n diag(lambda) and the scaled dual its previous update of the
- * mode left (zero at the start of a solve), and takes z as the new W.  BPP
- * and ADMM support R <= 32 (NNCP_ERR_UNSUPPORTED above) and any precision of
- * the MTTKRPs.  Takes effect at the next solve or iteration. */
+ * mode left (zero at the start of a solve), and takes z as the new W;
+ * NNCP_NLS_APG runs a fixed number of Nesterov accelerated projected
+ * gradient steps (FISTA form, step 1/L with L the largest absolute row sum
+ * of S) from W = H_n diag(lambda).  BPP, ADMM and APG support R <= 32
+ * (NNCP_ERR_UNSUPPORTED above) and any precision of the MTTKRPs.  Takes
+ * effect at the next solve or iteration. */
 #define NNCP_NLS_HALS 0
 #define NNCP_NLS_BPP  1
 #define NNCP_NLS_ADMM 2
+#define NNCP_NLS_APG  3
 nncp_status nncp_set_nls(nncp_ctx* ctx, int nls);
-/* ADMM iterations per mode update for NNCP_NLS_ADMM: 1 <= iters <= 10000
- * (NNCP_ERR_INVALID_ARG otherwise); default 5. */
-nncp_status nncp_set_admm_iters(nncp_ctx* ctx, int iters);
+/* Inner iterations per mode update of the iterative NLS updates
+ * (NNCP_NLS_ADMM, NNCP_NLS_APG): 1 <= iters <= 10000 (NNCP_ERR_INVALID_ARG
+ * otherwise); default 5. */
+nncp_status nncp_set_nls_iters(nncp_ctx* ctx, int iters);
 /* Bytes of device scratch the context needs for its current options
  * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
 nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);

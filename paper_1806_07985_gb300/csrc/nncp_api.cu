@@ -65,8 +65,8 @@ struct nncp_ctx {
   TcScratch tc = {};
 
   bool fuse_leaf = true;              // fuse first leaf multi-TTVs into partial MTTKRPs
-  int nls = NNCP_NLS_HALS;            // NLS-Update: HALS sweep, block principal pivoting, ADMM
-  int admm_iters = 5;                 // ADMM iterations per mode update
+  int nls = NNCP_NLS_HALS;            // NLS-Update: HALS, block principal pivoting, ADMM, APG
+  int nls_iters = 5;                  // inner iterations of the ADMM and APG updates
   float* U[kMaxModes] = {};           // ADMM duals, I_n x R, normalised frame (workspace)
   cudaGraphExec_t graph = nullptr;   // one outer iteration
   cudaGraphExec_t graph4 = nullptr;  // kGraphIters outer iterations, back to back
@@ -258,16 +258,28 @@ cudaError_t pm_left(nncp_ctx* c, float* out, cudaStream_t st, const TcLeaf* leaf
 }
 
 cudaError_t update_mode(nncp_ctx* c, int n, cudaStream_t st) {
+  if (c->nls == NNCP_NLS_APG) {
+    if (cluster_update_ok(c->dims[n], c->R)) {
+      cudaError_t e = launch_apg_rows(c->H[n], c->Mbuf, c->dims[n], c->R, c->nls_iters, c->st, st);
+      if (e != cudaSuccess) return e;
+      return launch_update_cluster(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                                   n == c->N - 1, c->st, st, 0);
+    }
+    cudaError_t e = launch_apg_update(c->H[n], c->Mbuf, c->dims[n], c->R, c->nls_iters, c->st, st);
+    if (e != cudaSuccess) return e;
+    return launch_finalize(c->H[n], c->dims[n], c->R, c->N, n, (n + 1) % c->N,
+                           hals_gram_blocks(c->dims[n]), n == c->N - 1, 0, 0.0, c->st, st);
+  }
   if (c->nls == NNCP_NLS_ADMM) {
     if (cluster_update_ok(c->dims[n], c->R)) {
       cudaError_t e = launch_admm_rows(c->H[n], c->U[n], c->Mbuf, c->dims[n], c->R,
-                                       c->admm_iters, c->st, st);
+                                       c->nls_iters, c->st, st);
       if (e != cudaSuccess) return e;
       return launch_update_cluster(c->H[n], c->Mbuf, c->dims[n], c->R, c->N, n, (n + 1) % c->N,
                                    n == c->N - 1, c->st, st, 0, c->U[n]);
     }
     cudaError_t e = launch_admm_update(c->H[n], c->U[n], c->Mbuf, c->dims[n], c->R,
-                                       c->admm_iters, c->st, st);
+                                       c->nls_iters, c->st, st);
     if (e != cudaSuccess) return e;
     return launch_finalize(c->H[n], c->dims[n], c->R, c->N, n, (n + 1) % c->N,
                            hals_gram_blocks(c->dims[n]), n == c->N - 1, 0, 0.0, c->st, st,
@@ -564,22 +576,24 @@ nncp_status nncp_set_dimtree(nncp_ctx* c, int enabled) {
 
 nncp_status nncp_set_nls(nncp_ctx* c, int nls) {
   if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
-  if (nls != NNCP_NLS_HALS && nls != NNCP_NLS_BPP && nls != NNCP_NLS_ADMM)
+  if (nls != NNCP_NLS_HALS && nls != NNCP_NLS_BPP && nls != NNCP_NLS_ADMM && nls != NNCP_NLS_APG)
     return fail(c, NNCP_ERR_INVALID_ARG, "unknown NLS update %d", nls);
   if (nls == NNCP_NLS_BPP && c->R > 32)
     return fail(c, NNCP_ERR_UNSUPPORTED, "block principal pivoting supports R <= 32");
   if (nls == NNCP_NLS_ADMM && c->R > 32)
     return fail(c, NNCP_ERR_UNSUPPORTED, "the ADMM update supports R <= 32");
+  if (nls == NNCP_NLS_APG && c->R > 32)
+    return fail(c, NNCP_ERR_UNSUPPORTED, "the accelerated gradient update supports R <= 32");
   c->nls = nls;
   drop_graph(c);
   return NNCP_OK;
 }
 
-nncp_status nncp_set_admm_iters(nncp_ctx* c, int iters) {
+nncp_status nncp_set_nls_iters(nncp_ctx* c, int iters) {
   if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
   if (iters < 1 || iters > 10000)
-    return fail(c, NNCP_ERR_INVALID_ARG, "ADMM iterations %d outside 1..10000", iters);
-  c->admm_iters = iters;
+    return fail(c, NNCP_ERR_INVALID_ARG, "NLS inner iterations %d outside 1..10000", iters);
+  c->nls_iters = iters;
   drop_graph(c);
   return NNCP_OK;
 }

@@ -203,6 +203,15 @@ cudaError_t launch_admm_rows(float* H, float* U, const float* M, int64_t In, int
 cudaError_t launch_admm_update(float* H, float* U, const float* M, int64_t In, int R, int iters,
                                SolveState st, cudaStream_t stream);
 
+// Accelerated projected gradient NLS update (R <= 32): `iters` FISTA steps on
+// every row from W = H diag(lam), W into H (unnormalised).  The _update form
+// adds the Gram partials and <M, W> (then launch_finalize); the _rows form is
+// for launch_update_cluster(sweep = 0).
+cudaError_t launch_apg_rows(float* H, const float* M, int64_t In, int R, int iters,
+                           SolveState st, cudaStream_t stream);
+cudaError_t launch_apg_update(float* H, const float* M, int64_t In, int R, int iters,
+                              SolveState st, cudaStream_t stream);
+
 // Gram partials of H as given (initialisation: W = H).
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream);

@@ -1405,6 +1405,116 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
   }
 }
 
+// ---- accelerated projected gradient NLS update -------------------------------
+// `iters` steps of Nesterov's accelerated projected gradient (FISTA form) on
+// every row's NNLS, R <= RMAX <= 32: with L = max_i sum_j |S_ij| (a bound on
+// the largest eigenvalue of S), x_k = max(0, y_k - (S y_k - m) / L),
+// t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, y_{k+1} = x_k + ((t_k - 1) / t_{k+1})
+// (x_k - x_{k-1}), from x_0 = y_1 = H diag(lam).  One thread per row keeps x,
+// y and the gradient in registers; the gradient accumulates the columns of S
+// (read as rows, S being symmetric) from shared-memory broadcasts.  S, H and
+// lambda are written two or more kernels earlier and staged before
+// griddepcontrol.wait; M after it.  x goes to H (unnormalised W).  L = 0
+// leaves W = H diag(lam).
+constexpr int kApgRows = 64;
+
+template <int RMAX>
+__global__ void __launch_bounds__(kApgRows)
+k_apg_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
+           const float* __restrict__ S, const double* __restrict__ lam, int iters,
+           const int* __restrict__ flags) {
+  __shared__ __align__(16) float Ss[RMAX][RMAX];
+  __shared__ float Xs[kApgRows][RMAX + 1], Ms[kApgRows][RMAX + 1];
+  __shared__ float lamf[RMAX];
+  __shared__ float linv_s;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const unsigned full = 0xffffffffu;
+  const long long row0 = (long long)blockIdx.x * kApgRows;
+  const int nrows = (int)min((long long)kApgRows, (long long)In - row0);
+#pragma unroll 1
+  for (int e = tid; e < nrows * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    cp_async4(&Xs[r][c], W + row0 * R + e);
+  }
+  for (int e = tid; e < RMAX * RMAX; e += blockDim.x) {
+    const int a = e / RMAX, b = e - a * RMAX;
+    Ss[a][b] = (a < R && b < R) ? S[a * R + b] : 0.0f;
+  }
+  if (tid < RMAX) lamf[tid] = tid < R ? (float)lam[tid] : 0.0f;
+  if (tid < 32) {
+    // L: largest absolute row sum, lane r summing row r
+    float rs = 0.0f;
+    if (lane < R)
+      for (int j = 0; j < R; ++j) rs += fabsf(S[lane * R + j]);
+    for (int o = 16; o > 0; o >>= 1) rs = fmaxf(rs, __shfl_xor_sync(full, rs, o));
+    if (lane == 0) linv_s = rs > 0.0f ? 1.0f / rs : 0.0f;
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (flags[0]) {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
+#pragma unroll 1
+  for (int e = tid; e < nrows * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    cp_async4(&Ms[r][c], M + row0 * R + e);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const float linv = linv_s;
+  if (tid < nrows) {
+    float x[RMAX], y[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      x[j] = j < R ? Xs[tid][j] * lamf[j] : 0.0f;
+      y[j] = x[j];
+    }
+    if (linv > 0.0f) {
+      float t = 1.0f;
+#pragma unroll 1
+      for (int it = 0; it < iters; ++it) {
+        // S is reread every step rather than held in registers
+        asm volatile("" ::: "memory");
+        float g[RMAX];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) g[j] = j < R ? -Ms[tid][j] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) {
+          const float4* Sj = reinterpret_cast<const float4*>(&Ss[j][0]);
+#pragma unroll
+          for (int i4 = 0; i4 < RMAX / 4; ++i4) {
+            const float4 sv = Sj[i4];
+            g[4 * i4] = fmaf(sv.x, y[j], g[4 * i4]);
+            g[4 * i4 + 1] = fmaf(sv.y, y[j], g[4 * i4 + 1]);
+            g[4 * i4 + 2] = fmaf(sv.z, y[j], g[4 * i4 + 2]);
+            g[4 * i4 + 3] = fmaf(sv.w, y[j], g[4 * i4 + 3]);
+          }
+        }
+        const float tn = 0.5f * (1.0f + sqrtf(fmaf(4.0f * t, t, 1.0f)));
+        const float beta = (t - 1.0f) / tn;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+          const float xn = fmaxf(0.0f, fmaf(-g[i], linv, y[i]));
+          y[i] = fmaf(beta, xn - x[i], xn);
+          x[i] = xn;
+        }
+        t = tn;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j)
+      if (j < R) Xs[tid][j] = x[j];
+  }
+  __syncthreads();
+  for (int e = tid; e < nrows * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    W[row0 * R + e] = Xs[r][c];
+  }
+}
+
 __global__ void k_solve_reset(SolveState st, int R, double tol) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) st.lam[r] = 1.0;
   if (threadIdx.x == 0) {
@@ -1573,6 +1683,25 @@ cudaError_t launch_admm_rows(float* H, float* U, const float* M, int64_t In, int
 cudaError_t launch_admm_update(float* H, float* U, const float* M, int64_t In, int R, int iters,
                                SolveState st, cudaStream_t stream) {
   cudaError_t e = launch_admm_rows(H, U, M, In, R, iters, st, stream);
+  if (e != cudaSuccess) return e;
+  return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
+                       stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       st.gram_part, (const int*)st.flags, 2);
+}
+
+cudaError_t launch_apg_rows(float* H, const float* M, int64_t In, int R, int iters,
+                           SolveState st, cudaStream_t stream) {
+  if (R > 32 || In > INT32_MAX) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((In + kApgRows - 1) / kApgRows)), block(kApgRows);
+  const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
+  auto k = rmax == 8 ? k_apg_rows<8> : (rmax == 16 ? k_apg_rows<16> : k_apg_rows<32>);
+  return launch_kernel(k, grid, block, 0, stream, H, M, (int)In, R, (const float*)st.S,
+                       (const double*)st.lam, iters, (const int*)st.flags);
+}
+
+cudaError_t launch_apg_update(float* H, const float* M, int64_t In, int R, int iters,
+                              SolveState st, cudaStream_t stream) {
+  cudaError_t e = launch_apg_rows(H, M, In, R, iters, st, stream);
   if (e != cudaSuccess) return e;
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
                        stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,

@@ -47,7 +47,7 @@ _SIGNATURES = [
     ("nncp_set_dimtree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_set_leaf_fusion", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_set_nls", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    ("nncp_set_admm_iters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("nncp_set_nls_iters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_solve_host_release", None, []),
     ("nncp_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -174,8 +174,8 @@ def nncp_set_leaf_fusion(ctx, enabled):
     _check(load().nncp_set_leaf_fusion(ctx, 1 if enabled else 0), ctx)
 
 
-NNCP_NLS_HALS, NNCP_NLS_BPP, NNCP_NLS_ADMM = 0, 1, 2
-NLS = {"hals": NNCP_NLS_HALS, "bpp": NNCP_NLS_BPP, "admm": NNCP_NLS_ADMM}
+NNCP_NLS_HALS, NNCP_NLS_BPP, NNCP_NLS_ADMM, NNCP_NLS_APG = 0, 1, 2, 3
+NLS = {"hals": NNCP_NLS_HALS, "bpp": NNCP_NLS_BPP, "admm": NNCP_NLS_ADMM, "apg": NNCP_NLS_APG}
 
 
 def nncp_set_nls(ctx, nls):
@@ -184,8 +184,8 @@ def nncp_set_nls(ctx, nls):
     _check(load().nncp_set_nls(ctx, int(nls)), ctx)
 
 
-def nncp_set_admm_iters(ctx, iters):
-    _check(load().nncp_set_admm_iters(ctx, int(iters)), ctx)
+def nncp_set_nls_iters(ctx, iters):
+    _check(load().nncp_set_nls_iters(ctx, int(iters)), ctx)
 
 
 def nncp_workspace_size(ctx):
@@ -544,8 +544,8 @@ class Context:
     def set_nls(self, nls):
         nncp_set_nls(self.ctx, nls)
 
-    def set_admm_iters(self, iters):
-        nncp_set_admm_iters(self.ctx, iters)
+    def set_nls_iters(self, iters):
+        nncp_set_nls_iters(self.ctx, iters)
 
     def solve(self, max_iters, tol=0.0):
         return nncp_solve(self.ctx, self.R, max_iters, tol)

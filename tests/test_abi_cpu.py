@@ -53,7 +53,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.nncp_solve(None, 1, 0.0, None, None, None) == 1
     assert lib.nncp_set_leaf_fusion(None, 1) == 1
     assert lib.nncp_set_nls(None, 1) == 1
-    assert lib.nncp_set_admm_iters(None, 5) == 1
+    assert lib.nncp_set_nls_iters(None, 5) == 1
     lib.nncp_destroy(None)  # no-op
 
 

@@ -30,7 +30,7 @@ def _solve(nn, dims, R, iters, x, H0, prec, admm_iters, split=0):
     c = nn.Context(dims, R, precision=prec, root_split=split)
     try:
         c.set_nls("admm")
-        c.set_admm_iters(admm_iters)
+        c.set_nls_iters(admm_iters)
         Hd = [torch.from_numpy(h.copy()).cuda() for h in H0]
         c.set_tensor(torch.from_numpy(x).cuda())
         c.set_factors(Hd)
@@ -94,7 +94,7 @@ def test_admm_arguments(nn):
             c.set_nls("admm")
         for bad in (0, 10001):
             with pytest.raises(nn.NNCPError):
-                c.set_admm_iters(bad)
-        c.set_admm_iters(7)
+                c.set_nls_iters(bad)
+        c.set_nls_iters(7)
     finally:
         c.close()
