@@ -48,6 +48,10 @@ def tensor_bytes_per_iter(dims, elem_bytes=4):
     return 2 * elem_bytes * n  # two passes over the tensor (root -> each half)
 
 
+NLS_NAMES = {"hals": "HALS", "bpp": "block principal pivoting",
+             "admm": "AO-ADMM", "apg": "accelerated projected gradient"}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -59,6 +63,10 @@ def parse():
     p.add_argument("--mode", default="step", choices=["step", "pm", "batched", "serving"],
                    help="pm: only the two root partial MTTKRPs (kernel profiling); batched / "
                         "serving: only that line")
+    p.add_argument("--nls", default="hals", choices=["hals", "bpp", "admm", "apg"],
+                   help="NLS update of the timed step (default HALS, the headline line)")
+    p.add_argument("--nls-iters", type=int, default=5,
+                   help="inner iterations of the ADMM and APG updates")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-dimtree-compare", action="store_true",
@@ -226,6 +234,10 @@ def run_ours(args):
         nncp.nncp_tensor_to_bf16(X, Xuse)
     H = [torch.from_numpy(h.copy()).cuda() for h in H0]
     ctx = nncp.Context(DIMS, RANK, precision=prec, root_split=1)
+    if args.nls != "hals":
+        ctx.set_nls(args.nls)
+        if args.nls in ("admm", "apg"):
+            ctx.set_nls_iters(args.nls_iters)
     ctx.set_tensor(Xuse)
     ctx.set_factors(H)
     ctx.solve_begin()
@@ -303,7 +315,9 @@ def run_ours(args):
                          "dims": list(DIMS), "rank": RANK, "precision": prec_name,
                          "step": "one outer BCD iteration (2 root partial MTTKRPs, the mode-2 "
                                  "leaf multi-TTV fused into the second where the tensor-core "
-                                 "path allows, the mode-3 multi-TTV, 3 HALS updates, fit)",
+                                 "path allows, the mode-3 multi-TTV, 3 "
+                                 f"{NLS_NAMES[args.nls]} updates, fit)",
+                         "nls": args.nls,
                          "bytes_per_step": bytes_step,
                          "l2": "inputs larger than L2 (512 MiB tensor), no flush",
                          "parallelism": f"replicas x{world}"},
