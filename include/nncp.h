@@ -120,7 +120,8 @@ nncp_status nncp_set_nls(nncp_ctx* ctx, int nls);
  * otherwise); default 5. */
 nncp_status nncp_set_nls_iters(nncp_ctx* ctx, int iters);
 /* Bytes of device scratch the context needs for its current options
- * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state). */
+ * (dimension-tree node temporaries, split-K partials, Gram/S/lambda state,
+ * and I_n x R floats per mode for the ADMM duals). */
 nncp_status nncp_workspace_size(const nncp_ctx* ctx, size_t* bytes);
 
 /* Hand the context a caller-allocated device buffer of at least
