@@ -1242,8 +1242,8 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
 // u = u + x - z, starting from z = H diag(lam) and u = U diag(lam) (the dual
 // this mode's previous update left, in the normalised frame).  Every row
 // shares S + rho I: warp 0 of each CTA factors it (warp_cholesky32, identity
-// outside R) and lane j forms column j of its inverse P by two triangular
-// solves against the factor in shared memory.  Then one thread per row keeps
+// outside R), inverts the factor in registers (Z = L^-1) and forms
+// P = Z^T Z through a copy of Z in shared memory.  Then one thread per row keeps
 // z, u, the right-hand side and x in registers; x accumulates the columns
 // of P (shared-memory broadcasts) times the right-hand side.  Rows are staged in and written
 // back through padded shared-memory tiles (coalesced).  z goes to H
@@ -1258,9 +1258,7 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
             int R, const float* __restrict__ S, const double* __restrict__ lam, int iters,
             const int* __restrict__ flags) {
   __shared__ __align__(16) float P[RMAX][RMAX];
-  __shared__ float Lt[32][33];
-  __shared__ float Y[32][33];
-  __shared__ float dinv_s[32];
+  __shared__ __align__(16) float Zt[32][36];  // rows of L^-1 (row stride 16-byte aligned)
   __shared__ float Zs[kAdmmRows][RMAX + 1], Us[kAdmmRows][RMAX + 1], Ms[kAdmmRows][RMAX + 1];
   __shared__ float lamf[RMAX];
   __shared__ float rho_s;
@@ -1292,45 +1290,52 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
                                    : (j == lane ? 1.0f : 0.0f);
       float dinv;
       warp_cholesky32(a, dinv);
+      // Z = L^-1, lane i holding row i: right-looking forward substitution on
+      // all 32 right-hand sides at once; row k is final once scaled and is
+      // broadcast by shuffles to the rows below it
+      float z[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j <= lane) Lt[lane][j] = a[j];
-      dinv_s[lane] = dinv;
+      for (int j = 0; j < 32; ++j) z[j] = j == lane ? 1.0f : 0.0f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (lane == k) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j <= k) z[j] *= dinv;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j <= k) {
+            const float zkj = __shfl_sync(full, z[j], k);
+            if (lane > k) z[j] = fmaf(-a[k], zkj, z[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) Zt[lane][j] = j <= lane ? z[j] : 0.0f;
       __syncwarp();
-      // lane j: L y = e_j, then L^T p = y (p = column j of the inverse), y in
-      // column j of Y (each lane touches only its own column: no conflicts)
-      // (four partial sums per dot product, off one dependency chain)
+      // P = Z^T Z: lane i accumulates row i, P(i, j) = sum_k Z(k, i) Z(k, j),
+      // from broadcasts of the rows of Z, and writes it as column i (so the
+      // column reads of the update loop get P's columns as computed)
+      float pr[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) pr[j] = 0.0f;
 #pragma unroll 1
-      for (int i = 0; i < 32; ++i) {
-        float v0 = i == lane ? 1.0f : 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
-        int k = 0;
-#pragma unroll 1
-        for (; k + 4 <= i; k += 4) {
-          v0 = fmaf(-Lt[i][k], Y[k][lane], v0);
-          v1 = fmaf(-Lt[i][k + 1], Y[k + 1][lane], v1);
-          v2 = fmaf(-Lt[i][k + 2], Y[k + 2][lane], v2);
-          v3 = fmaf(-Lt[i][k + 3], Y[k + 3][lane], v3);
+      for (int k = 0; k < 32; ++k) {
+        const float zki = Zt[k][lane];
+        const float4* zr = reinterpret_cast<const float4*>(&Zt[k][0]);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 v = zr[j4];
+          pr[4 * j4] = fmaf(zki, v.x, pr[4 * j4]);
+          pr[4 * j4 + 1] = fmaf(zki, v.y, pr[4 * j4 + 1]);
+          pr[4 * j4 + 2] = fmaf(zki, v.z, pr[4 * j4 + 2]);
+          pr[4 * j4 + 3] = fmaf(zki, v.w, pr[4 * j4 + 3]);
         }
-        for (; k < i; ++k) v0 = fmaf(-Lt[i][k], Y[k][lane], v0);
-        Y[i][lane] = ((v0 + v1) + (v2 + v3)) * dinv_s[i];
       }
-#pragma unroll 1
-      for (int i = 31; i >= 0; --i) {
-        float v0 = Y[i][lane], v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
-        int k = i + 1;
-#pragma unroll 1
-        for (; k + 4 <= 32; k += 4) {
-          v0 = fmaf(-Lt[k][i], Y[k][lane], v0);
-          v1 = fmaf(-Lt[k + 1][i], Y[k + 1][lane], v1);
-          v2 = fmaf(-Lt[k + 2][i], Y[k + 2][lane], v2);
-          v3 = fmaf(-Lt[k + 3][i], Y[k + 3][lane], v3);
-        }
-        for (; k < 32; ++k) v0 = fmaf(-Lt[k][i], Y[k][lane], v0);
-        Y[i][lane] = ((v0 + v1) + (v2 + v3)) * dinv_s[i];
-      }
-#pragma unroll 1
-      for (int i = 0; i < RMAX; ++i)
-        if (lane < RMAX) P[i][lane] = (i < R && lane < R) ? Y[i][lane] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j)
+        if (lane < RMAX) P[j][lane] = (j < R && lane < R) ? pr[j] : 0.0f;
     }
   }
   pdl_wait();
