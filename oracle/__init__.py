@@ -20,6 +20,17 @@ Parity status per function (the pins are listed in each docstring):
   * normalize / fit_identity / explicit_residual / nncp_hals: pinned
     (model invariance, identity == explicit residual, exact recovery of
     noise-free low-rank tensors to < 1e-10, non-increasing objective).
+  * nnls_bpp / bpp_update: pinned (KKT conditions, scipy.optimize.nnls,
+    enumeration of every passive set for small R, special cases, the limit
+    of repeated HALS sweeps, non-decreasing fit of the solve).
+  * admm_update: pinned (convergence to scipy.optimize.nnls with the scaled
+    dual equal to -y / rho, interior fixed point, many-iteration solve equal
+    to the BPP solve).  The carry of each mode's dual across outer
+    iterations in nncp_hals(nls="admm") changes only the inner convergence
+    speed and has no external reference ("parity unpinned" for that part).
+  * apg_update: pinned (convergence to scipy.optimize.nnls, exact one-step
+    scalar case, interior fixed point, many-step solve equal to the BPP
+    solve).
   * The final-fit value of a noisy solve has no external pin: it is the
     oracle's own trajectory ("parity unpinned" for that number alone).
 """
