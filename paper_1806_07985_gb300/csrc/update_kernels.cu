@@ -1243,17 +1243,21 @@ k_bpp_rows(float* __restrict__ W, const float* __restrict__ M, int In, int R,
 // this mode's previous update left, in the normalised frame).  Every row
 // shares S + rho I: warp 0 of each CTA factors it (warp_cholesky32, identity
 // outside R), inverts the factor in registers (Z = L^-1) and forms
-// P = Z^T Z through a copy of Z in shared memory.  Then one thread per row keeps
-// z, u, the right-hand side and x in registers; x accumulates the columns
-// of P (shared-memory broadcasts) times the right-hand side.  Rows are staged in and written
-// back through padded shared-memory tiles (coalesced).  z goes to H
-// (unnormalised W), u to U; the update's tail divides both by the new lambda.
+// P = Z^T Z through a copy of Z in shared memory.  Then kAdmmSplit threads
+// share a row, each keeping z, u, m and x of its RMAX / kAdmmSplit columns in
+// registers; the right-hand side is gathered across the row's lanes by
+// shuffles and x accumulates the owned part of the columns of P.  Rows are
+// staged in and written back through padded shared-memory tiles (coalesced).
+// z goes to H (unnormalised W), u to U; the update's tail divides both by the
+// new lambda.
 // trace(S) = 0 gives z = u = 0.  Everything but M is staged, and the inverse
 // formed, before griddepcontrol.wait (see the kernel).
-constexpr int kAdmmRows = 64;
+constexpr int kAdmmSplit = 4;                    // threads per row
+constexpr int kAdmmThreads = 64;
+constexpr int kAdmmRows = kAdmmThreads / kAdmmSplit;  // rows per CTA
 
 template <int RMAX>
-__global__ void __launch_bounds__(kAdmmRows)
+__global__ void __launch_bounds__(kAdmmThreads)
 k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restrict__ M, int In,
             int R, const float* __restrict__ S, const double* __restrict__ lam, int iters,
             const int* __restrict__ flags) {
@@ -1354,52 +1358,70 @@ k_admm_rows(float* __restrict__ W, float* __restrict__ U, const float* __restric
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   const float rho = rho_s;
-  if (tid < nrows) {
-    float z[RMAX], u[RMAX];
+  // thread q of a row's group of kAdmmSplit consecutive lanes owns columns
+  // [q * OWN, (q + 1) * OWN); every lane takes part in the shuffles (rows past
+  // I_n on zeros) and only rows below I_n are written
+  constexpr int OWN = RMAX / kAdmmSplit;
+  const int row = tid / kAdmmSplit, q = tid % kAdmmSplit, c0 = q * OWN;
+  const int src0 = lane & ~(kAdmmSplit - 1);
+  const bool live = row < nrows && rho > 0.0f;
+  float z[OWN], u[OWN], m[OWN];
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) {
-      z[j] = (j < R && rho > 0.0f) ? Zs[tid][j] * lamf[j] : 0.0f;
-      u[j] = (j < R && rho > 0.0f) ? Us[tid][j] * lamf[j] : 0.0f;
-    }
-    if (rho > 0.0f) {
+  for (int k = 0; k < OWN; ++k) {
+    const int c = c0 + k;
+    const bool v = live && c < R;
+    z[k] = v ? Zs[row][c] * lamf[c] : 0.0f;
+    u[k] = v ? Us[row][c] * lamf[c] : 0.0f;
+    m[k] = v ? Ms[row][c] : 0.0f;
+  }
+  if (rho > 0.0f) {
 #pragma unroll 1
-      for (int it = 0; it < iters; ++it) {
-        // P is reread every iteration rather than held in registers
-        asm volatile("" ::: "memory");
-        float b[RMAX], x[RMAX];
+    for (int it = 0; it < iters; ++it) {
+      // P is reread every iteration rather than held in registers
+      asm volatile("" ::: "memory");
+      float bown[OWN], x[OWN];
 #pragma unroll
-        for (int j = 0; j < RMAX; ++j) {
-          b[j] = j < R ? fmaf(rho, z[j] - u[j], Ms[tid][j]) : 0.0f;
-          x[j] = 0.0f;
-        }
-        // x = P b as a sum of the columns of P times b_j (P is symmetric, so
-        // column j is read as row j): RMAX independent accumulators
+      for (int k = 0; k < OWN; ++k) {
+        bown[k] = fmaf(rho, z[k] - u[k], m[k]);
+        x[k] = 0.0f;
+      }
+      // x = P b over the owned columns: column j of P (read as row j, P being
+      // symmetric) times b_j, b_j fetched from the lane that owns column j
 #pragma unroll
-        for (int j = 0; j < RMAX; ++j) {
-          const float4* Pj = reinterpret_cast<const float4*>(&P[j][0]);
+      for (int j = 0; j < RMAX; ++j) {
+        const float bj = __shfl_sync(full, bown[j % OWN], src0 | (j / OWN));
+        if constexpr (OWN % 4 == 0) {
+          const float4* Pj = reinterpret_cast<const float4*>(&P[j][c0]);
 #pragma unroll
-          for (int i4 = 0; i4 < RMAX / 4; ++i4) {
-            const float4 pv = Pj[i4];
-            x[4 * i4] = fmaf(pv.x, b[j], x[4 * i4]);
-            x[4 * i4 + 1] = fmaf(pv.y, b[j], x[4 * i4 + 1]);
-            x[4 * i4 + 2] = fmaf(pv.z, b[j], x[4 * i4 + 2]);
-            x[4 * i4 + 3] = fmaf(pv.w, b[j], x[4 * i4 + 3]);
+          for (int k4 = 0; k4 < OWN / 4; ++k4) {
+            const float4 pv = Pj[k4];
+            x[4 * k4] = fmaf(pv.x, bj, x[4 * k4]);
+            x[4 * k4 + 1] = fmaf(pv.y, bj, x[4 * k4 + 1]);
+            x[4 * k4 + 2] = fmaf(pv.z, bj, x[4 * k4 + 2]);
+            x[4 * k4 + 3] = fmaf(pv.w, bj, x[4 * k4 + 3]);
           }
-        }
+        } else {
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i) {
-          const float zn = fmaxf(0.0f, x[i] + u[i]);
-          u[i] = u[i] + (x[i] - zn);
-          z[i] = zn;
+          for (int k = 0; k < OWN; ++k) x[k] = fmaf(P[j][c0 + k], bj, x[k]);
         }
+      }
+#pragma unroll
+      for (int k = 0; k < OWN; ++k) {
+        const float zn = fmaxf(0.0f, x[k] + u[k]);
+        u[k] = u[k] + (x[k] - zn);
+        z[k] = zn;
       }
     }
+  }
+  if (row < nrows) {
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j)
-      if (j < R) {
-        Zs[tid][j] = z[j];
-        Us[tid][j] = u[j];
+    for (int k = 0; k < OWN; ++k) {
+      const int c = c0 + k;
+      if (c < R) {
+        Zs[row][c] = z[k];
+        Us[row][c] = u[k];
       }
+    }
   }
   __syncthreads();
   for (int e = tid; e < nrows * R; e += blockDim.x) {
@@ -1678,7 +1700,7 @@ cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, Solve
 cudaError_t launch_admm_rows(float* H, float* U, const float* M, int64_t In, int R, int iters,
                             SolveState st, cudaStream_t stream) {
   if (R > 32 || In > INT32_MAX) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((In + kAdmmRows - 1) / kAdmmRows)), block(kAdmmRows);
+  const dim3 grid((unsigned)((In + kAdmmRows - 1) / kAdmmRows)), block(kAdmmThreads);
   const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
   auto k = rmax == 8 ? k_admm_rows<8> : (rmax == 16 ? k_admm_rows<16> : k_admm_rows<32>);
   return launch_kernel(k, grid, block, 0, stream, H, U, M, (int)In, R, (const float*)st.S,
