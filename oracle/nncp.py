@@ -483,6 +483,8 @@ def nncp_hals(x, dims, H_init, max_iters, tol=0.0, use_dimtree=True, s=None,
     (event "inner") with copies-free references to the live state.
     Returns a dict with H (normalised), lam, fits, iters, eps.
     """
+    if nls not in ("hals", "bpp", "admm", "apg"):
+        raise ValueError(f"unknown NLS update {nls!r}")
     dims = tuple(int(d) for d in dims)
     x = np.asarray(x, dtype=np.float64)
     N = len(dims)

@@ -546,3 +546,11 @@ def test_planted_apg_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "apg_update", wrong)
     with pytest.raises(AssertionError):
         test_apg_converges_to_library_nnls(8)
+
+
+def test_unknown_nls_update_is_refused():
+    dims = (4, 3, 2)
+    x, _ = synth.lowrank_plus_noise(dims, 2, seed=110, noise=0.0)
+    H0 = synth.init_factors(dims, 2, seed=111)
+    with pytest.raises(ValueError):
+        oracle.nncp_hals(x.astype(np.float64), dims, H0, max_iters=1, nls="bp")
