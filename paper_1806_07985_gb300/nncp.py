@@ -180,6 +180,8 @@ NLS = {"hals": NNCP_NLS_HALS, "bpp": NNCP_NLS_BPP, "admm": NNCP_NLS_ADMM, "apg":
 
 def nncp_set_nls(ctx, nls):
     if isinstance(nls, str):
+        if nls not in NLS:
+            raise ValueError(f"unknown NLS update {nls!r}; one of {sorted(NLS)}")
         nls = NLS[nls]
     _check(load().nncp_set_nls(ctx, int(nls)), ctx)
 

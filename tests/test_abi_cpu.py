@@ -59,3 +59,10 @@ def test_null_arguments_are_rejected(lib):
 
 def test_version_string(lib):
     assert b"nncp-gb300" in lib.nncp_version()
+
+
+def test_binding_refuses_unknown_nls_name():
+    from paper_1806_07985_gb300 import nncp
+    with pytest.raises(ValueError):
+        nncp.nncp_set_nls(None, "bogus")
+    assert set(nncp.NLS) == {"hals", "bpp", "admm", "apg"}
