@@ -66,3 +66,13 @@ def test_binding_refuses_unknown_nls_name():
     with pytest.raises(ValueError):
         nncp.nncp_set_nls(None, "bogus")
     assert set(nncp.NLS) == {"hals", "bpp", "admm", "apg"}
+
+
+def test_nls_codes_match_the_header():
+    import re
+    from paper_1806_07985_gb300 import nncp
+    import pathlib
+    hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "nncp.h").read_text()
+    codes = {m.group(1).lower(): int(m.group(2))
+             for m in re.finditer(r"#define NNCP_NLS_(\w+)\s+(\d+)", hdr)}
+    assert codes == nncp.NLS
