@@ -134,7 +134,7 @@ nncp_status nncp_set_workspace(nncp_ctx* ctx, void* dev_ptr, size_t bytes);
 nncp_status nncp_set_tensor(nncp_ctx* ctx, const void* X_dev);
 
 /* Point the context at the N factor matrices (device, I_n x R row-major).
- * nncp_solve reads the initial values there and leaves the result there. */
+ * nncp_solve_bound reads the initial values there and leaves the result there. */
 nncp_status nncp_set_factors(nncp_ctx* ctx, float* const* H_dev);
 
 /* M_mode = X_(mode) (H_N (.) ... (.) H_{mode+1} (.) H_{mode-1} (.) ... (.) H_1)
@@ -154,18 +154,30 @@ nncp_status nncp_mttkrp(nncp_ctx* ctx, int mode, int use_dimtree, float* M_dev);
  * Asynchronous on the context's stream. */
 nncp_status nncp_partial_mttkrp(nncp_ctx* ctx, int side, float* T_dev);
 
-/* Full NNCP-HALS solve on the tensor and factors set above.
+/* Full NNCP-HALS solve of min_{H_n >= 0} ||X - [[lambda; H_1..H_N]]||
+ * (Eq. 1) for the tensor X_dev and the factors H_dev (N device pointers,
+ * I_n x R row-major: in, the initial factors; out, the result), with the
+ * outputs of Alg. 3 (column-normalised factors, lambda, the error).
+ * X_dev / H_dev may be NULL to keep what nncp_set_tensor / nncp_set_factors
+ * bound; passing the pointers already bound keeps the captured graphs.
  * Initialisation normalises the given factors (2-norm columns) and folds the
  * norms into lambda; each outer iteration updates modes 1..N in order (BCD,
- * Alg. 1) with MTTKRPs through the dimension tree and one HALS sweep, then
- * computes fit = 1 - eps with eps from the Sec. IV-B identity.  Stops when
- * |fit_k - fit_{k-1}| < tol (k >= 2) or k = max_iters.
+ * Alg. 1) with MTTKRPs through the dimension tree and the NLS update (one HALS
+ * sweep by default, Sec. II-B), then computes fit = 1 - eps with eps from the
+ * Sec. IV-B identity.  Stops when |fit_k - fit_{k-1}| < tol (k >= 2) or
+ * k = max_iters (1 <= max_iters <= 65536).
  * On return the factors hold H_1..H_N with unit-norm columns, lambda_out
  * (host, R doubles, may be NULL) the weights, *iters_out the outer
  * iterations run and *fit_out the last fit (either pointer may be NULL).
- * Blocks until done.  NNCP_ERR_NUMERIC if the fit became non-finite. */
-nncp_status nncp_solve(nncp_ctx* ctx, int max_iters, double tol, double* lambda_out,
-                       int* iters_out, double* fit_out);
+ * Blocks until done.  NNCP_ERR_NUMERIC if the fit became non-finite,
+ * NNCP_ERR_TIMEOUT if a tensor-core kernel gave up waiting. */
+nncp_status nncp_solve(nncp_ctx* ctx, const void* X_dev, float* const* H_dev, double* lambda_out,
+                       int max_iters, double tol, int* iters_out, double* fit_out);
+
+/* nncp_solve on the tensor and factors already bound (nncp_set_tensor,
+ * nncp_set_factors); same behaviour and outputs. */
+nncp_status nncp_solve_bound(nncp_ctx* ctx, int max_iters, double tol, double* lambda_out,
+                             int* iters_out, double* fit_out);
 
 /* Per-iteration fit history of the last nncp_solve (host array of at least
  * max_iters doubles); *count receives the number of iterations. */
@@ -238,8 +250,24 @@ nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float*
 /* Solve all tensors; factors are overwritten with the normalised results.
  * iters_out[t], fits_out[t] (host, count entries) and lambda_out (host, sum of
  * R_t doubles, tensor after tensor) may each be NULL.  Blocks until done. */
-nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iters_out,
-                             double* fits_out, double* lambda_out, void* stream);
+nncp_status nncp_batch_run(nncp_batch* b, int max_iters, double tol, int* iters_out,
+                           double* fits_out, double* lambda_out, void* stream);
+
+/* One call for `count` independent problems of any orders (the Eq. 1 problem
+ * for each, with the Alg. 3 outputs): tensor t has order N[t] (2..8), mode
+ * lengths dims[t][0..N[t]-1], rank R[t], tensor X_dev[t] and factors
+ * H_dev[t][0..N[t]-1] (device, layouts as above, within the limits of
+ * nncp_batch_create).  The tensors of each order are solved together as one
+ * batch (nncp_batch_create / _run, so the same bits as that path), each
+ * stopping on its own rule.  Outputs: factors overwritten in place, lambda[t]
+ * (host, R[t] doubles; the array or an entry may be NULL), iters[t] and
+ * fits[t] (host, count entries, may be NULL).  Allocates each batch's
+ * workspace with cudaMalloc and frees it before returning; blocks until done.
+ * On an error no further order is started; nncp_global_error says why. */
+nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims, const int* R,
+                             const void* const* X_dev, float* const* const* H_dev,
+                             double* const* lambda, int max_iters, double tol, int* iters,
+                             double* fits, void* stream);
 const char* nncp_batch_last_error(const nncp_batch* b);
 void nncp_batch_destroy(nncp_batch* b);
 
@@ -295,8 +323,8 @@ nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* 
  * NNCP_SERVER_SOLO_ELEMS elements (or the threshold given to
  * nncp_server_create_ex) share
  * the batched FP32 iteration of their order (root split 1, the same bits as
- * nncp_batch_solve); larger ones, which fill the GPU alone, each run the
- * single-problem solver of nncp_solve on their own stream -- root split by
+ * nncp_batch_run); larger ones, which fill the GPU alone, each run the
+ * single-problem solver of nncp_solve_bound on their own stream -- root split by
  * nncp_default_split, the request's precision (mode 1 padded as in
  * nncp_solve_host where that lets the tensor-core path tile the shape, FP32
  * SIMT where nothing does), the same bits as nncp_solve_host with that

@@ -350,8 +350,8 @@ nncp_status nncp_batch_set_data(nncp_batch* b, const float* const* X_dev, float*
   return NNCP_OK;
 }
 
-nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iters_out,
-                             double* fits_out, double* lambda_out, void* stream) {
+nncp_status nncp_batch_run(nncp_batch* b, int max_iters, double tol, int* iters_out,
+                           double* fits_out, double* lambda_out, void* stream) {
   if (!b) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null batch");
   if (!b->have_data) return bfail(b, NNCP_ERR_INVALID_ARG, "data not set");
   if (max_iters < 1 || max_iters > b->fit_cap)
@@ -421,6 +421,67 @@ nncp_status nncp_batch_solve(nncp_batch* b, int max_iters, double tol, int* iter
   cudaEventDestroy(ev);
   for (int t = 0; t < b->count; ++t)
     if (nf[t] & 1) return bfail(b, NNCP_ERR_NUMERIC, "tensor %d: non-finite fit", t);
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims, const int* R,
+                             const void* const* X_dev, float* const* const* H_dev,
+                             double* const* lambda, int max_iters, double tol, int* iters,
+                             double* fits, void* stream) {
+  if (count < 1 || !N || !dims || !R || !X_dev || !H_dev)
+    return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null argument or empty batch");
+  for (int t = 0; t < count; ++t)
+    if (N[t] < 2 || N[t] > kMaxModes || !dims[t] || !H_dev[t])
+      return bfail(nullptr, NNCP_ERR_INVALID_ARG, "tensor %d: N=%d not in [2,8] or null shape/factors",
+                   t, N[t]);
+  // one batch per order, tensors in their given order within it
+  for (int order = 2; order <= kMaxModes; ++order) {
+    std::vector<int> idx;
+    for (int t = 0; t < count; ++t)
+      if (N[t] == order) idx.push_back(t);
+    if (idx.empty()) continue;
+    const int c = (int)idx.size();
+    std::vector<int64_t> dm((size_t)c * order);
+    std::vector<int> rk(c);
+    std::vector<const float*> xs(c);
+    std::vector<float*> hs((size_t)c * order);
+    for (int i = 0; i < c; ++i) {
+      const int t = idx[i];
+      for (int n = 0; n < order; ++n) {
+        dm[(size_t)i * order + n] = dims[t][n];
+        hs[(size_t)i * order + n] = H_dev[t][n];
+      }
+      rk[i] = R[t];
+      xs[i] = static_cast<const float*>(X_dev[t]);
+    }
+    nncp_batch* b = nullptr;
+    nncp_status st = nncp_batch_create(c, order, dm.data(), rk.data(), max_iters, &b);
+    if (st != NNCP_OK) return st;  // the message is in nncp_global_error
+    void* ws = nullptr;
+    const cudaError_t e = cudaMalloc(&ws, std::max<size_t>(b->total, 256));
+    if (e != cudaSuccess) {
+      nncp_batch_destroy(b);
+      return bfail(nullptr, NNCP_ERR_OUT_OF_MEMORY, "workspace of %zu bytes: %s", b->total,
+                   cudaGetErrorString(e));
+    }
+    std::vector<int> it(c);
+    std::vector<double> ft(c);
+    std::vector<double> lam(b->plan.lam_total > 0 ? b->plan.lam_total : 1);
+    st = nncp_batch_set_workspace(b, ws, std::max<size_t>(b->total, 256));
+    if (st == NNCP_OK) st = nncp_batch_set_data(b, xs.data(), hs.data());
+    if (st == NNCP_OK) st = nncp_batch_run(b, max_iters, tol, it.data(), ft.data(), lam.data(), stream);
+    cudaFree(ws);
+    nncp_batch_destroy(b);
+    if (st != NNCP_OK) return st;
+    size_t o = 0;
+    for (int i = 0; i < c; ++i) {
+      const int t = idx[i];
+      if (iters) iters[t] = it[i];
+      if (fits) fits[t] = ft[i];
+      if (lambda && lambda[t]) memcpy(lambda[t], lam.data() + o, (size_t)rk[i] * sizeof(double));
+      o += (size_t)rk[i];
+    }
+  }
   return NNCP_OK;
 }
 

@@ -121,7 +121,7 @@ KrpDesc krp(const nncp_ctx* c, int first, int last) {
 struct Plan {
   size_t node_off[2][kMaxModes];
   size_t node_bytes[2][kMaxModes];
-  size_t M_off, upd_off, part_off, part_cap, gram_off, G_off, S_off, lam_off, scal_off,
+  size_t M_off, upd_off, part_off, part_cap, gram_off, G_off, S_off, S32_off, lam_off, scal_off,
       fits_off, flags_off, red_off;
   size_t dual_off[kMaxModes];
   int red_nparts;
@@ -182,8 +182,9 @@ Plan make_plan(const nncp_ctx* c) {
   int maxblocks = 0;
   for (int n = 0; n < N; ++n) maxblocks = std::max(maxblocks, hals_gram_blocks(c->dims[n]));
   p.gram_off = take((size_t)maxblocks * (R * R + 1) * sizeof(double));
-  p.G_off = take((size_t)N * R * R * sizeof(float));
-  p.S_off = take((size_t)R * R * sizeof(float));
+  p.G_off = take((size_t)N * R * R * sizeof(double));
+  p.S_off = take((size_t)N * R * R * sizeof(double));
+  p.S32_off = take((size_t)R * R * sizeof(float));
   p.lam_off = take((size_t)R * sizeof(double));
   p.scal_off = take(16 * sizeof(double));
   p.fits_off = take((size_t)kFitCapacity * sizeof(double));
@@ -208,8 +209,9 @@ void bind_workspace(nncp_ctx* c) {
   c->partials = reinterpret_cast<float*>(w + p.part_off);
   c->part_cap = p.part_cap;
   c->st.gram_part = reinterpret_cast<double*>(w + p.gram_off);
-  c->st.G = reinterpret_cast<float*>(w + p.G_off);
-  c->st.S = reinterpret_cast<float*>(w + p.S_off);
+  c->st.G = reinterpret_cast<double*>(w + p.G_off);
+  c->st.S = reinterpret_cast<double*>(w + p.S_off);
+  c->st.S32 = reinterpret_cast<float*>(w + p.S32_off);
   c->st.lam = reinterpret_cast<double*>(w + p.lam_off);
   c->st.scalars = reinterpret_cast<double*>(w + p.scal_off);
   c->st.fits = reinterpret_cast<double*>(w + p.fits_off);
@@ -755,8 +757,8 @@ nncp_status nncp_iterate(nncp_ctx* c, int iters) {
   return end_on_work(c);
 }
 
-nncp_status nncp_solve(nncp_ctx* c, int max_iters, double tol, double* lambda_out,
-                       int* iters_out, double* fit_out) {
+nncp_status nncp_solve_bound(nncp_ctx* c, int max_iters, double tol, double* lambda_out,
+                             int* iters_out, double* fit_out) {
   nncp_status s = check_ready(c);
   if (s != NNCP_OK) return s;
   if (max_iters < 1) return fail(c, NNCP_ERR_INVALID_ARG, "max_iters < 1");
@@ -794,6 +796,20 @@ nncp_status nncp_solve(nncp_ctx* c, int max_iters, double tol, double* lambda_ou
   }
   if (c->host_flags[3]) return fail(c, NNCP_ERR_NUMERIC, "non-finite fit at iteration %d", iters);
   return NNCP_OK;
+}
+
+nncp_status nncp_solve(nncp_ctx* c, const void* X_dev, float* const* H_dev, double* lambda_out,
+                       int max_iters, double tol, int* iters_out, double* fit_out) {
+  if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
+  nncp_status s;
+  // rebinding only what changed keeps the captured iteration graphs
+  if (X_dev && X_dev != c->X && (s = nncp_set_tensor(c, X_dev)) != NNCP_OK) return s;
+  if (H_dev) {
+    bool same = true;
+    for (int n = 0; n < c->N; ++n) same = same && H_dev[n] == c->H[n];
+    if (!same && (s = nncp_set_factors(c, H_dev)) != NNCP_OK) return s;
+  }
+  return nncp_solve_bound(c, max_iters, tol, lambda_out, iters_out, fit_out);
 }
 
 nncp_status nncp_fit_history(const nncp_ctx* cc, double* fits, int max_count, int* count) {
@@ -916,7 +932,7 @@ static nncp_status solve_host_uncached(int N, const int64_t* dims, int R, const 
   CKH(cudaMalloc(&dws, wsb));
   if ((s = nncp_set_workspace(c, dws, wsb)) != NNCP_OK ||
       (s = nncp_set_tensor(c, Xuse)) != NNCP_OK || (s = nncp_set_factors(c, dH)) != NNCP_OK ||
-      (s = nncp_solve(c, max_iters, tol, lambda_out, iters_out, fit_out)) != NNCP_OK) {
+      (s = nncp_solve_bound(c, max_iters, tol, lambda_out, iters_out, fit_out)) != NNCP_OK) {
     g_error = c->err;
     cleanup();
     return s;
@@ -1042,7 +1058,7 @@ nncp_status nncp_solve_host(int N, const int64_t* dims, int R, const float* X_ho
     CKP(cudaMemcpyAsync(P.dH[n], H_host[n], (size_t)dims[n] * R * sizeof(float),
                         cudaMemcpyHostToDevice, st));
   }
-  if ((s = nncp_solve(P.c, max_iters, tol, lambda_out, iters_out, fit_out)) != NNCP_OK) {
+  if ((s = nncp_solve_bound(P.c, max_iters, tol, lambda_out, iters_out, fit_out)) != NNCP_OK) {
     g_error = P.c->err;
     P.release();
     return s;

@@ -80,8 +80,12 @@ struct KrpDesc {
 
 // Per-solve device state (lives in the caller's workspace).
 struct SolveState {
-  float* G;         // N x R x R, Gram of each normalised factor
-  float* S;         // R x R, Hadamard of the Grams for the mode being updated
+  double* G;        // N x R x R, Gram of each normalised factor (float64)
+  double* S;        // N x R x R: S for mode m (the Hadamard of every Gram but
+                    // G_m, float64) at S + m R^2; an update of mode n reads
+                    // its own and writes next_mode's, so the two never alias
+  float* S32;       // R x R, float32 copy of the S of the mode updated next,
+                    // read by the per-row NLS arithmetic
   double* lam;      // R
   double* gram_part;  // blocks x (R*R + 1): per-block W^T W and <M, W>
   double* scalars;  // [0] alpha = ||X||^2, [1] beta, [2] gamma, [3] eps, [4] tol,
@@ -228,7 +232,8 @@ cudaError_t launch_finalize(float* H, int64_t In, int R, int N, int n, int next_
 // lambda = 1, flags and fit counter cleared, tolerance stored (before initialisation).
 cudaError_t launch_solve_reset(SolveState st, int R, double tol, cudaStream_t stream);
 
-// S = Hadamard of every Gram but mode's (float64 and float32 copies).
+// S = Hadamard of every Gram but mode's, in float64 (st.S + mode R^2) and as
+// the float32 copy st.S32.
 cudaError_t launch_compute_S(SolveState st, int N, int R, int mode, cudaStream_t stream);
 
 // Explicit residual ||X - [[lam; H]]||^2 accumulated in float64 into out[0];

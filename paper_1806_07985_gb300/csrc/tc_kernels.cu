@@ -28,9 +28,14 @@
 //   warps 2-7   Khatri-Rao B builders, two per B stage slot (each half of the
 //               stage's 64 contraction elements), so three stages are formed
 //               concurrently (their factor-row loads are L2 latency)
-//   warps 8-15  converters (hi/lo split, transposes); warps 8-11 also run the epilogue
-//               (tcgen05.ld TMEM -> registers -> global); a unit's epilogue runs
-//               after the next unit's conversions, TMEM being double-buffered.
+//   warps 8-15  converters (hi/lo split, transposes) and the epilogue
+//               (tcgen05.ld TMEM -> registers -> global, half of the columns
+//               each); an accumulator is read after the next one's
+//               conversions, TMEM holding two.
+// Split-BF16x3 accumulates at most kSegStages stages in one TMEM accumulator
+// and adds these segments in float32 registers: the tensor core's own
+// accumulation does not round to nearest, and over a long chain of
+// nonnegative products its bias exceeded the float32-level bound.
 // A work unit is one 128-row output tile over one contraction range; when the
 // output has fewer tiles than SMs the contraction is split and the per-range
 // partials are summed afterwards in a fixed order.
@@ -71,6 +76,12 @@ constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;  // B builder row of
 // A stage even where there are fewer TMA stages.  (Six stages, which fit for
 // R <= 32, measured slower on the 512^3 root -> left contraction.)
 constexpr int kSA = 4;
+// split-BF16x3: stages (of kKC contraction elements, 8 MMAs into one
+// accumulator each) per tensor-memory accumulation chain; see TcParams::seg
+#ifndef NNCP_TC_SEG_STAGES
+#define NNCP_TC_SEG_STAGES 8
+#endif
+constexpr int kSegStages = NNCP_TC_SEG_STAGES;
 static_assert(kSA <= kMaxSF, "A stages use conv_full barrier slots");
 constexpr int kNumBars = 3 * kMaxSF + 2 * kSB + 4 + kSA + 1;
 constexpr int kMiscBytes = kNumBars * 8 + 256;
@@ -88,6 +99,14 @@ struct TcParams {
   int direct;  // MMA reads the TMA stage (no converter)
   int bf16x;   // tensor stored as bf16
   int b_resident;  // every unit spans the whole contraction: B formed once per CTA
+  // Stages accumulated in one tensor-memory accumulator before it is added into
+  // float32 registers (split-BF16x3; one segment per unit otherwise).  The
+  // tensor core adds each MMA's products into the accumulator without
+  // rounding to nearest, which biases a long chain of nonnegative terms
+  // (measured 2.5e-5 relative over 108 stages of exactly split operands);
+  // bounding the chain bounds that bias, and the segments are summed with
+  // ordinary float32 adds.
+  int seg;
   long long M, K;
   int R, Rp;
   long long n_mt, nsplit, kper, n_units;
@@ -370,8 +389,10 @@ __device__ __forceinline__ Unit get_unit(const TcParams& p, long long u) {
 // ------------------------------------------------------------------ kernel --
 
 // LEAF: the fused first multi-TTV (TcParams::leaf_I > 0), a separate
-// instantiation so that the plain kernel carries none of its code.
-template <bool LEAF>
+// instantiation so that the plain kernel carries none of its code.  SPLIT:
+// the split-BF16x3 precision (A in tensor memory, segmented accumulation),
+// separate so that neither form carries the other's registers.
+template <bool LEAF, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   // Launched in a graph with programmatic serialization, the kernel may start
@@ -407,7 +428,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
   // split-BF16x3: the converters write A (hi and lo) to tensor memory; conv_full(i)
   // then marks A stage i written, a_empty(i) its MMAs done
   auto a_empty = [&](int i) { return bar0 + 8u * (3 * kMaxSF + 2 * kSB + 4 + i); };
-  const bool a_tmem = p.mode == NNCP_SPLIT_BF16X3;
+  constexpr bool a_tmem = SPLIT;
   const uint32_t drain_bar = bar0 + 8u * (kNumBars - 1);
   uint8_t* misc = gbase + p.sm.off_bar + kNumBars * 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);
@@ -439,8 +460,9 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(acc_full(i), 1);
-      // the four epilogue warps, and with the fused leaf its four warps too
-      mbar_init(acc_empty(i), LEAF ? 8 : 4);
+      // the eight converter warps (each reads half of the accumulator
+      // columns), and with the fused leaf its four warps too
+      mbar_init(acc_empty(i), LEAF ? 12 : 8);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -513,75 +535,87 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
       uint32_t pha = 0, phb = 0;
       const int nA = kSF;
       bool ok = true;
-      long long li = 0;
       const bool split = p.mode == NNCP_SPLIT_BF16X3;
       const bool tf32 = p.mode == NNCP_TF32;
       const uint32_t idesc_full = tf32 ? make_idesc(2, Rp) : make_idesc(1, 2 * Rp);
       const uint32_t idesc_hi = make_idesc(1, Rp);
       if (p.b_resident && n_units > blockIdx.x && !mbar_wait(b_full(0), 0, abort_flag, p.err))
         ok = false;
-      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
+      // accumulator segment g (over this CTA's units) uses buffer g & 1
+      const int P = SPLIT ? p.seg : (1 << 30);
+      long long g = 0;
+      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
         const Unit w = get_unit(p, u);
-        const int bsel = (int)(li & 1);
-        if (!mbar_wait(acc_empty(bsel), (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, p.err)) break;
-        tc_fence_after();
-        const uint32_t d = tmem_base + bsel * acc_cols;
-        for (int s = 0; s < w.nk && a_tmem; ++s) {
-          // A (hi, lo) in tensor memory stage sa, B in shared memory
-          if (!mbar_wait(conv_full(sa), pha, abort_flag, p.err) ||
-              (!p.b_resident && !mbar_wait(b_full(sb), phb, abort_flag, p.err))) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t ahi = tmem_base + a_col0 + 64u * sa;
-          const uint32_t b = b0 + (p.b_resident ? s : sb) * kBBytes;
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t bd = sw128_desc(b + kk * 32);
-            mma_f16_ta(d, ahi + kk * 8, bd, idesc_full, (s > 0 || kk > 0) ? 1u : 0u);
-            mma_f16_ta(d, ahi + 32 + kk * 8, bd, idesc_hi, 1u);
-          }
-          mma_commit(a_empty(sa));
-          if (!p.b_resident) mma_commit(b_empty(sb));
-          if (++sa == nsa) { sa = 0; pha ^= 1u; }
-          if (++sb == kSB) { sb = 0; phb ^= 1u; }
-        }
-        for (int s = 0; s < w.nk && !a_tmem; ++s) {
-          const uint32_t afull = p.direct ? raw_full(sa) : conv_full(sa);
-          const uint32_t aempty = raw_empty(sa);
-          if (!mbar_wait(afull, pha, abort_flag, p.err) ||
-              (!p.b_resident && !mbar_wait(b_full(sb), phb, abort_flag, p.err))) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a = raw0 + sa * kRawBytes;
-          const uint32_t b = b0 + (p.b_resident ? s : sb) * kBBytes;
-          if (tf32) {
-            // two fp32 sub-tiles of 32 contraction elements, K = 8 per MMA
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              const uint32_t t = kk >> 2, o = (kk & 3) * 32;
-              mma_tf32(d, sw128_desc(a + t * 16384 + o), sw128_desc(b + t * Rp * 128 + o),
-                       idesc_full, (s > 0 || kk > 0) ? 1u : 0u);
+        int bsel = 0;
+        uint32_t d = tmem_base;
+        for (int s = 0, sp = 0; s < w.nk; ++s, sp = (sp + 1 == P) ? 0 : sp + 1) {
+          if (sp == 0) {
+            bsel = (int)(g & 1);
+            if (!mbar_wait(acc_empty(bsel), (uint32_t)(((g >> 1) & 1) ^ 1), abort_flag, p.err)) {
+              ok = false;
+              break;
             }
-          } else {
+            tc_fence_after();
+            d = tmem_base + bsel * acc_cols;
+          }
+          if constexpr (SPLIT) {
+            // A (hi, lo) in tensor memory stage sa, B in shared memory
+            if (!mbar_wait(conv_full(sa), pha, abort_flag, p.err) ||
+                (!p.b_resident && !mbar_wait(b_full(sb), phb, abort_flag, p.err))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ahi = tmem_base + a_col0 + 64u * sa;
+            const uint32_t b = b0 + (p.b_resident ? s : sb) * kBBytes;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t o = kk * 32;
-              mma_f16(d, sw128_desc(a + o), sw128_desc(b + o), idesc_full,
-                      (s > 0 || kk > 0) ? 1u : 0u);
-              if (split) mma_f16(d, sw128_desc(a + 16384 + o), sw128_desc(b + o), idesc_hi, 1u);
+              const uint64_t bd = sw128_desc(b + kk * 32);
+              mma_f16_ta(d, ahi + kk * 8, bd, idesc_full, (sp > 0 || kk > 0) ? 1u : 0u);
+              mma_f16_ta(d, ahi + 32 + kk * 8, bd, idesc_hi, 1u);
             }
+            mma_commit(a_empty(sa));
+            if (!p.b_resident) mma_commit(b_empty(sb));
+            if (++sa == nsa) { sa = 0; pha ^= 1u; }
+            if (++sb == kSB) { sb = 0; phb ^= 1u; }
+          } else {
+            const uint32_t afull = p.direct ? raw_full(sa) : conv_full(sa);
+            const uint32_t aempty = raw_empty(sa);
+            if (!mbar_wait(afull, pha, abort_flag, p.err) ||
+                (!p.b_resident && !mbar_wait(b_full(sb), phb, abort_flag, p.err))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a = raw0 + sa * kRawBytes;
+            const uint32_t b = b0 + (p.b_resident ? s : sb) * kBBytes;
+            if (tf32) {
+              // two fp32 sub-tiles of 32 contraction elements, K = 8 per MMA
+#pragma unroll
+              for (int kk = 0; kk < 8; ++kk) {
+                const uint32_t t = kk >> 2, o = (kk & 3) * 32;
+                mma_tf32(d, sw128_desc(a + t * 16384 + o), sw128_desc(b + t * Rp * 128 + o),
+                         idesc_full, (sp > 0 || kk > 0) ? 1u : 0u);
+              }
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t o = kk * 32;
+                mma_f16(d, sw128_desc(a + o), sw128_desc(b + o), idesc_full,
+                        (sp > 0 || kk > 0) ? 1u : 0u);
+                if (split) mma_f16(d, sw128_desc(a + 16384 + o), sw128_desc(b + o), idesc_hi, 1u);
+              }
+            }
+            mma_commit(aempty);
+            if (!p.b_resident) mma_commit(b_empty(sb));
+            if (++sa == nA) { sa = 0; pha ^= 1u; }
+            if (++sb == kSB) { sb = 0; phb ^= 1u; }
           }
-          mma_commit(aempty);
-          if (!p.b_resident) mma_commit(b_empty(sb));
-          if (++sa == nA) { sa = 0; pha ^= 1u; }
-          if (++sb == kSB) { sb = 0; phb ^= 1u; }
+          if (sp == P - 1 || s + 1 == w.nk) {
+            mma_commit(acc_full(bsel));
+            ++g;
+          }
         }
-        if (!ok) break;
-        mma_commit(acc_full(bsel));
       }
       // all MMAs issued by this thread complete before TMEM is released
       mma_commit(drain_bar);
@@ -768,8 +802,10 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         float lacc[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) lacc[i] = 0.0f;
-        long long li = 0;
-        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
+        // accumulator segments in the order the MMA warp fills them
+        const int P = SPLIT ? p.seg : (1 << 30);
+        long long g = 0;
+        for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
           const Unit w = get_unit(p, u);
           uint32_t rest = (uint32_t)w.mt / nblk;  // the host fuses only below 2^31 tiles
           float qv = lane < R ? 1.0f : 0.0f;
@@ -779,31 +815,34 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
             if (lane < R) qv *= __ldg(p.leaf_krp.H[m] + (size_t)(rest - qm * dm) * R + lane);
             rest = qm;
           }
-          const int bsel = (int)(li & 1);
-          const bool got = mbar_wait(acc_full(bsel), (uint32_t)((li >> 1) & 1), abort_flag, p.err);
-          if (!__all_sync(0xffffffffu, got)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t tbase = tmem_base + ((uint32_t)(lq * 32) << 16) + bsel * acc_cols;
+          const int nseg = (w.nk + P - 1) / P;
+          for (int sg = 0; sg < nseg; ++sg, ++g) {
+            const int bsel = (int)(g & 1);
+            const bool got = mbar_wait(acc_full(bsel), (uint32_t)((g >> 1) & 1), abort_flag, p.err);
+            if (!__all_sync(0xffffffffu, got)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem_base + ((uint32_t)(lq * 32) << 16) + bsel * acc_cols;
 #pragma unroll
-          for (int c = 0; c < 32; c += 16) {
-            if (c < Rp) {
-              float v[16], v2[16];
-              tmem_ld16(tbase + c, v);
-              if (p.mode != NNCP_TF32) tmem_ld16(tbase + Rp + c, v2);
-              tmem_ld_wait();
+            for (int c = 0; c < 32; c += 16) {
+              if (c < Rp) {
+                float v[16], v2[16];
+                tmem_ld16(tbase + c, v);
+                if (p.mode != NNCP_TF32) tmem_ld16(tbase + Rp + c, v2);
+                tmem_ld_wait();
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const float x = p.mode != NNCP_TF32 ? v[i] + v2[i] : v[i];
-                lacc[c + i] = fmaf(x, __shfl_sync(0xffffffffu, qv, c + i), lacc[c + i]);
+                for (int i = 0; i < 16; ++i) {
+                  const float x = p.mode != NNCP_TF32 ? v[i] + v2[i] : v[i];
+                  lacc[c + i] = fmaf(x, __shfl_sync(0xffffffffu, qv, c + i), lacc[c + i]);
+                }
               }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(bsel));
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(acc_empty(bsel));
         }
         // this CTA's partial of the leaf: rows [128 (blockIdx mod nblk), +128)
         const long long i_lead = (long long)(blockIdx.x % nblk) * 128 + lq * 32 + lane;
@@ -824,43 +863,68 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     // quarter, so 32 consecutive rows per warp for both sources)
     const int m = (p.contract_fast && !a_tmem) ? ((ct >> 5) * 16 + (ct & 15)) : (ct & 127);
     const int kh = (p.contract_fast && !a_tmem) ? ((ct >> 4) & 1) : (ct >> 7);
-    const bool epi_warp = warp < kWarpConv + 4;   // warps 8-11 also run the epilogue
     const int q = warp & 3;                       // TMEM lane quarter of this warp
     const bool two = p.mode != NNCP_TF32;
     int sf = 0;
     uint32_t phf = 0;
     bool ok = true;
-    long long li = 0;
-    Unit prev;
-    prev.mt = -1;
-    auto epilogue = [&](const Unit& w, long long lj) -> bool {
+    // Epilogue, shared by the eight converter warps: warps 8-11 take the first
+    // half of the 16-column accumulator chunks, warps 12-15 the rest, of the
+    // rows in their lane quarter.  A unit's accumulator arrives in segments of
+    // at most P stages (buffer g & 1 for segment g over this CTA's units);
+    // each segment is added into float32 registers, and the unit's last one
+    // writes the row to global memory.  Segment g is taken once the
+    // conversions of segment g + 1 are done (the accumulators being double
+    // buffered, the MMAs of g + 1 run meanwhile).
+    const int P = SPLIT ? p.seg : (1 << 30);
+    const int nch = Rp >> 4;
+    const int cgrp = (warp - kWarpConv) >> 2;
+    const int c_lo = cgrp == 0 ? 0 : (nch + 1) >> 1;
+    const int c_n = cgrp == 0 ? (nch + 1) >> 1 : nch >> 1;  // chunks held, at most 2
+    float acc[32];
+    struct Seg {
+      long long mt, kbeg, g;
+      int first, last;
+    };
+    Seg pend;
+    pend.g = -1;
+    long long gseg = 0;
+    auto consume = [&](const Seg& sg) -> bool {
       pdl_wait();
-      const int bsel = (int)(lj & 1);
-      const bool got = mbar_wait(acc_full(bsel), (uint32_t)((lj >> 1) & 1), abort_flag, p.err);
+      const int bsel = (int)(sg.g & 1);
+      const bool got = mbar_wait(acc_full(bsel), (uint32_t)((sg.g >> 1) & 1), abort_flag, p.err);
       if (!__all_sync(0xffffffffu, got)) return false;
       tc_fence_after();
-      const long long row = w.mt * 128 + q * 32 + lane;
-      const long long kc = w.kbeg / p.kper;
-      float* dst = p.out + (p.nsplit > 1 ? kc * p.M * R : 0) + row * R;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + bsel * acc_cols;
-      for (int c = 0; c < Rp; c += 16) {
-        float v[16], v2[16];
-        tmem_ld16(tbase + c, v);
-        if (two) tmem_ld16(tbase + Rp + c, v2);
-        tmem_ld_wait();
-        if (two) {
+      const long long row = sg.mt * 128 + q * 32 + lane;
+      const long long kc = sg.kbeg / p.kper;
+      float* dst = p.out + (p.nsplit > 1 ? kc * p.M * R : 0) + row * R;
+      const bool store = (!SPLIT || sg.last) && row < p.M;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += v2[i];
-        }
-        if (row < p.M) {
-          if ((R & 3) == 0 && c + 16 <= R) {
-            float4* d4 = reinterpret_cast<float4*>(dst + c);
+      for (int j = 0; j < 2; ++j) {
+        if (j < c_n) {
+          const int c = (c_lo + j) * 16;
+          float v[16], v2[16];
+          tmem_ld16(tbase + c, v);
+          if (two) tmem_ld16(tbase + Rp + c, v2);
+          tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          } else {
-            for (int i = 0; i < 16; ++i)
-              if (c + i < R) dst[c + i] = v[i];
+          for (int i = 0; i < 16; ++i) {
+            const float x = two ? v[i] + v2[i] : v[i];
+            acc[16 * j + i] = (!SPLIT || sg.first) ? x : acc[16 * j + i] + x;
+          }
+          if (store) {
+            if ((R & 3) == 0 && c + 16 <= R) {
+              float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                d4[i] = make_float4(acc[16 * j + 4 * i], acc[16 * j + 4 * i + 1],
+                                    acc[16 * j + 4 * i + 2], acc[16 * j + 4 * i + 3]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (c + i < R) dst[c + i] = acc[16 * j + i];
+            }
           }
         }
       }
@@ -871,9 +935,9 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     };
     int sa = 0;
     uint32_t pha = 0;
-    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++li) {
+    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const Unit w = get_unit(p, u);
-      for (int s = 0; s < w.nk && a_tmem; ++s) {
+      for (int s = 0, sp = 0; s < w.nk && SPLIT; ++s, ++sp) {
         // wait for the TMA stage and the tensor-memory A stage, then, eight
         // elements of row m (half kh) at a time, read, split into hi + lo and
         // write both to A stage sa; release the TMA stage after the last read
@@ -912,8 +976,16 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         __syncwarp();
         if (lane == 0) mbar_arrive(conv_full(sa));
         if (++sa == nsa) { sa = 0; pha ^= 1u; }
+        if (sp + 1 == P || s + 1 == w.nk) {
+          if (pend.g >= 0 && !consume(pend)) {
+            ok = false;
+            break;
+          }
+          pend = Seg{w.mt, w.kbeg, gseg++, s < P, s + 1 == w.nk};
+          sp = -1;
+        }
       }
-      for (int s = 0; s < w.nk && !p.direct && !a_tmem; ++s) {
+      for (int s = 0; s < w.nk && !p.direct && !SPLIT; ++s) {
         const bool got = mbar_wait(raw_full(sf), phf, abort_flag, p.err);
         const uint32_t st = raw0 + sf * kRawBytes;
         // read phase: this thread's 32 source elements of row m, half kh
@@ -983,13 +1055,16 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
         if (lane == 0) mbar_arrive(conv_full(sf));
         if (++sf == kSF) { sf = 0; phf ^= 1u; }
       }
+      if (!SPLIT && ok) {
+        // one segment per unit
+        if (pend.g >= 0 && !consume(pend)) ok = false;
+        pend = Seg{w.mt, w.kbeg, gseg++, 1, 1};
+      }
       // every converter warp reaches this barrier once per unit, whether or not
       // its stage loop ended early, so all of them take the same exit decision
-      if (ok && epi_warp && prev.mt >= 0 && !epilogue(prev, li - 1)) ok = false;
       if (bar_red_or(2, kConvThreads, !ok)) { ok = false; break; }
-      prev = w;
     }
-    if (epi_warp && ok && prev.mt >= 0) epilogue(prev, li - 1);
+    if (ok && pend.g >= 0) consume(pend);
   }
 
   tc_fence_before();
@@ -1133,11 +1208,15 @@ bool tc_leaf_ok(int precision, int contract_fast, int64_t IL, int64_t IR, int R,
 int* tc_error_word(const TcScratch& s) { return static_cast<int*>(s.base); }
 
 cudaError_t tc_attributes_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_partial_mttkrp<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tc_partial_mttkrp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmemMax);
+  void (*const ks[4])(CUtensorMap, TcParams) = {
+      k_tc_partial_mttkrp<false, false>, k_tc_partial_mttkrp<false, true>,
+      k_tc_partial_mttkrp<true, false>, k_tc_partial_mttkrp<true, true>};
+  for (auto k : ks) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, int64_t IL,
@@ -1179,6 +1258,7 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
   p.contract_fast = contract_fast;
   p.bf16x = bf16x;
   p.direct = contract_fast && precision != NNCP_SPLIT_BF16X3;
+  p.seg = precision == NNCP_SPLIT_BF16X3 ? kSegStages : (1 << 30);
   p.M = pl.M;
   p.K = pl.K;
   p.R = R;
@@ -1206,11 +1286,11 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
     p.leaf_part = partials;
     if (256 + (size_t)grid * 128 * R * sizeof(float) > scratch.bytes) return cudaErrorInvalidValue;
   }
-  cudaError_t e =
-      leaf ? launch_kernel(k_tc_partial_mttkrp<true>, dim3(grid), dim3(kThreads), p.sm.total, st,
-                           map, p)
-           : launch_kernel(k_tc_partial_mttkrp<false>, dim3(grid), dim3(kThreads), p.sm.total,
-                           st, map, p);
+  const bool split = precision == NNCP_SPLIT_BF16X3;
+  void (*const kern)(CUtensorMap, TcParams) =
+      leaf ? (split ? k_tc_partial_mttkrp<true, true> : k_tc_partial_mttkrp<true, false>)
+           : (split ? k_tc_partial_mttkrp<false, true> : k_tc_partial_mttkrp<false, false>);
+  cudaError_t e = launch_kernel(kern, dim3(grid), dim3(kThreads), p.sm.total, st, map, p);
   if (e != cudaSuccess) return e;
   if (leaf) {
     // the CTAs' partial leaves, summed in CTA order

@@ -32,6 +32,13 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Butterfly sum: every lane ends with the same bits (each step adds the same
+// two values in the same order on both partners).
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // One HALS sweep per row, one warp per row; lane holds columns lane + 32*j.
 // Then the block's partial W^T W (float32 over <= 64 rows, stored as double)
 // and partial <M, W>.
@@ -176,10 +183,10 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   __shared__ double cinv[kMaxRank];
   for (int r = tid; r < R; r += blockDim.x) cinv[r] = c[r] > 0.0 ? 1.0 / c[r] : 0.0;
   __syncthreads();
-  float* Gn = st.G + (long long)n * R2;
+  double* Gn = st.G + (long long)n * R2;
   for (int t = tid; t < R2; t += blockDim.x) {
     const int a = t / R, b = t % R;
-    Gn[t] = (float)(GW[t] * cinv[a] * cinv[b]);
+    Gn[t] = GW[t] * cinv[a] * cinv[b];
   }
   for (long long t = tid; t < In * R; t += blockDim.x) {
     const int r = (int)(t % R);
@@ -188,8 +195,9 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
   }
   if (is_last) {
     // gamma = lam^T (S * G_N) lam = sum_ab S_ab (W^T W)_ab
+    const double* Sn = st.S + (long long)n * R2;
     double g = 0.0;
-    for (int t = tid; t < R2; t += blockDim.x) g += (double)st.S[t] * GW[t];
+    for (int t = tid; t < R2; t += blockDim.x) g += Sn[t] * GW[t];
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
     if ((tid & 31) == 0) red[tid >> 5] = g;
     __syncthreads();
@@ -202,13 +210,14 @@ k_finalize(float* __restrict__ H, long long In, int R, int N, int n, int next_mo
     }
   }
   __syncthreads();
-  // S for the next mode: Hadamard of every Gram but next_mode's
+  // S for the next mode: Hadamard of every Gram but next_mode's (float64)
   if (next_mode >= 0) {
     for (int t = tid; t < R2; t += blockDim.x) {
-      float s = 1.0f;
+      double s = 1.0;
       for (int k = 0; k < N; ++k)
         if (k != next_mode) s *= st.G[(long long)k * R2 + t];
-      st.S[t] = s;
+      st.S[(long long)next_mode * R2 + t] = s;
+      st.S32[t] = (float)s;
     }
   }
 }
@@ -260,7 +269,7 @@ __device__ __forceinline__ FF ff_warp_sum(FF v) {
 //   The finishing CTA forms lambda, G_n, the fit at n = N and S for the next
 //   mode.  Results do not depend on arrival order.
 constexpr int kMultiThreads = 512;
-constexpr int kGpreFloats = 6144;  // other modes' Grams staged for the next S (24 KB)
+constexpr int kGpreDoubles = 3072;  // other modes' Grams staged for the next S (24 KB)
 constexpr int kMultiMaxRows = 16384;
 
 template <int RMAX>
@@ -291,11 +300,14 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   float* Hs = St + RMAX * RMAX;         // ROWS x RP: H, then W
   float* Ms = Hs + ROWS * RP;           // ROWS x RP
   float* gpart = Ms + ROWS * RP;        // GROUPS x R x R, then W^T W
-  float* Gn = gpart + GROUPS * RMAX * RMAX;  // R x R: the new G_n
-  float* Gpre = Gn + RMAX * RMAX;       // the other modes' Grams for the next S
+  // R x R: the new G_n (float64; the float offsets above are multiples of 4)
+  double* Gn = reinterpret_cast<double*>(gpart + GROUPS * RMAX * RMAX);
+  double* Gpre = Gn + RMAX * RMAX;      // the other modes' Grams for the next S
   __shared__ __align__(16) float lamf[RMAX];
+  __shared__ double linv[RMAX];
   __shared__ float sinv[RMAX];
   __shared__ FF red[T / 32];
+  __shared__ double redd[T / 32];
   __shared__ FF beta_sh;
   __shared__ double scal_sh[3];  // alpha, previous fit, tol
   __shared__ int last_sh, it_sh;
@@ -309,11 +321,11 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
 #pragma unroll
   for (int e = tid; e < RMAX * RMAX; e += T) {
     const int r = e / RMAX, c = e % RMAX;
-    St[e] = (r < R && c < R) ? st.S[c * R + r] : 0.0f;
+    St[e] = (r < R && c < R) ? st.S32[c * R + r] : 0.0f;
   }
   for (int r = tid; r < RMAX; r += T) {
     lamf[r] = r < R ? (float)st.lam[r] : 0.0f;
-    const float srr = r < R ? st.S[r * R + r] : 0.0f;
+    const float srr = r < R ? st.S32[r * R + r] : 0.0f;
     sinv[r] = srr != 0.0f ? 1.0f / srr : 0.0f;
   }
   const float* Hg = H + (long long)row0 * R;
@@ -338,7 +350,7 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   }
   // the other modes' Grams for the next S, when they fit (slots in mode order)
   const int ng = N - (next_mode == n ? 1 : 2);
-  const bool gpre = ng > 0 && ng * R2 <= kGpreFloats;
+  const bool gpre = ng > 0 && ng * R2 <= kGpreDoubles;
   if (gpre) {
     for (int k = 0, slot = 0; k < N; ++k) {
       if (k == n || k == next_mode) continue;
@@ -526,20 +538,22 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
     }
   }
   __syncthreads();
-  // lambda = column norms of W; from here on lamf holds 1 / lambda
+  // lambda = column norms of W in float64; from here on lamf holds 1 / lambda
+  // (float32, for the row scaling) and linv the float64 reciprocal
   for (int r = tid; r < R; r += T) {
-    const float g = GW[r * R + r];
-    const float l = sqrtf(g);
-    st.lam[r] = (double)l;
-    lamf[r] = g > 0.0f ? 1.0f / l : 0.0f;
+    const double g = GW[r * R + r];
+    const double l = sqrt(g);
+    st.lam[r] = l;
+    linv[r] = g > 0.0 ? 1.0 / l : 0.0;
+    lamf[r] = (float)linv[r];
   }
   __syncthreads();
-  float* Gng = st.G + (long long)n * R2;
+  double* Gng = st.G + (long long)n * R2;
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
     const int e = tid + q * T;
     if (e < R2) {
-      const float v = GW[e] * lamf[e / R] * lamf[e % R];
+      const double v = (double)GW[e] * linv[e / R] * linv[e % R];
       Gn[e] = v;
       Gng[e] = v;
     }
@@ -593,21 +607,22 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   }
   if (is_last) {
     // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
-    // float-float over the thread's terms, the warp, then the warps in order
-    FF g{0.0f, 0.0f};
+    // float64 (S of this mode, written by an earlier update) over the
+    // thread's terms, the warp, then the warps in order
+    const double* Sn = st.S + (long long)n * R2;
+    double g = 0.0;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * T;
-      if (e < R2) g = ff_add(g, FF{St[(e % R) * RMAX + e / R] * GW[e], 0.0f});
+      if (e < R2) g = fma(Sn[e], (double)GW[e], g);
     }
-    g = ff_warp_sum(g);
+    g = warp_sum_d(g);
     __syncthreads();
-    if (lane == 0) red[warp] = g;
+    if (lane == 0) redd[warp] = g;
     __syncthreads();
     if (tid == 0) {
-      FF gs{0.0f, 0.0f};
-      for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
-      const double gamma = (double)gs.hi + (double)gs.lo;
+      double gamma = 0.0;
+      for (int k = 0; k < T / 32; ++k) gamma += redd[k];
       const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
       const double alpha = scal_sh[0], prev = scal_sh[1], tol = scal_sh[2];
       const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
@@ -634,7 +649,7 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   for (int q = 0; q < EPT; ++q) {
     const int e = tid + q * T;
     if (e < R2) {
-      float s = 1.0f;
+      double s = 1.0;
       for (int k = 0, slot = 0; k < N; ++k) {
         if (k == next_mode) continue;
         if (k == n) {
@@ -644,7 +659,8 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
           ++slot;
         }
       }
-      st.S[e] = s;
+      st.S[(long long)next_mode * R2 + e] = s;
+      st.S32[e] = (float)s;
     }
   }
 }
@@ -652,9 +668,8 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
 template <int RMAX>
 size_t multi_smem() {
   using C = MultiCfg<RMAX>;
-  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP + C::GROUPS * RMAX * RMAX + RMAX * RMAX +
-                  kGpreFloats) *
-         sizeof(float);
+  return (size_t)(RMAX * RMAX + 2 * C::ROWS * C::RP + C::GROUPS * RMAX * RMAX) * sizeof(float) +
+         (size_t)(RMAX * RMAX + kGpreDoubles) * sizeof(double);
 }
 
 // ---- thread-block cluster helpers (distributed shared memory) ---------------
@@ -752,11 +767,14 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   float* gpart = Ms + kClusterRowsMax * RP;    // GROUPS x R x R
   float* Gown = gpart + GROUPS * RMAX * RMAX;  // this CTA's W^T W (read by the cluster)
   float* GW = Gown + RMAX * RMAX;              // the cluster's W^T W
-  float* Gpre = GW + RMAX * RMAX;              // the other modes' Grams, this CTA's slice
+  // float64 from here (the float offsets above are multiples of 4)
+  double* Gpre = reinterpret_cast<double*>(GW + RMAX * RMAX);  // the other modes' Grams, this CTA's slice
+  double* Sd = Gpre + kGpreDoubles;            // S of this mode (float64), for gamma
   __shared__ __align__(16) float lamf[RMAX];
   __shared__ __align__(8) double lamd[RMAX];
   __shared__ float sinv[RMAX];
   __shared__ FF red[T / 32];
+  __shared__ double redd[T / 32];
   __shared__ FF beta_own, beta_sh;
   __shared__ __align__(8) double scal_sh[4];  // alpha, tol, previous fit
   __shared__ int flag_sh[2];                  // stop flag, iteration count
@@ -774,8 +792,12 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   for (int e = tid; e < RMAX * RMAX; e += T) {
     const int j = e / RMAX, c = e % RMAX;
     const int a = ((j & ~3) + c) & (RMAX - 1);
-    if (j < R && a < R) cp_async4(Srot + e, st.S + a * R + j);
+    if (j < R && a < R) cp_async4(Srot + e, st.S32 + a * R + j);
     else Srot[e] = 0.0f;
+  }
+  if (lead && is_last) {
+#pragma unroll 1
+    for (int e = tid; e < R2; e += T) cp_async8(Sd + e, st.S + (long long)n * R2 + e);
   }
   for (int r = tid; r < R; r += T) cp_async8(lamd + r, st.lam + r);
   const float* Hg = H + (long long)row0 * R;
@@ -799,14 +821,14 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   const int ssz = (R2 + (int)nrank - 1) / (int)nrank;
   const int s0 = min(R2, (int)rank * ssz), s1 = min(R2, s0 + ssz);
   const int ng = N - (next_mode == n ? 1 : 2);
-  const bool gpre = ng > 0 && ng * ssz <= kGpreFloats;
+  const bool gpre = ng > 0 && ng * ssz <= kGpreDoubles;
   if (gpre) {
 #pragma unroll 1
     for (int k = 0, slot = 0; k < N; ++k) {
       if (k == n || k == next_mode) continue;
 #pragma unroll 1
       for (int e = s0 + tid; e < s1; e += T)
-        cp_async4(Gpre + slot * ssz + (e - s0), st.G + (long long)k * R2 + e);
+        cp_async8(Gpre + slot * ssz + (e - s0), st.G + (long long)k * R2 + e);
       ++slot;
     }
   }
@@ -1000,12 +1022,14 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   cluster_arrive();
   __syncthreads();
 
-  // ---- lambda = column norms of W; from here on lamf holds 1 / lambda
+  // ---- lambda = column norms of W in float64; from here on lamd holds
+  // 1 / lambda and lamf its float32 value (for the row scaling)
   for (int r = tid; r < R; r += T) {
-    const float g = GW[r * R + r];
-    const float l = sqrtf(g);
-    if (lead) st.lam[r] = (double)l;
-    lamf[r] = g > 0.0f ? 1.0f / l : 0.0f;
+    const double g = GW[r * R + r];
+    const double l = sqrt(g);
+    if (lead) st.lam[r] = l;
+    lamd[r] = g > 0.0 ? 1.0 / l : 0.0;
+    lamf[r] = (float)lamd[r];
   }
   __syncthreads();
   // this CTA's rows of H = W / lambda (multiplication by the float32 reciprocal)
@@ -1032,12 +1056,12 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   }
   // this CTA's slice of G_n and of S for the next mode: Hadamard of every Gram
   // but next_mode's, in mode order (mode n's is the new one)
-  float* Gng = st.G + (long long)n * R2;
+  double* Gng = st.G + (long long)n * R2;
 #pragma unroll 1
   for (int e = s0 + tid; e < s1; e += T) {
-    const float gn = GW[e] * lamf[e / R] * lamf[e % R];
+    const double gn = (double)GW[e] * lamd[e / R] * lamd[e % R];
     Gng[e] = gn;
-    float s = 1.0f;
+    double s = 1.0;
     for (int k = 0, slot = 0; k < N; ++k) {
       if (k == next_mode) continue;
       if (k == n) {
@@ -1047,24 +1071,21 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
         ++slot;
       }
     }
-    st.S[e] = s;
+    st.S[(long long)next_mode * R2 + e] = s;
+    st.S32[e] = (float)s;
   }
   if (lead && is_last) {
     // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
-    // float-float over the thread's terms, the warp, then the warps in order
-    FF g{0.0f, 0.0f};
+    // float64 over the thread's terms, the warp, then the warps in order
+    double g = 0.0;
 #pragma unroll 1
-    for (int e = tid; e < R2; e += T) {
-      const int a = e / R, b = e % R;
-      g = ff_add(g, FF{Srot[b * RMAX + ((a - (b & ~3)) & (RMAX - 1))] * GW[e], 0.0f});
-    }
-    g = ff_warp_sum(g);
-    if (lane == 0) red[warp] = g;
+    for (int e = tid; e < R2; e += T) g = fma(Sd[e], (double)GW[e], g);
+    g = warp_sum_d(g);
+    if (lane == 0) redd[warp] = g;
     __syncthreads();
     if (tid == 0) {
-      FF gs{0.0f, 0.0f};
-      for (int k = 0; k < T / 32; ++k) gs = ff_add(gs, red[k]);
-      const double gamma = (double)gs.hi + (double)gs.lo;
+      double gamma = 0.0;
+      for (int k = 0; k < T / 32; ++k) gamma += redd[k];
       const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
       const double alpha = scal_sh[0], tol = scal_sh[1], prev = scal_sh[2];
       const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
@@ -1092,8 +1113,8 @@ template <int RMAX>
 size_t cluster_smem() {
   using C = ClusterCfg<RMAX>;
   return (size_t)(RMAX * RMAX + 2 * kClusterRowsMax * C::RP + C::GROUPS * RMAX * RMAX +
-                  2 * RMAX * RMAX + kGpreFloats) *
-         sizeof(float);
+                  2 * RMAX * RMAX) * sizeof(float) +
+         (size_t)(kGpreDoubles + RMAX * RMAX) * sizeof(double);
 }
 
 // ---- warp Cholesky ------------------------------------------------------------
@@ -1558,10 +1579,11 @@ __global__ void k_solve_reset(SolveState st, int R, double tol) {
 __global__ void k_compute_S(SolveState st, int N, int R, int mode) {
   const int R2 = R * R;
   for (int t = threadIdx.x; t < R2; t += blockDim.x) {
-    float s = 1.0f;
+    double s = 1.0;
     for (int k = 0; k < N; ++k)
       if (k != mode) s *= st.G[(long long)k * R2 + t];
-    st.S[t] = s;
+    st.S[(long long)mode * R2 + t] = s;
+    st.S32[t] = (float)s;
   }
 }
 
@@ -1674,7 +1696,7 @@ cudaError_t launch_hals_gram(float* H, const float* M, int64_t In, int R, SolveS
                              cudaStream_t stream) {
   size_t smem = hals_smem(R);
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), smem, stream,
-                       H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       H, M, (long long)In, R, st.S32, (const double*)st.lam,
                        st.gram_part, (const int*)st.flags, 1);
 }
 
@@ -1684,7 +1706,7 @@ cudaError_t launch_bpp_rows(float* H, const float* M, int64_t In, int R, SolveSt
   const long long ctas = (In + kBppWarps - 1) / kBppWarps;
   const int grid = (int)std::max(1LL, std::min(ctas, (long long)num_sms * 4));
   return launch_kernel(k_bpp_rows, dim3(grid), dim3(kBppWarps * 32), 0, stream, H, M, (int)In, R,
-                       (const float*)st.S, (const int*)st.flags);
+                       st.S32, (const int*)st.flags);
 }
 
 cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, SolveState st,
@@ -1693,7 +1715,7 @@ cudaError_t launch_bpp_update(float* H, const float* M, int64_t In, int R, Solve
   if (e != cudaSuccess) return e;
   // Gram partials and <M, W> of the new W (no sweep)
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
-                       stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       stream, H, M, (long long)In, R, st.S32, (const double*)st.lam,
                        st.gram_part, (const int*)st.flags, 2);
 }
 
@@ -1703,7 +1725,7 @@ cudaError_t launch_admm_rows(float* H, float* U, const float* M, int64_t In, int
   const dim3 grid((unsigned)((In + kAdmmRows - 1) / kAdmmRows)), block(kAdmmThreads);
   const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
   auto k = rmax == 8 ? k_admm_rows<8> : (rmax == 16 ? k_admm_rows<16> : k_admm_rows<32>);
-  return launch_kernel(k, grid, block, 0, stream, H, U, M, (int)In, R, (const float*)st.S,
+  return launch_kernel(k, grid, block, 0, stream, H, U, M, (int)In, R, st.S32,
                        (const double*)st.lam, iters, (const int*)st.flags);
 }
 
@@ -1712,7 +1734,7 @@ cudaError_t launch_admm_update(float* H, float* U, const float* M, int64_t In, i
   cudaError_t e = launch_admm_rows(H, U, M, In, R, iters, st, stream);
   if (e != cudaSuccess) return e;
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
-                       stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       stream, H, M, (long long)In, R, st.S32, (const double*)st.lam,
                        st.gram_part, (const int*)st.flags, 2);
 }
 
@@ -1722,7 +1744,7 @@ cudaError_t launch_apg_rows(float* H, const float* M, int64_t In, int R, int ite
   const dim3 grid((unsigned)((In + kApgRows - 1) / kApgRows)), block(kApgRows);
   const int rmax = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
   auto k = rmax == 8 ? k_apg_rows<8> : (rmax == 16 ? k_apg_rows<16> : k_apg_rows<32>);
-  return launch_kernel(k, grid, block, 0, stream, H, M, (int)In, R, (const float*)st.S,
+  return launch_kernel(k, grid, block, 0, stream, H, M, (int)In, R, st.S32,
                        (const double*)st.lam, iters, (const int*)st.flags);
 }
 
@@ -1731,7 +1753,7 @@ cudaError_t launch_apg_update(float* H, const float* M, int64_t In, int R, int i
   cudaError_t e = launch_apg_rows(H, M, In, R, iters, st, stream);
   if (e != cudaSuccess) return e;
   return launch_kernel(k_hals_gram, dim3(hals_gram_blocks(In)), dim3(kHalsThreads), hals_smem(R),
-                       stream, H, M, (long long)In, R, (const float*)st.S, (const double*)st.lam,
+                       stream, H, M, (long long)In, R, st.S32, (const double*)st.lam,
                        st.gram_part, (const int*)st.flags, 2);
 }
 
@@ -1739,7 +1761,7 @@ cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream) {
   size_t smem = hals_smem(R);
   k_hals_gram<<<hals_gram_blocks(In), kHalsThreads, smem, stream>>>(
-      const_cast<float*>(H), nullptr, In, R, st.S, st.lam, st.gram_part, st.flags, 0);
+      const_cast<float*>(H), nullptr, In, R, st.S32, st.lam, st.gram_part, st.flags, 0);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@ is a small convenience wrapper that allocates the workspace with torch.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
@@ -56,7 +57,10 @@ _SIGNATURES = [
     ("nncp_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("nncp_partial_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("nncp_iteration_kernels", ctypes.c_int, [ctypes.c_void_p, _c_intp]),
-    ("nncp_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_dblp, _c_intp, _c_dblp]),
+    ("nncp_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_vpp, _c_dblp, ctypes.c_int,
+                                  ctypes.c_double, _c_intp, _c_dblp]),
+    ("nncp_solve_bound", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_dblp,
+                                        _c_intp, _c_dblp]),
     ("nncp_fit_history", ctypes.c_int, [ctypes.c_void_p, _c_dblp, ctypes.c_int, _c_intp]),
     ("nncp_fit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dblp]),
     ("nncp_solve_begin", ctypes.c_int, [ctypes.c_void_p]),
@@ -72,8 +76,12 @@ _SIGNATURES = [
     ("nncp_batch_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("nncp_batch_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("nncp_batch_set_data", ctypes.c_int, [ctypes.c_void_p, _c_vpp, _c_vpp]),
-    ("nncp_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_intp, _c_dblp,
-                                        _c_dblp, ctypes.c_void_p]),
+    ("nncp_batch_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_intp, _c_dblp,
+                                      _c_dblp, ctypes.c_void_p]),
+    ("nncp_batch_solve", ctypes.c_int, [ctypes.c_int, _c_intp, ctypes.POINTER(_c_i64p), _c_intp,
+                                        _c_vpp, ctypes.POINTER(_c_vpp), ctypes.POINTER(_c_dblp),
+                                        ctypes.c_int, ctypes.c_double, _c_intp, _c_dblp,
+                                        ctypes.c_void_p]),
     ("nncp_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_batch_destroy", None, [ctypes.c_void_p]),
     ("nncp_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -223,12 +231,24 @@ def nncp_iteration_kernels(ctx):
     return n.value
 
 
-def nncp_solve(ctx, R, max_iters, tol):
+def nncp_solve(ctx, R, X, H, max_iters, tol):
+    """Solve on the device tensor X and factors H (None keeps the bound ones);
+    returns (lambda, iterations, fit)."""
     lam = (ctypes.c_double * R)()
     iters = ctypes.c_int()
     fit = ctypes.c_double()
-    _check(load().nncp_solve(ctx, int(max_iters), float(tol), lam, ctypes.byref(iters),
-                             ctypes.byref(fit)), ctx)
+    harr = None if H is None else (ctypes.c_void_p * len(H))(*[int(h.data_ptr()) for h in H])
+    _check(load().nncp_solve(ctx, _ptr(X), harr, lam, int(max_iters), float(tol),
+                             ctypes.byref(iters), ctypes.byref(fit)), ctx)
+    return list(lam), iters.value, fit.value
+
+
+def nncp_solve_bound(ctx, R, max_iters, tol):
+    lam = (ctypes.c_double * R)()
+    iters = ctypes.c_int()
+    fit = ctypes.c_double()
+    _check(load().nncp_solve_bound(ctx, int(max_iters), float(tol), lam, ctypes.byref(iters),
+                                   ctypes.byref(fit)), ctx)
     return list(lam), iters.value, fit.value
 
 
@@ -283,11 +303,66 @@ def nncp_solve_host(dims, R, X_host, H_host, precision=NNCP_FP32_SIMT, root_spli
 
 
 def nncp_mttkrp_noalloc(dims, R, X, H, mode, M, stream=None):
-    """Direct MTTKRP of `mode` (1-based) that allocates nothing on the device;
-    X, H[n] and M are caller-owned CUDA tensors."""
+    """Direct MTTKRP of `mode` (1-based) that allocates nothing on the device.
+
+    X (prod(dims) float32), H[n] ((dims[n], R) float32) and M ((dims[mode-1], R)
+    float32) are caller-owned, contiguous CUDA tensors on one device; the C
+    side reads exactly those extents, so they are checked here first.  The
+    call is asynchronous on `stream` (default: torch's current stream)."""
+    import torch
+    dims = [int(d) for d in dims]
+    R = int(R)
+    if not 1 <= int(mode) <= len(dims):
+        raise ValueError(f"mode {mode} not in [1, {len(dims)}]")
+    if len(H) != len(dims):
+        raise ValueError(f"{len(H)} factors for an order-{len(dims)} tensor")
+
+    def need(t, name, shape):
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous float32")
+        if t.device != X.device:
+            raise ValueError(f"{name} is on {t.device}, X on {X.device}")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+    need(X, "X", None)
+    if X.numel() != math.prod(dims):
+        raise ValueError(f"X has {X.numel()} elements, dims give {math.prod(dims)}")
+    for n, h in enumerate(H):
+        need(h, f"H[{n}]", (dims[n], R))
+    need(M, "M", (dims[int(mode) - 1], R))
+    if stream is None:
+        with torch.cuda.device(X.device):
+            stream = torch.cuda.current_stream()
     arr = (ctypes.c_void_p * len(H))(*[int(h.data_ptr()) for h in H])
-    _check(load().nncp_mttkrp_noalloc(len(dims), _dims(dims), int(R), _ptr(X), arr, int(mode),
-                                      _ptr(M), _stream(stream)))
+    with torch.cuda.device(X.device):
+        _check(load().nncp_mttkrp_noalloc(len(dims), _dims(dims), R, _ptr(X), arr, int(mode),
+                                          _ptr(M), _stream(stream)))
+
+
+def nncp_batch_solve(shapes, ranks, X, H, max_iters, tol, stream=None):
+    """One-call batched solve of independent problems of any orders.
+
+    shapes[t]: mode lengths of tensor t; ranks[t]: its rank; X[t]: its CUDA
+    tensor; H[t]: its list of CUDA factors, overwritten with the result.
+    Returns (iters, fits, lambdas) lists."""
+    count = len(shapes)
+    Ns = (ctypes.c_int * count)(*[len(sh) for sh in shapes])
+    dim_arrs = [_dims(sh) for sh in shapes]
+    dims = (_c_i64p * count)(*[ctypes.cast(d, _c_i64p) for d in dim_arrs])
+    Rs = (ctypes.c_int * count)(*[int(r) for r in ranks])
+    xs = (ctypes.c_void_p * count)(*[int(x.data_ptr()) for x in X])
+    h_arrs = [(ctypes.c_void_p * len(h))(*[int(f.data_ptr()) for f in h]) for h in H]
+    hs = (_c_vpp * count)(*[ctypes.cast(a, _c_vpp) for a in h_arrs])
+    lam_arrs = [(ctypes.c_double * int(r))() for r in ranks]
+    lams = (_c_dblp * count)(*[ctypes.cast(a, _c_dblp) for a in lam_arrs])
+    iters = (ctypes.c_int * count)()
+    fits = (ctypes.c_double * count)()
+    _check(load().nncp_batch_solve(count, Ns, dims, Rs, xs, hs, lams, int(max_iters), float(tol),
+                                   iters, fits, _stream(stream)))
+    return list(iters), list(fits), [list(a) for a in lam_arrs]
 
 
 def _bcheck(status, b):
@@ -330,8 +405,8 @@ class Batch:
         iters = (ctypes.c_int * self.count)()
         fits = (ctypes.c_double * self.count)()
         lam = (ctypes.c_double * max(1, sum(self.ranks)))()
-        _bcheck(load().nncp_batch_solve(self.b, int(max_iters), float(tol), iters, fits, lam,
-                                        _stream(stream)), self.b)
+        _bcheck(load().nncp_batch_run(self.b, int(max_iters), float(tol), iters, fits, lam,
+                                      _stream(stream)), self.b)
         lams, o = [], 0
         for r in self.ranks:
             lams.append(list(lam[o:o + r]))
@@ -550,7 +625,13 @@ class Context:
         nncp_set_nls_iters(self.ctx, iters)
 
     def solve(self, max_iters, tol=0.0):
-        return nncp_solve(self.ctx, self.R, max_iters, tol)
+        return nncp_solve_bound(self.ctx, self.R, max_iters, tol)
+
+    def solve_on(self, X, H, max_iters, tol=0.0):
+        """nncp_solve with the tensor and factors passed in the call."""
+        self._keep = [X] + self._keep[1:] if self._keep else [X]
+        self._factors = list(H)
+        return nncp_solve(self.ctx, self.R, X, self._factors, max_iters, tol)
 
     def fit_history(self, max_count=1 << 16):
         return nncp_fit_history(self.ctx, max_count)

@@ -50,7 +50,11 @@ def test_null_arguments_are_rejected(lib):
     assert lib.nncp_create(3, None, 4, None) == 1
     assert lib.nncp_set_options(None, 0, 0, None) == 1
     assert lib.nncp_mttkrp(None, 1, 0, None) == 1
-    assert lib.nncp_solve(None, 1, 0.0, None, None, None) == 1
+    assert lib.nncp_solve(None, None, None, None, 1, 0.0, None, None) == 1
+    assert lib.nncp_solve_bound(None, 1, 0.0, None, None, None) == 1
+    assert lib.nncp_batch_solve(0, None, None, None, None, None, None, 1, 0.0, None, None,
+                                None) == 1
+    assert lib.nncp_batch_run(None, 1, 0.0, None, None, None, None) == 1
     assert lib.nncp_set_leaf_fusion(None, 1) == 1
     assert lib.nncp_set_nls(None, 1) == 1
     assert lib.nncp_set_nls_iters(None, 5) == 1

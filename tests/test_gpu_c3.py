@@ -33,12 +33,10 @@ def data():
     return x, H0
 
 
-# split-BF16x3 keeps ~16 bits of each operand (hi + lo, each rounded to bf16's
-# 8 bits): up to 2^-16 relative per operand.  On random data the residuals
-# cancel over long sums (1e-5 holds, see test_gpu_tc.py); this tensor's
-# Gaussian-smoothed spatial factors make neighbouring residuals alike, and the
-# 262144-term contraction of modes 3 and 4 measures 3.3e-5.
-@pytest.mark.parametrize("precision,tol", [("fp32_simt", 1e-5), ("split_bf16x3", 5e-5),
+# FP32 SIMT and split-BF16x3 are held to the float32-equivalent 1e-5; TF32
+# (10-bit operand mantissas) to 2e-3.  Split-BF16x3's 262144-term contraction
+# of modes 1-2 is where a long tensor-core accumulation chain would show.
+@pytest.mark.parametrize("precision,tol", [("fp32_simt", 1e-5), ("split_bf16x3", 1e-5),
                                            ("tf32", 2e-3)])
 def test_c3_sampled_rows_every_mode(nn, data, precision, tol):
     x, H0 = data
@@ -74,9 +72,9 @@ def oracle3(data):
     return ref
 
 
-# The Sec. IV-B identity turns an MTTKRP error e into ~e/eps^2 of eps^2 (here
-# eps ~ 0.05): split-BF16x3's 3e-5 on this tensor moves the identity's fit by
-# ~6e-4, so that mode is held to the explicit residual of its own factors.
+# Three outer iterations against the FP64 oracle: factors and lambda 1e-3,
+# the Sec. IV-B identity fit 1e-4 absolute, and for split-BF16x3 also the
+# explicit residual of its own factors 1e-4.
 @pytest.mark.parametrize("precision", ["fp32_simt", "split_bf16x3"])
 def test_c3_solve_matches_oracle(nn, data, oracle3, precision):
     x, H0 = data
@@ -94,10 +92,8 @@ def test_c3_solve_matches_oracle(nn, data, oracle3, precision):
         for n in range(4):
             assert rel_fro(H[n].cpu().numpy(), ref["H"][n]) <= 1e-3, (precision, n)
         assert rel_fro(np.array(lam), ref["lam"]) <= 1e-3
-        if precision == "fp32_simt":
-            assert abs(fit - ref["fits"][-1]) <= 1e-4, (fit, ref["fits"][-1])
-        else:
-            assert abs(fit - ref["fits"][-1]) <= 2e-3, (fit, ref["fits"][-1])
+        assert abs(fit - ref["fits"][-1]) <= 1e-4, (fit, ref["fits"][-1])
+        if precision == "split_bf16x3":
             exact = c.fit(exact=True)
             assert abs(exact - ref["fit_exact"]) <= 1e-4, (exact, ref["fit_exact"])
     finally:
