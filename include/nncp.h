@@ -303,6 +303,20 @@ nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* 
                                 const float* const* H_dev, int mode, float* M_dev,
                                 void* stream);
 
+/* Throughput probe (a measurement utility; the paper has no counterpart): one
+ * launch on `stream` of a kernel that runs at the device's peak rate of
+ *   kind 0: float32 FFMA on the CUDA cores (8 independent chains per thread,
+ *           2048 threads per SM), the bound of NNCP_FP32_SIMT;
+ *   kind 1: dense tcgen05 MMAs, kind::tf32, M = 128, N = 256, operands in
+ *           shared memory, one CTA per SM (the bound of NNCP_TF32);
+ *   kind 2: the same with kind::f16 bf16 operands.
+ * reps (1..2^24) scales the work; *flops_out receives the floating-point
+ * operations the launch performs (2 per multiply-add).  sink_dev: 16 bytes
+ * of device memory, 16-byte aligned, that the kernels may write (the MMA
+ * probe sets its first int to 1 if its bounded wait expired).  The caller
+ * times the launch with events on the stream. */
+nncp_status nncp_peak_probe(int kind, int reps, void* sink_dev, void* stream, double* flops_out);
+
 /* ---- Server: continuous batching of independent solve requests ----------
  * Each request is one NNCP-HALS problem (Alg. 1 with the normalisation and
  * error steps of Alg. 3, Sec. II-B HALS, Sec. IV-B fit; the paper has no

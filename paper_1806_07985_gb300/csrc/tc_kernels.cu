@@ -1302,3 +1302,136 @@ cudaError_t tc_partial_mttkrp(int precision, int contract_fast, const void* X, i
 }
 
 }  // namespace nncp
+
+// ------------------------------------------------------------ peak probes --
+// Throughput probes that give the roofline fractions of the compute-bound
+// paths a measured denominator: float32 FFMA on the CUDA cores, and dense
+// tcgen05 MMAs (kind::tf32 and kind::f16 bf16, M = 128, N = 256, operands in
+// shared memory, accumulator in tensor memory), one CTA per SM.  The caller
+// times the launch with events on the stream.
+
+namespace nncp {
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+__global__ void __launch_bounds__(kProbeThreads)
+k_probe_ffma(int reps, float seed, float* sink) {
+  float a[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) a[c] = seed + (float)(threadIdx.x + c);
+  const float m = 0.999999f, b = 1e-7f;
+#pragma unroll 1
+  for (int i = 0; i < reps; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) a[c] = fmaf(a[c], m, b);
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) s += a[c];
+  if (s == 12345.678f) sink[0] = s;  // keeps the chains live
+}
+
+// One elected thread issues `reps` x 4 MMAs of M = 128, N = 256 into one
+// tensor-memory accumulator from zero-filled shared-memory operands.
+template <bool TF32>
+__global__ void __launch_bounds__(128, 1) k_probe_mma(int reps, int* err) {
+  extern __shared__ uint8_t psm[];
+  const uint32_t raw = smem_u32(psm);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* g = psm + (base - raw);
+  const uint32_t a0 = base, b0 = base + 16384;           // A 128 x 128 B, B 256 x 128 B
+  const uint32_t bar = base + 16384 + 32768;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(g + 16384 + 32768 + 64);
+  for (int i = threadIdx.x; i < (16384 + 32768) / 16; i += blockDim.x)
+    sts128(base + 16 * i, 0u, 0u, 0u, 0u);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(256u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, 256u);
+    for (int i = 0; i < reps; ++i) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = sw128_desc(a0 + kk * 32), bd = sw128_desc(b0 + kk * 32);
+        if (TF32)
+          mma_tf32(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        else
+          mma_f16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      }
+    }
+    mma_commit(bar);
+    const long long t0 = clock64();
+    bool done = false;
+    while (!(done = mbar_test(bar, 0)) && clock64() - t0 < kWaitCycles) {
+    }
+    if (!done) atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                 : "memory");
+  }
+}
+
+}  // namespace
+}  // namespace nncp
+
+extern "C" nncp_status nncp_peak_probe(int kind, int reps, void* sink_dev, void* stream,
+                                       double* flops_out) {
+  using namespace nncp;
+  if (reps < 1 || reps > (1 << 24) || !flops_out || !sink_dev ||
+      (reinterpret_cast<uintptr_t>(sink_dev) & 15)) {
+    record_global_error("nncp_peak_probe: reps in [1, 2^24], flops_out and a 16-byte aligned sink");
+    return NNCP_ERR_INVALID_ARG;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    record_global_error("nncp_peak_probe: no device");
+    return NNCP_ERR_CUDA;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (kind == 0) {
+    const int blocks = sms * 8;  // 2048 threads per SM
+    e = launch_kernel(k_probe_ffma, dim3(blocks), dim3(kProbeThreads), 0, st, reps, 1.0f,
+                      static_cast<float*>(sink_dev));
+    *flops_out = 2.0 * kProbeChains * 16 * (double)reps * blocks * kProbeThreads;
+  } else if (kind == 1 || kind == 2) {
+    const int smem = 1024 + 16384 + 32768 + 128;
+    auto k = kind == 1 ? k_probe_mma<true> : k_probe_mma<false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = launch_kernel(k, dim3(sms), dim3(128), smem, st, reps, static_cast<int*>(sink_dev));
+    // K per MMA: 8 (tf32) or 16 (bf16) elements of a 32-byte step
+    *flops_out = 2.0 * 128 * 256 * (kind == 1 ? 8 : 16) * 4.0 * reps * sms;
+  } else {
+    record_global_error("nncp_peak_probe: kind must be 0 (FFMA), 1 (TF32 MMA) or 2 (BF16 MMA)");
+    return NNCP_ERR_INVALID_ARG;
+  }
+  if (e != cudaSuccess) {
+    record_global_error(cudaGetErrorString(e));
+    return NNCP_ERR_CUDA;
+  }
+  return NNCP_OK;
+}

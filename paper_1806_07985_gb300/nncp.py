@@ -97,6 +97,8 @@ _SIGNATURES = [
     ("nncp_server_clock", ctypes.c_double, [ctypes.c_void_p]),
     ("nncp_server_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_server_destroy", None, [ctypes.c_void_p]),
+    ("nncp_peak_probe", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       _c_dblp]),
     ("nncp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_global_error", ctypes.c_char_p, []),
     ("nncp_destroy", None, [ctypes.c_void_p]),
@@ -363,6 +365,19 @@ def nncp_batch_solve(shapes, ranks, X, H, max_iters, tol, stream=None):
     _check(load().nncp_batch_solve(count, Ns, dims, Rs, xs, hs, lams, int(max_iters), float(tol),
                                    iters, fits, _stream(stream)))
     return list(iters), list(fits), [list(a) for a in lam_arrs]
+
+
+PROBES = {"ffma": 0, "tf32": 1, "bf16": 2}
+
+
+def nncp_peak_probe(kind, reps, sink, stream=None):
+    """Launch one throughput probe (kind "ffma", "tf32" or "bf16"; see the
+    header); returns the floating-point operations it performs.  sink: a
+    CUDA tensor of at least 16 bytes."""
+    flops = ctypes.c_double()
+    _check(load().nncp_peak_probe(PROBES.get(kind, kind), int(reps), _ptr(sink), _stream(stream),
+                                  ctypes.byref(flops)))
+    return flops.value
 
 
 def _bcheck(status, b):

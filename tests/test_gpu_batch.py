@@ -133,3 +133,41 @@ def test_batch_bits_do_not_depend_on_the_widest_rank(nn):
         assert k1[t] == k2[t] and f1[t] == f2[t] and l1[t] == l2[t]
         for a, b in zip(H1[t], H2[t]):
             assert np.array_equal(a, b)
+
+
+def test_one_call_batch_solve_mixed_orders(nn):
+    # nncp_batch_solve: tensors of orders 3 and 4 interleaved in one call; each
+    # order is solved as its own batch, so the bits equal the batch path's, and
+    # the results match the oracle
+    p3 = _problems(4, seed0=11, N=3, hi=30)
+    p4 = _problems(3, seed0=12, N=4, hi=12)
+    mixed = [p3[0], p4[0], p3[1], p3[2], p4[1], p4[2], p3[3]]
+    iters = 8
+    X = [torch.from_numpy(p[2]).cuda() for p in mixed]
+    H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in mixed]
+    k, fits, lams = nn.nncp_batch_solve([p[0] for p in mixed], [p[1] for p in mixed], X, H,
+                                        iters, 0.0)
+    Hs = [[h.cpu().numpy() for h in hs] for hs in H]
+    for probs in (p3, p4):
+        kb, fb, lb, Hb = _run_batch(nn, probs, iters)
+        for i, p in enumerate(probs):
+            t = next(j for j, q in enumerate(mixed) if q is p)
+            assert k[t] == kb[i] == iters
+            assert fits[t] == fb[i]
+            assert lams[t] == lb[i]
+            for n in range(len(p[0])):
+                assert np.array_equal(Hs[t][n], Hb[i][n])
+    for t, (dims, R, x, H0) in enumerate(mixed):
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=iters, use_dimtree=True, s=1)
+        assert abs(fits[t] - ref["fits"][-1]) <= 1e-4, t
+        assert rel_fro(np.array(lams[t]), ref["lam"]) <= 1e-3, t
+
+
+def test_one_call_batch_solve_rejects_bad_orders(nn):
+    dims, R = (8, 6, 5), 2
+    X = [torch.zeros(240, device="cuda")]
+    H = [[torch.zeros(d, R, device="cuda") for d in dims]]
+    with pytest.raises(nn.NNCPError) as info:
+        nn.nncp_batch_solve([(8,)], [R], X, [H[0][:1]], 2, 0.0)  # order 1
+    assert info.value.status == nn.NNCP_ERR_INVALID_ARG

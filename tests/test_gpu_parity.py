@@ -272,3 +272,35 @@ def test_update_configurations_match_oracle(nn, dims, R):
     for n in range(len(dims)):
         assert rel_fro(Hg[n], ref["H"][n]) <= 1e-4, n
     assert rel_fro(lam, ref["lam"]) <= 1e-4
+
+
+def test_solve_with_tensor_and_factors_in_the_call(nn):
+    # nncp_solve(ctx, X, H, ...) binds the tensor and factors itself: the same
+    # bits as binding them first and calling nncp_solve_bound, and the oracle's
+    # result
+    dims, R = (30, 26, 22), 5
+    x, _ = synth.lowrank_plus_noise(dims, R, seed=41, noise=0.01)
+    H0 = synth.init_factors(dims, R, seed=42)
+    ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                           max_iters=6, use_dimtree=True)
+    c, X, Hd = _ctx(nn, dims, R, x, H0)
+    try:
+        lam_a, k_a, fit_a = c.solve(6)
+        Ha = [h.cpu().numpy() for h in Hd]
+        H2 = [_dev(h) for h in H0]
+        X2 = _dev(x)
+        lam_b, k_b, fit_b = c.solve_on(X2, H2, 6)
+        Hb = [h.cpu().numpy() for h in H2]
+        # the pointers just bound again: graphs kept, same bits
+        for h, h0 in zip(H2, H0):
+            h.copy_(torch.from_numpy(h0))
+        lam_c, k_c, fit_c = c.solve_on(X2, H2, 6)
+    finally:
+        c.close()
+    assert k_a == k_b == k_c == 6
+    assert lam_a == lam_b == lam_c and fit_a == fit_b == fit_c
+    for a, b in zip(Ha, Hb):
+        assert np.array_equal(a, b)
+    assert abs(fit_b - ref["fits"][-1]) <= FIT_TOL
+    for n in range(3):
+        assert rel_fro(Hb[n], ref["H"][n]) <= 1e-3
