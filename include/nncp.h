@@ -154,6 +154,23 @@ nncp_status nncp_mttkrp(nncp_ctx* ctx, int mode, int use_dimtree, float* M_dev);
  * Asynchronous on the context's stream. */
 nncp_status nncp_partial_mttkrp(nncp_ctx* ctx, int side, float* T_dev);
 
+/* M_mode through the dimension tree (Sec. IV-A, Fig. 1) for the current
+ * factors, reusing the tree nodes that earlier calls left and whose factors
+ * have not changed since: a node {a..b} holds the tensor contracted with
+ * every factor outside modes a..b, and is recomputed only when one of those
+ * was reported changed by nncp_factor_changed.  Called in BCD order (modes
+ * 1..N, each factor reported changed right after its update) this reads the
+ * tensor twice per sweep -- the local MTTKRP of Alg. 2, whose factor updates
+ * happen outside the library.  M_dev: I_mode x R row-major, device.
+ * Asynchronous on the context's stream.  Any other call that computes
+ * (nncp_mttkrp, nncp_partial_mttkrp, a solve) or rebinds data forgets the
+ * cached nodes. */
+nncp_status nncp_mttkrp_cached(nncp_ctx* ctx, int mode, float* M_dev);
+
+/* Reports that the caller has changed factor `mode` (1..N) in place: tree
+ * nodes computed from it are recomputed at their next use. */
+nncp_status nncp_factor_changed(nncp_ctx* ctx, int mode);
+
 /* Full NNCP-HALS solve of min_{H_n >= 0} ||X - [[lambda; H_1..H_N]]||
  * (Eq. 1) for the tensor X_dev and the factors H_dev (N device pointers,
  * I_n x R row-major: in, the initial factors; out, the result), with the
@@ -302,6 +319,81 @@ void nncp_batch_destroy(nncp_batch* b);
 nncp_status nncp_mttkrp_noalloc(int N, const int64_t* dims, int R, const float* X_dev,
                                 const float* const* H_dev, int mode, float* M_dev,
                                 void* stream);
+
+/* ---- Par-NNCP: one processor of a P_1 x ... x P_N grid (Alg. 2) ---------
+ * The tensor is block-partitioned (Sec. IV-C "Data Distribution"): mode n is
+ * cut into P_n contiguous blocks, block k = [floor(k I_n / P_n),
+ * floor((k+1) I_n / P_n)), and processor p = (p_1..p_N) holds the block of its
+ * coordinates, stored mode-1 fastest.  Every processor of the mode-n slice
+ * (same p_n) holds the rows of factor n in block p_n; within that block each
+ * slice member owns a contiguous piece of the rows, cut in P / P_n parts in
+ * the order of the members' other coordinates (mode 1 fastest).  The object
+ * does one processor's local computation; the caller runs the collectives
+ * between the calls, per inner iteration n (Alg. 2):
+ *   nncp_par_mttkrp    local MTTKRP of the block through a local dimension
+ *                      tree (nncp_mttkrp_cached): block-rows x R;
+ *   [Reduce-Scatter of it over the mode-n slice: the owned rows of M(n)]
+ *   nncp_par_update    HALS sweep (Sec. II-B) on the owned rows of
+ *                      W = H_n diag(lambda) with S = the Hadamard of the other
+ *                      Grams, and this processor's W^T W and <M, W>;
+ *   [All-Reduce of those R*R + 1 doubles over every processor]
+ *   nncp_par_normalize lambda = column norms (float64), H_n = W / lambda on
+ *                      the owned rows, G_n, and at n = N the fit (Sec. IV-B)
+ *                      and the stopping test;
+ *   [All-Gather of the owned rows over the mode-n slice into the block.]
+ * Initialisation (Alg. 2, first loop): nncp_par_alpha_local +
+ * [All-Reduce] + nncp_par_begin, then for every mode nncp_par_update with
+ * M_owned = NULL (the Gram of the rows as given), [All-Reduce],
+ * nncp_par_normalize with init = 1 (norms folded into lambda), [All-Gather].
+ * Device buffers are the caller's: the local tensor block (float32), the N
+ * factor blocks (block-rows x R, row-major, bound by nncp_par_set_data; the
+ * owned rows of mode n start at row owned_lo - block_lo), M blocks and owned
+ * rows.  The Grams, lambda, alpha and the fits are float64 host state held
+ * redundantly by every processor. */
+typedef struct nncp_par nncp_par;
+/* dims: global mode lengths; grid: P_1..P_N (1 <= P_n <= I_n); coords: this
+ * processor's p_1..p_N (0-based); precision of the local partial MTTKRPs
+ * (NNCP_ERR_UNSUPPORTED if the local block cannot use it). */
+nncp_status nncp_par_create(int N, const int64_t* dims, const int* grid, const int* coords, int R,
+                            nncp_precision precision, nncp_par** out);
+/* Layout of mode `mode` (1..N): factor block [block_lo, block_lo + block_rows),
+ * owned rows [owned_lo, owned_lo + owned_rows) (global row indices), and this
+ * processor's index and the member count of its mode-n slice.  Any output
+ * may be NULL. */
+nncp_status nncp_par_layout(const nncp_par* p, int mode, int64_t* block_lo, int64_t* block_rows,
+                            int64_t* owned_lo, int64_t* owned_rows, int* slice_index,
+                            int* slice_size);
+nncp_status nncp_par_workspace_size(const nncp_par* p, size_t* bytes);
+/* Caller-allocated device workspace (256-byte aligned); `stream` is the
+ * stream every call of this object runs on. */
+nncp_status nncp_par_set_workspace(nncp_par* p, void* dev_ptr, size_t bytes, void* stream);
+nncp_status nncp_par_set_data(nncp_par* p, const float* X_local, float* const* H_block);
+/* ||X_p||^2 of the local block (float64), for the All-Reduce giving alpha. */
+nncp_status nncp_par_alpha_local(nncp_par* p, const float* X_local, double* local);
+/* Starts a solve: alpha = ||X||^2 (the All-Reduce of the local values), the
+ * stopping tolerance on |fit_k - fit_{k-1}|; lambda = 1, no fits yet. */
+nncp_status nncp_par_begin(nncp_par* p, double alpha, double tol);
+/* Local MTTKRP of mode `mode` into M_block (block-rows x R, device). */
+nncp_status nncp_par_mttkrp(nncp_par* p, int mode, float* M_block);
+/* HALS sweep on the owned rows (H_owned, device, in place: W) against
+ * M_owned (device, the owned rows after the Reduce-Scatter), or, with
+ * M_owned = NULL, no sweep (initialisation).  partial (host, R*R + 1
+ * doubles): this processor's W^T W and <M, W>.  Blocks until done. */
+nncp_status nncp_par_update(nncp_par* p, int mode, const float* M_owned, float* H_owned,
+                            double* partial);
+/* From the All-Reduced sums (host, R*R + 1 doubles): lambda (init = 1:
+ * multiplied into lambda), H_owned = W / lambda, G_n; at mode N (init = 0)
+ * the fit of the iteration (*fit_out) and *stop_out = 1 when
+ * |fit_k - fit_{k-1}| < tol or the fit is not finite (NNCP_ERR_NUMERIC).
+ * Blocks until done. */
+nncp_status nncp_par_normalize(nncp_par* p, int mode, const double* sums, float* H_owned, int init,
+                               double* fit_out, int* stop_out);
+/* lambda (host, R doubles), the fits of the iterations so far (host, up to
+ * max_fits) and their count; any output may be NULL. */
+nncp_status nncp_par_result(const nncp_par* p, double* lambda_out, double* fits, int max_fits,
+                            int* iters_out);
+const char* nncp_par_last_error(const nncp_par* p);
+void nncp_par_destroy(nncp_par* p);
 
 /* Throughput probe (a measurement utility; the paper has no counterpart): one
  * launch on `stream` of a kernel that runs at the device's peak rate of

@@ -74,6 +74,12 @@ struct nncp_ctx {
   int* host_flags = nullptr;  // pinned
   double* host_dbl = nullptr; // pinned
   bool initialised = false;   // nncp_solve_begin ran on the current state
+  // nncp_mttkrp_cached: versions of the factors (bumped by nncp_factor_changed)
+  // and, per tree node [half][depth], whether it holds a result and the
+  // factor versions it was computed from
+  uint64_t fver[kMaxModes] = {};
+  bool node_ok[2][kMaxModes] = {};
+  uint64_t node_ver[2][kMaxModes][kMaxModes] = {};
   std::string err;
 };
 
@@ -224,7 +230,15 @@ void bind_workspace(nncp_ctx* c) {
   c->tc.bytes = p.tc_bytes;
 }
 
+// Forget every cached tree node (their buffers are shared with the solver and
+// the read-only tree walk, and the bound tensor, factors or layout may change).
+void tree_cache_clear(nncp_ctx* c) {
+  for (int h = 0; h < 2; ++h)
+    for (int d = 0; d < kMaxModes; ++d) c->node_ok[h][d] = false;
+}
+
 void drop_graph(nncp_ctx* c) {
+  tree_cache_clear(c);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->graph4) cudaGraphExecDestroy(c->graph4);
   c->graph = nullptr;
@@ -330,6 +344,20 @@ cudaError_t visit(nncp_ctx* c, const float* T, int a, int last, int h, int base,
   e = launch_mttv_first(T, c->dims[a], prod(c->dims, a + 1, last), c->H[a], R, child, st);
   if (e != cudaSuccess) return e;
   return visit(c, child, a + 1, last, h, base, st);
+}
+
+// Node {a..last} of half h at depth d = a - first depends on every factor
+// outside {a..last}.
+bool node_current(const nncp_ctx* c, int h, int d, int a, int last) {
+  if (!c->node_ok[h][d]) return false;
+  for (int k = 0; k < c->N; ++k)
+    if ((k < a || k > last) && c->node_ver[h][d][k] != c->fver[k]) return false;
+  return true;
+}
+
+void node_stamp(nncp_ctx* c, int h, int d) {
+  c->node_ok[h][d] = true;
+  for (int k = 0; k < c->N; ++k) c->node_ver[h][d][k] = c->fver[k];
 }
 
 cudaError_t run_iteration(nncp_ctx* c, cudaStream_t st) {
@@ -685,6 +713,7 @@ nncp_status nncp_set_factors(nncp_ctx* c, float* const* H_dev) {
 nncp_status nncp_mttkrp(nncp_ctx* c, int mode, int use_dimtree, float* M_dev) {
   nncp_status s = check_ready(c);
   if (s != NNCP_OK) return s;
+  tree_cache_clear(c);
   if (mode < 1 || mode > c->N) return fail(c, NNCP_ERR_INVALID_ARG, "mode %d not in [1, N]", mode);
   if (!M_dev) return fail(c, NNCP_ERR_INVALID_ARG, "output is NULL");
   const int n = mode - 1, N = c->N, R = c->R, sp = c->split;
@@ -729,6 +758,52 @@ nncp_status nncp_partial_mttkrp(nncp_ctx* c, int side, float* T_dev) {
   return NNCP_OK;
 }
 
+nncp_status nncp_factor_changed(nncp_ctx* c, int mode) {
+  if (!c) return fail(nullptr, NNCP_ERR_INVALID_ARG, "null context");
+  if (mode < 1 || mode > c->N) return fail(c, NNCP_ERR_INVALID_ARG, "mode %d not in [1, N]", mode);
+  ++c->fver[mode - 1];
+  return NNCP_OK;
+}
+
+nncp_status nncp_mttkrp_cached(nncp_ctx* c, int mode, float* M_dev) {
+  nncp_status s = check_ready(c);
+  if (s != NNCP_OK) return s;
+  if (mode < 1 || mode > c->N) return fail(c, NNCP_ERR_INVALID_ARG, "mode %d not in [1, N]", mode);
+  if (!M_dev) return fail(c, NNCP_ERR_INVALID_ARG, "output is NULL");
+  const int n = mode - 1, N = c->N, R = c->R, sp = c->split;
+  cudaStream_t st = c->user_stream;
+  const bool left = n < sp;
+  const int h = left ? 0 : 1, first = left ? 0 : sp, last = left ? sp - 1 : N - 1;
+  if (first == last) {
+    // a one-mode half: its partial MTTKRP is M(n) itself
+    CK(left ? pm_right(c, M_dev, st) : pm_left(c, M_dev, st));
+    return NNCP_OK;
+  }
+  float* T = c->node[h][0];
+  if (!node_current(c, h, 0, first, last)) {
+    CK(left ? pm_right(c, T, st) : pm_left(c, T, st));
+    node_stamp(c, h, 0);
+  }
+  for (int a = first; a < n; ++a) {
+    const int d = a + 1 - first;  // depth of the child node {a+1..last}
+    if (a + 1 == last) {
+      // the child is the one-mode node {last} = M(last)
+      CK(launch_mttv_first(T, c->dims[a], prod(c->dims, a + 1, last), c->H[a], R, M_dev, st));
+      return NNCP_OK;
+    }
+    float* child = c->node[h][d];
+    if (!node_current(c, h, d, a + 1, last)) {
+      CK(launch_mttv_first(T, c->dims[a], prod(c->dims, a + 1, last), c->H[a], R, child, st));
+      node_stamp(c, h, d);
+    }
+    T = child;
+  }
+  KrpDesc rest = krp(c, n + 1, last);
+  CK(launch_mttv_leaf(T, c->dims[n], prod(c->dims, n + 1, last), rest, R, M_dev, c->partials,
+                      c->part_cap, c->num_sms, st));
+  return NNCP_OK;
+}
+
 nncp_status nncp_iteration_kernels(nncp_ctx* c, int* count) {
   nncp_status s = check_ready(c);
   if (s != NNCP_OK) return s;
@@ -741,6 +816,7 @@ nncp_status nncp_iteration_kernels(nncp_ctx* c, int* count) {
 nncp_status nncp_solve_begin(nncp_ctx* c) {
   nncp_status s = check_ready(c);
   if (s != NNCP_OK) return s;
+  tree_cache_clear(c);
   if ((s = begin_on_work(c)) != NNCP_OK) return s;
   if ((s = solve_init(c, 0.0)) != NNCP_OK) return s;
   if ((s = ensure_graph(c)) != NNCP_OK) return s;
@@ -751,6 +827,7 @@ nncp_status nncp_iterate(nncp_ctx* c, int iters) {
   nncp_status s = check_ready(c);
   if (s != NNCP_OK) return s;
   if (!c->initialised) return fail(c, NNCP_ERR_INVALID_ARG, "call nncp_solve_begin first");
+  tree_cache_clear(c);
   if ((s = ensure_graph(c)) != NNCP_OK) return s;
   if ((s = begin_on_work(c)) != NNCP_OK) return s;
   CK(launch_iterations(c, iters));
@@ -761,6 +838,7 @@ nncp_status nncp_solve_bound(nncp_ctx* c, int max_iters, double tol, double* lam
                              int* iters_out, double* fit_out) {
   nncp_status s = check_ready(c);
   if (s != NNCP_OK) return s;
+  tree_cache_clear(c);
   if (max_iters < 1) return fail(c, NNCP_ERR_INVALID_ARG, "max_iters < 1");
   if (max_iters > kFitCapacity) return fail(c, NNCP_ERR_INVALID_ARG, "max_iters > %d", kFitCapacity);
   if ((s = begin_on_work(c)) != NNCP_OK) return s;

@@ -216,6 +216,10 @@ cudaError_t launch_apg_rows(float* H, const float* M, int64_t In, int R, int ite
 cudaError_t launch_apg_update(float* H, const float* M, int64_t In, int R, int iters,
                               SolveState st, cudaStream_t stream);
 
+// H(i, r) *= inv(r) over `rows` rows (inv: R floats, device).
+cudaError_t launch_scale_columns(float* H, int64_t rows, int R, const float* inv,
+                                 cudaStream_t stream);
+
 // Gram partials of H as given (initialisation: W = H).
 cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
                              cudaStream_t stream);

@@ -1765,6 +1765,23 @@ cudaError_t launch_gram_only(const float* H, int64_t In, int R, SolveState st,
   return cudaGetLastError();
 }
 
+// H(i, r) *= inv(r) for `rows` rows of R columns (row-major).
+__global__ void k_scale_columns(float* __restrict__ H, long long n, int R,
+                                const float* __restrict__ inv) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    H[e] *= inv[e % R];
+}
+
+cudaError_t launch_scale_columns(float* H, int64_t rows, int R, const float* inv,
+                                 cudaStream_t stream) {
+  const long long n = (long long)rows * R;
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  k_scale_columns<<<blocks, 256, 0, stream>>>(H, n, R, inv);
+  return cudaGetLastError();
+}
+
 bool multi_update_ok(int64_t In, int R) { return In <= kMultiMaxRows && R <= 64; }
 
 // partial scratch needed by the multi-CTA update (floats)

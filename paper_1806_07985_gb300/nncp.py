@@ -56,6 +56,8 @@ _SIGNATURES = [
     ("nncp_set_factors", ctypes.c_int, [ctypes.c_void_p, _c_vpp]),
     ("nncp_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("nncp_partial_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_mttkrp_cached", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_factor_changed", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("nncp_iteration_kernels", ctypes.c_int, [ctypes.c_void_p, _c_intp]),
     ("nncp_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_vpp, _c_dblp, ctypes.c_int,
                                   ctypes.c_double, _c_intp, _c_dblp]),
@@ -99,6 +101,24 @@ _SIGNATURES = [
     ("nncp_server_destroy", None, [ctypes.c_void_p]),
     ("nncp_peak_probe", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        _c_dblp]),
+    ("nncp_par_create", ctypes.c_int, [ctypes.c_int, _c_i64p, _c_intp, _c_intp, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("nncp_par_layout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i64p, _c_i64p, _c_i64p,
+                                       _c_i64p, _c_intp, _c_intp]),
+    ("nncp_par_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("nncp_par_set_workspace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                              ctypes.c_void_p]),
+    ("nncp_par_set_data", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_vpp]),
+    ("nncp_par_alpha_local", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_dblp]),
+    ("nncp_par_begin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
+    ("nncp_par_mttkrp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("nncp_par_update", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, _c_dblp]),
+    ("nncp_par_normalize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dblp, ctypes.c_void_p,
+                                          ctypes.c_int, _c_dblp, _c_intp]),
+    ("nncp_par_result", ctypes.c_int, [ctypes.c_void_p, _c_dblp, _c_dblp, ctypes.c_int, _c_intp]),
+    ("nncp_par_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("nncp_par_destroy", None, [ctypes.c_void_p]),
     ("nncp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_global_error", ctypes.c_char_p, []),
     ("nncp_destroy", None, [ctypes.c_void_p]),
@@ -225,6 +245,14 @@ def nncp_mttkrp(ctx, mode, use_dimtree, M):
 
 def nncp_partial_mttkrp(ctx, side, T):
     _check(load().nncp_partial_mttkrp(ctx, int(side), _ptr(T)), ctx)
+
+
+def nncp_mttkrp_cached(ctx, mode, M):
+    _check(load().nncp_mttkrp_cached(ctx, int(mode), _ptr(M)), ctx)
+
+
+def nncp_factor_changed(ctx, mode):
+    _check(load().nncp_factor_changed(ctx, int(mode)), ctx)
 
 
 def nncp_iteration_kernels(ctx):
@@ -579,6 +607,91 @@ def _scheck(status, s):
         raise NNCPError(status, (msg or b"").decode())
 
 
+def _pcheck(status, p):
+    if status != NNCP_OK:
+        lib = load()
+        msg = lib.nncp_par_last_error(p) if p else lib.nncp_global_error()
+        raise NNCPError(status, (msg or b"").decode())
+
+
+class ParRank:
+    """One processor of a Par-NNCP grid (nncp_par_*; argument marshalling only).
+
+    The local computation between the collectives of Alg. 2: see the
+    nncp_par_* declarations for the protocol.  The workspace is allocated with
+    torch on the current CUDA device."""
+
+    def __init__(self, dims, grid, coords, R, precision=NNCP_FP32_SIMT, stream=None):
+        import torch
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.N, self.R = len(dims), int(R)
+        self.p = ctypes.c_void_p()
+        g = (ctypes.c_int * self.N)(*[int(v) for v in grid])
+        c = (ctypes.c_int * self.N)(*[int(v) for v in coords])
+        _pcheck(load().nncp_par_create(self.N, _dims(dims), g, c, self.R, int(precision),
+                                       ctypes.byref(self.p)), None)
+        n = ctypes.c_size_t()
+        _pcheck(load().nncp_par_workspace_size(self.p, ctypes.byref(n)), self.p)
+        self.ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device="cuda")
+        _pcheck(load().nncp_par_set_workspace(self.p, _ptr(self.ws), n.value, _stream(stream)),
+                self.p)
+
+    def layout(self, mode):
+        """(block_lo, block_rows, owned_lo, owned_rows, slice_index, slice_size)."""
+        v = [ctypes.c_int64() for _ in range(4)] + [ctypes.c_int() for _ in range(2)]
+        _pcheck(load().nncp_par_layout(self.p, int(mode), *[ctypes.byref(x) for x in v]), self.p)
+        return tuple(x.value for x in v)
+
+    def set_data(self, X_local, H_block):
+        self._keep = (X_local, list(H_block))
+        arr = (ctypes.c_void_p * len(H_block))(*[int(h.data_ptr()) for h in H_block])
+        _pcheck(load().nncp_par_set_data(self.p, _ptr(X_local), arr), self.p)
+
+    def alpha_local(self, X_local):
+        a = ctypes.c_double()
+        _pcheck(load().nncp_par_alpha_local(self.p, _ptr(X_local), ctypes.byref(a)), self.p)
+        return a.value
+
+    def begin(self, alpha, tol):
+        _pcheck(load().nncp_par_begin(self.p, float(alpha), float(tol)), self.p)
+
+    def mttkrp(self, mode, M_block):
+        _pcheck(load().nncp_par_mttkrp(self.p, int(mode), _ptr(M_block)), self.p)
+
+    def update(self, mode, M_owned, H_owned):
+        part = (ctypes.c_double * (self.R * self.R + 1))()
+        _pcheck(load().nncp_par_update(self.p, int(mode), _ptr(M_owned), _ptr(H_owned), part),
+                self.p)
+        return list(part)
+
+    def normalize(self, mode, sums, H_owned, init):
+        arr = (ctypes.c_double * len(sums))(*[float(v) for v in sums])
+        fit = ctypes.c_double()
+        stop = ctypes.c_int()
+        _pcheck(load().nncp_par_normalize(self.p, int(mode), arr, _ptr(H_owned), int(bool(init)),
+                                          ctypes.byref(fit), ctypes.byref(stop)), self.p)
+        return fit.value, bool(stop.value)
+
+    def result(self, max_fits=1 << 16):
+        lam = (ctypes.c_double * self.R)()
+        fits = (ctypes.c_double * max_fits)()
+        n = ctypes.c_int()
+        _pcheck(load().nncp_par_result(self.p, lam, fits, int(max_fits), ctypes.byref(n)), self.p)
+        return list(lam), list(fits[: n.value])
+
+    def close(self):
+        if self.p:
+            load().nncp_par_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def nncp_last_error(ctx):
     return load().nncp_last_error(ctx).decode()
 
@@ -623,6 +736,13 @@ class Context:
     def partial_mttkrp(self, side, out):
         nncp_partial_mttkrp(self.ctx, side, out)
         return out
+
+    def mttkrp_cached(self, mode, out):
+        nncp_mttkrp_cached(self.ctx, mode, out)
+        return out
+
+    def factor_changed(self, mode):
+        nncp_factor_changed(self.ctx, mode)
 
     def iteration_kernels(self):
         return nncp_iteration_kernels(self.ctx)
