@@ -398,7 +398,7 @@ def run_peaks(nncp, torch):
     probe kernels (nncp_peak_probe), timed with events on the current stream."""
     sink = torch.zeros(4, dtype=torch.int32, device="cuda")
     out = {}
-    for kind, reps in (("ffma", 5000), ("tf32", 20000), ("bf16", 20000)):
+    for kind, reps in (("ffma", 5000), ("ffma2", 2500), ("tf32", 20000), ("bf16", 20000)):
         nncp.nncp_peak_probe(kind, 64, sink)
         torch.cuda.synchronize()
         best = None
@@ -413,7 +413,8 @@ def run_peaks(nncp, torch):
             best = tf if best is None else max(best, tf)
         out[f"{kind}_tflops"] = round(best, 1)
     out["probe_ok"] = int(sink[0].item()) == 0
-    out["how"] = ("nncp_peak_probe: FFMA 8 chains x 2048 threads per SM; tcgen05.mma kind::tf32 / "
+    out["how"] = ("nncp_peak_probe: FFMA (and packed fma.rn.f32x2) 8 chains x 2048 threads per SM; "
+                  "tcgen05.mma kind::tf32 / "
                   "kind::f16 M=128 N=256 from shared memory, one CTA per SM; best of 3, CUDA events")
     return out
 

@@ -401,7 +401,8 @@ void nncp_par_destroy(nncp_par* p);
  *           2048 threads per SM), the bound of NNCP_FP32_SIMT;
  *   kind 1: dense tcgen05 MMAs, kind::tf32, M = 128, N = 256, operands in
  *           shared memory, one CTA per SM (the bound of NNCP_TF32);
- *   kind 2: the same with kind::f16 bf16 operands.
+ *   kind 2: the same with kind::f16 bf16 operands;
+ *   kind 3: packed float32 pairs (fma.rn.f32x2, two FMAs per instruction).
  * reps (1..2^24) scales the work; *flops_out receives the floating-point
  * operations the launch performs (2 per multiply-add).  sink_dev: 16 bytes
  * of device memory, 16-byte aligned, that the kernels may write (the MMA

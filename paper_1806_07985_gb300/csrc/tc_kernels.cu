@@ -1336,6 +1336,43 @@ k_probe_ffma(int reps, float seed, float* sink) {
   if (s == 12345.678f) sink[0] = s;  // keeps the chains live
 }
 
+// The same with packed pairs: fma.rn.f32x2 performs two float32 FMAs (each
+// rounded to nearest, as fmaf) per instruction.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__global__ void __launch_bounds__(kProbeThreads)
+k_probe_ffma2(int reps, float seed, float* sink) {
+  unsigned long long a[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) {
+    const float2 v = make_float2(seed + (float)(threadIdx.x + c), seed - (float)c);
+    a[c] = *reinterpret_cast<const unsigned long long*>(&v);
+  }
+  const float2 mv = make_float2(0.999999f, 0.999998f), bv = make_float2(1e-7f, 2e-7f);
+  const unsigned long long m = *reinterpret_cast<const unsigned long long*>(&mv);
+  const unsigned long long b = *reinterpret_cast<const unsigned long long*>(&bv);
+#pragma unroll 1
+  for (int i = 0; i < reps; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) a[c] = ffma2(a[c], m, b);
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) {
+    const float2 v = *reinterpret_cast<const float2*>(&a[c]);
+    s += v.x + v.y;
+  }
+  if (s == 12345.678f) sink[0] = s;  // keeps the chains live
+}
+
 // One elected thread issues `reps` x 4 MMAs of M = 128, N = 256 into one
 // tensor-memory accumulator from zero-filled shared-memory operands.
 template <bool TF32>
@@ -1417,6 +1454,11 @@ extern "C" nncp_status nncp_peak_probe(int kind, int reps, void* sink_dev, void*
     e = launch_kernel(k_probe_ffma, dim3(blocks), dim3(kProbeThreads), 0, st, reps, 1.0f,
                       static_cast<float*>(sink_dev));
     *flops_out = 2.0 * kProbeChains * 16 * (double)reps * blocks * kProbeThreads;
+  } else if (kind == 3) {
+    const int blocks = sms * 8;
+    e = launch_kernel(k_probe_ffma2, dim3(blocks), dim3(kProbeThreads), 0, st, reps, 1.0f,
+                      static_cast<float*>(sink_dev));
+    *flops_out = 4.0 * kProbeChains * 16 * (double)reps * blocks * kProbeThreads;
   } else if (kind == 1 || kind == 2) {
     const int smem = 1024 + 16384 + 32768 + 128;
     auto k = kind == 1 ? k_probe_mma<true> : k_probe_mma<false>;
@@ -1426,7 +1468,7 @@ extern "C" nncp_status nncp_peak_probe(int kind, int reps, void* sink_dev, void*
     // K per MMA: 8 (tf32) or 16 (bf16) elements of a 32-byte step
     *flops_out = 2.0 * 128 * 256 * (kind == 1 ? 8 : 16) * 4.0 * reps * sms;
   } else {
-    record_global_error("nncp_peak_probe: kind must be 0 (FFMA), 1 (TF32 MMA) or 2 (BF16 MMA)");
+    record_global_error("nncp_peak_probe: kind must be 0 (FFMA), 1 (TF32 MMA), 2 (BF16 MMA) or 3 (packed FFMA2)");
     return NNCP_ERR_INVALID_ARG;
   }
   if (e != cudaSuccess) {

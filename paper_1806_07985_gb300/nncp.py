@@ -395,11 +395,11 @@ def nncp_batch_solve(shapes, ranks, X, H, max_iters, tol, stream=None):
     return list(iters), list(fits), [list(a) for a in lam_arrs]
 
 
-PROBES = {"ffma": 0, "tf32": 1, "bf16": 2}
+PROBES = {"ffma": 0, "tf32": 1, "bf16": 2, "ffma2": 3}
 
 
 def nncp_peak_probe(kind, reps, sink, stream=None):
-    """Launch one throughput probe (kind "ffma", "tf32" or "bf16"; see the
+    """Launch one throughput probe (kind "ffma", "tf32", "bf16" or "ffma2"; see the
     header); returns the floating-point operations it performs.  sink: a
     CUDA tensor of at least 16 bytes."""
     flops = ctypes.c_double()
