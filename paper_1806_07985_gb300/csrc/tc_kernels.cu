@@ -19,8 +19,10 @@
 // named barrier separates the reads from the writes, and the result overwrites
 // the TMA stage).  Precision modes:
 //   TF32         kind::tf32 on the float32 tensor (direct when K-major);
-//   SPLIT_BF16X3 x = hi + lo in bf16, K = Khi + Klo: D = hi*[Khi|Klo] + lo*Khi
-//                (three products, float32 accumulation in TMEM);
+//   SPLIT_BF16X3 x = hi + lo in bf16, K = Khi + Klo: D = [hi*Khi | hi*Klo +
+//                lo*Khi] (three products in two float32 TMEM accumulators,
+//                added in the epilogue; the large product hi*Khi alone in the
+//                first, so fewer additions meet it);
 //   BF16_STORED  the tensor is bf16 in HBM: D = X*[Khi|Klo].
 //
 // Warp roles (16 warps, one CTA per SM, persistent over work units):
@@ -28,10 +30,10 @@
 //   warps 2-7   Khatri-Rao B builders, two per B stage slot (each half of the
 //               stage's 64 contraction elements), so three stages are formed
 //               concurrently (their factor-row loads are L2 latency)
-//   warps 8-15  converters (hi/lo split, transposes) and the epilogue
-//               (tcgen05.ld TMEM -> registers -> global, half of the columns
-//               each); an accumulator is read after the next one's
-//               conversions, TMEM holding two.
+//   warps 8-15  converters (hi/lo split, transposes); warps 8-11 (8-15 above
+//               32 rank columns) also run the epilogue (tcgen05.ld TMEM ->
+//               registers -> global); an accumulator is read after the next
+//               one's conversions, TMEM holding two.
 // Split-BF16x3 accumulates at most kSegStages stages in one TMEM accumulator
 // and adds these segments in float32 registers: the tensor core's own
 // accumulation does not round to nearest, and over a long chain of
@@ -76,10 +78,11 @@ constexpr int kOffsBytes = kSB * kKC * (kMaxModes + 1) * 4;  // B builder row of
 // A stage even where there are fewer TMA stages.  (Six stages, which fit for
 // R <= 32, measured slower on the 512^3 root -> left contraction.)
 constexpr int kSA = 4;
-// split-BF16x3: stages (of kKC contraction elements, 8 MMAs into one
-// accumulator each) per tensor-memory accumulation chain; see TcParams::seg
+// split-BF16x3: stages (of kKC contraction elements, four MMAs of hi*Khi
+// into the first accumulator each) per tensor-memory accumulation chain;
+// see TcParams::seg
 #ifndef NNCP_TC_SEG_STAGES
-#define NNCP_TC_SEG_STAGES 8
+#define NNCP_TC_SEG_STAGES 16
 #endif
 constexpr int kSegStages = NNCP_TC_SEG_STAGES;
 static_assert(kSA <= kMaxSF, "A stages use conv_full barrier slots");
@@ -103,7 +106,8 @@ struct TcParams {
   // float32 registers (split-BF16x3; one segment per unit otherwise).  The
   // tensor core adds each MMA's products into the accumulator without
   // rounding to nearest, which biases a long chain of nonnegative terms
-  // (measured 2.5e-5 relative over 108 stages of exactly split operands);
+  // (measured 2.5e-5 relative over 108 stages of exactly split operands;
+  // 1.7e-6 with chains of 16 stages);
   // bounding the chain bounds that bias, and the segments are summed with
   // ordinary float32 adds.
   int seg;
@@ -460,9 +464,9 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(acc_full(i), 1);
-      // the eight converter warps (each reads half of the accumulator
-      // columns), and with the fused leaf its four warps too
-      mbar_init(acc_empty(i), LEAF ? 12 : 8);
+      // the epilogue warps (warps 8-11, or 8-15 above 32 rank columns), and
+      // with the fused leaf its four warps too
+      mbar_init(acc_empty(i), (p.Rp > 32 ? 8 : 4) + (LEAF ? 4 : 0));
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -572,7 +576,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t bd = sw128_desc(b + kk * 32);
               mma_f16_ta(d, ahi + kk * 8, bd, idesc_full, (sp > 0 || kk > 0) ? 1u : 0u);
-              mma_f16_ta(d, ahi + 32 + kk * 8, bd, idesc_hi, 1u);
+              mma_f16_ta(d + Rp, ahi + 32 + kk * 8, bd, idesc_hi, 1u);
             }
             mma_commit(a_empty(sa));
             if (!p.b_resident) mma_commit(b_empty(sb));
@@ -868,9 +872,9 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     int sf = 0;
     uint32_t phf = 0;
     bool ok = true;
-    // Epilogue, shared by the eight converter warps: warps 8-11 take the first
-    // half of the 16-column accumulator chunks, warps 12-15 the rest, of the
-    // rows in their lane quarter.  A unit's accumulator arrives in segments of
+    // Epilogue: warps 8-11 read the rows in their lane quarter (above 32 rank
+    // columns warps 12-15 take the second half of the 16-column chunks).  A
+    // unit's accumulator arrives in segments of
     // at most P stages (buffer g & 1 for segment g over this CTA's units);
     // each segment is added into float32 registers, and the unit's last one
     // writes the row to global memory.  Segment g is taken once the
@@ -879,8 +883,13 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     const int P = SPLIT ? p.seg : (1 << 30);
     const int nch = Rp >> 4;
     const int cgrp = (warp - kWarpConv) >> 2;
-    const int c_lo = cgrp == 0 ? 0 : (nch + 1) >> 1;
-    const int c_n = cgrp == 0 ? (nch + 1) >> 1 : nch >> 1;  // chunks held, at most 2
+    // up to 32 rank columns warps 8-11 hold whole rows and warps 12-15 keep
+    // converting meanwhile; above, the two groups share the columns
+    const bool epi_all = Rp > 32;
+    const bool epi = epi_all || cgrp == 0;
+    const int c_lo = (epi_all && cgrp == 1) ? (nch + 1) >> 1 : 0;
+    const int c_n = epi_all ? (cgrp == 0 ? (nch + 1) >> 1 : nch >> 1)
+                            : (cgrp == 0 ? nch : 0);  // chunks held, at most 2
     float acc[32];
     struct Seg {
       long long mt, kbeg, g;
@@ -890,6 +899,7 @@ k_tc_partial_mttkrp(const __grid_constant__ CUtensorMap tmap, TcParams p) {
     pend.g = -1;
     long long gseg = 0;
     auto consume = [&](const Seg& sg) -> bool {
+      if (!epi) return true;
       pdl_wait();
       const int bsel = (int)(sg.g & 1);
       const bool got = mbar_wait(acc_full(bsel), (uint32_t)((sg.g >> 1) & 1), abort_flag, p.err);

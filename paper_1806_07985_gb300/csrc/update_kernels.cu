@@ -32,6 +32,27 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// 1 / sqrt(g) and sqrt(g) in float64 for a float32 g: a float32 estimate
+// refined by two steps of Newton's iteration for the reciprocal square root,
+// r <- r (3 - g r^2) / 2, each of which squares the relative error (~2^-22
+// -> ~2^-43 -> below float64 rounding).  A few dependent multiply-adds
+// instead of a float64 square root and a float64 division, which on this
+// GPU's float64 pipe cost about a microsecond per mode update.  g = 0 gives
+// 0 and 0; a non-finite g takes the plain functions, so NaN propagates.
+__device__ __forceinline__ void rsqrt_sqrt_f64(float g32, double* rinv, double* root) {
+  if (g32 > 0.0f && g32 < INFINITY) {
+    const double g = g32;
+    double r = (double)rsqrtf(g32);
+    r = r * (1.5 - 0.5 * g * r * r);
+    r = r * (1.5 - 0.5 * g * r * r);
+    *rinv = r;
+    *root = g * r;
+  } else {
+    *root = sqrt((double)g32);
+    *rinv = g32 > 0.0f ? 1.0 / *root : 0.0;
+  }
+}
+
 // Butterfly sum: every lane ends with the same bits (each step adds the same
 // two values in the same order on both partners).
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -541,11 +562,11 @@ k_update_multi(float* __restrict__ H, const float* __restrict__ M, int In, int R
   // lambda = column norms of W in float64; from here on lamf holds 1 / lambda
   // (float32, for the row scaling) and linv the float64 reciprocal
   for (int r = tid; r < R; r += T) {
-    const double g = GW[r * R + r];
-    const double l = sqrt(g);
+    double l, li;
+    rsqrt_sqrt_f64(GW[r * R + r], &li, &l);
     st.lam[r] = l;
-    linv[r] = g > 0.0 ? 1.0 / l : 0.0;
-    lamf[r] = (float)linv[r];
+    linv[r] = li;
+    lamf[r] = (float)li;
   }
   __syncthreads();
   double* Gng = st.G + (long long)n * R2;
@@ -1025,11 +1046,11 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   // ---- lambda = column norms of W in float64; from here on lamd holds
   // 1 / lambda and lamf its float32 value (for the row scaling)
   for (int r = tid; r < R; r += T) {
-    const double g = GW[r * R + r];
-    const double l = sqrt(g);
+    double l, li;
+    rsqrt_sqrt_f64(GW[r * R + r], &li, &l);
     if (lead) st.lam[r] = l;
-    lamd[r] = g > 0.0 ? 1.0 / l : 0.0;
-    lamf[r] = (float)lamd[r];
+    lamd[r] = li;
+    lamf[r] = (float)li;
   }
   __syncthreads();
   // this CTA's rows of H = W / lambda (multiplication by the float32 reciprocal)
@@ -1077,15 +1098,20 @@ k_update_cluster(float* __restrict__ H, const float* __restrict__ M, int In, int
   if (lead && is_last) {
     // gamma = lambda^T (S * G_N) lambda = sum_ab S_ab (W^T W)_ab (Sec. IV-B),
     // float64 over the thread's terms, the warp, then the warps in order
-    double g = 0.0;
+    double g0 = 0.0, g1 = 0.0;  // two chains, joined in a fixed order
 #pragma unroll 1
-    for (int e = tid; e < R2; e += T) g = fma(Sd[e], (double)GW[e], g);
-    g = warp_sum_d(g);
+    for (int e = tid; e < R2; e += 2 * T) {
+      g0 = fma(Sd[e], (double)GW[e], g0);
+      if (e + T < R2) g1 = fma(Sd[e + T], (double)GW[e + T], g1);
+    }
+    double g = warp_sum_d(g0 + g1);
     if (lane == 0) redd[warp] = g;
     __syncthreads();
     if (tid == 0) {
-      double gamma = 0.0;
-      for (int k = 0; k < T / 32; ++k) gamma += redd[k];
+      // the eight warps' sums as a fixed tree
+      static_assert(T / 32 == 8, "gamma tree over eight warps");
+      const double gamma = ((redd[0] + redd[1]) + (redd[2] + redd[3])) +
+                           ((redd[4] + redd[5]) + (redd[6] + redd[7]));
       const double beta = (double)beta_sh.hi + (double)beta_sh.lo;
       const double alpha = scal_sh[0], tol = scal_sh[1], prev = scal_sh[2];
       const double eps = sqrt(fmax(0.0, alpha - 2.0 * beta + gamma) / alpha);
