@@ -672,6 +672,7 @@ def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3
+    schedule = b.schedule()
     b.close()
     elems = [int(np.prod(p[0])) for p in probs]
     tensor_bytes = sum(2 * 4 * e * k for e, k in zip(elems, iters))
@@ -679,7 +680,10 @@ def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
                        f"|dfit|<{BATCH_TOL:g} or {iters_cap} iters, FP32",
            "solves_per_s": round(count / t, 1), "seconds": round(t, 4),
            "iters_mean": round(float(np.mean(iters)), 1), "iters_max": int(max(iters)),
-           "tensor_GBps": round(tensor_bytes / t / 1e9, 1)}
+           "tensor_GBps": round(tensor_bytes / t / 1e9, 1),
+           "root_phase_schedule": {"pm_right": schedule[0], "pm_left": schedule[1],
+                                   "codes": "0 one CTA per work item, 1 persistent CTAs on a "
+                                            "work counter; chosen by the library's tuner"}}
     if no_plain:
         return out
     sample = list(range(0, count, max(1, count // 32)))[:32]

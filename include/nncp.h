@@ -285,6 +285,16 @@ nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims
                              const void* const* X_dev, float* const* const* H_dev,
                              double* const* lambda, int max_iters, double tol, int* iters,
                              double* fits, void* stream);
+/* Schedule of the two root partial MTTKRP phases (the paper has no
+ * counterpart; a launch-shape choice): 0 = one CTA per work item, scheduled by
+ * the hardware; 1 = one wave of persistent CTAs taking items from a counter;
+ * -1 (the default) = chosen at the next nncp_batch_run by timing both on this
+ * batch, cached per class of batch (order, largest rank, magnitudes of the
+ * tensor count and element total) for the process.  An item is computed the
+ * same way under either, so the results are the same bits. */
+nncp_status nncp_batch_set_schedule(nncp_batch* b, int pm_right, int pm_left);
+/* The schedule the last run used (NNCP_ERR_NOT_READY before the first). */
+nncp_status nncp_batch_get_schedule(const nncp_batch* b, int* pm_right, int* pm_left);
 const char* nncp_batch_last_error(const nncp_batch* b);
 void nncp_batch_destroy(nncp_batch* b);
 

@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -190,6 +192,11 @@ struct nncp_batch {
   cudaGraphExec_t graph = nullptr;
   int* host_done = nullptr;
   bool have_data = false;
+  // schedule of the two root phases: -1 = chosen by the tuner at the next run
+  int want_right = -1, want_left = -1;
+  BSchedule sched;
+  bool sched_set = false;
+  size_t off_queues = 0;
   std::string err;
 };
 
@@ -230,6 +237,7 @@ void plan(nncp_batch* b) {
   b->off_alpha_first = take((C + 1) * sizeof(int));
   b->off_alpha_part = take(std::max(1, b->plan.alpha.count) * sizeof(double));
   b->off_done = take(sizeof(int) * 4);
+  b->off_queues = take(sizeof(int) * 2);
   b->off_out_iters = take(C * sizeof(int));
   b->off_out_fits = take(C * sizeof(double));
   b->off_out_lam = take(std::max<size_t>(1, b->plan.lam_total) * sizeof(double));
@@ -249,6 +257,109 @@ T* at(nncp_batch* b, size_t off) {
 }
 
 }  // namespace
+
+// ---- schedule tuner ----------------------------------------------------------
+// The root phases' schedule (one CTA per item, or persistent CTAs taking items
+// from a counter) changes which CTA computes an item, never how: a tensor's
+// bits are the same under every schedule, so it can be chosen by timing.
+// Key: the batch's order, largest rank and the binary magnitudes of its tensor
+// count and element total (compositions of one class share the choice); the
+// choice is cached for the process.
+struct SchedKey {
+  int N, rmax, count_log2, elems_log2;
+  bool operator<(const SchedKey& o) const {
+    if (N != o.N) return N < o.N;
+    if (rmax != o.rmax) return rmax < o.rmax;
+    if (count_log2 != o.count_log2) return count_log2 < o.count_log2;
+    return elems_log2 < o.elems_log2;
+  }
+};
+std::mutex g_sched_mu;
+std::map<SchedKey, BSchedule> g_sched_cache;
+
+int ilog2(long long v) {
+  int l = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++l;
+  }
+  return l;
+}
+
+SchedKey sched_key(const nncp_batch* b) {
+  long long elems = 0;
+  for (const BTensor& t : b->ts) elems += t.I;
+  return SchedKey{b->N, b->plan.rmax, ilog2(b->count), ilog2(elems)};
+}
+
+// Median of three timed launches of one root phase under schedule `mode`.
+nncp_status time_phase(nncp_batch* b, int right, int mode, float* ms) {
+  BTensor* d_ts = at<BTensor>(b, b->off_ts);
+  const int4* d_items = at<int4>(b, b->off_items);
+  int* q = at<int>(b, b->off_queues);
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  float t[4];
+  for (int r = 0; r < 4; ++r) {
+    BCK(cudaEventRecord(e0, b->work));
+    if (mode) BCK(cudaMemsetAsync(q, 0, sizeof(int), b->work));
+    BCK(right ? launch_pm_right(b->plan, d_ts, d_items, mode ? q : nullptr, b->work)
+              : launch_pm_left(b->plan, d_ts, d_items, mode ? q : nullptr, b->work));
+    BCK(cudaEventRecord(e1, b->work));
+    BCK(cudaEventSynchronize(e1));
+    BCK(cudaEventElapsedTime(&t[r], e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::sort(t + 1, t + 4);  // the first launch is a warm-up
+  *ms = t[2];
+  return NNCP_OK;
+}
+
+// Chooses b->sched: a fixed request as given, else the cached choice for the
+// batch's class, else the faster schedule of each root phase, timed here
+// (after initialisation, before the iteration graph is captured).
+nncp_status choose_schedule(nncp_batch* b) {
+  const SchedKey key = sched_key(b);
+  BSchedule sch;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    auto it = g_sched_cache.find(key);
+    if (it != g_sched_cache.end()) {
+      sch = it->second;
+      cached = true;
+    }
+  }
+  if (!cached && (b->want_right < 0 || b->want_left < 0)) {
+    for (int right = 0; right < 2; ++right) {
+      float best = 0.0f;
+      int pick = 0;
+      for (int mode = 0; mode < 2; ++mode) {
+        float ms = 0.0f;
+        nncp_status st = time_phase(b, right, mode, &ms);
+        if (st != NNCP_OK) return st;
+        if (mode == 0 || ms < best) {
+          best = ms;
+          pick = mode;
+        }
+      }
+      (right ? sch.pm_right : sch.pm_left) = pick;
+    }
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    g_sched_cache[key] = sch;
+  }
+  if (b->want_right >= 0) sch.pm_right = b->want_right;
+  if (b->want_left >= 0) sch.pm_left = b->want_left;
+  if (!b->sched_set || sch.pm_right != b->sched.pm_right || sch.pm_left != b->sched.pm_left) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->sched = sch;
+  b->sched_set = true;
+  return NNCP_OK;
+}
 
 extern "C" {
 
@@ -373,10 +484,15 @@ nncp_status nncp_batch_run(nncp_batch* b, int max_iters, double tol, int* iters_
   BCK(cudaMemsetAsync(done, 0, sizeof(int), b->work));
   BCK(b_launch_init(b->plan, d_ts, d_items, at<double>(b, b->off_alpha_part),
                     at<int>(b, b->off_alpha_first), b->work));
+  {
+    const nncp_status st = choose_schedule(b);
+    if (st != NNCP_OK) return st;
+  }
   if (!b->graph) {
     cudaGraph_t g;
     BCK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = b_launch_iteration(b->plan, d_ts, d_items, done, b->work);
+    cudaError_t e = b_launch_iteration(b->plan, d_ts, d_items, done, b->work, b->sched,
+                                       at<int>(b, b->off_queues));
     cudaError_t e2 = cudaStreamEndCapture(b->work, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (e2 == cudaSuccess) cudaGraphDestroy(g);
@@ -482,6 +598,23 @@ nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims
       o += (size_t)rk[i];
     }
   }
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_set_schedule(nncp_batch* b, int pm_right, int pm_left) {
+  if (!b) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null batch");
+  if (pm_right < -1 || pm_right > 1 || pm_left < -1 || pm_left > 1)
+    return bfail(b, NNCP_ERR_INVALID_ARG, "schedules are -1 (tuned), 0 or 1");
+  b->want_right = pm_right;
+  b->want_left = pm_left;
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_get_schedule(const nncp_batch* b, int* pm_right, int* pm_left) {
+  if (!b || !pm_right || !pm_left) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null argument");
+  if (!b->sched_set) return bfail(const_cast<nncp_batch*>(b), NNCP_ERR_NOT_READY, "no run yet");
+  *pm_right = b->sched.pm_right;
+  *pm_left = b->sched.pm_left;
   return NNCP_OK;
 }
 

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "batch_kernels.cuh"
 
 namespace nncp {
@@ -302,19 +304,36 @@ __device__ __forceinline__ void pm_right_item(const BTensor& t, int chunk, float
   }
 }
 
+// Work item w of a phase for this CTA: with queue == NULL the CTA's own
+// index (one CTA per item, the hardware schedules them); otherwise the next
+// item taken from the phase's counter by a persistent CTA (-1: none left).
+// Either way an item is computed the same way, so the choice changes no bits.
+__device__ __forceinline__ int next_item(int* queue, int n_items, int* slot, bool first) {
+  if (!queue) return first ? (int)blockIdx.x : -1;
+  __syncthreads();  // every thread has read the previous item
+  if (threadIdx.x == 0) *slot = atomicAdd(queue, 1);
+  __syncthreads();
+  return *slot < n_items ? *slot : -1;
+}
+
 template <int RMAX>
 __global__ void __launch_bounds__(kThreads, RMAX <= 16 ? 4 : (RMAX <= 32 ? 3 : 2))
-k_b_pm_right(const BTensor* __restrict__ ts, const int4* __restrict__ items) {
+k_b_pm_right(const BTensor* __restrict__ ts, const int4* __restrict__ items, int n_items,
+             int* queue) {
   extern __shared__ __align__(16) float smem[];
-  const int4 it = items[blockIdx.x];
-  const BTensor& t = ts[it.x];
-  if (tensor_done(t)) return;
-  switch (b_rq(t.R)) {
-    case 1: pm_right_item<1>(t, it.y, smem); break;
-    case 2: pm_right_item<2>(t, it.y, smem); break;
-    case 4: pm_right_item<4>(t, it.y, smem); break;
-    case 8: if constexpr (RMAX >= 32) pm_right_item<8>(t, it.y, smem); break;
-    default: if constexpr (RMAX >= 64) pm_right_item<16>(t, it.y, smem); break;
+  __shared__ int slot;
+  for (int w = next_item(queue, n_items, &slot, true); w >= 0;
+       w = next_item(queue, n_items, &slot, false)) {
+    const int4 it = items[w];
+    const BTensor& t = ts[it.x];
+    if (tensor_done(t)) continue;
+    switch (b_rq(t.R)) {
+      case 1: pm_right_item<1>(t, it.y, smem); break;
+      case 2: pm_right_item<2>(t, it.y, smem); break;
+      case 4: pm_right_item<4>(t, it.y, smem); break;
+      case 8: if constexpr (RMAX >= 32) pm_right_item<8>(t, it.y, smem); break;
+      default: if constexpr (RMAX >= 64) pm_right_item<16>(t, it.y, smem); break;
+    }
   }
 }
 
@@ -465,17 +484,22 @@ __device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* 
 
 template <int RMAX>
 __global__ void __launch_bounds__(kThreads, RMAX <= 16 ? 3 : 2)
-k_b_pm_left(const BTensor* __restrict__ ts, const int4* __restrict__ items) {
+k_b_pm_left(const BTensor* __restrict__ ts, const int4* __restrict__ items, int n_items,
+            int* queue) {
   extern __shared__ __align__(16) float smem[];
-  const int4 it = items[blockIdx.x];
-  const BTensor& t = ts[it.x];
-  if (tensor_done(t)) return;
-  switch (b_rqb_left((int)t.dims[0], t.R)) {
-    case 1: pm_left_item<1>(t, it.y, smem); break;
-    case 2: pm_left_item<2>(t, it.y, smem); break;
-    case 4: pm_left_item<4>(t, it.y, smem); break;
-    case 8: if constexpr (RMAX >= 32) pm_left_item<8>(t, it.y, smem); break;
-    default: if constexpr (RMAX >= 64) pm_left_item<16>(t, it.y, smem); break;
+  __shared__ int slot;
+  for (int w = next_item(queue, n_items, &slot, true); w >= 0;
+       w = next_item(queue, n_items, &slot, false)) {
+    const int4 it = items[w];
+    const BTensor& t = ts[it.x];
+    if (tensor_done(t)) continue;
+    switch (b_rqb_left((int)t.dims[0], t.R)) {
+      case 1: pm_left_item<1>(t, it.y, smem); break;
+      case 2: pm_left_item<2>(t, it.y, smem); break;
+      case 4: pm_left_item<4>(t, it.y, smem); break;
+      case 8: if constexpr (RMAX >= 32) pm_left_item<8>(t, it.y, smem); break;
+      default: if constexpr (RMAX >= 64) pm_left_item<16>(t, it.y, smem); break;
+    }
   }
 }
 
@@ -771,30 +795,57 @@ cudaError_t batch_attributes_init() {
 
 namespace {
 
-cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, cudaStream_t st) {
+// Grid of a root phase: one CTA per item (queue NULL), or one wave of
+// persistent CTAs (every CTA that fits at once at this shared-memory size)
+// taking items from the counter `queue`.
+template <typename K>
+int phase_grid(K kernel, size_t smem, int n_items, const int* queue) {
+  if (!queue) return n_items;
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return std::max(1, std::min(n_items, sms * per_sm));
+}
+
+}  // namespace
+
+cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
+                            cudaStream_t st) {
   const size_t sm = (size_t)(2 * kTileFloats + kWsFloats) * sizeof(float);
   const int n = p.pmr.count;
   const int4* it = items + p.pmr.off;
   if (n > 0) {
-    if (p.rmax <= 16) k_b_pm_right<16><<<n, kThreads, sm, st>>>(ts, it);
-    else if (p.rmax <= 32) k_b_pm_right<32><<<n, kThreads, sm, st>>>(ts, it);
-    else k_b_pm_right<64><<<n, kThreads, sm, st>>>(ts, it);
+    if (p.rmax <= 16)
+      k_b_pm_right<16><<<phase_grid(k_b_pm_right<16>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
+    else if (p.rmax <= 32)
+      k_b_pm_right<32><<<phase_grid(k_b_pm_right<32>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
+    else
+      k_b_pm_right<64><<<phase_grid(k_b_pm_right<64>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
   }
   if (p.pmr_red.count > 0)
     k_b_reduce<<<p.pmr_red.count, kReduceBlock, 0, st>>>(ts, items + p.pmr_red.off);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, cudaStream_t st) {
+cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
+                           cudaStream_t st) {
   const int n = p.pml.count;
   if (n == 0) return cudaSuccess;
   const int4* it = items + p.pml.off;
   const size_t sm = (size_t)(left_fixed_floats() + p.hs_floats) * sizeof(float);
-  if (p.rmax <= 16) k_b_pm_left<16><<<n, kThreads, sm, st>>>(ts, it);
-  else if (p.rmax <= 32) k_b_pm_left<32><<<n, kThreads, sm, st>>>(ts, it);
-  else k_b_pm_left<64><<<n, kThreads, sm, st>>>(ts, it);
+  if (p.rmax <= 16)
+    k_b_pm_left<16><<<phase_grid(k_b_pm_left<16>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
+  else if (p.rmax <= 32)
+    k_b_pm_left<32><<<phase_grid(k_b_pm_left<32>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
+  else
+    k_b_pm_left<64><<<phase_grid(k_b_pm_left<64>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
   return cudaGetLastError();
 }
+
+namespace {
 
 cudaError_t launch_update(const BPlan& p, BTensor* ts, int n, int* done_count, cudaStream_t st) {
   if (p.rmax <= 16) k_b_update<16><<<p.count, 256, update_smem<16>(), st>>>(ts, n, done_count);
@@ -815,12 +866,14 @@ cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double
 }
 
 cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, int* done_count,
-                               cudaStream_t st) {
+                               cudaStream_t st, const BSchedule& sch, int* queues) {
   if (p.count == 0) return cudaSuccess;
   const int N = p.N;
-  cudaError_t e = launch_pm_right(p, ts, items, st);
+  cudaError_t e = cudaSuccess;
+  if (sch.pm_right || sch.pm_left) e = cudaMemsetAsync(queues, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = launch_pm_right(p, ts, items, sch.pm_right ? queues : nullptr, st);
   if (e == cudaSuccess) e = launch_update(p, ts, 0, done_count, st);
-  if (e == cudaSuccess) e = launch_pm_left(p, ts, items, st);
+  if (e == cudaSuccess) e = launch_pm_left(p, ts, items, sch.pm_left ? queues + 1 : nullptr, st);
   // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
   for (int a = 1; a < N && e == cudaSuccess; ++a) {
     if (a == N - 1) {

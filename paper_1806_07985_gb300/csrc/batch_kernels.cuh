@@ -110,9 +110,23 @@ cudaError_t batch_attributes_init();
 // alpha, normalisation, Grams and S of every tensor of the plan
 cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double* alpha_part,
                           const int* alpha_first, cudaStream_t st);
-// one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1)
+// How the two root phases run: 0 = one CTA per work item (scheduled by the
+// hardware), 1 = one wave of persistent CTAs taking items from a counter.
+// A tensor's bits are the same under every schedule.
+struct BSchedule {
+  int pm_right = 0, pm_left = 0;
+};
+// The root phases alone (no state changes but their outputs, which every
+// iteration recomputes): what the schedule tuner times.  queue: a device
+// counter set to 0 before the launch, or NULL for one CTA per item.
+cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
+                            cudaStream_t st);
+cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
+                           cudaStream_t st);
+// one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1);
+// queues: two device ints for the persistent schedules
 cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, int* done_count,
-                               cudaStream_t st);
+                               cudaStream_t st, const BSchedule& sch, int* queues);
 // per tensor: iterations, last fit, lambda into contiguous arrays, and a state
 // word (bit 0: non-finite fit, bit 1: stopped)
 cudaError_t launch_b_gather(const BTensor* ts, int count, int* iters, double* fits,

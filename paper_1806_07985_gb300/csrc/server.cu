@@ -560,7 +560,7 @@ void worker_main(nncp_server* s) {
       if (g.members.empty()) continue;
       swept = true;
       if (g.dirty) e = upload_group(s, g, N);
-      if (e == cudaSuccess) e = b_launch_iteration(g.plan, g.d_ts, g.d_items, s->d_done, s->st);
+      if (e == cudaSuccess) e = b_launch_iteration(g.plan, g.d_ts, g.d_items, s->d_done, s->st, BSchedule(), nullptr);
       if (e == cudaSuccess)
         e = launch_b_gather(g.d_ts, (int)g.members.size(), g.d_iters, g.d_fits, nullptr, nullptr,
                             g.d_state, s->st);

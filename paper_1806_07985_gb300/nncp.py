@@ -84,6 +84,8 @@ _SIGNATURES = [
                                         _c_vpp, ctypes.POINTER(_c_vpp), ctypes.POINTER(_c_dblp),
                                         ctypes.c_int, ctypes.c_double, _c_intp, _c_dblp,
                                         ctypes.c_void_p]),
+    ("nncp_batch_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("nncp_batch_get_schedule", ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_intp]),
     ("nncp_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_batch_destroy", None, [ctypes.c_void_p]),
     ("nncp_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -455,6 +457,15 @@ class Batch:
             lams.append(list(lam[o:o + r]))
             o += r
         return list(iters), list(fits), lams
+
+    def set_schedule(self, pm_right=-1, pm_left=-1):
+        """Root-phase schedules: 0 one CTA per item, 1 persistent, -1 tuned."""
+        _bcheck(load().nncp_batch_set_schedule(self.b, int(pm_right), int(pm_left)), self.b)
+
+    def schedule(self):
+        r, l = ctypes.c_int(), ctypes.c_int()
+        _bcheck(load().nncp_batch_get_schedule(self.b, ctypes.byref(r), ctypes.byref(l)), self.b)
+        return r.value, l.value
 
     def close(self):
         if self.b:

@@ -183,3 +183,44 @@ def test_one_call_batch_solve_rejects_bad_orders(nn):
     with pytest.raises(nn.NNCPError) as info:
         nn.nncp_batch_solve([(8,)], [R], X, [H[0][:1]], 2, 0.0)  # order 1
     assert info.value.status == nn.NNCP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("sched", [(0, 0), (1, 1), (0, 1), (1, 0)])
+def test_root_phase_schedules_give_the_same_bits(nn, sched):
+    # one CTA per work item or persistent CTAs taking items from a counter:
+    # which CTA computes an item changes, how it is computed does not
+    probs = _problems(10, seed0=31, hi=60)
+    ref = _run_batch(nn, probs, 5)
+    b = nn.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=5)
+    try:
+        b.set_schedule(*sched)
+        X = [torch.from_numpy(p[2]).cuda() for p in probs]
+        H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
+        b.set_data(X, H)
+        k, fits, lams = b.solve(5, 0.0)
+        assert b.schedule() == sched
+        Hs = [[h.cpu().numpy() for h in hs] for hs in H]
+    finally:
+        b.close()
+    assert k == ref[0] and fits == ref[1] and lams == ref[2]
+    for a, c in zip(Hs, ref[3]):
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y)
+
+
+def test_schedule_tuner_picks_a_valid_schedule(nn):
+    probs = _problems(6, seed0=41)
+    b = nn.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=3)
+    try:
+        with pytest.raises(nn.NNCPError):
+            b.schedule()                     # before the first run
+        with pytest.raises(nn.NNCPError):
+            b.set_schedule(2, 0)
+        X = [torch.from_numpy(p[2]).cuda() for p in probs]
+        H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
+        b.set_data(X, H)
+        b.solve(3, 0.0)
+        r, l = b.schedule()
+        assert r in (0, 1) and l in (0, 1)
+    finally:
+        b.close()
