@@ -301,7 +301,7 @@ def run_ours(args):
     x_bytes = Xuse.numel() * Xuse.element_size()
     dom = max(pm, key=lambda s: pm[s])
     achieved = x_bytes / (pm[dom] * 1e-3) / 1e9
-    kernel_key = f"pm_{'right' if dom == 0 else 'left'}_{prec_name}_512x512x512_R32"
+    kernel_key = f"pm_{'left' if dom == 0 else 'right'}_{prec_name}_512x512x512_R32"
     traffic = recorded_traffic(kernel_key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
