@@ -683,7 +683,9 @@ def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
            "tensor_GBps": round(tensor_bytes / t / 1e9, 1),
            "root_phase_schedule": {"pm_right": schedule[0], "pm_left": schedule[1],
                                    "codes": "0 one CTA per work item, 1 persistent CTAs on a "
-                                            "work counter; chosen by the library's tuner"}}
+                                            "work counter, 2 (root -> {1}) persistent CTAs "
+                                            "streaming tiles through a shared-memory ring; "
+                                            "chosen by the library's tuner"}}
     if no_plain:
         return out
     sample = list(range(0, count, max(1, count // 32)))[:32]

@@ -237,7 +237,7 @@ void plan(nncp_batch* b) {
   b->off_alpha_first = take((C + 1) * sizeof(int));
   b->off_alpha_part = take(std::max(1, b->plan.alpha.count) * sizeof(double));
   b->off_done = take(sizeof(int) * 4);
-  b->off_queues = take(sizeof(int) * 2);
+  b->off_queues = take(sizeof(int) * 4);  // root-phase counters, error word
   b->off_out_iters = take(C * sizeof(int));
   b->off_out_fits = take(C * sizeof(double));
   b->off_out_lam = take(std::max<size_t>(1, b->plan.lam_total) * sizeof(double));
@@ -304,8 +304,8 @@ nncp_status time_phase(nncp_batch* b, int right, int mode, float* ms) {
   for (int r = 0; r < 4; ++r) {
     BCK(cudaEventRecord(e0, b->work));
     if (mode) BCK(cudaMemsetAsync(q, 0, sizeof(int), b->work));
-    BCK(right ? launch_pm_right(b->plan, d_ts, d_items, mode ? q : nullptr, b->work)
-              : launch_pm_left(b->plan, d_ts, d_items, mode ? q : nullptr, b->work));
+    BCK(right ? launch_pm_right(b->plan, d_ts, d_items, mode, q, q + 2, b->work)
+              : launch_pm_left(b->plan, d_ts, d_items, mode, q, q + 2, b->work));
     BCK(cudaEventRecord(e1, b->work));
     BCK(cudaEventSynchronize(e1));
     BCK(cudaEventElapsedTime(&t[r], e0, e1));
@@ -336,7 +336,7 @@ nncp_status choose_schedule(nncp_batch* b) {
     for (int right = 0; right < 2; ++right) {
       float best = 0.0f;
       int pick = 0;
-      for (int mode = 0; mode < 2; ++mode) {
+      for (int mode = 0; mode < (right ? kRightSchedules : kLeftSchedules); ++mode) {
         float ms = 0.0f;
         nncp_status st = time_phase(b, right, mode, &ms);
         if (st != NNCP_OK) return st;
@@ -482,6 +482,8 @@ nncp_status nncp_batch_run(nncp_batch* b, int max_iters, double tol, int* iters_
                       b->work));
   int* done = at<int>(b, b->off_done);
   BCK(cudaMemsetAsync(done, 0, sizeof(int), b->work));
+  int* d_err = at<int>(b, b->off_queues) + 2;
+  BCK(cudaMemsetAsync(d_err, 0, sizeof(int), b->work));
   BCK(b_launch_init(b->plan, d_ts, d_items, at<double>(b, b->off_alpha_part),
                     at<int>(b, b->off_alpha_first), b->work));
   {
@@ -531,10 +533,13 @@ nncp_status nncp_batch_run(nncp_batch* b, int max_iters, double tol, int* iters_
     BCK(cudaMemcpyAsync(lambda_out, d_lam, b->plan.lam_total * sizeof(double),
                         cudaMemcpyDeviceToHost, b->work));
   BCK(cudaMemcpyAsync(nf.data(), d_nf, b->count * sizeof(int), cudaMemcpyDeviceToHost, b->work));
+  BCK(cudaMemcpyAsync(b->host_done + 1, d_err, sizeof(int), cudaMemcpyDeviceToHost, b->work));
   BCK(cudaStreamSynchronize(b->work));
   BCK(cudaEventRecord(ev, b->work));
   BCK(cudaStreamWaitEvent(user, ev, 0));
   cudaEventDestroy(ev);
+  if (b->host_done[1])
+    return bfail(b, NNCP_ERR_TIMEOUT, "a streamed root kernel gave up waiting on its pipeline");
   for (int t = 0; t < b->count; ++t)
     if (nf[t] & 1) return bfail(b, NNCP_ERR_NUMERIC, "tensor %d: non-finite fit", t);
   return NNCP_OK;
@@ -603,8 +608,10 @@ nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims
 
 nncp_status nncp_batch_set_schedule(nncp_batch* b, int pm_right, int pm_left) {
   if (!b) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null batch");
-  if (pm_right < -1 || pm_right > 1 || pm_left < -1 || pm_left > 1)
-    return bfail(b, NNCP_ERR_INVALID_ARG, "schedules are -1 (tuned), 0 or 1");
+  if (pm_right < -1 || pm_right >= kRightSchedules || pm_left < -1 || pm_left >= kLeftSchedules)
+    return bfail(b, NNCP_ERR_INVALID_ARG,
+                 "schedules are -1 (tuned), 0..%d (root -> {1}) and 0..%d (root -> {2..N})",
+                 kRightSchedules - 1, kLeftSchedules - 1);
   b->want_right = pm_right;
   b->want_left = pm_left;
   return NNCP_OK;

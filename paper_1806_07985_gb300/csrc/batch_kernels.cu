@@ -138,6 +138,7 @@ template <int NPENDING>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING) : "memory");
 }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // floats [0, L) of src (16-byte aligned) to Xs[0, L)
 __device__ __forceinline__ void tile_copy_dense(float* Xs, const float* __restrict__ src, int L) {
@@ -335,6 +336,425 @@ k_b_pm_right(const BTensor* __restrict__ ts, const int4* __restrict__ items, int
       default: if constexpr (RMAX >= 64) pm_right_item<16>(t, it.y, smem); break;
     }
   }
+}
+
+// ------------------------------------- streamed root -> {1} (schedule 2) --
+//
+// The arithmetic of pm_right_item (every output's products and sums in the
+// same order, so the same bits) with its jobs split over the warps of a
+// persistent CTA, the tiles passing through a ring of shared-memory stages:
+//   warp 0, scheduler: takes items from the counter (several at a time while
+//                      it meets converged tensors), skips those, and writes
+//                      each item's descriptor into a ring of item slots;
+//   warp 1, loader:    copies an item's descriptor into the header of every
+//                      stage of it and the stage's rows of X_(1)^T into the
+//                      stage (cp.async, L2 evict-first), arriving on the
+//                      stage's full barrier as the copies land;
+//   warps 2-4, builders: take stages in turn and form a stage's Khatri-Rao
+//                      rows;
+//   warps 5-12, consumers (the 256 threads of pm_right_item): contract each
+//                      tile and free its stage; at the end of an item they
+//                      add the column groups in group order through the last
+//                      stage's tile area, then free it.
+// The scheduler runs ahead of the loader and the loader ahead of the rest, so
+// tiles stream in across item boundaries.  Every wait is on an mbarrier and
+// bounded (about two seconds): on expiry a thread records the error word and
+// leaves, and the waits of the other roles then expire in turn.
+
+constexpr int kWsBuildWarps = 3, kWsConsWarps = 8;
+constexpr int kWsConsFirstWarp = 2 + kWsBuildWarps;
+constexpr int kWsThreads = 32 * (kWsConsFirstWarp + kWsConsWarps);
+constexpr int kWsStageFloats = kTileFloats + kWsFloats;
+constexpr int kWsItemSlots = 4;
+// Khatri-Rao entries (row, rank group) per builder lane and round: a tile has at most kWsFloats / 4
+constexpr int kWsBuildPer = 4;
+constexpr int kWsBuildRounds = (kWsFloats / 4 + 32 * kWsBuildPer - 1) / (32 * kWsBuildPer);
+constexpr long long kWsWaitCycles = 4000000000LL;
+
+// One item as the builders and consumers need it (w < 0: no more items);
+// H[m - 1] is factor m + 1 (mode 1's is not used).
+struct WsDesc {
+  int w, I1, R, N, nj, j0, j1, ntile;
+  int dims[kMaxModes];
+  float* out;
+  const float* H[kMaxModes - 1];
+};
+struct WsHeader {
+  WsDesc d;
+  int k;  // tile within the item
+  int pad[3];
+};
+struct WsSlot {
+  WsDesc d;
+  const float* X;
+};
+static_assert(sizeof(WsDesc) % 8 == 0 && sizeof(WsHeader) % 16 == 0 && sizeof(WsSlot) % 8 == 0,
+              "descriptor layout");
+constexpr int kWsDescWords = (int)(sizeof(WsDesc) / 4);
+static_assert(kWsDescWords <= 32, "one descriptor word per lane");
+
+__device__ __forceinline__ void mb_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// arrives once every cp.async this thread has issued so far has landed
+__device__ __forceinline__ void mb_arrive_cp_async(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mb_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, int* err) {
+  if (mb_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mb_test(bar, parity)) {
+    if (clock64() - t0 > kWsWaitCycles) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16_hint(float* dst, const float* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+
+// Shared memory of the streamed kernel: S stages (X tile, Khatri-Rao tile),
+// their headers, the item slots and the barriers.
+struct WsSmem {
+  float* stage0;
+  WsHeader* hdr;
+  WsSlot* slot;
+  uint32_t bar0;
+  int S;
+  __device__ float* xs(int s) const { return stage0 + (size_t)s * kWsStageFloats; }
+  __device__ uint32_t full(int s) const { return bar0 + 8u * s; }
+  __device__ uint32_t empty(int s) const { return bar0 + 8u * (S + s); }
+  __device__ uint32_t hfull(int s) const { return bar0 + 8u * (2 * S + s); }
+  __device__ uint32_t islot_full(int i) const { return bar0 + 8u * (3 * S + i); }
+  __device__ uint32_t islot_empty(int i) const { return bar0 + 8u * (3 * S + kWsItemSlots + i); }
+  __device__ uint32_t red_full() const { return bar0 + 8u * (3 * S + 2 * kWsItemSlots); }
+  __device__ uint32_t red_empty() const { return bar0 + 8u * (3 * S + 2 * kWsItemSlots + 1); }
+  __device__ uint32_t cons_sync() const { return bar0 + 8u * (3 * S + 2 * kWsItemSlots + 2); }
+};
+
+__host__ __device__ constexpr size_t ws_smem_bytes(int S) {
+  return (size_t)S * kWsStageFloats * sizeof(float) + (size_t)S * sizeof(WsHeader) +
+         (size_t)kWsItemSlots * sizeof(WsSlot) +
+         (size_t)(3 * S + 2 * kWsItemSlots + 3) * sizeof(uint64_t);
+}
+
+__device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restrict__ items,
+                             int n_items, int* queue, const WsSmem& sm, int* err) {
+  const int lane = threadIdx.x & 31;
+  int m = 0;      // item slots filled
+  int grab = 1;   // candidates taken per round: doubles while they are all converged
+  bool more = true;
+  while (more) {
+    const int c = lane < grab ? atomicAdd(queue, 1) : n_items;
+    const bool live = c < n_items;
+    const bool active = live && !tensor_done(ts[items[c].x]);
+    unsigned act = __ballot_sync(0xffffffffu, active);
+    more = __ballot_sync(0xffffffffu, live) == (grab >= 32 ? 0xffffffffu : (1u << grab) - 1u);
+    grab = act ? 1 : min(32, 2 * grab);
+    while (act) {
+      const int src = __ffs(act) - 1;
+      act &= act - 1;
+      const int w = __shfl_sync(0xffffffffu, c, src);
+      const int sl = m % kWsItemSlots;
+      if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err)) return;
+      if (lane == 0) {
+        const int4 it = items[w];
+        const BTensor& t = ts[it.x];
+        WsSlot q;
+        WsDesc& d = q.d;
+        d.w = w;
+        d.I1 = (int)t.dims[0];
+        d.R = t.R;
+        d.N = t.N;
+        d.nj = t.rows_r;
+        const int J = (int)(t.I / d.I1);
+        d.j0 = it.y * (int)t.jchunk;
+        d.j1 = min(J, d.j0 + (int)t.jchunk);
+        d.ntile = (d.j1 - d.j0 + d.nj - 1) / d.nj;
+        for (int n = 0; n < kMaxModes; ++n) d.dims[n] = n < d.N ? (int)t.dims[n] : 0;
+        for (int n = 1; n < kMaxModes; ++n) d.H[n - 1] = n < d.N ? t.H[n] : nullptr;
+        d.out = t.part + (long long)it.y * d.I1 * d.R;
+        q.X = t.X;
+        sm.slot[sl] = q;
+      }
+      __syncwarp();
+      if (lane == 0) mb_arrive(sm.islot_full(sl));
+      ++m;
+    }
+  }
+  // no more items
+  const int sl = m % kWsItemSlots;
+  if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err)) return;
+  if (lane == 0) sm.slot[sl].d.w = -1;
+  __syncwarp();
+  if (lane == 0) mb_arrive(sm.islot_full(sl));
+}
+
+__device__ void ws_loader(const WsSmem& sm, int* err) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t pol = l2_evict_first_policy();
+  int n = 0;  // stages posted
+  for (int m = 0;; ++m) {
+    const int sl = m % kWsItemSlots;
+    if (!mb_wait(sm.islot_full(sl), (m / kWsItemSlots) & 1, err)) break;
+    const WsDesc& d = sm.slot[sl].d;
+    const int w = d.w, I1 = d.I1, nj = d.nj, j0 = d.j0, j1 = d.j1;
+    // the last item is followed by one stop stage per builder warp
+    const int ntile = w >= 0 ? d.ntile : kWsBuildWarps;
+    const float* X = sm.slot[sl].X;
+    const uint32_t word = lane < kWsDescWords ? reinterpret_cast<const uint32_t*>(&d)[lane] : 0u;
+    __syncwarp();
+    if (lane == 0) mb_arrive(sm.islot_empty(sl));
+    bool ok = true;
+    for (int k = 0; k < ntile; ++k, ++n) {
+      const int s = n % sm.S;
+      if (!mb_wait(sm.empty(s), ((n / sm.S) & 1) ^ 1, err)) {
+        ok = false;
+        break;
+      }
+      if (lane < kWsDescWords) reinterpret_cast<uint32_t*>(&sm.hdr[s].d)[lane] = word;
+      if (lane == 0) sm.hdr[s].k = k;
+      if (w >= 0) {
+        const int jt = j0 + k * nj, L = min(nj, j1 - jt) * I1;
+        const float* src = X + (long long)jt * I1;
+        float* dst = sm.xs(s);
+        const int L4 = L & ~3;
+        for (int e = 4 * lane; e < L4; e += 128) cp_async16_hint(dst + e, src + e, pol);
+        if (L4 + lane < L) cp_async4(dst + L4 + lane, src + L4 + lane);
+      }
+      mb_arrive_cp_async(sm.full(s));
+      __syncwarp();
+      if (lane == 0) mb_arrive(sm.hfull(s));
+    }
+    if (!ok || w < 0) break;
+  }
+  cp_async_wait_all();
+}
+
+// Builder warp b forms the Khatri-Rao tiles of stages b, b + 3, b + 6, ...
+__device__ void ws_builder(const WsSmem& sm, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int b = (threadIdx.x >> 5) - 2;
+  for (int n = b;; n += kWsBuildWarps) {
+    const int s = n % sm.S;
+    if (!mb_wait(sm.hfull(s), (n / sm.S) & 1, err)) return;
+    const WsHeader& h = sm.hdr[s];
+    const int w = h.d.w;
+    if (w >= 0) {
+      const int R = h.d.R, N = h.d.N, RQB = b_rq(R), lg = __ffs(RQB) - 1;
+      const int jt = h.d.j0 + h.k * h.d.nj, njk = min(h.d.nj, h.d.j1 - jt);
+      const int ne = njk * RQB;
+      float4* W = reinterpret_cast<float4*>(sm.xs(s) + kTileFloats);
+      for (int rd = 0; rd < kWsBuildRounds; ++rd) {
+        const int e0 = lane + 32 * kWsBuildPer * rd;
+        if (e0 >= ne) break;
+        // every entry of this round at once, so that the factor-row loads of
+        // all of them are in flight together
+        float4 v[kWsBuildPer];
+        int rem[kWsBuildPer];
+#pragma unroll
+        for (int u = 0; u < kWsBuildPer; ++u) {
+          rem[u] = jt + ((e0 + 32 * u) >> lg);
+          v[u] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+        }
+        for (int m = 1; m < N; ++m) {
+          const int dm = h.d.dims[m];
+          const float* Hm = h.d.H[m - 1];
+#pragma unroll
+          for (int u = 0; u < kWsBuildPer; ++u) {
+            const int e = e0 + 32 * u;
+            if (e < ne) {
+              const int jm = rem[u] % dm;
+              rem[u] /= dm;
+              const float4 hv = ld_rank4(Hm + jm * R, 4 * (e & (RQB - 1)), R);
+              v[u].x *= hv.x;
+              v[u].y *= hv.y;
+              v[u].z *= hv.z;
+              v[u].w *= hv.w;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kWsBuildPer; ++u) {
+          const int e = e0 + 32 * u;
+          if (e < ne) W[e] = v[u];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mb_arrive(sm.full(s));
+    if (w < 0) return;
+  }
+}
+
+// One item's tiles (the first already waited for), then its group sum.
+// false: a wait expired.
+template <int RQB>
+__device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const WsSmem& sm,
+                           int* err) {
+  const int ct = threadIdx.x - 32 * kWsConsFirstWarp;  // 0 .. 255
+  const int lane = threadIdx.x & 31;
+  const int R = d.R, I1 = d.I1, nj = d.nj, j0 = d.j0, j1 = d.j1, ntile = d.ntile;
+  float* out = d.out;
+  const int G = kGroupThreads / I1;
+  const int g = ct / I1, i = ct - g * I1;
+  const bool act = g < G;
+  float acc[RQB][4];
+#pragma unroll
+  for (int u = 0; u < RQB; ++u)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[u][b] = 0.0f;
+  int s = 0;
+  for (int k = 0; k < ntile; ++k, ++n) {
+    s = n % sm.S;
+    if (k > 0 && !mb_wait(sm.full(s), (n / sm.S) & 1, err)) return false;
+    const int jt = j0 + k * nj, njk = min(nj, j1 - jt);
+    if (act) {
+      const float* xp = sm.xs(s) + i;
+      const float4* W4 = reinterpret_cast<const float4*>(sm.xs(s) + kTileFloats);
+#pragma unroll 2
+      for (int jj = g; jj < njk; jj += G) {
+        const float x = xp[jj * I1];
+#pragma unroll
+        for (int u = 0; u < RQB; ++u) fma4(acc[u], x, W4[jj * RQB + u]);
+      }
+    }
+    if (k + 1 < ntile || G == 1) {
+      __syncwarp();
+      if (lane == 0) mb_arrive(sm.empty(s));
+    }
+  }
+  if (G > 1) {
+    // column groups added in group order, through the last stage's tile area
+    // (still held), up to 4 rank groups at a time, once every consumer warp
+    // is done reading that tile
+    __syncwarp();
+    if (lane == 0) mb_arrive(sm.cons_sync());
+    if (!mb_wait(sm.cons_sync(), nsync & 1, err)) return false;
+    ++nsync;
+    float4* red = reinterpret_cast<float4*>(sm.xs(s));
+#pragma unroll
+    for (int u0 = 0; u0 < RQB; u0 += 4) {
+      const uint32_t par = nred & 1;
+      ++nred;
+      if (u0 > 0 && !mb_wait(sm.red_empty(), par ^ 1, err)) return false;
+      if (act) {
+#pragma unroll
+        for (int u = u0; u < u0 + 4 && u < RQB; ++u)
+          red[(u - u0) * kThreads + ct] = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+      }
+      __syncwarp();
+      if (lane == 0) mb_arrive(sm.red_full());
+      if (ct < I1) {
+        if (!mb_wait(sm.red_full(), par, err)) return false;
+#pragma unroll
+        for (int u = u0; u < u0 + 4 && u < RQB; ++u) {
+          float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          for (int gg = 0; gg < G; ++gg) {
+            const float4 v = red[(u - u0) * kThreads + gg * I1 + ct];
+            s4[0] += v.x;
+            s4[1] += v.y;
+            s4[2] += v.z;
+            s4[3] += v.w;
+          }
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (4 * u + b < R) out[ct * R + 4 * u + b] = s4[b];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mb_arrive(sm.red_empty());
+    }
+    __syncwarp();
+    if (lane == 0) mb_arrive(sm.empty(s));
+  } else if (act) {
+#pragma unroll
+    for (int u = 0; u < RQB; ++u)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * u + b < R) out[i * R + 4 * u + b] = acc[u][b];
+  }
+  return true;
+}
+
+template <int RMAX>
+__device__ void ws_consumer(const WsSmem& sm, int* err) {
+  int nred = 0, nsync = 0;
+  for (int n = 0;;) {
+    const int s = n % sm.S;
+    if (!mb_wait(sm.full(s), (n / sm.S) & 1, err)) return;
+    const WsDesc& d = sm.hdr[s].d;
+    if (d.w < 0) return;
+    bool ok = true;
+    switch (b_rq(d.R)) {
+      case 1: ok = ws_consume<1>(d, n, nred, nsync, sm, err); break;
+      case 2: ok = ws_consume<2>(d, n, nred, nsync, sm, err); break;
+      case 4: ok = ws_consume<4>(d, n, nred, nsync, sm, err); break;
+      case 8: if constexpr (RMAX >= 32) ok = ws_consume<8>(d, n, nred, nsync, sm, err); break;
+      default: if constexpr (RMAX >= 64) ok = ws_consume<16>(d, n, nred, nsync, sm, err); break;
+    }
+    if (!ok) return;
+  }
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(kWsThreads, RMAX <= 16 ? 2 : 1)
+k_b_pm_right_ws(const BTensor* __restrict__ ts, const int4* __restrict__ items, int n_items,
+                int* queue, int S, int* err) {
+  extern __shared__ __align__(16) float smem[];
+  WsSmem sm;
+  sm.S = S;
+  sm.stage0 = smem;
+  sm.hdr = reinterpret_cast<WsHeader*>(smem + (size_t)S * kWsStageFloats);
+  sm.slot = reinterpret_cast<WsSlot*>(sm.hdr + S);
+  sm.bar0 = smem_u32(sm.slot + kWsItemSlots);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mb_init(sm.full(s), 32 + 1);  // the loader lanes' copies + the stage's builder warp
+      mb_init(sm.empty(s), kWsConsWarps);
+      mb_init(sm.hfull(s), 1);
+    }
+    for (int i = 0; i < kWsItemSlots; ++i) {
+      mb_init(sm.islot_full(i), 1);
+      mb_init(sm.islot_empty(i), 1);
+    }
+    mb_init(sm.red_full(), kWsConsWarps);
+    mb_init(sm.red_empty(), kWsConsWarps);
+    mb_init(sm.cons_sync(), kWsConsWarps);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0)
+    ws_scheduler(ts, items, n_items, queue, sm, err);
+  else if (warp == 1)
+    ws_loader(sm, err);
+  else if (warp < kWsConsFirstWarp)
+    ws_builder(sm, err);
+  else
+    ws_consumer<RMAX>(sm, err);
 }
 
 // M = sum of a phase's partial chunks in chunk order.  Item (tensor, block of
@@ -787,6 +1207,12 @@ cudaError_t batch_attributes_init() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, right);
+  int dev = 0, optin = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right_ws<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right_ws<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right_ws<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
@@ -812,12 +1238,48 @@ int phase_grid(K kernel, size_t smem, int n_items, const int* queue) {
 
 }  // namespace
 
-cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
-                            cudaStream_t st) {
+namespace {
+
+// Streamed root -> {1}: as many ring stages (at most 8) as fit at two CTAs per
+// SM (RMAX 16) or one, and one wave of CTAs.
+template <int RMAX>
+cudaError_t launch_pm_right_ws(const BTensor* ts, const int4* it, int n, int* queue, int* err,
+                               cudaStream_t st) {
+  int dev = 0, sms = 1, smem_sm = 0, reserved = 0, optin = 0, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int want = RMAX <= 16 ? 2 : 1;
+  const size_t budget = std::min<size_t>((size_t)optin, (size_t)(smem_sm / want - reserved));
+  int S = 8;
+  while (S > kWsBuildWarps + 1 && ws_smem_bytes(S) > budget) --S;
+  const size_t bytes = ws_smem_bytes(S);
+  if (bytes > (size_t)optin) return cudaErrorInvalidConfiguration;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pm_right_ws<RMAX>, kWsThreads,
+                                                    bytes) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int grid = std::max(1, std::min(n, sms * per_sm));
+  k_b_pm_right_ws<RMAX><<<grid, kWsThreads, bytes, st>>>(ts, it, n, queue, S, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int mode,
+                            int* queue, int* err, cudaStream_t st) {
   const size_t sm = (size_t)(2 * kTileFloats + kWsFloats) * sizeof(float);
   const int n = p.pmr.count;
   const int4* it = items + p.pmr.off;
-  if (n > 0) {
+  if (mode == 0 || !queue) queue = nullptr;
+  if (n > 0 && mode == 2 && queue && err) {
+    cudaError_t e = p.rmax <= 16   ? launch_pm_right_ws<16>(ts, it, n, queue, err, st)
+                    : p.rmax <= 32 ? launch_pm_right_ws<32>(ts, it, n, queue, err, st)
+                                   : launch_pm_right_ws<64>(ts, it, n, queue, err, st);
+    if (e != cudaSuccess) return e;
+  } else if (n > 0) {
     if (p.rmax <= 16)
       k_b_pm_right<16><<<phase_grid(k_b_pm_right<16>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
     else if (p.rmax <= 32)
@@ -830,8 +1292,9 @@ cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items
   return cudaGetLastError();
 }
 
-cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
-                           cudaStream_t st) {
+cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int mode,
+                           int* queue, int* /*err*/, cudaStream_t st) {
+  if (mode == 0) queue = nullptr;
   const int n = p.pml.count;
   if (n == 0) return cudaSuccess;
   const int4* it = items + p.pml.off;
@@ -870,10 +1333,14 @@ cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, i
   if (p.count == 0) return cudaSuccess;
   const int N = p.N;
   cudaError_t e = cudaSuccess;
-  if (sch.pm_right || sch.pm_left) e = cudaMemsetAsync(queues, 0, 2 * sizeof(int), st);
-  if (e == cudaSuccess) e = launch_pm_right(p, ts, items, sch.pm_right ? queues : nullptr, st);
+  const bool counters = queues && (sch.pm_right || sch.pm_left);
+  if (counters) e = cudaMemsetAsync(queues, 0, 2 * sizeof(int), st);
+  int* err = queues ? queues + 2 : nullptr;
+  if (e == cudaSuccess)
+    e = launch_pm_right(p, ts, items, counters ? sch.pm_right : 0, queues, err, st);
   if (e == cudaSuccess) e = launch_update(p, ts, 0, done_count, st);
-  if (e == cudaSuccess) e = launch_pm_left(p, ts, items, sch.pm_left ? queues + 1 : nullptr, st);
+  if (e == cudaSuccess)
+    e = launch_pm_left(p, ts, items, counters ? sch.pm_left : 0, queues ? queues + 1 : nullptr, err, st);
   // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
   for (int a = 1; a < N && e == cudaSuccess; ++a) {
     if (a == N - 1) {

@@ -111,20 +111,26 @@ cudaError_t batch_attributes_init();
 cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double* alpha_part,
                           const int* alpha_first, cudaStream_t st);
 // How the two root phases run: 0 = one CTA per work item (scheduled by the
-// hardware), 1 = one wave of persistent CTAs taking items from a counter.
-// A tensor's bits are the same under every schedule.
+// hardware), 1 = one wave of persistent CTAs taking items from a counter,
+// 2 (root -> {1} only) = one wave of persistent CTAs taking items from a
+// counter, with the tiles streamed through a ring of shared-memory stages by
+// a loader warp, Khatri-Rao rows formed by builder warps and the contraction
+// on the remaining warps.  A tensor's bits are the same under every schedule.
 struct BSchedule {
   int pm_right = 0, pm_left = 0;
 };
+constexpr int kRightSchedules = 3, kLeftSchedules = 2;
 // The root phases alone (no state changes but their outputs, which every
 // iteration recomputes): what the schedule tuner times.  queue: a device
-// counter set to 0 before the launch, or NULL for one CTA per item.
-cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
-                            cudaStream_t st);
-cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int* queue,
-                           cudaStream_t st);
+// counter set to 0 before the launch (unused by schedule 0); err: a device
+// int that a streamed launch sets to 1 when one of its bounded waits expires.
+cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int mode,
+                            int* queue, int* err, cudaStream_t st);
+cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int mode,
+                           int* queue, int* err, cudaStream_t st);
 // one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1);
-// queues: two device ints for the persistent schedules
+// queues: three device ints (the two root phases' counters and the error
+// word of the streamed schedule), or NULL for schedule 0 everywhere
 cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, int* done_count,
                                cudaStream_t st, const BSchedule& sch, int* queues);
 // per tensor: iterations, last fit, lambda into contiguous arrays, and a state

@@ -185,27 +185,58 @@ def test_one_call_batch_solve_rejects_bad_orders(nn):
     assert info.value.status == nn.NNCP_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("sched", [(0, 0), (1, 1), (0, 1), (1, 0)])
-def test_root_phase_schedules_give_the_same_bits(nn, sched):
-    # one CTA per work item or persistent CTAs taking items from a counter:
-    # which CTA computes an item changes, how it is computed does not
-    probs = _problems(10, seed0=31, hi=60)
-    ref = _run_batch(nn, probs, 5)
-    b = nn.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=5)
+def _run_batch_sched(nn, probs, iters, sched):
+    b = nn.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=iters)
     try:
         b.set_schedule(*sched)
         X = [torch.from_numpy(p[2]).cuda() for p in probs]
         H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
         b.set_data(X, H)
-        k, fits, lams = b.solve(5, 0.0)
+        k, fits, lams = b.solve(iters, 0.0)
         assert b.schedule() == sched
-        Hs = [[h.cpu().numpy() for h in hs] for hs in H]
+        return k, fits, lams, [[h.cpu().numpy() for h in hs] for hs in H]
     finally:
         b.close()
-    assert k == ref[0] and fits == ref[1] and lams == ref[2]
-    for a, c in zip(Hs, ref[3]):
+
+
+# batch compositions for the schedule tests: few items; more items than
+# resident CTAs (each streamed CTA takes several, its stage ring wraps inside
+# and across items); ranks up to 40 (64-wide rank blocks) with first modes
+# above 128 (one column group, no group sum); order 4; order 2
+_SCHED_SETS = {
+    "small": dict(count=10, seed0=31, hi=60),
+    "many_items": dict(count=48, seed0=33, lo=40, hi=128, ranks=(4, 8, 16)),
+    "wide_rank": dict(count=8, seed0=35, lo=20, hi=200, ranks=(12, 24, 40)),
+    "order4": dict(count=8, seed0=37, N=4, lo=6, hi=20, ranks=(3, 5, 8)),
+    "order2": dict(count=8, seed0=39, N=2, lo=16, hi=250, ranks=(2, 7, 16)),
+}
+
+
+@pytest.mark.parametrize("sched", [(1, 1), (0, 1), (1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("which", sorted(_SCHED_SETS))
+def test_root_phase_schedules_give_the_same_bits(nn, which, sched):
+    # one CTA per work item, persistent CTAs taking items from a counter, or
+    # the streamed root -> {1} kernel: which CTA (and which warp) computes a
+    # product changes, the order of every output's sums does not
+    probs = _problems(**_SCHED_SETS[which])
+    ref = _run_batch_sched(nn, probs, 5, (0, 0))
+    got = _run_batch_sched(nn, probs, 5, sched)
+    assert got[0] == ref[0] and got[1] == ref[1] and got[2] == ref[2]
+    for a, c in zip(got[3], ref[3]):
         for x, y in zip(a, c):
             assert np.array_equal(x, y)
+
+
+def test_streamed_schedule_matches_the_oracle_at_wide_ranks(nn):
+    probs = _problems(count=4, seed0=43, lo=24, hi=150, ranks=(24, 40))
+    iters = 6
+    k, fits, lams, Hs = _run_batch_sched(nn, probs, iters, (2, 1))
+    for t, (dims, R, x, H0) in enumerate(probs):
+        ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
+                               max_iters=iters, use_dimtree=True, s=1)
+        assert k[t] == iters
+        assert abs(fits[t] - ref["fits"][-1]) <= 1e-4, (t, dims, R)
+        assert rel_fro(np.array(lams[t]), ref["lam"]) <= 1e-3, t
 
 
 def test_schedule_tuner_picks_a_valid_schedule(nn):
@@ -215,12 +246,14 @@ def test_schedule_tuner_picks_a_valid_schedule(nn):
         with pytest.raises(nn.NNCPError):
             b.schedule()                     # before the first run
         with pytest.raises(nn.NNCPError):
-            b.set_schedule(2, 0)
+            b.set_schedule(3, 0)
+        with pytest.raises(nn.NNCPError):
+            b.set_schedule(0, 2)
         X = [torch.from_numpy(p[2]).cuda() for p in probs]
         H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
         b.set_data(X, H)
         b.solve(3, 0.0)
         r, l = b.schedule()
-        assert r in (0, 1) and l in (0, 1)
+        assert r in (0, 1, 2) and l in (0, 1)
     finally:
         b.close()
