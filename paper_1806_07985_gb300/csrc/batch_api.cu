@@ -539,7 +539,9 @@ nncp_status nncp_batch_run(nncp_batch* b, int max_iters, double tol, int* iters_
   BCK(cudaStreamWaitEvent(user, ev, 0));
   cudaEventDestroy(ev);
   if (b->host_done[1])
-    return bfail(b, NNCP_ERR_TIMEOUT, "a streamed root kernel gave up waiting on its pipeline");
+    return bfail(b, NNCP_ERR_TIMEOUT,
+                 "a streamed root kernel gave up waiting on its pipeline (wait site %d)",
+                 b->host_done[1] - 1);
   for (int t = 0; t < b->count; ++t)
     if (nf[t] & 1) return bfail(b, NNCP_ERR_NUMERIC, "tensor %d: non-finite fit", t);
   return NNCP_OK;

@@ -414,12 +414,16 @@ __device__ __forceinline__ bool mb_test(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, int* err) {
-  if (mb_test(bar, parity)) return true;
+// Bounded wait of a whole warp (all 32 lanes call it, converged): every lane
+// polls (and so acquires the phase), the warp decides together, so a warp
+// never splits over an expired wait (the lanes read one clock).  On expiry
+// the first wait site to give up is recorded in *err (1 + site).
+__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, int* err, int site) {
+  if (__all_sync(0xffffffffu, mb_test(bar, parity))) return true;
   const long long t0 = clock64();
-  while (!mb_test(bar, parity)) {
+  while (!__all_sync(0xffffffffu, mb_test(bar, parity))) {
     if (clock64() - t0 > kWsWaitCycles) {
-      atomicExch(err, 1);
+      if ((threadIdx.x & 31) == 0) atomicCAS(err, 0, 1 + site);
       return false;
     }
   }
@@ -479,7 +483,7 @@ __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restr
       act &= act - 1;
       const int w = __shfl_sync(0xffffffffu, c, src);
       const int sl = m % kWsItemSlots;
-      if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err)) return;
+      if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err, 1)) return;
       if (lane == 0) {
         const int4 it = items[w];
         const BTensor& t = ts[it.x];
@@ -507,7 +511,7 @@ __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restr
   }
   // no more items
   const int sl = m % kWsItemSlots;
-  if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err)) return;
+  if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err, 2)) return;
   if (lane == 0) sm.slot[sl].d.w = -1;
   __syncwarp();
   if (lane == 0) mb_arrive(sm.islot_full(sl));
@@ -519,7 +523,7 @@ __device__ void ws_loader(const WsSmem& sm, int* err) {
   int n = 0;  // stages posted
   for (int m = 0;; ++m) {
     const int sl = m % kWsItemSlots;
-    if (!mb_wait(sm.islot_full(sl), (m / kWsItemSlots) & 1, err)) break;
+    if (!mb_wait(sm.islot_full(sl), (m / kWsItemSlots) & 1, err, 3)) break;
     const WsDesc& d = sm.slot[sl].d;
     const int w = d.w, I1 = d.I1, nj = d.nj, j0 = d.j0, j1 = d.j1;
     // the last item is followed by one stop stage per builder warp
@@ -531,7 +535,7 @@ __device__ void ws_loader(const WsSmem& sm, int* err) {
     bool ok = true;
     for (int k = 0; k < ntile; ++k, ++n) {
       const int s = n % sm.S;
-      if (!mb_wait(sm.empty(s), ((n / sm.S) & 1) ^ 1, err)) {
+      if (!mb_wait(sm.empty(s), ((n / sm.S) & 1) ^ 1, err, 4)) {
         ok = false;
         break;
       }
@@ -560,7 +564,7 @@ __device__ void ws_builder(const WsSmem& sm, int* err) {
   const int b = (threadIdx.x >> 5) - 2;
   for (int n = b;; n += kWsBuildWarps) {
     const int s = n % sm.S;
-    if (!mb_wait(sm.hfull(s), (n / sm.S) & 1, err)) return;
+    if (!mb_wait(sm.hfull(s), (n / sm.S) & 1, err, 5)) return;
     const WsHeader& h = sm.hdr[s];
     const int w = h.d.w;
     if (w >= 0) {
@@ -630,7 +634,7 @@ __device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const
   int s = 0;
   for (int k = 0; k < ntile; ++k, ++n) {
     s = n % sm.S;
-    if (k > 0 && !mb_wait(sm.full(s), (n / sm.S) & 1, err)) return false;
+    if (k > 0 && !mb_wait(sm.full(s), (n / sm.S) & 1, err, 6)) return false;
     const int jt = j0 + k * nj, njk = min(nj, j1 - jt);
     if (act) {
       const float* xp = sm.xs(s) + i;
@@ -653,14 +657,14 @@ __device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const
     // is done reading that tile
     __syncwarp();
     if (lane == 0) mb_arrive(sm.cons_sync());
-    if (!mb_wait(sm.cons_sync(), nsync & 1, err)) return false;
+    if (!mb_wait(sm.cons_sync(), nsync & 1, err, 7)) return false;
     ++nsync;
     float4* red = reinterpret_cast<float4*>(sm.xs(s));
 #pragma unroll
     for (int u0 = 0; u0 < RQB; u0 += 4) {
       const uint32_t par = nred & 1;
       ++nred;
-      if (u0 > 0 && !mb_wait(sm.red_empty(), par ^ 1, err)) return false;
+      if (u0 > 0 && !mb_wait(sm.red_empty(), par ^ 1, err, 8)) return false;
       if (act) {
 #pragma unroll
         for (int u = u0; u < u0 + 4 && u < RQB; ++u)
@@ -668,8 +672,8 @@ __device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const
       }
       __syncwarp();
       if (lane == 0) mb_arrive(sm.red_full());
+      if ((ct & ~31) < I1 && !mb_wait(sm.red_full(), par, err, 9)) return false;  // warps with readers
       if (ct < I1) {
-        if (!mb_wait(sm.red_full(), par, err)) return false;
 #pragma unroll
         for (int u = u0; u < u0 + 4 && u < RQB; ++u) {
           float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -705,7 +709,7 @@ __device__ void ws_consumer(const WsSmem& sm, int* err) {
   int nred = 0, nsync = 0;
   for (int n = 0;;) {
     const int s = n % sm.S;
-    if (!mb_wait(sm.full(s), (n / sm.S) & 1, err)) return;
+    if (!mb_wait(sm.full(s), (n / sm.S) & 1, err, 10)) return;
     const WsDesc& d = sm.hdr[s].d;
     if (d.w < 0) return;
     bool ok = true;
@@ -1294,7 +1298,7 @@ cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items
 
 cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int mode,
                            int* queue, int* /*err*/, cudaStream_t st) {
-  if (mode == 0) queue = nullptr;
+  if (mode == 0 || !queue) queue = nullptr;
   const int n = p.pml.count;
   if (n == 0) return cudaSuccess;
   const int4* it = items + p.pml.off;

@@ -112,10 +112,11 @@ cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double
                           const int* alpha_first, cudaStream_t st);
 // How the two root phases run: 0 = one CTA per work item (scheduled by the
 // hardware), 1 = one wave of persistent CTAs taking items from a counter,
-// 2 (root -> {1} only) = one wave of persistent CTAs taking items from a
-// counter, with the tiles streamed through a ring of shared-memory stages by
-// a loader warp, Khatri-Rao rows formed by builder warps and the contraction
-// on the remaining warps.  A tensor's bits are the same under every schedule.
+// 2 (root -> {1} only) = one wave of persistent CTAs with the work split by
+// warp role: a scheduler warp takes items from a counter, a loader warp
+// streams the tiles through a ring of shared-memory stages, builder warps
+// form the Khatri-Rao rows, and the remaining warps contract.  A tensor's
+// bits are the same under every schedule.
 struct BSchedule {
   int pm_right = 0, pm_left = 0;
 };
