@@ -80,6 +80,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 4096-tensor batched solve (context line 'batched')")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--batch-schedule", default=None,
+                   help="root-phase schedules 'R,L' of the batched line (default: the library's tuner)")
     p.add_argument("--batch-iters", type=int, default=None,
                    help="cap the batched solve at this many iterations (profiling)")
     p.add_argument("--no-plain", action="store_true",
@@ -219,7 +221,8 @@ def run_ours(args):
     nncp.load()
     if args.mode in ("batched", "serving"):
         if rank == 0:
-            out = (run_batched(nncp, torch, args.batch_count, args.batch_iters, args.no_plain)
+            out = (run_batched(nncp, torch, args.batch_count, args.batch_iters, args.no_plain,
+                               args.batch_schedule)
                    if args.mode == "batched" else
                    run_serving(nncp, torch, args.serve_requests, args.no_plain))
             print(json.dumps({"mode": args.mode, args.mode: out}), flush=True)
@@ -341,7 +344,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_4way:
         result["hsi_4way"] = run_4way(nncp, torch, prec_name, max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_batched:
-        result["batched"] = run_batched(nncp, torch, args.batch_count)
+        result["batched"] = run_batched(nncp, torch, args.batch_count,
+                                        fixed_schedule=args.batch_schedule)
     if rank == 0 and world == 1 and not args.no_serving:
         result["serving"] = run_serving(nncp, torch, args.serve_requests)
     if rank == 0:
@@ -647,7 +651,7 @@ SERVE_ITERS, SERVE_TOL = 150, 1e-4      # stopping rule of the serving workload
 FIT_TOL = 1e-4                          # same fit accuracy: |fit - plain fit| bound
 
 
-def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
+def run_batched(nncp, torch, count, max_iters=None, no_plain=False, fixed_schedule=None):
     """4096 uneven 3-way tensors (I_n log-uniform in [16, 128], R in {4, 8, 16})
     solved together to |dfit| < 1e-5 or 200 iterations, against the plain
     one-problem-at-a-time solver on an evenly spaced sample of 32 of them."""
@@ -660,6 +664,8 @@ def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
     H = [[h.clone() for h in hs] for hs in H0]
     iters_cap = max_iters or BATCH_ITERS
     b = nncp.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=BATCH_ITERS)
+    if fixed_schedule:
+        b.set_schedule(*[int(v) for v in fixed_schedule.split(",")])
     b.set_data(X, H)
     b.solve(3, 0.0)                      # graph capture and warm-up
     for hs, h0 in zip(H, H0):
@@ -684,8 +690,8 @@ def run_batched(nncp, torch, count, max_iters=None, no_plain=False):
            "root_phase_schedule": {"pm_right": schedule[0], "pm_left": schedule[1],
                                    "codes": "0 one CTA per work item, 1 persistent CTAs on a "
                                             "work counter, 2 (root -> {1}) persistent CTAs "
-                                            "streaming tiles through a shared-memory ring; "
-                                            "chosen by the library's tuner"}}
+                                            "streaming tiles through a shared-memory ring",
+                                   "chosen_by": "fixed" if fixed_schedule else "the library's tuner"}}
     if no_plain:
         return out
     sample = list(range(0, count, max(1, count // 32)))[:32]
