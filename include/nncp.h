@@ -301,6 +301,12 @@ nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims
  * kernel gave up waiting on its pipeline (bounded waits, about two seconds)
  * returns NNCP_ERR_TIMEOUT. */
 nncp_status nncp_batch_set_schedule(nncp_batch* b, int pm_right, int pm_left);
+/* Test hook for the failure path: the limit, in SM clock cycles, of every
+ * bounded wait of the streamed schedule's kernel (0, the default, is about
+ * two seconds).  A tiny limit makes waits that are merely not yet satisfied
+ * expire, so a run returns NNCP_ERR_TIMEOUT without any fault or hang; the
+ * batch stays usable.  cycles < 0: NNCP_ERR_INVALID_ARG. */
+nncp_status nncp_batch_set_wait_limit(nncp_batch* b, long long cycles);
 /* The schedule the last run used (NNCP_ERR_NOT_READY before the first). */
 nncp_status nncp_batch_get_schedule(const nncp_batch* b, int* pm_right, int* pm_left);
 const char* nncp_batch_last_error(const nncp_batch* b);

@@ -194,6 +194,7 @@ struct nncp_batch {
   bool have_data = false;
   // schedule of the two root phases: -1 = chosen by the tuner at the next run
   int want_right = -1, want_left = -1;
+  long long wait_cycles = 0;  // bounded-wait limit of the streamed kernel (0: default)
   BSchedule sched;
   bool sched_set = false;
   size_t off_queues = 0;
@@ -304,7 +305,7 @@ nncp_status time_phase(nncp_batch* b, int right, int mode, float* ms) {
   for (int r = 0; r < 4; ++r) {
     BCK(cudaEventRecord(e0, b->work));
     if (mode) BCK(cudaMemsetAsync(q, 0, sizeof(int), b->work));
-    BCK(right ? launch_pm_right(b->plan, d_ts, d_items, mode, q, q + 2, b->work)
+    BCK(right ? launch_pm_right(b->plan, d_ts, d_items, mode, q, q + 2, b->work, b->wait_cycles)
               : launch_pm_left(b->plan, d_ts, d_items, mode, q, q + 2, b->work));
     BCK(cudaEventRecord(e1, b->work));
     BCK(cudaEventSynchronize(e1));
@@ -352,7 +353,9 @@ nncp_status choose_schedule(nncp_batch* b) {
   }
   if (b->want_right >= 0) sch.pm_right = b->want_right;
   if (b->want_left >= 0) sch.pm_left = b->want_left;
-  if (!b->sched_set || sch.pm_right != b->sched.pm_right || sch.pm_left != b->sched.pm_left) {
+  sch.wait_cycles = b->wait_cycles;
+  if (!b->sched_set || sch.pm_right != b->sched.pm_right || sch.pm_left != b->sched.pm_left ||
+      sch.wait_cycles != b->sched.wait_cycles) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
@@ -616,6 +619,13 @@ nncp_status nncp_batch_set_schedule(nncp_batch* b, int pm_right, int pm_left) {
                  kRightSchedules - 1, kLeftSchedules - 1);
   b->want_right = pm_right;
   b->want_left = pm_left;
+  return NNCP_OK;
+}
+
+nncp_status nncp_batch_set_wait_limit(nncp_batch* b, long long cycles) {
+  if (!b) return bfail(nullptr, NNCP_ERR_INVALID_ARG, "null batch");
+  if (cycles < 0) return bfail(b, NNCP_ERR_INVALID_ARG, "wait limit %lld < 0", cycles);
+  b->wait_cycles = cycles;
   return NNCP_OK;
 }
 

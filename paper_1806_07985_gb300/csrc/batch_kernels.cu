@@ -417,12 +417,14 @@ __device__ __forceinline__ bool mb_test(uint32_t bar, uint32_t parity) {
 // Bounded wait of a whole warp (all 32 lanes call it, converged): every lane
 // polls (and so acquires the phase), the warp decides together, so a warp
 // never splits over an expired wait (the lanes read one clock).  On expiry
-// the first wait site to give up is recorded in *err (1 + site).
-__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, int* err, int site) {
+// the first wait site to give up is recorded in *err (1 + site).  `limit`:
+// clock64 cycles (kWsWaitCycles unless a test shortens it).
+__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, long long limit, int* err,
+                                        int site) {
   if (__all_sync(0xffffffffu, mb_test(bar, parity))) return true;
   const long long t0 = clock64();
   while (!__all_sync(0xffffffffu, mb_test(bar, parity))) {
-    if (clock64() - t0 > kWsWaitCycles) {
+    if (clock64() - t0 > limit) {
       if ((threadIdx.x & 31) == 0) atomicCAS(err, 0, 1 + site);
       return false;
     }
@@ -448,6 +450,7 @@ struct WsSmem {
   WsSlot* slot;
   uint32_t bar0;
   int S;
+  long long wait;  // bounded-wait limit, clock64 cycles
   __device__ float* xs(int s) const { return stage0 + (size_t)s * kWsStageFloats; }
   __device__ uint32_t full(int s) const { return bar0 + 8u * s; }
   __device__ uint32_t empty(int s) const { return bar0 + 8u * (S + s); }
@@ -483,7 +486,7 @@ __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restr
       act &= act - 1;
       const int w = __shfl_sync(0xffffffffu, c, src);
       const int sl = m % kWsItemSlots;
-      if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err, 1)) return;
+      if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, sm.wait, err, 1)) return;
       if (lane == 0) {
         const int4 it = items[w];
         const BTensor& t = ts[it.x];
@@ -511,7 +514,7 @@ __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restr
   }
   // no more items
   const int sl = m % kWsItemSlots;
-  if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, err, 2)) return;
+  if (!mb_wait(sm.islot_empty(sl), ((m / kWsItemSlots) & 1) ^ 1, sm.wait, err, 2)) return;
   if (lane == 0) sm.slot[sl].d.w = -1;
   __syncwarp();
   if (lane == 0) mb_arrive(sm.islot_full(sl));
@@ -523,7 +526,7 @@ __device__ void ws_loader(const WsSmem& sm, int* err) {
   int n = 0;  // stages posted
   for (int m = 0;; ++m) {
     const int sl = m % kWsItemSlots;
-    if (!mb_wait(sm.islot_full(sl), (m / kWsItemSlots) & 1, err, 3)) break;
+    if (!mb_wait(sm.islot_full(sl), (m / kWsItemSlots) & 1, sm.wait, err, 3)) break;
     const WsDesc& d = sm.slot[sl].d;
     const int w = d.w, I1 = d.I1, nj = d.nj, j0 = d.j0, j1 = d.j1;
     // the last item is followed by one stop stage per builder warp
@@ -535,7 +538,7 @@ __device__ void ws_loader(const WsSmem& sm, int* err) {
     bool ok = true;
     for (int k = 0; k < ntile; ++k, ++n) {
       const int s = n % sm.S;
-      if (!mb_wait(sm.empty(s), ((n / sm.S) & 1) ^ 1, err, 4)) {
+      if (!mb_wait(sm.empty(s), ((n / sm.S) & 1) ^ 1, sm.wait, err, 4)) {
         ok = false;
         break;
       }
@@ -564,7 +567,7 @@ __device__ void ws_builder(const WsSmem& sm, int* err) {
   const int b = (threadIdx.x >> 5) - 2;
   for (int n = b;; n += kWsBuildWarps) {
     const int s = n % sm.S;
-    if (!mb_wait(sm.hfull(s), (n / sm.S) & 1, err, 5)) return;
+    if (!mb_wait(sm.hfull(s), (n / sm.S) & 1, sm.wait, err, 5)) return;
     const WsHeader& h = sm.hdr[s];
     const int w = h.d.w;
     if (w >= 0) {
@@ -634,7 +637,7 @@ __device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const
   int s = 0;
   for (int k = 0; k < ntile; ++k, ++n) {
     s = n % sm.S;
-    if (k > 0 && !mb_wait(sm.full(s), (n / sm.S) & 1, err, 6)) return false;
+    if (k > 0 && !mb_wait(sm.full(s), (n / sm.S) & 1, sm.wait, err, 6)) return false;
     const int jt = j0 + k * nj, njk = min(nj, j1 - jt);
     if (act) {
       const float* xp = sm.xs(s) + i;
@@ -657,14 +660,14 @@ __device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const
     // is done reading that tile
     __syncwarp();
     if (lane == 0) mb_arrive(sm.cons_sync());
-    if (!mb_wait(sm.cons_sync(), nsync & 1, err, 7)) return false;
+    if (!mb_wait(sm.cons_sync(), nsync & 1, sm.wait, err, 7)) return false;
     ++nsync;
     float4* red = reinterpret_cast<float4*>(sm.xs(s));
 #pragma unroll
     for (int u0 = 0; u0 < RQB; u0 += 4) {
       const uint32_t par = nred & 1;
       ++nred;
-      if (u0 > 0 && !mb_wait(sm.red_empty(), par ^ 1, err, 8)) return false;
+      if (u0 > 0 && !mb_wait(sm.red_empty(), par ^ 1, sm.wait, err, 8)) return false;
       if (act) {
 #pragma unroll
         for (int u = u0; u < u0 + 4 && u < RQB; ++u)
@@ -672,7 +675,7 @@ __device__ bool ws_consume(const WsDesc& d, int& n, int& nred, int& nsync, const
       }
       __syncwarp();
       if (lane == 0) mb_arrive(sm.red_full());
-      if ((ct & ~31) < I1 && !mb_wait(sm.red_full(), par, err, 9)) return false;  // warps with readers
+      if ((ct & ~31) < I1 && !mb_wait(sm.red_full(), par, sm.wait, err, 9)) return false;  // warps with readers
       if (ct < I1) {
 #pragma unroll
         for (int u = u0; u < u0 + 4 && u < RQB; ++u) {
@@ -709,7 +712,7 @@ __device__ void ws_consumer(const WsSmem& sm, int* err) {
   int nred = 0, nsync = 0;
   for (int n = 0;;) {
     const int s = n % sm.S;
-    if (!mb_wait(sm.full(s), (n / sm.S) & 1, err, 10)) return;
+    if (!mb_wait(sm.full(s), (n / sm.S) & 1, sm.wait, err, 10)) return;
     const WsDesc& d = sm.hdr[s].d;
     if (d.w < 0) return;
     bool ok = true;
@@ -727,10 +730,11 @@ __device__ void ws_consumer(const WsSmem& sm, int* err) {
 template <int RMAX>
 __global__ void __launch_bounds__(kWsThreads, RMAX <= 16 ? 2 : 1)
 k_b_pm_right_ws(const BTensor* __restrict__ ts, const int4* __restrict__ items, int n_items,
-                int* queue, int S, int* err) {
+                int* queue, int S, int* err, long long wait_cycles) {
   extern __shared__ __align__(16) float smem[];
   WsSmem sm;
   sm.S = S;
+  sm.wait = wait_cycles > 0 ? wait_cycles : kWsWaitCycles;
   sm.stage0 = smem;
   sm.hdr = reinterpret_cast<WsHeader*>(smem + (size_t)S * kWsStageFloats);
   sm.slot = reinterpret_cast<WsSlot*>(sm.hdr + S);
@@ -1248,7 +1252,7 @@ namespace {
 // SM (RMAX 16) or one, and one wave of CTAs.
 template <int RMAX>
 cudaError_t launch_pm_right_ws(const BTensor* ts, const int4* it, int n, int* queue, int* err,
-                               cudaStream_t st) {
+                               long long wait_cycles, cudaStream_t st) {
   int dev = 0, sms = 1, smem_sm = 0, reserved = 0, optin = 0, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1266,22 +1270,22 @@ cudaError_t launch_pm_right_ws(const BTensor* ts, const int4* it, int n, int* qu
       per_sm < 1)
     per_sm = 1;
   const int grid = std::max(1, std::min(n, sms * per_sm));
-  k_b_pm_right_ws<RMAX><<<grid, kWsThreads, bytes, st>>>(ts, it, n, queue, S, err);
+  k_b_pm_right_ws<RMAX><<<grid, kWsThreads, bytes, st>>>(ts, it, n, queue, S, err, wait_cycles);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int mode,
-                            int* queue, int* err, cudaStream_t st) {
+                            int* queue, int* err, cudaStream_t st, long long wait_cycles) {
   const size_t sm = (size_t)(2 * kTileFloats + kWsFloats) * sizeof(float);
   const int n = p.pmr.count;
   const int4* it = items + p.pmr.off;
   if (mode == 0 || !queue) queue = nullptr;
   if (n > 0 && mode == 2 && queue && err) {
-    cudaError_t e = p.rmax <= 16   ? launch_pm_right_ws<16>(ts, it, n, queue, err, st)
-                    : p.rmax <= 32 ? launch_pm_right_ws<32>(ts, it, n, queue, err, st)
-                                   : launch_pm_right_ws<64>(ts, it, n, queue, err, st);
+    cudaError_t e = p.rmax <= 16   ? launch_pm_right_ws<16>(ts, it, n, queue, err, wait_cycles, st)
+                    : p.rmax <= 32 ? launch_pm_right_ws<32>(ts, it, n, queue, err, wait_cycles, st)
+                                   : launch_pm_right_ws<64>(ts, it, n, queue, err, wait_cycles, st);
     if (e != cudaSuccess) return e;
   } else if (n > 0) {
     if (p.rmax <= 16)
@@ -1341,7 +1345,7 @@ cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, i
   if (counters) e = cudaMemsetAsync(queues, 0, 2 * sizeof(int), st);
   int* err = queues ? queues + 2 : nullptr;
   if (e == cudaSuccess)
-    e = launch_pm_right(p, ts, items, counters ? sch.pm_right : 0, queues, err, st);
+    e = launch_pm_right(p, ts, items, counters ? sch.pm_right : 0, queues, err, st, sch.wait_cycles);
   if (e == cudaSuccess) e = launch_update(p, ts, 0, done_count, st);
   if (e == cudaSuccess)
     e = launch_pm_left(p, ts, items, counters ? sch.pm_left : 0, queues ? queues + 1 : nullptr, err, st);

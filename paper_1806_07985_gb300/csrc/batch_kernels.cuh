@@ -119,6 +119,7 @@ cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double
 // bits are the same under every schedule.
 struct BSchedule {
   int pm_right = 0, pm_left = 0;
+  long long wait_cycles = 0;  // bounded-wait limit of the streamed kernel (0: about 2 s)
 };
 constexpr int kRightSchedules = 3, kLeftSchedules = 2;
 // The root phases alone (no state changes but their outputs, which every
@@ -126,7 +127,7 @@ constexpr int kRightSchedules = 3, kLeftSchedules = 2;
 // counter set to 0 before the launch (unused by schedule 0); err: a device
 // int that a streamed launch sets to 1 when one of its bounded waits expires.
 cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int mode,
-                            int* queue, int* err, cudaStream_t st);
+                            int* queue, int* err, cudaStream_t st, long long wait_cycles = 0);
 cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int mode,
                            int* queue, int* err, cudaStream_t st);
 // one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1);

@@ -85,6 +85,7 @@ _SIGNATURES = [
                                         ctypes.c_int, ctypes.c_double, _c_intp, _c_dblp,
                                         ctypes.c_void_p]),
     ("nncp_batch_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("nncp_batch_set_wait_limit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     ("nncp_batch_get_schedule", ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_intp]),
     ("nncp_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("nncp_batch_destroy", None, [ctypes.c_void_p]),
@@ -463,6 +464,11 @@ class Batch:
         only) persistent and streamed through a shared-memory ring by warp
         roles, -1 tuned."""
         _bcheck(load().nncp_batch_set_schedule(self.b, int(pm_right), int(pm_left)), self.b)
+
+    def set_wait_limit(self, cycles=0):
+        """Bounded-wait limit of the streamed kernel in SM cycles (0: the default,
+        about two seconds); a test hook for the timeout path."""
+        _bcheck(load().nncp_batch_set_wait_limit(self.b, int(cycles)), self.b)
 
     def schedule(self):
         r, l = ctypes.c_int(), ctypes.c_int()

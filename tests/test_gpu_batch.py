@@ -227,6 +227,41 @@ def test_root_phase_schedules_give_the_same_bits(nn, which, sched):
             assert np.array_equal(x, y)
 
 
+def test_streamed_schedule_reports_an_expired_wait(nn):
+    # the failure path without any fault or hang: a wait limit of one cycle
+    # makes the streamed kernel's waits that are merely not yet satisfied
+    # expire; the run reports NNCP_ERR_TIMEOUT naming the wait site, and the
+    # same batch, limit restored, then solves to schedule 0's bits
+    probs = _problems(**_SCHED_SETS["many_items"])
+    iters = 3
+    ref = _run_batch_sched(nn, probs, iters, (0, 0))
+    b = nn.Batch([p[0] for p in probs], [p[1] for p in probs], max_iters=iters)
+    try:
+        with pytest.raises(nn.NNCPError):
+            b.set_wait_limit(-1)
+        b.set_schedule(2, 0)
+        X = [torch.from_numpy(p[2]).cuda() for p in probs]
+        H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
+        b.set_data(X, H)
+        b.set_wait_limit(1)
+        with pytest.raises(nn.NNCPError) as info:
+            b.solve(iters, 0.0)
+        assert info.value.status == nn.NNCP_ERR_TIMEOUT
+        assert "wait site" in str(info.value)
+        for hs, p in zip(H, probs):
+            for h, h0 in zip(hs, p[3]):
+                h.copy_(torch.from_numpy(h0))
+        b.set_wait_limit(0)
+        k, fits, lams = b.solve(iters, 0.0)
+        Hs = [[h.cpu().numpy() for h in hs] for hs in H]
+    finally:
+        b.close()
+    assert k == ref[0] and fits == ref[1] and lams == ref[2]
+    for a, c in zip(Hs, ref[3]):
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y)
+
+
 def test_streamed_schedule_matches_the_oracle_at_wide_ranks(nn):
     probs = _problems(count=4, seed0=43, lo=24, hi=150, ranks=(24, 40))
     iters = 6
