@@ -911,7 +911,7 @@ __device__ __forceinline__ void pm_left_item(const BTensor& t, int item, float* 
 }
 
 template <int RMAX>
-__global__ void __launch_bounds__(kThreads, RMAX <= 16 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, RMAX <= 16 ? 4 : 2)
 k_b_pm_left(const BTensor* __restrict__ ts, const int4* __restrict__ items, int n_items,
             int* queue) {
   extern __shared__ __align__(16) float smem[];
@@ -1007,9 +1007,9 @@ __global__ void __launch_bounds__(256) k_b_mttv_leaf(const BTensor* __restrict__
 
 // child node {a+1..N} from node {a..N}: out(j, r) = sum_i T[(i + I_a j) R + r] H_a(i, r)
 // with the updated H_a; the output is M when the child is a leaf.  Item
-// (tensor, block of first_jb[a] rows j); warp per row j: lanes = (i phase,
-// rank) read the row's I_a x R block coalesced, then add their i phases in
-// a fixed shuffle tree.
+// (tensor, block of first_jb[a] rows j); warp per row j (two rows at a time,
+// for more loads in flight): lanes = (i phase, rank) read the row's I_a x R
+// block coalesced, then add their i phases in a fixed shuffle tree.
 __global__ void __launch_bounds__(256) k_b_mttv_first(const BTensor* __restrict__ ts,
                                                       const int4* __restrict__ items, int a) {
   const int4 it = items[blockIdx.x];
@@ -1030,18 +1030,32 @@ __global__ void __launch_bounds__(256) k_b_mttv_first(const BTensor* __restrict_
     const int Rb = min(32, R - rb), S = 32 / Rb;
     const int sub = lane / Rb, r = rb + lane - sub * Rb;
     const bool act = sub < S;
-    for (int j = j0 + warp; j < j1; j += nwarp) {
+    for (int j = j0 + warp; j < j1; j += 2 * nwarp) {
+      const int j2 = j + nwarp;
+      const bool two = j2 < j1;
       const float* Tj = T + (long long)j * E;
-      float acc = 0.0f;
+      const float* Tk = T + (long long)(two ? j2 : j) * E;
+      float acc = 0.0f, acc2 = 0.0f;
       if (act) {
-#pragma unroll 4
-        for (int i = sub; i < Ia; i += S) acc = fmaf(Tj[i * R + r], __ldg(Ha + i * R + r), acc);
+#pragma unroll 8
+        for (int i = sub; i < Ia; i += S) {
+          const float h = __ldg(Ha + i * R + r);
+          acc = fmaf(Tj[i * R + r], h, acc);
+          acc2 = fmaf(Tk[i * R + r], h, acc2);
+        }
       }
       for (int o = 1; o < S; o <<= 1) {
         const float v = __shfl_down_sync(0xffffffffu, acc, o * Rb);
-        if (act && (sub & (2 * o - 1)) == 0 && sub + o < S) acc += v;
+        const float v2 = __shfl_down_sync(0xffffffffu, acc2, o * Rb);
+        if (act && (sub & (2 * o - 1)) == 0 && sub + o < S) {
+          acc += v;
+          acc2 += v2;
+        }
       }
-      if (act && sub == 0) out[(long long)j * R + r] = acc;
+      if (act && sub == 0) {
+        out[(long long)j * R + r] = acc;
+        if (two) out[(long long)j2 * R + r] = acc2;
+      }
     }
   }
 }
