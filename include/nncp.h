@@ -288,16 +288,15 @@ nncp_status nncp_batch_solve(int count, const int* N, const int64_t* const* dims
 /* Schedule of the two root partial MTTKRP phases (the paper has no
  * counterpart; a launch-shape choice): 0 = one CTA per work item, scheduled by
  * the hardware; 1 = one wave of persistent CTAs taking items from a counter;
- * 2 (pm_right, root -> {1}, only) = one wave of persistent CTAs taking items
- * from a counter, each streaming its tiles through a ring of shared-memory
- * stages (a scheduler warp, a loader warp, Khatri-Rao builder warps,
- * contraction warps);
+ * 2 = one wave of persistent CTAs taking items from a counter, each
+ * streaming its tiles through rings of shared-memory stages (a scheduler
+ * warp, a loader warp, builder warps that form Khatri-Rao rows for pm_right
+ * or restride the tile and stage H_1 for pm_left, contraction warps);
  * -1 (the default) = chosen at the next nncp_batch_run by timing every
  * schedule on this batch, cached per class of batch (order, largest rank,
  * magnitudes of the tensor count and element total) for the process.  An
  * output is computed the same way under each, so the results are the same
- * bits.  pm_right in -1..2, pm_left in -1..1, else NNCP_ERR_INVALID_ARG.  A
- * run whose streamed
+ * bits.  Both in -1..2, else NNCP_ERR_INVALID_ARG.  A run whose streamed
  * kernel gave up waiting on its pipeline (bounded waits, about two seconds)
  * returns NNCP_ERR_TIMEOUT. */
 nncp_status nncp_batch_set_schedule(nncp_batch* b, int pm_right, int pm_left);

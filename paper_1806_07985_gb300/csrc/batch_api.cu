@@ -306,7 +306,7 @@ nncp_status time_phase(nncp_batch* b, int right, int mode, float* ms) {
     BCK(cudaEventRecord(e0, b->work));
     if (mode) BCK(cudaMemsetAsync(q, 0, sizeof(int), b->work));
     BCK(right ? launch_pm_right(b->plan, d_ts, d_items, mode, q, q + 2, b->work, b->wait_cycles)
-              : launch_pm_left(b->plan, d_ts, d_items, mode, q, q + 2, b->work));
+              : launch_pm_left(b->plan, d_ts, d_items, mode, q, q + 2, b->work, b->wait_cycles));
     BCK(cudaEventRecord(e1, b->work));
     BCK(cudaEventSynchronize(e1));
     BCK(cudaEventElapsedTime(&t[r], e0, e1));

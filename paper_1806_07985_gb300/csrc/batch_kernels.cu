@@ -372,10 +372,12 @@ constexpr int kWsBuildRounds = (kWsFloats / 4 + 32 * kWsBuildPer - 1) / (32 * kW
 constexpr long long kWsWaitCycles = 4000000000LL;
 
 // One item as the builders and consumers need it (w < 0: no more items);
-// H[m - 1] is factor m + 1 (mode 1's is not used).
+// seq: the item's position in this CTA's sequence; dims[m - 1] and H[m - 1]
+// are I_{m+1} and factor m + 1 (root -> {1}); for root -> {2..N}, H[0] is H_1.
 struct WsDesc {
   int w, I1, R, N, nj, j0, j1, ntile;
-  int dims[kMaxModes];
+  int seq;
+  int dims[kMaxModes - 1];
   float* out;
   const float* H[kMaxModes - 1];
 };
@@ -468,8 +470,9 @@ __host__ __device__ constexpr size_t ws_smem_bytes(int S) {
          (size_t)(3 * S + 2 * kWsItemSlots + 3) * sizeof(uint64_t);
 }
 
+template <bool LEFT, typename SM>
 __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restrict__ items,
-                             int n_items, int* queue, const WsSmem& sm, int* err) {
+                             int n_items, int* queue, const SM& sm, int* err) {
   const int lane = threadIdx.x & 31;
   int m = 0;      // item slots filled
   int grab = 1;   // candidates taken per round: doubles while they are all converged
@@ -496,14 +499,29 @@ __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restr
         d.I1 = (int)t.dims[0];
         d.R = t.R;
         d.N = t.N;
-        d.nj = t.rows_r;
+        d.seq = m;
         const int J = (int)(t.I / d.I1);
-        d.j0 = it.y * (int)t.jchunk;
-        d.j1 = min(J, d.j0 + (int)t.jchunk);
+        if (LEFT) {  // rows [j0, j1) of X_(1)^T in tiles of rows_l, H_1, T = node {2..N}
+          d.nj = t.rows_l;
+          d.j0 = it.y * d.nj * kLeftItemTiles;
+          d.j1 = min(J, d.j0 + d.nj * kLeftItemTiles);
+          for (int n = 1; n < kMaxModes; ++n) {
+            d.dims[n - 1] = 0;
+            d.H[n - 1] = nullptr;
+          }
+          d.H[0] = t.H[0];
+          d.out = t.node[1];
+        } else {     // chunk it.y of the columns, Khatri-Rao factors 2..N, a partial of M(1)
+          d.nj = t.rows_r;
+          d.j0 = it.y * (int)t.jchunk;
+          d.j1 = min(J, d.j0 + (int)t.jchunk);
+          for (int n = 1; n < kMaxModes; ++n) {
+            d.dims[n - 1] = n < d.N ? (int)t.dims[n] : 0;
+            d.H[n - 1] = n < d.N ? t.H[n] : nullptr;
+          }
+          d.out = t.part + (long long)it.y * d.I1 * d.R;
+        }
         d.ntile = (d.j1 - d.j0 + d.nj - 1) / d.nj;
-        for (int n = 0; n < kMaxModes; ++n) d.dims[n] = n < d.N ? (int)t.dims[n] : 0;
-        for (int n = 1; n < kMaxModes; ++n) d.H[n - 1] = n < d.N ? t.H[n] : nullptr;
-        d.out = t.part + (long long)it.y * d.I1 * d.R;
         q.X = t.X;
         sm.slot[sl] = q;
       }
@@ -520,7 +538,10 @@ __device__ void ws_scheduler(const BTensor* __restrict__ ts, const int4* __restr
   if (lane == 0) mb_arrive(sm.islot_full(sl));
 }
 
-__device__ void ws_loader(const WsSmem& sm, int* err) {
+// the loader of both streamed kernels: stage headers and dense tiles of
+// rows of X_(1)^T; the last item is followed by one stop stage per builder warp
+template <typename SM>
+__device__ void ws_loader(const SM& sm, int* err) {
   const int lane = threadIdx.x & 31;
   const uint64_t pol = l2_evict_first_policy();
   int n = 0;  // stages posted
@@ -529,7 +550,6 @@ __device__ void ws_loader(const WsSmem& sm, int* err) {
     if (!mb_wait(sm.islot_full(sl), (m / kWsItemSlots) & 1, sm.wait, err, 3)) break;
     const WsDesc& d = sm.slot[sl].d;
     const int w = d.w, I1 = d.I1, nj = d.nj, j0 = d.j0, j1 = d.j1;
-    // the last item is followed by one stop stage per builder warp
     const int ntile = w >= 0 ? d.ntile : kWsBuildWarps;
     const float* X = sm.slot[sl].X;
     const uint32_t word = lane < kWsDescWords ? reinterpret_cast<const uint32_t*>(&d)[lane] : 0u;
@@ -588,7 +608,7 @@ __device__ void ws_builder(const WsSmem& sm, int* err) {
           v[u] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
         }
         for (int m = 1; m < N; ++m) {
-          const int dm = h.d.dims[m];
+          const int dm = h.d.dims[m - 1];
           const float* Hm = h.d.H[m - 1];
 #pragma unroll
           for (int u = 0; u < kWsBuildPer; ++u) {
@@ -756,7 +776,7 @@ k_b_pm_right_ws(const BTensor* __restrict__ ts, const int4* __restrict__ items, 
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   if (warp == 0)
-    ws_scheduler(ts, items, n_items, queue, sm, err);
+    ws_scheduler<false>(ts, items, n_items, queue, sm, err);
   else if (warp == 1)
     ws_loader(sm, err);
   else if (warp < kWsConsFirstWarp)
@@ -929,6 +949,326 @@ k_b_pm_left(const BTensor* __restrict__ ts, const int4* __restrict__ items, int 
       default: if constexpr (RMAX >= 64) pm_left_item<16>(t, it.y, smem); break;
     }
   }
+}
+
+// ------------------------------------ streamed root -> {2..N} (schedule 2) --
+//
+// The arithmetic of pm_left_item (same sums in the same order, so the same
+// bits) with its jobs split over the warps of a persistent CTA, built from
+// the parts of the streamed root -> {1} kernel:
+//   warp 0, scheduler and warp 1, loader: as there (ws_scheduler<true>,
+//                      ws_loader): dense tiles of rows of X_(1)^T into a ring
+//                      of SD stages;
+//   warps 2-4, builders: take the dense stages in turn; at an item's first
+//                      tile stage H_1 (rank padded with zeros) into one of two
+//                      H slots; copy the tile to the odd row stride S = I_1 | 1
+//                      (conflict-free column reads) into a ring of SO stages,
+//                      with the header; free the dense stage;
+//   warps 5-12, consumers (the 256 threads of pm_left_item): the (row, rank
+//                      block) passes over each odd-stride tile, group sums
+//                      through a small buffer, rows of T written out; an odd
+//                      stage is freed after its tile, an H slot after its item.
+// Waits: mbarriers, warp-uniform and bounded, an error word.
+
+struct WlHeader {
+  WsDesc d;
+  int k;      // tile within the item
+  int hslot;  // H slot of the item
+  int pad[2];
+};
+static_assert(sizeof(WlHeader) % 16 == 0, "header layout");
+
+// Shared-memory counter helpers: a consumer warp's release of an odd stage,
+// and the builder's bounded, warp-uniform wait for a number of releases
+// (an exact count: builders fill the odd ring out of order, so a parity wait
+// could pass on a phase two laps old).
+__device__ __forceinline__ void smem_add_release(const unsigned* p, unsigned v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned smem_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool count_wait(const unsigned* p, unsigned target, long long limit,
+                                           int* err, int site) {
+  if (__all_sync(0xffffffffu, smem_ld_acquire(p) >= target)) return true;
+  const long long t0 = clock64();
+  while (!__all_sync(0xffffffffu, smem_ld_acquire(p) >= target)) {
+    if (clock64() - t0 > limit) {
+      if ((threadIdx.x & 31) == 0) atomicCAS(err, 0, 1 + site);
+      return false;
+    }
+  }
+  return true;
+}
+
+struct WlSmem {
+  float* stage0;  // SD dense stages of kTileFloats
+  float* odd0;    // SO odd-stride stages of kLeftStageFloats
+  float* hs0;     // two H slots of hs_floats
+  float4* red;    // kThreads
+  WsHeader* hdr;  // SD (dense, written by the loader)
+  WlHeader* ohdr; // SO (odd, written by the builders)
+  WsSlot* slot;
+  unsigned* ocons;  // SO: consumer-warp releases of each odd stage so far
+  uint32_t bar0;
+  int S, SO, hs_floats;
+  long long wait;
+  __device__ float* xs(int s) const { return stage0 + (size_t)s * kTileFloats; }
+  __device__ float* os(int o) const { return odd0 + (size_t)o * kLeftStageFloats; }
+  __device__ float* hs(int h) const { return hs0 + (size_t)h * hs_floats; }
+  __device__ uint32_t full(int s) const { return bar0 + 8u * s; }
+  __device__ uint32_t empty(int s) const { return bar0 + 8u * (S + s); }
+  __device__ uint32_t hfull(int s) const { return bar0 + 8u * (2 * S + s); }
+  __device__ uint32_t ofull(int o) const { return bar0 + 8u * (3 * S + o); }
+  __device__ uint32_t islot_full(int i) const { return bar0 + 8u * (3 * S + SO + i); }
+  __device__ uint32_t islot_empty(int i) const { return bar0 + 8u * (3 * S + SO + kWsItemSlots + i); }
+  __device__ uint32_t hslot_empty(int h) const {
+    return bar0 + 8u * (3 * S + SO + 2 * kWsItemSlots + h);
+  }
+  __device__ uint32_t red_full() const { return bar0 + 8u * (3 * S + SO + 2 * kWsItemSlots + 2); }
+  __device__ uint32_t red_empty() const { return bar0 + 8u * (3 * S + SO + 2 * kWsItemSlots + 3); }
+  __host__ __device__ static constexpr int bars(int S, int SO) { return 3 * S + SO + 2 * kWsItemSlots + 4; }
+};
+
+__host__ __device__ constexpr size_t wl_smem_bytes(int S, int SO, int hs_floats) {
+  return (size_t)S * kTileFloats * sizeof(float) + (size_t)SO * kLeftStageFloats * sizeof(float) +
+         2 * (size_t)hs_floats * sizeof(float) + (size_t)kThreads * sizeof(float4) +
+         (size_t)S * sizeof(WsHeader) + (size_t)SO * sizeof(WlHeader) +
+         (size_t)kWsItemSlots * sizeof(WsSlot) + (size_t)WlSmem::bars(S, SO) * sizeof(uint64_t) +
+         (size_t)((SO + 1) / 2) * sizeof(uint64_t);
+}
+
+// Builder warp b handles dense stages b, b + 3, b + 6, ...; dense stage n
+// becomes odd stage n % SO.
+__device__ void wl_builder(const WlSmem& sm, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int b = (threadIdx.x >> 5) - 2;
+  for (int n = b;; n += kWsBuildWarps) {
+    const int s = n % sm.S, o = n % sm.SO;
+    if (!mb_wait(sm.hfull(s), (n / sm.S) & 1, sm.wait, err, 20)) return;
+    const WsHeader& h = sm.hdr[s];
+    const int w = h.d.w, k = h.k;
+    if (w < 0) {
+      if (k == 0) {  // the first stop stage ends the odd ring too
+        if (!count_wait(sm.ocons + o, kWsConsWarps * (unsigned)(n / sm.SO), sm.wait, err, 21)) return;
+        if (lane == 0) sm.ohdr[o].d.w = -1;
+        __syncwarp();
+        if (lane == 0) mb_arrive(sm.ofull(o));
+      }
+      return;
+    }
+    const int I1 = h.d.I1, R = h.d.R, seq = h.d.seq;
+    const int jt = h.d.j0 + k * h.d.nj, njk = min(h.d.nj, h.d.j1 - jt);
+    const float* H1 = h.d.H[0];
+    const uint32_t word = reinterpret_cast<const uint32_t*>(&h.d)[lane];
+    if (!mb_wait(sm.full(s), (n / sm.S) & 1, sm.wait, err, 22)) return;
+    if (!count_wait(sm.ocons + o, kWsConsWarps * (unsigned)(n / sm.SO), sm.wait, err, 23)) return;
+    const int hslot = seq & 1;
+    if (k == 0) {  // H_1 of the item, rank padded to Rp with zeros
+      if (!mb_wait(sm.hslot_empty(hslot), ((seq >> 1) & 1) ^ 1, sm.wait, err, 24)) return;
+      float* hd = sm.hs(hslot);
+      const int Rp = b_rank_pad(R);
+      for (int e = lane; e < I1 * Rp; e += 32) {
+        const int i = e / Rp, r = e - i * Rp;
+        hd[e] = r < R ? __ldg(H1 + i * R + r) : 0.0f;
+      }
+    }
+    // the tile at odd row stride: four consecutive elements per lane and step
+    const float* src = sm.xs(s);
+    float* dst = sm.os(o);
+    const int ST = I1 | 1, L = njk * I1, L4 = L & ~3;
+    int row = (4 * lane) / I1, col = 4 * lane - row * I1;
+    const int drow = 128 / I1, dcol = 128 - drow * I1;
+    for (int e = 4 * lane; e < L4; e += 128) {
+      const float4 v = *reinterpret_cast<const float4*>(src + e);
+      int r = row, c = col;
+      dst[r * ST + c] = v.x;
+      if (++c == I1) c = 0, ++r;
+      dst[r * ST + c] = v.y;
+      if (++c == I1) c = 0, ++r;
+      dst[r * ST + c] = v.z;
+      if (++c == I1) c = 0, ++r;
+      dst[r * ST + c] = v.w;
+      row += drow;
+      col += dcol;
+      if (col >= I1) {
+        col -= I1;
+        ++row;
+      }
+    }
+    if (L4 + lane < L) {
+      const int e = L4 + lane, r = e / I1;
+      dst[r * ST + (e - r * I1)] = src[e];
+    }
+    reinterpret_cast<uint32_t*>(&sm.ohdr[o].d)[lane] = word;
+    if (lane == 0) {
+      sm.ohdr[o].k = k;
+      sm.ohdr[o].hslot = hslot;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mb_arrive(sm.empty(s));  // the dense stage has been read
+      mb_arrive(sm.ofull(o));  // the odd stage, its header and the H slot are written
+    }
+  }
+}
+
+// One item of root -> {2..N} (its first odd stage already waited for).
+template <int RQB>
+__device__ bool wl_consume(const WlHeader& h0, int& n, int& nred, const WlSmem& sm, int* err) {
+  const int ct = threadIdx.x - 32 * kWsConsFirstWarp;  // 0 .. 255
+  const int lane = threadIdx.x & 31;
+  const WsDesc& d = h0.d;
+  const int R = d.R, I1 = d.I1, nj = d.nj, jb0 = d.j0, jb1 = d.j1, ntile = d.ntile;
+  const int hslot = h0.hslot;
+  float* T = d.out;
+  const int Rq = b_rq(R), ST = I1 | 1;
+  const int NB = Rq / RQB;
+  const int P = nj * NB;
+  const int G = P >= kGroupThreads ? 1 : kGroupThreads / P;
+  const int npass = (P + kThreads - 1) / kThreads;
+  const int g = G > 1 ? ct / P : 0;
+  const int ia = g * I1 / G, ib = (g + 1) * I1 / G;
+  const float4* H4 = reinterpret_cast<const float4*>(sm.hs(hslot));
+  for (int k = 0; k < ntile; ++k, ++n) {
+    const int o = n % sm.SO;
+    if (k > 0 && !mb_wait(sm.ofull(o), (n / sm.SO) & 1, sm.wait, err, 25)) return false;
+    const int jt = jb0 + k * nj, njk = min(nj, jb1 - jt);
+    const float* Xs = sm.os(o);
+    for (int p = 0; p < npass; ++p) {
+      const int pair = G > 1 ? ct - g * P : ct + kThreads * p;
+      const int jl = pair / NB, qb = pair - jl * NB;
+      const bool v = g < G && pair < P && jl < njk;
+      float a[RQB][4];
+#pragma unroll
+      for (int u = 0; u < RQB; ++u)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) a[u][b] = 0.0f;
+      if (v) {
+        const float* xp = Xs + jl * ST;
+        const float4* hp = H4 + qb * RQB;
+#pragma unroll 4
+        for (int i = ia; i < ib; ++i) {
+          const float x = xp[i];
+#pragma unroll
+          for (int u = 0; u < RQB; ++u) fma4(a[u], x, hp[i * Rq + u]);
+        }
+      }
+      if (G > 1) {  // RQB == 1 here
+        const uint32_t par = nred & 1;
+        ++nred;
+        if (!mb_wait(sm.red_empty(), par ^ 1, sm.wait, err, 26)) return false;
+        if (g < G) sm.red[ct] = make_float4(a[0][0], a[0][1], a[0][2], a[0][3]);
+        __syncwarp();
+        if (lane == 0) mb_arrive(sm.red_full());
+        if ((ct & ~31) < P && !mb_wait(sm.red_full(), par, sm.wait, err, 27)) return false;
+        if (ct < P) {
+          const int jl0 = ct / NB, q0 = ct - jl0 * NB;
+          if (jl0 < njk) {
+            float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int gg = 0; gg < G; ++gg) {
+              const float4 wv = sm.red[gg * P + ct];
+              s4[0] += wv.x;
+              s4[1] += wv.y;
+              s4[2] += wv.z;
+              s4[3] += wv.w;
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (4 * q0 + b < R) T[(long long)(jt + jl0) * R + 4 * q0 + b] = s4[b];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mb_arrive(sm.red_empty());
+      } else if (v) {
+#pragma unroll
+        for (int u = 0; u < RQB; ++u)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = 4 * (qb * RQB + u) + b;
+            if (r < R) T[(long long)(jt + jl) * R + r] = a[u][b];
+          }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) smem_add_release(sm.ocons + o, 1u);
+  }
+  __syncwarp();
+  if (lane == 0) mb_arrive(sm.hslot_empty(hslot));
+  return true;
+}
+
+template <int RMAX>
+__device__ void wl_consumer(const WlSmem& sm, int* err) {
+  int nred = 0;
+  for (int n = 0;;) {
+    const int o = n % sm.SO;
+    if (!mb_wait(sm.ofull(o), (n / sm.SO) & 1, sm.wait, err, 28)) return;
+    const WlHeader& h = sm.ohdr[o];
+    if (h.d.w < 0) return;
+    bool ok = true;
+    switch (b_rqb_left(h.d.I1, h.d.R)) {
+      case 1: ok = wl_consume<1>(h, n, nred, sm, err); break;
+      case 2: ok = wl_consume<2>(h, n, nred, sm, err); break;
+      case 4: ok = wl_consume<4>(h, n, nred, sm, err); break;
+      case 8: if constexpr (RMAX >= 32) ok = wl_consume<8>(h, n, nred, sm, err); break;
+      default: if constexpr (RMAX >= 64) ok = wl_consume<16>(h, n, nred, sm, err); break;
+    }
+    if (!ok) return;
+  }
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(kWsThreads, RMAX <= 16 ? 2 : 1)
+k_b_pm_left_ws(const BTensor* __restrict__ ts, const int4* __restrict__ items, int n_items,
+               int* queue, int S, int SO, int hs_floats, int* err, long long wait_cycles) {
+  extern __shared__ __align__(16) float smem[];
+  WlSmem sm;
+  sm.S = S;
+  sm.SO = SO;
+  sm.hs_floats = hs_floats;
+  sm.wait = wait_cycles > 0 ? wait_cycles : kWsWaitCycles;
+  sm.stage0 = smem;
+  sm.odd0 = smem + (size_t)S * kTileFloats;
+  sm.hs0 = sm.odd0 + (size_t)SO * kLeftStageFloats;
+  sm.red = reinterpret_cast<float4*>(sm.hs0 + 2 * (size_t)hs_floats);
+  sm.hdr = reinterpret_cast<WsHeader*>(sm.red + kThreads);
+  sm.ohdr = reinterpret_cast<WlHeader*>(sm.hdr + S);
+  sm.slot = reinterpret_cast<WsSlot*>(sm.ohdr + SO);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm.slot + kWsItemSlots);
+  sm.bar0 = smem_u32(bars);
+  sm.ocons = reinterpret_cast<unsigned*>(bars + WlSmem::bars(S, SO));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mb_init(sm.full(s), 32);  // the loader lanes' copies
+      mb_init(sm.empty(s), 1);  // the builder warp of the stage
+      mb_init(sm.hfull(s), 1);  // the loader's header
+    }
+    for (int o = 0; o < SO; ++o) {
+      mb_init(sm.ofull(o), 1);  // the builder warp of the stage
+      sm.ocons[o] = 0u;
+    }
+    for (int i = 0; i < kWsItemSlots; ++i) {
+      mb_init(sm.islot_full(i), 1);
+      mb_init(sm.islot_empty(i), 1);
+    }
+    mb_init(sm.hslot_empty(0), kWsConsWarps);
+    mb_init(sm.hslot_empty(1), kWsConsWarps);
+    mb_init(sm.red_full(), kWsConsWarps);
+    mb_init(sm.red_empty(), kWsConsWarps);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0)
+    ws_scheduler<true>(ts, items, n_items, queue, sm, err);
+  else if (warp == 1)
+    ws_loader(sm, err);
+  else if (warp < kWsConsFirstWarp)
+    wl_builder(sm, err);
+  else
+    wl_consumer<RMAX>(sm, err);
 }
 
 // ---------------------------------------------------------- multi-TTVs --
@@ -1235,6 +1575,9 @@ cudaError_t batch_attributes_init() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right_ws<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right_ws<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_right_ws<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left_ws<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left_ws<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left_ws<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_pm_left<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, left);
@@ -1288,6 +1631,42 @@ cudaError_t launch_pm_right_ws(const BTensor* ts, const int4* it, int n, int* qu
   return cudaGetLastError();
 }
 
+// Streamed root -> {2..N}: the largest dense / odd-stride rings (at least
+// three dense stages, one per builder's stop stage) that fit beside the two
+// H_1 slots at two CTAs per SM (RMAX 16, when they fit) or one.
+template <int RMAX>
+cudaError_t launch_pm_left_ws(const BTensor* ts, const int4* it, int n, int* queue, int hs_floats,
+                              int* err, long long wait_cycles, cudaStream_t st) {
+  int dev = 0, sms = 1, smem_sm = 0, reserved = 0, optin = 0, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  static const int cand[][2] = {{4, 3}, {4, 2}, {3, 3}, {3, 2}};
+  int S = 0, SO = 0;
+  // two CTAs per SM at ranks <= 16 when the H_1 slots leave room, else one
+  for (int want = RMAX <= 16 ? 2 : 1; want >= 1 && S == 0; --want) {
+    const size_t budget = std::min<size_t>((size_t)optin, (size_t)(smem_sm / want - reserved));
+    for (const auto& c : cand)
+      if (wl_smem_bytes(c[0], c[1], hs_floats) <= budget) {
+        S = c[0];
+        SO = c[1];
+        break;
+      }
+  }
+  if (S == 0) return cudaErrorInvalidConfiguration;
+  const size_t bytes = wl_smem_bytes(S, SO, hs_floats);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pm_left_ws<RMAX>, kWsThreads,
+                                                    bytes) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int grid = std::max(1, std::min(n, sms * per_sm));
+  k_b_pm_left_ws<RMAX><<<grid, kWsThreads, bytes, st>>>(ts, it, n, queue, S, SO, hs_floats, err,
+                                                        wait_cycles);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int mode,
@@ -1315,11 +1694,15 @@ cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items
 }
 
 cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int mode,
-                           int* queue, int* /*err*/, cudaStream_t st) {
+                           int* queue, int* err, cudaStream_t st, long long wait_cycles) {
   if (mode == 0 || !queue) queue = nullptr;
   const int n = p.pml.count;
   if (n == 0) return cudaSuccess;
   const int4* it = items + p.pml.off;
+  if (mode == 2 && queue && err)
+    return p.rmax <= 16   ? launch_pm_left_ws<16>(ts, it, n, queue, p.hs_floats, err, wait_cycles, st)
+           : p.rmax <= 32 ? launch_pm_left_ws<32>(ts, it, n, queue, p.hs_floats, err, wait_cycles, st)
+                          : launch_pm_left_ws<64>(ts, it, n, queue, p.hs_floats, err, wait_cycles, st);
   const size_t sm = (size_t)(left_fixed_floats() + p.hs_floats) * sizeof(float);
   if (p.rmax <= 16)
     k_b_pm_left<16><<<phase_grid(k_b_pm_left<16>, sm, n, queue), kThreads, sm, st>>>(ts, it, n, queue);
@@ -1362,7 +1745,8 @@ cudaError_t b_launch_iteration(const BPlan& p, BTensor* ts, const int4* items, i
     e = launch_pm_right(p, ts, items, counters ? sch.pm_right : 0, queues, err, st, sch.wait_cycles);
   if (e == cudaSuccess) e = launch_update(p, ts, 0, done_count, st);
   if (e == cudaSuccess)
-    e = launch_pm_left(p, ts, items, counters ? sch.pm_left : 0, queues ? queues + 1 : nullptr, err, st);
+    e = launch_pm_left(p, ts, items, counters ? sch.pm_left : 0, queues ? queues + 1 : nullptr, err, st,
+                       sch.wait_cycles);
   // node {2..N} walk (Fig. 1 shape): leaf M(a), update, child node
   for (int a = 1; a < N && e == cudaSuccess; ++a) {
     if (a == N - 1) {

@@ -112,16 +112,17 @@ cudaError_t b_launch_init(const BPlan& p, BTensor* ts, const int4* items, double
                           const int* alpha_first, cudaStream_t st);
 // How the two root phases run: 0 = one CTA per work item (scheduled by the
 // hardware), 1 = one wave of persistent CTAs taking items from a counter,
-// 2 (root -> {1} only) = one wave of persistent CTAs with the work split by
-// warp role: a scheduler warp takes items from a counter, a loader warp
-// streams the tiles through a ring of shared-memory stages, builder warps
-// form the Khatri-Rao rows, and the remaining warps contract.  A tensor's
-// bits are the same under every schedule.
+// 2 = one wave of persistent CTAs with the work split by warp role: a
+// scheduler warp takes items from a counter, a loader warp streams dense
+// tiles through a ring of shared-memory stages, builder warps form the
+// Khatri-Rao rows (root -> {1}) or restride the tile and stage H_1
+// (root -> {2..N}), and the remaining warps contract.  A tensor's bits are
+// the same under every schedule.
 struct BSchedule {
   int pm_right = 0, pm_left = 0;
-  long long wait_cycles = 0;  // bounded-wait limit of the streamed kernel (0: about 2 s)
+  long long wait_cycles = 0;  // bounded-wait limit of the streamed kernels (0: about 2 s)
 };
-constexpr int kRightSchedules = 3, kLeftSchedules = 2;
+constexpr int kRightSchedules = 3, kLeftSchedules = 3;
 // The root phases alone (no state changes but their outputs, which every
 // iteration recomputes): what the schedule tuner times.  queue: a device
 // counter set to 0 before the launch (unused by schedule 0); err: a device
@@ -129,7 +130,7 @@ constexpr int kRightSchedules = 3, kLeftSchedules = 2;
 cudaError_t launch_pm_right(const BPlan& p, const BTensor* ts, const int4* items, int mode,
                             int* queue, int* err, cudaStream_t st, long long wait_cycles = 0);
 cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items, int mode,
-                           int* queue, int* err, cudaStream_t st);
+                           int* queue, int* err, cudaStream_t st, long long wait_cycles = 0);
 // one outer iteration (Alg. 1 over the Fig. 1 tree with root split 1);
 // queues: three device ints (the two root phases' counters and the error
 // word of the streamed schedule), or NULL for schedule 0 everywhere

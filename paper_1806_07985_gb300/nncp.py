@@ -460,9 +460,8 @@ class Batch:
         return list(iters), list(fits), lams
 
     def set_schedule(self, pm_right=-1, pm_left=-1):
-        """Root-phase schedules: 0 one CTA per item, 1 persistent, 2 (root -> {1}
-        only) persistent and streamed through a shared-memory ring by warp
-        roles, -1 tuned."""
+        """Root-phase schedules: 0 one CTA per item, 1 persistent, 2 persistent
+        and streamed through shared-memory rings by warp roles, -1 tuned."""
         _bcheck(load().nncp_batch_set_schedule(self.b, int(pm_right), int(pm_left)), self.b)
 
     def set_wait_limit(self, cycles=0):

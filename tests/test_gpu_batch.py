@@ -212,12 +212,12 @@ _SCHED_SETS = {
 }
 
 
-@pytest.mark.parametrize("sched", [(1, 1), (0, 1), (1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("sched", [(1, 1), (0, 1), (1, 0), (2, 0), (0, 2), (2, 2), (1, 2)])
 @pytest.mark.parametrize("which", sorted(_SCHED_SETS))
 def test_root_phase_schedules_give_the_same_bits(nn, which, sched):
     # one CTA per work item, persistent CTAs taking items from a counter, or
-    # the streamed root -> {1} kernel: which CTA (and which warp) computes a
-    # product changes, the order of every output's sums does not
+    # the streamed kernels: which CTA (and which warp) computes a product
+    # changes, the order of every output's sums does not
     probs = _problems(**_SCHED_SETS[which])
     ref = _run_batch_sched(nn, probs, 5, (0, 0))
     got = _run_batch_sched(nn, probs, 5, sched)
@@ -227,7 +227,8 @@ def test_root_phase_schedules_give_the_same_bits(nn, which, sched):
             assert np.array_equal(x, y)
 
 
-def test_streamed_schedule_reports_an_expired_wait(nn):
+@pytest.mark.parametrize("sched", [(2, 0), (0, 2)])
+def test_streamed_schedule_reports_an_expired_wait(nn, sched):
     # the failure path without any fault or hang: a wait limit of one cycle
     # makes the streamed kernel's waits that are merely not yet satisfied
     # expire; the run reports NNCP_ERR_TIMEOUT naming the wait site, and the
@@ -239,7 +240,7 @@ def test_streamed_schedule_reports_an_expired_wait(nn):
     try:
         with pytest.raises(nn.NNCPError):
             b.set_wait_limit(-1)
-        b.set_schedule(2, 0)
+        b.set_schedule(*sched)
         X = [torch.from_numpy(p[2]).cuda() for p in probs]
         H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
         b.set_data(X, H)
@@ -265,7 +266,7 @@ def test_streamed_schedule_reports_an_expired_wait(nn):
 def test_streamed_schedule_matches_the_oracle_at_wide_ranks(nn):
     probs = _problems(count=4, seed0=43, lo=24, hi=150, ranks=(24, 40))
     iters = 6
-    k, fits, lams, Hs = _run_batch_sched(nn, probs, iters, (2, 1))
+    k, fits, lams, Hs = _run_batch_sched(nn, probs, iters, (2, 2))
     for t, (dims, R, x, H0) in enumerate(probs):
         ref = oracle.nncp_hals(x.astype(np.float64), dims, [h.astype(np.float64) for h in H0],
                                max_iters=iters, use_dimtree=True, s=1)
@@ -283,12 +284,12 @@ def test_schedule_tuner_picks_a_valid_schedule(nn):
         with pytest.raises(nn.NNCPError):
             b.set_schedule(3, 0)
         with pytest.raises(nn.NNCPError):
-            b.set_schedule(0, 2)
+            b.set_schedule(0, 3)
         X = [torch.from_numpy(p[2]).cuda() for p in probs]
         H = [[torch.from_numpy(h.copy()).cuda() for h in p[3]] for p in probs]
         b.set_data(X, H)
         b.solve(3, 0.0)
         r, l = b.schedule()
-        assert r in (0, 1, 2) and l in (0, 1)
+        assert r in (0, 1, 2) and l in (0, 1, 2)
     finally:
         b.close()
