@@ -193,6 +193,29 @@ __global__ void k_reduce_chunks(const float* __restrict__ part, long long E, int
   }
 }
 
+// The sums of k_reduce_chunks<1> (chunk c into accumulator c mod 4, the chunks
+// past the last multiple of four into accumulator 0, then (a0 + a1) + (a2 + a3),
+// so the same bits) with one accumulator per lane of a quad: four times the
+// threads, each with a quarter of the dependent loads.
+__global__ void k_reduce_chunks_quad(const float* __restrict__ part, long long E, int C,
+                                     float* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  const long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 2;
+  const int q = threadIdx.x & 3;
+  const int C4 = C & ~3;
+  float s = 0.0f;
+  if (e < E) {
+#pragma unroll 4
+    for (int c = q; c < C4; c += 4) s += __ldg(part + (long long)c * E + e);
+    if (q == 0)
+      for (int c = C4; c < C; ++c) s += __ldg(part + (long long)c * E + e);
+  }
+  const float u = s + __shfl_down_sync(0xffffffffu, s, 1);  // q = 0: a0 + a1, q = 2: a2 + a3
+  const float v = u + __shfl_down_sync(0xffffffffu, u, 2);  // q = 0: (a0 + a1) + (a2 + a3)
+  if (q == 0 && e < E) out[e] = v;
+}
+
 // Multi-TTV leaf: out(i, r) = sum_k T[(i + I*k)*R + r] * KK(k, r).
 // Threads cover consecutive flattened (i, r) positions (V per thread, V = 4
 // when R % 4 == 0), so every k step reads one contiguous run of the node
@@ -448,11 +471,14 @@ cudaError_t launch_reduce_chunks(const float* part, int64_t E, int C, float* out
   const bool v4 = E % 4 == 0 && E / 4 >= (int64_t)num_sms * 8 * 256 &&
                   reinterpret_cast<uintptr_t>(part) % 16 == 0 &&
                   reinterpret_cast<uintptr_t>(out) % 16 == 0;
-  const long long Ev = v4 ? E / 4 : E;
+  if (!v4)  // small outputs: a quad of threads per output (same sums)
+    return launch_kernel(k_reduce_chunks_quad, dim3((unsigned)ceil_div(4 * (long long)E, 256)),
+                         dim3(256), 0, st, part, (long long)E, C, out);
+  const long long Ev = E / 4;
   int blocks = (int)min(ceil_div(Ev, 256), (long long)num_sms * 8);
   if (blocks < 1) blocks = 1;
-  return launch_kernel(v4 ? k_reduce_chunks<4> : k_reduce_chunks<1>, dim3(blocks), dim3(256), 0,
-                       st, part, (long long)E, C, out);
+  return launch_kernel(k_reduce_chunks<4>, dim3(blocks), dim3(256), 0, st, part, (long long)E, C,
+                       out);
 }
 
 size_t mttv_leaf_partials(int64_t I, int64_t K, int R, int num_sms) {
