@@ -366,9 +366,9 @@ constexpr int kWsConsFirstWarp = 2 + kWsBuildWarps;
 constexpr int kWsThreads = 32 * (kWsConsFirstWarp + kWsConsWarps);
 constexpr int kWsStageFloats = kTileFloats + kWsFloats;
 constexpr int kWsItemSlots = 4;
-// Khatri-Rao entries (row, rank group) per builder lane and round: a tile has at most kWsFloats / 4
+// Khatri-Rao entries (row, rank group) per builder lane and pass: a tile has at most kWsFloats / 4
 constexpr int kWsBuildPer = 4;
-constexpr int kWsBuildRounds = (kWsFloats / 4 + 32 * kWsBuildPer - 1) / (32 * kWsBuildPer);
+constexpr int kWsBuildPasses = (kWsFloats / 4 + 32 * kWsBuildPer - 1) / (32 * kWsBuildPer);
 constexpr long long kWsWaitCycles = 4000000000LL;
 
 // One item as the builders and consumers need it (w < 0: no more items);
@@ -595,10 +595,10 @@ __device__ void ws_builder(const WsSmem& sm, int* err) {
       const int jt = h.d.j0 + h.k * h.d.nj, njk = min(h.d.nj, h.d.j1 - jt);
       const int ne = njk * RQB;
       float4* W = reinterpret_cast<float4*>(sm.xs(s) + kTileFloats);
-      for (int rd = 0; rd < kWsBuildRounds; ++rd) {
+      for (int rd = 0; rd < kWsBuildPasses; ++rd) {
         const int e0 = lane + 32 * kWsBuildPer * rd;
         if (e0 >= ne) break;
-        // every entry of this round at once, so that the factor-row loads of
+        // every entry of this pass at once, so that the factor-row loads of
         // all of them are in flight together
         float4 v[kWsBuildPer];
         int rem[kWsBuildPer];
