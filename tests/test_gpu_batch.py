@@ -209,7 +209,19 @@ _SCHED_SETS = {
     "wide_rank": dict(count=8, seed0=35, lo=20, hi=200, ranks=(12, 24, 40)),
     "order4": dict(count=8, seed0=37, N=4, lo=6, hi=20, ranks=(3, 5, 8)),
     "order2": dict(count=8, seed0=39, N=2, lo=16, hi=250, ranks=(2, 7, 16)),
+    "order5": dict(count=6, seed0=41, N=5, lo=3, hi=11, ranks=(2, 6, 16)),
+    "edges": None,   # _edge_problems: first modes 1, 2, 3, 4, 255, 256; ranks 1 and 64
 }
+
+
+def _edge_problems():
+    probs = []
+    for t, (dims, R) in enumerate([((1, 50, 60), 12), ((256, 9, 7), 5), ((255, 3, 17), 64),
+                                   ((2, 2, 2), 1), ((3, 40, 41), 33), ((4, 128, 3), 16),
+                                   ((256, 64, 2), 1), ((7, 1, 200), 8)]):
+        x, _ = synth.lowrank_plus_noise(dims, R, seed=6000 + t, noise=0.01)
+        probs.append((dims, R, x, synth.init_factors(dims, R, seed=7000 + t)))
+    return probs
 
 
 @pytest.mark.parametrize("sched", [(1, 1), (0, 1), (1, 0), (2, 0), (0, 2), (2, 2), (1, 2)])
@@ -218,7 +230,7 @@ def test_root_phase_schedules_give_the_same_bits(nn, which, sched):
     # one CTA per work item, persistent CTAs taking items from a counter, or
     # the streamed kernels: which CTA (and which warp) computes a product
     # changes, the order of every output's sums does not
-    probs = _problems(**_SCHED_SETS[which])
+    probs = _edge_problems() if which == "edges" else _problems(**_SCHED_SETS[which])
     ref = _run_batch_sched(nn, probs, 5, (0, 0))
     got = _run_batch_sched(nn, probs, 5, sched)
     assert got[0] == ref[0] and got[1] == ref[1] and got[2] == ref[2]
