@@ -51,15 +51,18 @@ __device__ __forceinline__ float krp_value(const KrpDesc& d, const int* off, int
   return v;
 }
 
+// X elements each thread stages per contraction tile
+constexpr int kXPer = kBK * kBI / kThreads;
+
 template <bool kSlow>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q, KrpDesc KL,
               KrpDesc KQ, int R, long long kchunk, float* __restrict__ out,
               long long out_chunk_stride) {
   pdl_wait();  // no early trigger: a large grid; its successor spreads as CTAs exit
   __shared__ __align__(16) float Xs[kBK][kBI + 4];
   __shared__ __align__(16) float Ws[kBK][kRT];
-  __shared__ TileRows rows[kBK];
+  __shared__ TileRows rows[2][kBK];  // this tile's and the next one's
 
   const long long Ktot = L * Q;
   const long long i0 = (long long)blockIdx.x * kBI;
@@ -76,7 +79,8 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
 
-  for (long long k0 = kbeg; k0 < kend; k0 += kBK) {
+  // row metadata of the tile at k0 into rows[buf] (threads < kBK)
+  auto tile_rows = [&](long long k0, int buf) {
     if (tid < kBK) {
       long long k = k0 + tid;
       TileRows tr;
@@ -89,28 +93,51 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
       } else {
         tr.xbase = 0;
       }
-      rows[tid] = tr;
+      rows[buf][tid] = tr;
     }
+  };
+  // this thread's X elements of the tile described by rows[buf]: element
+  // (i, k) at xbase(k) + L*i, read along whichever of i and k is contiguous
+  float xr[kXPer];
+  auto load_x = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < kXPer; ++u) {
+      const int e = tid + kThreads * u;
+      int kk, ii;
+      if (kSlow) { kk = e / kBI; ii = e % kBI; }   // L == 1: rows contiguous in i
+      else       { kk = e % kBK; ii = e / kBK; }   // contiguous in k (l fastest)
+      const long long i = i0 + ii;
+      xr[u] = (rows[buf][kk].valid && i < I) ? __ldg(X + rows[buf][kk].xbase + L * i) : 0.0f;
+    }
+  };
+
+  int cur = 0;
+  if (kbeg < kend) {
+    tile_rows(kbeg, 0);
     __syncthreads();
+    load_x(0);
+  }
+  for (long long k0 = kbeg; k0 < kend; k0 += kBK, cur ^= 1) {
+    const bool more = k0 + kBK < kend;
     for (int e = tid; e < kBK * kRT; e += kThreads) {
       int kk = e / kRT, rr = e % kRT;
       int r = r0 + rr;
       float w = 0.0f;
-      if (rows[kk].valid && r < R)
-        w = krp_value(KL, rows[kk].off, r) * krp_value(KQ, rows[kk].off + kMaxModes, r);
+      if (rows[cur][kk].valid && r < R)
+        w = krp_value(KL, rows[cur][kk].off, r) * krp_value(KQ, rows[cur][kk].off + kMaxModes, r);
       Ws[kk][rr] = w;
     }
-    // X tile: element (i, k) at xbase(k) + L*i; coalesce along whichever is contiguous
-    for (int e = tid; e < kBK * kBI; e += kThreads) {
+#pragma unroll
+    for (int u = 0; u < kXPer; ++u) {
+      const int e = tid + kThreads * u;
       int kk, ii;
-      if (kSlow) { kk = e / kBI; ii = e % kBI; }   // L == 1: rows contiguous in i
-      else       { kk = e % kBK; ii = e / kBK; }   // contiguous in k (l fastest)
-      long long i = i0 + ii;
-      float v = 0.0f;
-      if (rows[kk].valid && i < I) v = __ldg(X + rows[kk].xbase + L * i);
-      Xs[kk][ii] = v;
+      if (kSlow) { kk = e / kBI; ii = e % kBI; }
+      else       { kk = e % kBK; ii = e / kBK; }
+      Xs[kk][ii] = xr[u];
     }
+    if (more) tile_rows(k0 + kBK, cur ^ 1);
     __syncthreads();
+    if (more) load_x(cur ^ 1);  // the next tile's tensor values stream in during this tile
 #pragma unroll 8
     for (int kk = 0; kk < kBK; ++kk) {
       float4 xv = *reinterpret_cast<const float4*>(&Xs[kk][ty * 4]);
