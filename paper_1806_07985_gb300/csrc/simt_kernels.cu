@@ -99,7 +99,46 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
   // this thread's X elements of the tile described by rows[buf]: element
   // (i, k) at xbase(k) + L*i, read along whichever of i and k is contiguous
   float xr[kXPer];
+  // L == 1 with I % 4 == 0 and X 16-byte aligned: every tile row is four-float
+  // aligned, so thread tid reads four consecutive i of rows tid / 32 + 8 v.
+  // L % 32 == 0 (and X aligned): a tile's 32 k share q and have consecutive l,
+  // and chunks and totals are multiples of 32, so a tile is wholly valid or
+  // not; thread tid reads four consecutive k of row i = (tid + 256 v) / 8.
+  const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  const bool vec = kSlow && (I & 3) == 0 && aligned;
+  const bool veck = !kSlow && (L & 31) == 0 && aligned;
   auto load_x = [&](int buf) {
+    if (veck) {
+#pragma unroll
+      for (int v = 0; v < kXPer / 4; ++v) {
+        const int id = tid + kThreads * v, ii = id >> 3, kk = 4 * (id & 7);
+        const long long i = i0 + ii;
+        float4 x4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (rows[buf][kk].valid && i < I)
+          x4 = __ldg(reinterpret_cast<const float4*>(X + rows[buf][kk].xbase + L * i));
+        xr[4 * v] = x4.x;
+        xr[4 * v + 1] = x4.y;
+        xr[4 * v + 2] = x4.z;
+        xr[4 * v + 3] = x4.w;
+      }
+      return;
+    }
+    if (vec) {
+      const int ii = 4 * (tid & 31);
+#pragma unroll
+      for (int v = 0; v < kXPer / 4; ++v) {
+        const int kk = (tid >> 5) + 8 * v;
+        const long long i = i0 + ii;
+        float4 x4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (rows[buf][kk].valid && i < I)  // i < I covers i .. i + 3 (I % 4 == 0)
+          x4 = __ldg(reinterpret_cast<const float4*>(X + rows[buf][kk].xbase + i));
+        xr[4 * v] = x4.x;
+        xr[4 * v + 1] = x4.y;
+        xr[4 * v + 2] = x4.z;
+        xr[4 * v + 3] = x4.w;
+      }
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < kXPer; ++u) {
       const int e = tid + kThreads * u;
@@ -127,13 +166,27 @@ k_simt_mttkrp(const float* __restrict__ X, long long L, long long I, long long Q
         w = krp_value(KL, rows[cur][kk].off, r) * krp_value(KQ, rows[cur][kk].off + kMaxModes, r);
       Ws[kk][rr] = w;
     }
+    if (veck) {
 #pragma unroll
-    for (int u = 0; u < kXPer; ++u) {
-      const int e = tid + kThreads * u;
-      int kk, ii;
-      if (kSlow) { kk = e / kBI; ii = e % kBI; }
-      else       { kk = e % kBK; ii = e / kBK; }
-      Xs[kk][ii] = xr[u];
+      for (int v = 0; v < kXPer / 4; ++v) {
+        const int id = tid + kThreads * v, ii = id >> 3, kk = 4 * (id & 7);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Xs[kk + j][ii] = xr[4 * v + j];
+      }
+    } else if (vec) {
+#pragma unroll
+      for (int v = 0; v < kXPer / 4; ++v)
+        *reinterpret_cast<float4*>(&Xs[(tid >> 5) + 8 * v][4 * (tid & 31)]) =
+            make_float4(xr[4 * v], xr[4 * v + 1], xr[4 * v + 2], xr[4 * v + 3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kXPer; ++u) {
+        const int e = tid + kThreads * u;
+        int kk, ii;
+        if (kSlow) { kk = e / kBI; ii = e % kBI; }
+        else       { kk = e % kBK; ii = e / kBK; }
+        Xs[kk][ii] = xr[u];
+      }
     }
     if (more) tile_rows(k0 + kBK, cur ^ 1);
     __syncthreads();
