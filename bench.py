@@ -689,8 +689,8 @@ def run_batched(nncp, torch, count, max_iters=None, no_plain=False, fixed_schedu
            "tensor_GBps": round(tensor_bytes / t / 1e9, 1),
            "root_phase_schedule": {"pm_right": schedule[0], "pm_left": schedule[1],
                                    "codes": "0 one CTA per work item, 1 persistent CTAs on a "
-                                            "work counter, 2 (root -> {1}) persistent CTAs "
-                                            "streaming tiles through a shared-memory ring",
+                                            "work counter, 2 persistent CTAs streaming tiles "
+                                            "through shared-memory rings by warp role",
                                    "chosen_by": "fixed" if fixed_schedule else "the library's tuner"}}
     if no_plain:
         return out
