@@ -115,9 +115,11 @@ void b_build_plan(const BTensor* ts, int C, int N, BPlan* p) {
   p->lam_total = 0;
   int rmax = 1;
   p->hs_floats = 0;
+  p->max_rows = 1;
   for (int t = 0; t < C; ++t) {
     rmax = std::max(rmax, ts[t].R);
     p->hs_floats = std::max(p->hs_floats, (int)ts[t].dims[0] * b_rank_pad(ts[t].R));
+    for (int n = 0; n < N; ++n) p->max_rows = std::max(p->max_rows, (int)ts[t].dims[n]);
     p->lam_off[t] = (int)p->lam_total;
     p->lam_total += ts[t].R;
   }

@@ -1408,7 +1408,7 @@ __global__ void __launch_bounds__(256) k_b_mttv_first(const BTensor* __restrict_
 // S for the next mode -- all in shared memory.
 template <int RMAX>
 __global__ void __launch_bounds__(256)
-k_b_update(BTensor* __restrict__ ts, int n, int* __restrict__ done_count) {
+k_b_update(BTensor* __restrict__ ts, int n, int* __restrict__ done_count, int rows) {
   BTensor& t = ts[blockIdx.x];
   if (tensor_done(t)) return;
   constexpr int RP = RMAX + 1;
@@ -1416,12 +1416,14 @@ k_b_update(BTensor* __restrict__ ts, int n, int* __restrict__ done_count) {
   const int In = (int)t.dims[n];
   const int tid = threadIdx.x;
   extern __shared__ __align__(16) float bsm[];
+  // rows: the longest mode of the batch, so that small tensors leave room for
+  // more CTAs per SM
   float* St = bsm;                 // RMAX x RMAX, St[r][c] = S[c][r], zero padded
-  float* Ws = St + RMAX * RMAX;    // kBatchMaxI x RP (W, then H)
-  float* Ms = Ws + kBatchMaxI * RP;  // kBatchMaxI x RP (M)
+  float* Ws = St + RMAX * RMAX;    // rows x RP (W, then H)
+  float* Ms = Ws + rows * RP;      // rows x RP (M)
   __shared__ float lamf[RMAX], sinv[RMAX];
-  __shared__ double GW[kBatchMaxRank * kBatchMaxRank];
-  __shared__ double cinv[kBatchMaxRank];
+  __shared__ double GW[RMAX * RMAX];
+  __shared__ double cinv[RMAX];
   __shared__ double red[8];
   float* Hn = t.H[n];
   // staging with the global loads of a loop issued in batches
@@ -1549,8 +1551,8 @@ __global__ void k_b_gather(const BTensor* __restrict__ ts, int count, int* iters
 }
 
 template <int RMAX>
-size_t update_smem() {
-  return (size_t)(RMAX * RMAX + 2 * kBatchMaxI * (RMAX + 1)) * sizeof(float);
+size_t update_smem(int rows = kBatchMaxI) {
+  return (size_t)(RMAX * RMAX + 2 * rows * (RMAX + 1)) * sizeof(float);
 }
 
 }  // namespace
@@ -1716,9 +1718,13 @@ cudaError_t launch_pm_left(const BPlan& p, const BTensor* ts, const int4* items,
 namespace {
 
 cudaError_t launch_update(const BPlan& p, BTensor* ts, int n, int* done_count, cudaStream_t st) {
-  if (p.rmax <= 16) k_b_update<16><<<p.count, 256, update_smem<16>(), st>>>(ts, n, done_count);
-  else if (p.rmax <= 32) k_b_update<32><<<p.count, 256, update_smem<32>(), st>>>(ts, n, done_count);
-  else k_b_update<64><<<p.count, 256, update_smem<64>(), st>>>(ts, n, done_count);
+  const int rows = p.max_rows;
+  if (p.rmax <= 16)
+    k_b_update<16><<<p.count, 256, update_smem<16>(rows), st>>>(ts, n, done_count, rows);
+  else if (p.rmax <= 32)
+    k_b_update<32><<<p.count, 256, update_smem<32>(rows), st>>>(ts, n, done_count, rows);
+  else
+    k_b_update<64><<<p.count, 256, update_smem<64>(rows), st>>>(ts, n, done_count, rows);
   return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ struct BPhase {
 };
 struct BPlan {
   int count = 0, N = 0, rmax = 16, hs_floats = 0;
+  int max_rows = 1;  // longest mode of any tensor of the batch
   std::vector<int4> items;
   BPhase alpha, pmr, pmr_red, pml;
   BPhase leaf[kMaxModes], leaf_red[kMaxModes], first[kMaxModes];
