@@ -23,7 +23,7 @@ constexpr int kTileFloats = 4096;
 constexpr int kWsFloats = 2048;       // Khatri-Rao tile (rows x padded rank)
 constexpr int kLeftMaxRows = 512;     // padded X tile <= kTileFloats + kLeftMaxRows
 constexpr int kRightTileTarget = 32768;  // elements per root -> {1} chunk
-constexpr int kLeftItemTiles = 8;        // tiles per root -> {2..N} item
+constexpr int kLeftItemTiles = 16;       // tiles per root -> {2..N} item
 // rank groups of four, rounded up to a power of two (1 .. 16), and the padded rank
 __host__ __device__ inline int b_rq(int R) {
   int q = 1;
